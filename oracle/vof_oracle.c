@@ -1,0 +1,716 @@
+/*
+ * vof_oracle.c -- plain FP64 CPU oracle for the PLIC / split-VOF / consistent
+ * energy-advection hot path of Malan, Malan, Zaleski & Rousseau,
+ * "A Geometric VOF Method for Interface Resolved Phase Change and
+ * Conservative Thermal Energy Advection" (arXiv:2001.03477).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * the package's smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header, table or helper with the CUDA path.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so x86
+ * and aarch64 hosts give the same bits).
+ *
+ * Conventions (Sec. 3, MAC grid):
+ *   cells   [nz][ny][nx], x fastest, index (k*ny + j)*nx + i
+ *   x-faces [nz][ny][nx+1], y-faces [nz][ny+1][nx], z-faces [nz+1][ny][nx];
+ *           face f along an axis lies between cells f-1 and f.
+ *   bc[axis] = 0 periodic (face n is face 0; the stored face-n value is not
+ *   read), 1 zero-gradient (out-of-range cell indices clamp to the boundary
+ *   cell).
+ *   par = {h, Cp_l, Cp_g, T_sat, eps_mixed}.
+ *   PLIC plane in a cell's local unit cube (origin at its low corner):
+ *   liquid is { x : m.x <= alpha }, m points from liquid into gas (Eq.
+ *   plane_m), |m1|+|m2|+|m3| = 1.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------ */
+/* Indexing                                                            */
+/* ------------------------------------------------------------------ */
+
+static int map_index(int i, int n, int bc) {
+    if (bc == 0) {
+        int r = i % n;
+        return r < 0 ? r + n : r;
+    }
+    if (i < 0) return 0;
+    if (i >= n) return n - 1;
+    return i;
+}
+
+static long cell_id(const int dims[3], const int bc[3], int i, int j, int k) {
+    int ii = map_index(i, dims[0], bc[0]);
+    int jj = map_index(j, dims[1], bc[1]);
+    int kk = map_index(k, dims[2], bc[2]);
+    return ((long)kk * dims[1] + jj) * dims[0] + ii;
+}
+
+/* face f (0..n) along `axis` at transverse cell position (i,j,k) of the
+   other two axes; periodic axes read face n from face 0 */
+static long face_id(const int dims[3], const int bc[3], int axis, int i, int j, int k) {
+    int nx = dims[0], ny = dims[1];
+    int p[3] = {i, j, k};
+    if (bc[axis] == 0 && p[axis] == dims[axis]) p[axis] = 0;
+    if (axis == 0) return ((long)p[2] * ny + p[1]) * (nx + 1) + p[0];
+    if (axis == 1) return ((long)p[2] * (ny + 1) + p[1]) * nx + p[0];
+    return ((long)p[2] * ny + p[1]) * nx + p[0];
+}
+
+/* ------------------------------------------------------------------ */
+/* Volume under a plane in the unit cube  (Scardovelli & Zaleski 2000, */
+/* cited in Sec. 3.2 and 3.3.2)                                         */
+/* ------------------------------------------------------------------ */
+
+/* V for sorted 0 <= m1 <= m2 <= m3, m1+m2+m3 = 1, 0 < a <= 1/2.
+   Each branch is the inclusion-exclusion volume
+     [a^3 - sum_i <a-m_i>^3 + sum_{i<j} <a-m_i-m_j>^3] / (6 m1 m2 m3)
+   restricted to the range of a where its terms are active, written so that
+   no branch divides a cancelling numerator by a vanishing m1. */
+static double vol_sorted_low(double m1, double m2, double m3, double a) {
+    double m12 = m1 + m2;
+    if (a < m1) {
+        /* only a^3 is active */
+        return a * a * a / (6.0 * m1 * m2 * m3);
+    }
+    /* a^3 - (a-m1)^3 = m1 (3a^2 - 3a m1 + m1^2), divided by 6 m1 m2 m3 */
+    double v2 = a * (a - m1) / (2.0 * m2 * m3) + m1 * m1 / (6.0 * m2 * m3);
+    if (a < m2) return v2;
+    double t2 = a - m2; /* 0 <= t2 <= m1 in the remaining branches */
+    double v3 = v2 - t2 * t2 * t2 / (6.0 * m1 * m2 * m3);
+    double top = m12 < m3 ? m12 : m3;
+    if (a < top) return v3;
+    if (m12 <= m3) {
+        /* a^3 - (a-m1)^3 - (a-m2)^3 + (a-m1-m2)^3 = 3 m1 m2 (2a - m1 - m2) */
+        return (2.0 * a - m12) / (2.0 * m3);
+    }
+    /* m3 < m1 + m2 and m3 <= a <= 1/2: the (a-m3)^3 term is active too */
+    double t3 = a - m3;
+    return v3 - t3 * t3 * t3 / (6.0 * m1 * m2 * m3);
+}
+
+static void sort3(double v[3]) {
+    double t;
+    if (v[0] > v[1]) { t = v[0]; v[0] = v[1]; v[1] = t; }
+    if (v[1] > v[2]) { t = v[1]; v[1] = v[2]; v[2] = t; }
+    if (v[0] > v[1]) { t = v[0]; v[0] = v[1]; v[1] = t; }
+}
+
+/* volume of {x in [0,1]^3 : m.x <= alpha} for m >= 0 with sum 1 */
+static double vol_pos(const double mpos[3], double alpha) {
+    if (alpha <= 0.0) return 0.0;
+    if (alpha >= 1.0) return 1.0;
+    double s[3] = {mpos[0], mpos[1], mpos[2]};
+    sort3(s);
+    if (alpha <= 0.5) return vol_sorted_low(s[0], s[1], s[2], alpha);
+    /* central symmetry of the cube: V(alpha) = 1 - V(1 - alpha) */
+    return 1.0 - vol_sorted_low(s[0], s[1], s[2], 1.0 - alpha);
+}
+
+/* mirror m to non-negative components and L1-normalise; returns the shift
+   applied to alpha (alpha_mirror = alpha + shift) and the L1 norm */
+static void mirror_normalise(const double m[3], double mpos[3], double *shift, double *l1) {
+    double sh = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (m[d] < 0.0) { mpos[d] = -m[d]; sh -= m[d]; }
+        else mpos[d] = m[d];
+    }
+    double s = mpos[0] + mpos[1] + mpos[2];
+    *shift = sh;
+    *l1 = s;
+    if (s > 0.0) { mpos[0] /= s; mpos[1] /= s; mpos[2] /= s; }
+}
+
+/* Liquid volume fraction of the unit cube under the plane m.x <= alpha,
+   any m (signs, scale). */
+ORC_API double orc_volume(const double m[3], double alpha) {
+    double mp[3], sh, l1;
+    mirror_normalise(m, mp, &sh, &l1);
+    if (l1 == 0.0) return alpha >= 0.0 ? 1.0 : 0.0;
+    return vol_pos(mp, (alpha + sh) / l1);
+}
+
+/* Plane constant alpha with orc_volume(m, alpha) = c: bisection on the
+   monotone volume function (the oracle's stand-in for the analytic
+   inversion of Scardovelli & Zaleski, Sec. 3.2). */
+ORC_API double orc_alpha(const double m[3], double c) {
+    double mp[3], sh, l1;
+    mirror_normalise(m, mp, &sh, &l1);
+    if (l1 == 0.0) return 0.0;
+    if (c <= 0.0) return (0.0 - sh);
+    if (c >= 1.0) return (l1 - sh);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = lo + 0.5 * (hi - lo);
+        if (!(mid > lo && mid < hi)) break;
+        if (vol_pos(mp, mid) < c) lo = mid;
+        else hi = mid;
+    }
+    double vl = fabs(vol_pos(mp, lo) - c), vh = fabs(vol_pos(mp, hi) - c);
+    double am = (vh < vl) ? hi : lo;
+    return am * l1 - sh;
+}
+
+/* Liquid volume (in units of the cell volume) inside the slab
+   x_axis in [x0, x0+delta] of the unit cube, by the change of variable
+   x_axis = x0 + delta*xi that maps the slab onto a unit cube. */
+ORC_API double orc_slab_volume(const double m[3], double alpha, int axis, double x0, double delta) {
+    if (delta <= 0.0) return 0.0;
+    double mm[3] = {m[0], m[1], m[2]};
+    mm[axis] = m[axis] * delta;
+    double a2 = alpha - m[axis] * x0;
+    return delta * orc_volume(mm, a2);
+}
+
+/* Area of the polygon cut by the plane m.x = alpha from the unit cube,
+   built explicitly: edge intersections, angular sort, triangle fan. */
+ORC_API double orc_plane_area(const double m[3], double alpha) {
+    double pts[24][3];
+    int np = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v) {
+                double p0[3], p1[3];
+                p0[ax] = 0.0; p0[b1] = u; p0[b2] = v;
+                p1[ax] = 1.0; p1[b1] = u; p1[b2] = v;
+                double f0 = m[0] * p0[0] + m[1] * p0[1] + m[2] * p0[2] - alpha;
+                double f1 = m[0] * p1[0] + m[1] * p1[1] + m[2] * p1[2] - alpha;
+                if (f0 == 0.0 && np < 24) { memcpy(pts[np++], p0, sizeof p0); }
+                if (f1 == 0.0 && np < 24) { memcpy(pts[np++], p1, sizeof p1); }
+                if (((f0 < 0.0 && f1 > 0.0) || (f0 > 0.0 && f1 < 0.0)) && np < 24) {
+                    double t = f0 / (f0 - f1);
+                    double q[3] = {p0[0], p0[1], p0[2]};
+                    q[ax] = t;
+                    memcpy(pts[np++], q, sizeof q);
+                }
+            }
+    }
+    if (np < 3) return 0.0;
+    double nrm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    if (nrm == 0.0) return 0.0;
+    double n[3] = {m[0] / nrm, m[1] / nrm, m[2] / nrm};
+    double cen[3] = {0, 0, 0};
+    for (int q = 0; q < np; ++q)
+        for (int d = 0; d < 3; ++d) cen[d] += pts[q][d] / np;
+    /* in-plane basis */
+    int ks = 0;
+    for (int d = 1; d < 3; ++d)
+        if (fabs(n[d]) < fabs(n[ks])) ks = d;
+    double ex[3] = {0, 0, 0};
+    ex[ks] = 1.0;
+    double b1[3] = {n[1] * ex[2] - n[2] * ex[1], n[2] * ex[0] - n[0] * ex[2], n[0] * ex[1] - n[1] * ex[0]};
+    double l = sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]);
+    for (int d = 0; d < 3; ++d) b1[d] /= l;
+    double b2[3] = {n[1] * b1[2] - n[2] * b1[1], n[2] * b1[0] - n[0] * b1[2], n[0] * b1[1] - n[1] * b1[0]};
+    double ang[24];
+    for (int q = 0; q < np; ++q) {
+        double r[3] = {pts[q][0] - cen[0], pts[q][1] - cen[1], pts[q][2] - cen[2]};
+        ang[q] = atan2(r[0] * b2[0] + r[1] * b2[1] + r[2] * b2[2], r[0] * b1[0] + r[1] * b1[1] + r[2] * b1[2]);
+    }
+    /* insertion sort by angle */
+    for (int a = 1; a < np; ++a) {
+        double ka = ang[a], kp[3] = {pts[a][0], pts[a][1], pts[a][2]};
+        int b = a - 1;
+        while (b >= 0 && ang[b] > ka) {
+            ang[b + 1] = ang[b];
+            memcpy(pts[b + 1], pts[b], sizeof kp);
+            --b;
+        }
+        ang[b + 1] = ka;
+        memcpy(pts[b + 1], kp, sizeof kp);
+    }
+    double area = 0.0;
+    for (int q = 0; q < np; ++q) {
+        const double *p = pts[q], *r = pts[(q + 1) % np];
+        double u[3] = {p[0] - cen[0], p[1] - cen[1], p[2] - cen[2]};
+        double v[3] = {r[0] - cen[0], r[1] - cen[1], r[2] - cen[2]};
+        double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+        area += 0.5 * (cx * n[0] + cy * n[1] + cz * n[2]);
+    }
+    return fabs(area);
+}
+
+/* ------------------------------------------------------------------ */
+/* Interface normal: Mixed Youngs-Centered (Aulisa et al. 2007, cited   */
+/* in Sec. 3.2).  Stencil s[(dz*3 + dy)*3 + dx], offsets dx,dy,dz in    */
+/* 0..2 for -1..+1.  The operation order below is part of the method    */
+/* definition used by this project (so that candidate choices are       */
+/* reproducible); no contraction to FMA.                                */
+/* ------------------------------------------------------------------ */
+
+static double S3(const double s[27], int x, int y, int z) { return s[((z + 1) * 3 + (y + 1)) * 3 + (x + 1)]; }
+
+/* value at offset r along axis d, p along t1, q along t2 */
+static double Sax(const double s[27], int d, int r, int p, int q) {
+    int o[3];
+    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    o[d] = r; o[t1] = p; o[t2] = q;
+    return S3(s, o[0], o[1], o[2]);
+}
+
+/* Youngs: m = -grad c, gradient with (1,2,1)x(1,2,1) transverse weights */
+ORC_API void orc_youngs(const double s[27], double m[3]) {
+    static const double w[3] = {1.0, 2.0, 1.0};
+    for (int d = 0; d < 3; ++d) {
+        double g = 0.0;
+        for (int q = -1; q <= 1; ++q)
+            for (int p = -1; p <= 1; ++p) {
+                double diff = Sax(s, d, 1, p, q) - Sax(s, d, -1, p, q);
+                g = g + (w[p + 1] * w[q + 1]) * diff;
+            }
+        m[d] = -g;
+    }
+    double l1 = fabs(m[0]) + fabs(m[1]) + fabs(m[2]);
+    if (l1 > 0.0) { m[0] /= l1; m[1] /= l1; m[2] /= l1; }
+    else { m[0] = 1.0; m[1] = 0.0; m[2] = 0.0; }
+}
+
+/* Centred-columns candidate along axis d: heights = column sums of three
+   cells along d, transverse slopes by central differences, orientation
+   from the lower vs upper layer sums (lower >= upper: liquid below). */
+ORC_API void orc_cc_candidate(const double s[27], int d, double m[3]) {
+    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    double h[3][3];
+    for (int q = -1; q <= 1; ++q)
+        for (int p = -1; p <= 1; ++p) {
+            double col = Sax(s, d, -1, p, q);
+            col = col + Sax(s, d, 0, p, q);
+            col = col + Sax(s, d, 1, p, q);
+            h[p + 1][q + 1] = col;
+        }
+    double lower = 0.0, upper = 0.0;
+    for (int q = -1; q <= 1; ++q)
+        for (int p = -1; p <= 1; ++p) {
+            lower = lower + Sax(s, d, -1, p, q);
+            upper = upper + Sax(s, d, 1, p, q);
+        }
+    double sg = (lower >= upper) ? 1.0 : -1.0;
+    double a1 = -(h[2][1] - h[0][1]) * 0.5;
+    double a2 = -(h[1][2] - h[1][0]) * 0.5;
+    double l1 = fabs(a1) + fabs(a2) + 1.0;
+    m[t1] = a1 / l1;
+    m[t2] = a2 / l1;
+    m[d] = sg / l1;
+}
+
+/* MYC normal.  rule 0 (the project's frozen choice): keep the best
+   centred-columns candidate unless its dominant component exceeds the
+   dominant component of the Youngs normal, in which case take Youngs (ties
+   keep the columns).  With this test the normal is exact for every plane
+   whose centred columns span the interface (the plane test of Sec. 4.1).
+   rule 1 is the reverse test, kept only for the selection experiment. */
+ORC_API void orc_myc_rule(const double s[27], double m[3], int rule) {
+    double best[3];
+    int bd = 0;
+    orc_cc_candidate(s, 0, best);
+    for (int d = 1; d < 3; ++d) {
+        double cand[3];
+        orc_cc_candidate(s, d, cand);
+        if (fabs(cand[d]) > fabs(best[bd])) {
+            best[0] = cand[0]; best[1] = cand[1]; best[2] = cand[2];
+            bd = d;
+        }
+    }
+    double y[3];
+    orc_youngs(s, y);
+    double ymax = fabs(y[0]);
+    if (fabs(y[1]) > ymax) ymax = fabs(y[1]);
+    if (fabs(y[2]) > ymax) ymax = fabs(y[2]);
+    double cmax = fabs(best[bd]);
+    int use_cc = (rule == 0) ? (cmax <= ymax) : (cmax >= ymax);
+    if (use_cc) { m[0] = best[0]; m[1] = best[1]; m[2] = best[2]; }
+    else { m[0] = y[0]; m[1] = y[1]; m[2] = y[2]; }
+}
+
+ORC_API void orc_myc(const double s[27], double m[3]) { orc_myc_rule(s, m, 0); }
+
+static void gather_stencil(const int dims[3], const int bc[3], const double *c, int i, int j, int k, double s[27]) {
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                s[((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1)] = c[cell_id(dims, bc, i + dx, j + dy, k + dz)];
+}
+
+static int is_mixed(double c, double eps) { return c > eps && c < 1.0 - eps; }
+
+/* ------------------------------------------------------------------ */
+/* Reconstruction of every cell (Sec. 3.2: MYC normal + plane constant) */
+/* ------------------------------------------------------------------ */
+
+ORC_API void orc_reconstruct(const int dims[3], const int bc[3], const double par[5], const double *c,
+                             double *m_soa, double *alpha, unsigned char *mixed) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    double eps = par[4];
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                long id = ((long)k * dims[1] + j) * dims[0] + i;
+                double cv = c[id];
+                if (is_mixed(cv, eps)) {
+                    double s[27], m[3];
+                    gather_stencil(dims, bc, c, i, j, k, s);
+                    orc_myc(s, m);
+                    m_soa[id] = m[0]; m_soa[N + id] = m[1]; m_soa[2 * N + id] = m[2];
+                    alpha[id] = orc_alpha(m, cv);
+                    mixed[id] = 1;
+                } else {
+                    m_soa[id] = 0.0; m_soa[N + id] = 0.0; m_soa[2 * N + id] = 0.0;
+                    alpha[id] = 0.0;
+                    mixed[id] = 0;
+                }
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* WENO5 face value (Jiang-Shu weights, Shu 2009; cited in Sec. 3.4.1)  */
+/* v[0..4] = upwind-ordered values around the donor (v[2] = donor).     */
+/* ------------------------------------------------------------------ */
+
+ORC_API double orc_weno5(const double v[5], double epsw) {
+    double vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4];
+    if (vm2 == v0 && vm1 == v0 && vp1 == v0 && vp2 == v0) return v0;
+    double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+    double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+    double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+    double d0 = vm2 - 2.0 * vm1 + v0, e0 = vm2 - 4.0 * vm1 + 3.0 * v0;
+    double d1 = vm1 - 2.0 * v0 + vp1, e1 = vm1 - vp1;
+    double d2 = v0 - 2.0 * vp1 + vp2, e2 = 3.0 * v0 - 4.0 * vp1 + vp2;
+    double b0 = (13.0 / 12.0) * d0 * d0 + 0.25 * e0 * e0;
+    double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
+    double b2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
+    double a0 = 0.1 / ((epsw + b0) * (epsw + b0));
+    double a1 = 0.6 / ((epsw + b1) * (epsw + b1));
+    double a2 = 0.3 / ((epsw + b2) * (epsw + b2));
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+#define ORC_EPSW 1e-6
+
+static double heat_cap(const double par[5], double c) { return par[1] * c + par[2] * (1.0 - c); }
+
+/* ------------------------------------------------------------------ */
+/* Frozen step-start state for the Weymouth-Yue dilatation terms:       */
+/*   cc = 1 if c^n > 1/2 else 0;  theta = C_p(cc) * T^n, T^n = e/C_p(c)  */
+/* ------------------------------------------------------------------ */
+
+ORC_API void orc_frozen(const int dims[3], const double par[5], const double *c, const double *e,
+                        unsigned char *cc, double *theta) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    for (long id = 0; id < N; ++id) {
+        unsigned char b = c[id] > 0.5 ? 1 : 0;
+        double Tn = e[id] / heat_cap(par, c[id]);
+        cc[id] = b;
+        theta[id] = heat_cap(par, (double)b) * Tn;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* One direction sweep: geometric VOF face fluxes (Sec. 3.3.1, the      */
+/* Weymouth-Yue split scheme) with the energy fluxed in tandem using    */
+/* the same fluxed volumes (Eq. disc_et_adv and the sweep procedure of  */
+/* Sec. 3.4.1).                                                         */
+/* ------------------------------------------------------------------ */
+
+/* face flux at face f of the line through (p1,p2) along axis */
+static void face_flux(const int dims[3], const int bc[3], const double par[5], int axis, const double *c,
+                      const double *T, double a, const int pos[3], double *F, double *G) {
+    /* pos = cell coordinates of the cell on the + side of the face */
+    if (a == 0.0) { *F = 0.0; *G = 0.0; return; }
+    int don[3] = {pos[0], pos[1], pos[2]};
+    if (a > 0.0) don[axis] -= 1;
+    long did = cell_id(dims, bc, don[0], don[1], don[2]);
+    double cd = c[did];
+    double Fv;
+    if (is_mixed(cd, par[4])) {
+        double s[27], m[3];
+        gather_stencil(dims, bc, c, don[0], don[1], don[2], s);
+        orc_myc(s, m);
+        double al = orc_alpha(m, cd);
+        double da = fabs(a);
+        double x0 = a > 0.0 ? 1.0 - da : 0.0;
+        double vol = orc_slab_volume(m, al, axis, x0, da);
+        Fv = a > 0.0 ? vol : -vol;
+    } else {
+        Fv = cd * a;
+    }
+    /* WENO5 stencil centred on the donor, ordered upwind to downwind */
+    double v[5];
+    for (int r = -2; r <= 2; ++r) {
+        int q[3] = {don[0], don[1], don[2]};
+        q[axis] += (a > 0.0) ? r : -r;
+        v[r + 2] = T[cell_id(dims, bc, q[0], q[1], q[2])];
+    }
+    double Tf = orc_weno5(v, ORC_EPSW);
+    *F = Fv;
+    *G = (Tf * par[1]) * Fv + (Tf * par[2]) * (a - Fv);
+}
+
+/* Sweep along `axis`.  c, e are updated in place.  cc/theta: frozen state.
+   Optional outputs: Fout/Gout face fluxes in the face layout of `axis`.
+   diag[0] += clipped volume (sum of c_unclipped - c_clipped). */
+ORC_API void orc_sweep(const int dims[3], const int bc[3], const double par[5], int axis, double *c, double *e,
+                       const double *uf, double dt, const unsigned char *cc, const double *theta, double *Fout,
+                       double *Gout, double *diag) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    double lam = dt / par[0];
+    double *T = (double *)malloc(sizeof(double) * N);
+    double *cn = (double *)malloc(sizeof(double) * N);
+    double *en = (double *)malloc(sizeof(double) * N);
+    for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c[id]);
+    double clip = 0.0;
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                long id = ((long)k * dims[1] + j) * dims[0] + i;
+                int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                hi[axis] += 1;
+                double al = uf[face_id(dims, bc, axis, lo[0], lo[1], lo[2])] * lam;
+                double ar = uf[face_id(dims, bc, axis, hi[0], hi[1], hi[2])] * lam;
+                double Fl, Gl, Fr, Gr;
+                face_flux(dims, bc, par, axis, c, T, al, lo, &Fl, &Gl);
+                face_flux(dims, bc, par, axis, c, T, ar, hi, &Fr, &Gr);
+                double ccv = (double)cc[id], th = theta[id];
+                double lf = Fl - ccv * al, rf = Fr - ccv * ar;
+                double cnew = (c[id] + lf) - rf;
+                double le = Gl - th * al, re = Gr - th * ar;
+                double enew = (e[id] + le) - re;
+                double cc2 = cnew;
+                if (cc2 < 0.0) cc2 = 0.0;
+                if (cc2 > 1.0) cc2 = 1.0;
+                clip += cnew - cc2;
+                cn[id] = cc2;
+                en[id] = enew;
+                if (Fout || Gout) {
+                    long fl = face_id(dims, bc, axis, lo[0], lo[1], lo[2]);
+                    if (Fout) Fout[fl] = Fl;
+                    if (Gout) Gout[fl] = Gl;
+                    if (hi[axis] == dims[axis]) {
+                        /* last face of the line: stored at its own slot even
+                           for periodic axes (where it equals face 0) */
+                        int nx = dims[0], ny = dims[1];
+                        long fh;
+                        if (axis == 0) fh = ((long)hi[2] * ny + hi[1]) * (nx + 1) + hi[0];
+                        else if (axis == 1) fh = ((long)hi[2] * (ny + 1) + hi[1]) * nx + hi[0];
+                        else fh = ((long)hi[2] * ny + hi[1]) * nx + hi[0];
+                        if (Fout) Fout[fh] = Fr;
+                        if (Gout) Gout[fh] = Gr;
+                    }
+                }
+            }
+    memcpy(c, cn, sizeof(double) * N);
+    memcpy(e, en, sizeof(double) * N);
+    if (diag) diag[0] += clip;
+    free(T); free(cn); free(en);
+}
+
+/* Energy sweep from given VOF face fluxes F (the unfused form of the same
+   update): e is advanced with G = T_f (C_pl F + C_pg (a - F)), T from the
+   pre-sweep (c_before, e). */
+ORC_API void orc_energy_consistent(const int dims[3], const int bc[3], const double par[5], int axis,
+                                   const double *c_before, double *e, const double *Fface, const double *uf,
+                                   double dt, const double *theta) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    double lam = dt / par[0];
+    double *T = (double *)malloc(sizeof(double) * N);
+    double *en = (double *)malloc(sizeof(double) * N);
+    for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c_before[id]);
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                long id = ((long)k * dims[1] + j) * dims[0] + i;
+                double Gs[2], as[2];
+                for (int side = 0; side < 2; ++side) {
+                    int p[3] = {i, j, k};
+                    p[axis] += side;
+                    double a = uf[face_id(dims, bc, axis, p[0], p[1], p[2])] * lam;
+                    long fid;
+                    {
+                        int nx = dims[0], ny = dims[1];
+                        if (axis == 0) fid = ((long)p[2] * ny + p[1]) * (nx + 1) + p[0];
+                        else if (axis == 1) fid = ((long)p[2] * (ny + 1) + p[1]) * nx + p[0];
+                        else fid = ((long)p[2] * ny + p[1]) * nx + p[0];
+                    }
+                    double F = Fface[fid];
+                    as[side] = a;
+                    if (a == 0.0) { Gs[side] = 0.0; continue; }
+                    int don[3] = {p[0], p[1], p[2]};
+                    if (a > 0.0) don[axis] -= 1;
+                    double v[5];
+                    for (int r = -2; r <= 2; ++r) {
+                        int q[3] = {don[0], don[1], don[2]};
+                        q[axis] += (a > 0.0) ? r : -r;
+                        v[r + 2] = T[cell_id(dims, bc, q[0], q[1], q[2])];
+                    }
+                    double Tf = orc_weno5(v, ORC_EPSW);
+                    Gs[side] = (Tf * par[1]) * F + (Tf * par[2]) * (a - F);
+                }
+                double th = theta[id];
+                double le = Gs[0] - th * as[0], re = Gs[1] - th * as[1];
+                en[id] = (e[id] + le) - re;
+            }
+    memcpy(e, en, sizeof(double) * N);
+    free(T); free(en);
+}
+
+/* ------------------------------------------------------------------ */
+/* Step 2: interface shift for phase change (Sec. 3.3.2, Eqs.           */
+/* vof_step2_full, Delta d, alpha^{n+1}) and the energy change          */
+/* Delta e = Delta c (C_pl - C_pg) T_Gamma (end of Sec. 3.4.1).          */
+/*                                                                      */
+/* Every mixed cell moves its own plane: alpha* = alpha + |m|_2 dd,      */
+/* capped to the cell, c = V(m, alpha*).  The movement that a cap cuts   */
+/* off is carried on in the neighbours the interface moves into: a pure  */
+/* cell of the receding phase takes the volume swept inside it by the    */
+/* shifted plane of an adjacent mixed cell, extended across the shared   */
+/* face, edge or corner (the largest such sweep over its 26 neighbours;  */
+/* for a plane they all agree).                                         */
+/* dd: per-cell shift in cell units (NULL -> dd_uniform).               */
+/* diag[0] += sum Delta c, diag[1] += volume lost to the [0,1] clamp of  */
+/* the receiving cells, diag[2] += sum Delta e.                          */
+/* ------------------------------------------------------------------ */
+
+ORC_API void orc_phase_shift(const int dims[3], const int bc[3], const double par[5], double *c, double *e,
+                             const double *dd, double dd_uniform, double *diag) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    double eps = par[4];
+    double *cn = (double *)malloc(sizeof(double) * N);
+    double *pm = (double *)malloc(sizeof(double) * 4 * N); /* m (unmirrored) and alpha of mixed cells */
+    double *ps = (double *)malloc(sizeof(double) * N);     /* |m|_2 dd of mixed cells (0: not moving) */
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                long id = ((long)k * dims[1] + j) * dims[0] + i;
+                double ct = c[id];
+                cn[id] = ct;
+                ps[id] = 0.0;
+                double ddv = dd ? dd[id] : dd_uniform;
+                if (!is_mixed(ct, eps) || ddv == 0.0) continue;
+                double s[27], m[3];
+                gather_stencil(dims, bc, c, i, j, k, s);
+                orc_myc(s, m);
+                double al = orc_alpha(m, ct);
+                double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                double sft = mn2 * ddv;
+                /* cap alpha* to the cell: [sum of negative m_i, sum of positive m_i] */
+                double lo = 0.0, hi = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    if (m[d] < 0.0) lo += m[d];
+                    else hi += m[d];
+                }
+                double ast = al + sft;
+                if (ast < lo) ast = lo;
+                if (ast > hi) ast = hi;
+                cn[id] = orc_volume(m, ast);
+                pm[4 * id + 0] = m[0]; pm[4 * id + 1] = m[1]; pm[4 * id + 2] = m[2]; pm[4 * id + 3] = al;
+                ps[id] = sft;
+            }
+    double unpl = 0.0;
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                long id = ((long)k * dims[1] + j) * dims[0] + i;
+                double ct = c[id];
+                if (is_mixed(ct, eps)) continue;
+                int full = ct >= 1.0 - eps;
+                double best = 0.0;
+                for (int oz = -1; oz <= 1; ++oz)
+                    for (int oy = -1; oy <= 1; ++oy)
+                        for (int ox = -1; ox <= 1; ++ox) {
+                            if (!ox && !oy && !oz) continue;
+                            int q[3] = {i + ox, j + oy, k + oz};
+                            int out = 0;
+                            for (int ax = 0; ax < 3; ++ax)
+                                if (bc[ax] != 0 && (q[ax] < 0 || q[ax] >= dims[ax])) out = 1;
+                            if (out) continue;
+                            long qid = cell_id(dims, bc, q[0], q[1], q[2]);
+                            double sft = ps[qid];
+                            if (sft == 0.0) continue;
+                            /* evaporation (sft < 0) eats into liquid cells,
+                               condensation into gas cells */
+                            if ((sft < 0.0) != full) continue;
+                            const double *mq = pm + 4 * qid;
+                            /* this cell's coordinates are the neighbour's
+                               minus the offset (-ox,-oy,-oz) from it */
+                            double shiftv = -(mq[0] * (-ox) + mq[1] * (-oy) + mq[2] * (-oz));
+                            double a_old = mq[3] + shiftv;
+                            double a_new = (mq[3] + sft) + shiftv;
+                            double sw = orc_volume(mq, a_new) - orc_volume(mq, a_old);
+                            if (fabs(sw) > fabs(best)) best = sw;
+                        }
+                if (best != 0.0) {
+                    double v = ct + best;
+                    double vc = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+                    unpl += v - vc;
+                    cn[id] = vc;
+                }
+            }
+    double sdc = 0.0, sde = 0.0;
+    double dCp = par[1] - par[2];
+    for (long id = 0; id < N; ++id) {
+        double dc = cn[id] - c[id];
+        double de = dc * dCp * par[3];
+        sdc += dc;
+        sde += de;
+        c[id] = cn[id];
+        e[id] = e[id] + de;
+    }
+    if (diag) { diag[0] += sdc; diag[1] += unpl; diag[2] += sde; }
+    free(cn); free(pm); free(ps);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sums (compensated) and one full time step                            */
+/* ------------------------------------------------------------------ */
+
+ORC_API double orc_sum(const double *x, long n) {
+    double s = 0.0, comp = 0.0;
+    for (long q = 0; q < n; ++q) {
+        double t = s + x[q];
+        if (fabs(s) >= fabs(x[q])) comp += (s - t) + x[q];
+        else comp += (x[q] - t) + s;
+        s = t;
+    }
+    return s + comp;
+}
+
+/* One step: 3 Strang-alternated sweeps (x,y,z on even steps, z,y,x on
+   odd) with frozen cc/theta, then the phase-change shift.
+   sums[0..5] = {sum c, sum e, clipped (sweeps), sum dc (shift),
+                 unplaced (shift), sum de (shift)}. */
+ORC_API void orc_step(const int dims[3], const int bc[3], const double par[5], double *c, double *e,
+                      const double *u, const double *v, const double *w, double dt, long step_index,
+                      const double *dd, double dd_uniform, double *sums) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    unsigned char *cc = (unsigned char *)malloc(N);
+    double *theta = (double *)malloc(sizeof(double) * N);
+    orc_frozen(dims, par, c, e, cc, theta);
+    const double *uf[3] = {u, v, w};
+    double clip = 0.0;
+    for (int s = 0; s < 3; ++s) {
+        int axis = (step_index % 2 == 0) ? s : 2 - s;
+        orc_sweep(dims, bc, par, axis, c, e, uf[axis], dt, cc, theta, NULL, NULL, &clip);
+    }
+    double sh[3] = {0, 0, 0};
+    orc_phase_shift(dims, bc, par, c, e, dd, dd_uniform, sh);
+    if (sums) {
+        sums[0] = orc_sum(c, N);
+        sums[1] = orc_sum(e, N);
+        sums[2] = clip;
+        sums[3] = sh[0];
+        sums[4] = sh[1];
+        sums[5] = sh[2];
+    }
+    free(cc); free(theta);
+}
+
+ORC_API void orc_run(const int dims[3], const int bc[3], const double par[5], double *c, double *e,
+                     const double *u, const double *v, const double *w, double dt, long step0, long nsteps,
+                     const double *dd, double dd_uniform, double *sums) {
+    for (long s = 0; s < nsteps; ++s) orc_step(dims, bc, par, c, e, u, v, w, dt, step0 + s, dd, dd_uniform, sums);
+}

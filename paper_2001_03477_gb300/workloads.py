@@ -1,0 +1,261 @@
+"""Seeded synthetic inputs shaped like the paper's validation cases.
+
+This module only builds initial data (volume fractions of analytic shapes,
+temperature fields, face velocities).  It contains none of the method's
+arithmetic: no interface normal, no plane constant, no flux.  Volume
+fractions are obtained by integrating chord lengths of the analytic shape
+through each cell on an n x n midpoint rule, so they depend only on the
+shape, not on any PLIC routine.
+
+Cases (Sec. 4 of Malan et al.):
+  * translating sphere with T = 1 in the liquid (periodic box),
+  * vapour bubble in superheated liquid (Sec. 4.4), radial liquid velocity
+    built from exact face solid angles (discretely divergence free),
+  * deformation field (LeVeque) with exact face averages.
+
+Water / steam data are those of Table atm_water (Sec. 4.3).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# Table atm_water: saturated water at 1 atm
+RHO_L, RHO_G = 958.0, 0.6
+CP_L_SPEC, CP_G_SPEC = 4216.0, 2080.0
+H_FG_WATER = 2.257e6  # J/kg, not printed in the paper; reproduces delta(10 s)
+T_SAT_WATER = 373.15
+
+
+# ---------------------------------------------------------------------------
+# Volume fractions of analytic shapes by chord integration
+# ---------------------------------------------------------------------------
+
+def _chord_fraction(lo_x, hi_x, ys, zs, chord_fn):
+    """Mean over (y,z) points of the length of {x in [lo_x,hi_x]} inside the
+    shape divided by (hi_x - lo_x).  chord_fn(y, z) -> (x0, x1) interval
+    (x0 > x1 when empty).  Arrays broadcast over cells."""
+    x0, x1 = chord_fn(ys, zs)
+    a = np.maximum(x0, lo_x[..., None, None])
+    b = np.minimum(x1, hi_x[..., None, None])
+    ln = np.clip(b - a, 0.0, None)
+    return ln.mean(axis=(-1, -2)) / (hi_x - lo_x)
+
+
+def ellipsoid_fractions(shape, h, centre, axes, rot=None, inside=1.0, nsub=32, chunk=4096):
+    """Volume fraction of the ellipsoid {(R^T (x - c))_i^2 / a_i^2 <= 1} in
+    each cell of a grid with cell size h (tuple or scalar), shape (nz,ny,nx).
+    inside=1 gives liquid inside; inside=0 gives the complement."""
+    nz, ny, nx = shape
+    hx, hy, hz = (h, h, h) if np.isscalar(h) else h
+    c = np.asarray(centre, dtype=np.float64)
+    ax = np.asarray(axes, dtype=np.float64)
+    R = np.eye(3) if rot is None else np.asarray(rot, dtype=np.float64)
+    # quadratic form Q = R diag(1/a^2) R^T
+    Q = R @ np.diag(1.0 / ax ** 2) @ R.T
+    rmax = ax.max()
+    rmin = ax.min()
+    zc = (np.arange(nz) + 0.5) * hz
+    yc = (np.arange(ny) + 0.5) * hy
+    xc = (np.arange(nx) + 0.5) * hx
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    # classify by distance of the cell centre (conservative bounds)
+    half_diag = 0.5 * math.sqrt(hx * hx + hy * hy + hz * hz)
+    d = np.stack([X - c[0], Y - c[1], Z - c[2]], axis=-1)
+    qv = np.einsum("...i,ij,...j->...", d, Q, d)
+    dist = np.sqrt(np.einsum("...i,...i->...", d, d))
+    frac = np.where(qv <= 1.0, 1.0, 0.0)
+    # cells that can intersect the surface: inside the outer shell, outside
+    # the inner one
+    cand = (dist <= rmax + half_diag) & ~(dist < rmin - half_diag)
+    # exact classification of candidates by sub-integration
+    idx = np.argwhere(cand)
+    t = (np.arange(nsub) + 0.5) / nsub
+    qxx, qxy, qxz, qyy, qyz, qzz = Q[0, 0], Q[0, 1], Q[0, 2], Q[1, 1], Q[1, 2], Q[2, 2]
+
+    def chord(ys, zs):
+        # solve qxx x^2 + 2 x (qxy y + qxz z) + (qyy y^2 + 2 qyz y z + qzz z^2 - 1) = 0 in local coords
+        b = qxy * ys + qxz * zs
+        cc = qyy * ys * ys + 2.0 * qyz * ys * zs + qzz * zs * zs - 1.0
+        disc = b * b - qxx * cc
+        sq = np.sqrt(np.clip(disc, 0.0, None))
+        x0 = (-b - sq) / qxx
+        x1 = (-b + sq) / qxx
+        empty = disc < 0.0
+        x0 = np.where(empty, 1.0, x0)
+        x1 = np.where(empty, 0.0, x1)
+        return x0 + c[0], x1 + c[0]
+
+    for s in range(0, len(idx), chunk):
+        blk = idx[s:s + chunk]
+        k, j, i = blk[:, 0], blk[:, 1], blk[:, 2]
+        lo_x = i * hx
+        hi_x = (i + 1) * hx
+        ys = (j[:, None, None] + t[None, :, None]) * hy - c[1]
+        zs = (k[:, None, None] + t[None, None, :]) * hz - c[2]
+        ys, zs = np.broadcast_arrays(ys, zs)
+        frac[k, j, i] = _chord_fraction(lo_x, hi_x, ys, zs, chord)
+    frac = np.clip(frac, 0.0, 1.0)
+    if inside == 0.0:
+        frac = 1.0 - frac
+    return frac
+
+
+def sphere_fractions(shape, h, centre, radius, inside=1.0, nsub=32):
+    return ellipsoid_fractions(shape, h, centre, (radius, radius, radius), inside=inside, nsub=nsub)
+
+
+# ---------------------------------------------------------------------------
+# Face velocities
+# ---------------------------------------------------------------------------
+
+def uniform_faces(shape, vel):
+    nz, ny, nx = shape
+    u = np.full((nz, ny, nx + 1), float(vel[0]))
+    v = np.full((nz, ny + 1, nx), float(vel[1]))
+    w = np.full((nz + 1, ny, nx), float(vel[2]))
+    return u, v, w
+
+
+def _solid_angle_tri(r1, r2, r3):
+    """Signed solid angle of triangle (r1,r2,r3) seen from the origin
+    (Van Oosterom & Strackee 1983)."""
+    l1 = np.linalg.norm(r1, axis=-1)
+    l2 = np.linalg.norm(r2, axis=-1)
+    l3 = np.linalg.norm(r3, axis=-1)
+    num = np.einsum("...i,...i->...", r1, np.cross(r2, r3))
+    den = (l1 * l2 * l3 + np.einsum("...i,...i->...", r1, r2) * l3
+           + np.einsum("...i,...i->...", r1, r3) * l2 + np.einsum("...i,...i->...", r2, r3) * l1)
+    return 2.0 * np.arctan2(num, den)
+
+
+def radial_faces(shape, h, centre, strength, r_cut):
+    """Face-normal velocities of the source field strength * r_hat / r^2
+    about `centre`: each face gets strength * Omega / h^2 with Omega the
+    exact signed solid angle of the face (oriented along +axis).  Faces whose
+    centre lies closer than r_cut get 0 (deep inside the vapour, where the
+    field is irrelevant).  Cells away from the cut are divergence free to
+    round-off."""
+    nz, ny, nx = shape
+    c = np.asarray(centre, dtype=np.float64)
+    out = []
+    for axis in range(3):
+        fs = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][axis]
+        kk, jj, ii = np.meshgrid(np.arange(fs[0]), np.arange(fs[1]), np.arange(fs[2]), indexing="ij")
+        # low corner of the face in physical coordinates
+        base = np.stack([ii * h, jj * h, kk * h], axis=-1) - c
+        e1 = np.zeros(3); e2 = np.zeros(3)
+        t1, t2 = [(1, 2), (2, 0), (0, 1)][axis]  # right-handed: t1 x t2 = +axis
+        e1[t1] = h; e2[t2] = h
+        p0 = base
+        p1 = base + e1
+        p2 = base + e1 + e2
+        p3 = base + e2
+        om = _solid_angle_tri(p0, p1, p2) + _solid_angle_tri(p0, p2, p3)
+        fc = base + 0.5 * (e1 + e2)
+        rc = np.linalg.norm(fc, axis=-1)
+        vel = strength * om / (h * h)
+        vel = np.where(rc < r_cut, 0.0, vel)
+        out.append(np.ascontiguousarray(vel))
+    return tuple(out)
+
+
+def deformation_faces(shape, h, t, period=3.0):
+    """Exact face averages of the LeVeque (1996) deformation field
+       u =  2 sin^2(pi x) sin(2 pi y) sin(2 pi z) g(t)
+       v = -sin(2 pi x) sin^2(pi y) sin(2 pi z) g(t)
+       w = -sin(2 pi x) sin(2 pi y) sin^2(pi z) g(t),  g = cos(pi t / T)
+    on a grid of cell size h over [0, n h]."""
+    nz, ny, nx = shape
+    g = math.cos(math.pi * t / period)
+
+    def avg_sin2pi(n):  # average of sin(2 pi s) over each cell [i h, (i+1) h]
+        lo = np.arange(n) * h
+        return (np.cos(2 * np.pi * lo) - np.cos(2 * np.pi * (lo + h))) / (2 * np.pi * h)
+
+    def avg_sin2(n):  # average of sin^2(pi s) = 1/2 - cos(2 pi s)/2
+        lo = np.arange(n) * h
+        return 0.5 - (np.sin(2 * np.pi * (lo + h)) - np.sin(2 * np.pi * lo)) / (4 * np.pi * h)
+
+    xf = np.arange(nx + 1) * h
+    yf = np.arange(ny + 1) * h
+    zf = np.arange(nz + 1) * h
+    u = 2.0 * g * (np.sin(np.pi * xf) ** 2)[None, None, :] * avg_sin2pi(ny)[None, :, None] * avg_sin2pi(nz)[:, None, None]
+    v = -g * avg_sin2pi(nx)[None, None, :] * (np.sin(np.pi * yf) ** 2)[None, :, None] * avg_sin2pi(nz)[:, None, None]
+    w = -g * avg_sin2pi(nx)[None, None, :] * avg_sin2pi(ny)[None, :, None] * (np.sin(np.pi * zf) ** 2)[:, None, None]
+    return (np.ascontiguousarray(u), np.ascontiguousarray(v), np.ascontiguousarray(w))
+
+
+# ---------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    shape: tuple          # (nz, ny, nx)
+    bc: tuple             # per axis (x, y, z): 0 periodic, 1 zero-gradient
+    h: float
+    Cp_l: float
+    Cp_g: float
+    T_sat: float
+    dt: float
+    nsteps: int
+    dd_uniform: float
+    c: np.ndarray
+    e: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    eps: float = 1e-12
+
+    @property
+    def cells(self):
+        return int(np.prod(self.shape))
+
+
+def translating_sphere(n=32, nsteps=64, dd=-0.01, nsub=32):
+    """Sphere R=0.2 at (0.4,0.4,0.4) in the periodic unit box, velocity
+    (1, 0.5, 0.25) at CFL 0.25 (dt = 0.25 h), T = 1 in the liquid and 0 in
+    the gas, volumetric heat capacity ratio 1000:1, radial shift dd cells per
+    step (negative: evaporation)."""
+    h = 1.0 / n
+    shape = (n, n, n)
+    c = sphere_fractions(shape, h, (0.4, 0.4, 0.4), 0.2, nsub=nsub)
+    Cp_l, Cp_g = 1000.0, 1.0
+    e = c * Cp_l * 1.0
+    u, v, w = uniform_faces(shape, (1.0, 0.5, 0.25))
+    dt = 0.25 * h
+    return Workload("translating-sphere-%d^3" % n, shape, (0, 0, 0), h, Cp_l, Cp_g, 1.0, dt, nsteps, dd, c, e, u, v, w)
+
+
+def bubble_growth(n=256, nsteps=500, R0=0.1, delta=0.02, Ja=0.5, cells_per_step=0.02, nsub=16):
+    """Vapour bubble R0 at the centre of the unit box (liquid outside,
+    zero-gradient faces), water/steam properties of Table atm_water.
+    T = T_sat in the vapour and T_sat + dT erf((r-R0)/delta) in the liquid,
+    dT = Ja rho_g h_fg / (rho_l c_pl).  Radial liquid velocity
+    (1 - rho_g/rho_l) Rdot (R0/r)^2 from face solid angles, Rdot such that
+    the interface moves `cells_per_step` cells per step; Step 2 shift
+    dd = -(rho_g/rho_l) Rdot dt / h."""
+    h = 1.0 / n
+    shape = (n, n, n)
+    centre = (0.5, 0.5, 0.5)
+    c = sphere_fractions(shape, h, centre, R0, inside=0.0, nsub=nsub)
+    Cp_l = RHO_L * CP_L_SPEC
+    Cp_g = RHO_G * CP_G_SPEC
+    dT = Ja * RHO_G * H_FG_WATER / (RHO_L * CP_L_SPEC)
+    zc = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(zc, zc, zc, indexing="ij")
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    from scipy.special import erf
+    T = np.where(r > R0, T_SAT_WATER + dT * erf((r - R0) / delta), T_SAT_WATER)
+    e = (Cp_l * c + Cp_g * (1.0 - c)) * T
+    dt = 1.0e-3
+    Rdot = cells_per_step * h / dt
+    A = (1.0 - RHO_G / RHO_L) * Rdot * R0 * R0
+    u, v, w = radial_faces(shape, h, centre, A, 0.5 * R0)
+    dd = -(RHO_G / RHO_L) * Rdot * dt / h
+    return Workload("bubble-growth-%d^3" % n, shape, (1, 1, 1), h, Cp_l, Cp_g, T_SAT_WATER, dt, nsteps, dd,
+                    c, e, u, v, w)
