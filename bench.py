@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark: Gcell/s of one full time step of the PLIC / split-VOF /
+consistent-energy hot path (three direction sweeps + phase-change shift +
+FP64 sums) on the 256^3 vapour-bubble growth workload (Sec. 4.4 shape:
+vapour sphere R0 = 0.1 in superheated water, erf thermal layer of
+thickness 0.02, Ja = 0.5, radial liquid velocity, mass-flux-driven shift).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+One rank per GPU (torchrun for N > 1); every rank advances its own replica
+of the workload (weak scaling, no collective on the data path); the timed
+region is bracketed by a barrier and a device synchronise, the time is the
+max over ranks, and rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell/s per 3-sweep PLIC+energy advection step; % of HBM roofline"
+UNIT = "Gcell/s"
+N_CELLS = 256
+# algorithmic bytes per cell of one sweep launch: read c, e, face velocity
+# (8 B each) and the 1-byte frozen-state flag; write c, e
+SWEEP_BYTES_PER_CELL = 8 + 8 + 8 + 1 + 8 + 8
+# per step: 3 sweeps + zeroing the state (1 B) + shift (read c, e; write c, e)
+STEP_BYTES_PER_CELL = 3 * SWEEP_BYTES_PER_CELL + 1 + 32
+MY_KERNELS_PER_STEP = 7  # 3 sweeps, 1 shift, 3 reductions
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def sweep_traffic_from_profile():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it
+    names this kernel build; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json.txt")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def load_workload():
+    from paper_2001_03477_gb300 import workloads as W
+    return W.bubble_growth(n=N_CELLS, nsub=8)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2001_03477_gb300 as P
+    from paper_2001_03477_gb300 import build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(P.LIB_PATH):
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    wl = load_workload()
+    g = P.Grid(wl.shape[2], wl.shape[1], wl.shape[0], wl.bc, wl.h, wl.Cp_l, wl.Cp_g, wl.T_sat)
+    c0 = torch.from_numpy(wl.c).to(dev)
+    e0 = torch.from_numpy(wl.e).to(dev)
+    u = torch.from_numpy(wl.u).to(dev)
+    v = torch.from_numpy(wl.v).to(dev)
+    w = torch.from_numpy(wl.w).to(dev)
+    c, e = c0.clone(), e0.clone()
+    st = P.Stepper(g, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region --------------------------------------
+    for s in range(args.warmup):
+        st.step(c, e, u, v, w, wl.dt, s, dd_uniform=wl.dd_uniform)
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for s in range(args.steps):
+        st.step(c, e, u, v, w, wl.dt, args.warmup + s, dd_uniform=wl.dd_uniform)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    sums = st.sums.cpu().numpy()
+    cells = wl.cells
+    value = cells * args.steps * world / (ms * 1e-3) / 1e9
+
+    # ---- per-kernel durations (same launch configuration) ------------------
+    # the three sweeps and the shift launched one by one through the C ABI,
+    # each bracketed by CUDA events on the launching stream
+    c2, e2 = torch.empty_like(c), torch.empty_like(e)
+    state = torch.zeros(wl.shape, dtype=torch.uint8, device=dev)
+    theta = torch.zeros(wl.shape, dtype=torch.float64, device=dev)
+    reps = max(3, min(args.steps, 50))
+    names = ["sweep_x", "sweep_y", "sweep_z", "shift"]
+    evs = {k: [] for k in names}
+    barrier()
+    for r in range(reps):
+        for k, fn, uf in (("sweep_x", P.vof_advect_sweep_x, u), ("sweep_y", P.vof_advect_sweep_y, v),
+                          ("sweep_z", P.vof_advect_sweep_z, w)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(g, c, e, c2, e2, uf, wl.dt, state, theta)
+            b.record(stream)
+            evs[k].append((a, b))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.vof_phase_change_shift(g, c, e, c2, e2, None, wl.dd_uniform)
+        b.record(stream)
+        evs["shift"].append((a, b))
+    barrier()
+    kern_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in evs[k]])) for k in names}
+    sweep_ms = float(np.mean([kern_ms["sweep_x"], kern_ms["sweep_y"], kern_ms["sweep_z"]]))
+    peak, peak_kind = measured_peak_gbs()
+    sweep_bytes = SWEEP_BYTES_PER_CELL * cells
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    traffic = sweep_traffic_from_profile()
+
+    # ---- end to end through the public API with host buffers ---------------
+    # each step the face velocities of the liquid (produced by the flow
+    # solver on the host) are copied in from pinned memory, the step runs,
+    # and its sums are read back
+    uh = torch.from_numpy(wl.u).pin_memory()
+    vh = torch.from_numpy(wl.v).pin_memory()
+    wh = torch.from_numpy(wl.w).pin_memory()
+    sums_h = torch.empty(P.VOF_NSUMS, dtype=torch.float64).pin_memory()
+    c.copy_(c0); e.copy_(e0)
+    e2e_steps = max(3, min(args.steps, 100))
+    for s in range(2):
+        u.copy_(uh, non_blocking=True); v.copy_(vh, non_blocking=True); w.copy_(wh, non_blocking=True)
+        st.step(c, e, u, v, w, wl.dt, s, dd_uniform=wl.dd_uniform)
+        sums_h.copy_(st.sums, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        u.copy_(uh, non_blocking=True); v.copy_(vh, non_blocking=True); w.copy_(wh, non_blocking=True)
+        st.step(c, e, u, v, w, wl.dt, s, dd_uniform=wl.dd_uniform)
+        sums_h.copy_(st.sums, non_blocking=True)
+        stream.synchronize()
+        _ = float(sums_h[0])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+    e2e_value = cells * e2e_steps * world / e2e_s / 1e9
+    h2d = (wl.u.nbytes + wl.v.nbytes + wl.w.nbytes)
+
+    if rank == 0:
+        cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
+        out = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"bubble-growth {N_CELLS}^3 (vapour R0=0.1, erf layer 0.02, Ja=0.5, water/steam "
+                                   f"Cp ratio {wl.Cp_l / wl.Cp_g:.1f}, radial u_l, uniform shift {wl.dd_uniform:.3e} cells/step)",
+                       "cells": cells, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (c, e, u, v, w: %.2f GB resident)" % (
+                           (wl.c.nbytes + wl.e.nbytes + h2d) / 1e9),
+                       "algorithmic_bytes_per_cell_step": STEP_BYTES_PER_CELL,
+                       "hbm_roofline_frac_step": round(value / world * STEP_BYTES_PER_CELL / peak, 4)},
+            "roofline": {"bound": "hbm", "kernel": "k_sweep (x/y/z mean)", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "algorithmic_bytes_per_launch": sweep_bytes},
+            "kernel_ms": {k: round(v_, 5) for k, v_ in kern_ms.items()},
+            "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": P.VOF_NSUMS * 8},
+            "gpu_launches": MY_KERNELS_PER_STEP * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "final_sums": [float(x) for x in sums],
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_sample(nz_slab=8):
+    """A bounded sample of the workload for the CPU oracle: the z-slab of
+    nz_slab planes through the bubble centre (interface-rich), with its own
+    face velocities; returns the oracle grid and arrays."""
+    import oracle as O
+    wl = load_workload()
+    n = N_CELLS
+    k0 = n // 2 - nz_slab // 2
+    c = np.ascontiguousarray(wl.c[k0:k0 + nz_slab])
+    e = np.ascontiguousarray(wl.e[k0:k0 + nz_slab])
+    u = np.ascontiguousarray(wl.u[k0:k0 + nz_slab])
+    v = np.ascontiguousarray(wl.v[k0:k0 + nz_slab])
+    w = np.ascontiguousarray(wl.w[k0:k0 + nz_slab + 1])
+    g = O.Grid(n, n, nz_slab, wl.bc, wl.h, wl.Cp_l, wl.Cp_g, wl.T_sat)
+    return O, g, wl, c, e, u, v, w
+
+
+def cpu_baseline(budget_s=15.0):
+    O, g, wl, c, e, u, v, w = oracle_sample()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        c, e, _ = O.step(g, c, e, u, v, w, wl.dt, steps, dd_uniform=wl.dd_uniform)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cells = c.size
+    return {"value": round(cells * steps / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps on the 256x256x8 z-slab through the bubble centre "
+                      f"({cells} cells, {dt:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    O, g, wl, c, e, u, v, w = oracle_sample(nz_slab=2)
+    for s in range(args.warmup):
+        c, e, _ = O.step(g, c, e, u, v, w, wl.dt, s, dd_uniform=wl.dd_uniform)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        c, e, _ = O.step(g, c, e, u, v, w, wl.dt, args.warmup + s, dd_uniform=wl.dd_uniform)
+    dt = time.perf_counter() - t0
+    cells = c.size
+    value = cells * args.steps / dt / 1e9
+    sample = (f"each step: one oracle step on the 256x256x2 z-slab through the bubble centre ({cells} cells), "
+              f"single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"bubble-growth {N_CELLS}^3 (oracle sample)", "cells": cells,
+                      "parallelism": "host, 1 thread"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * vofgb.h -- C ABI of the GB300 (sm_103a) library for the hot path of the
+ * one-fluid phase-change method of Malan, Malan, Zaleski & Rousseau,
+ * "A Geometric VOF Method for Interface Resolved Phase Change and
+ * Conservative Thermal Energy Advection" (arXiv:2001.03477):
+ *   - PLIC reconstruction: MYC normal and plane constant (Sec. 3.2,
+ *     Eq. plane_m),
+ *   - Step 1, direction-split geometric VOF sweeps with divergence-free
+ *     liquid velocity (Sec. 3.3.1, Eq. vof_step1_full; Weymouth-Yue split),
+ *     the thermal energy fluxed in tandem with the same geometric fluxes
+ *     (Sec. 3.4.1, Eq. disc_et_adv),
+ *   - Step 2, the phase-change interface shift (Sec. 3.3.2,
+ *     Eqs. vof_step2_full, Delta d, alpha^{n+1}) with the energy change
+ *     Delta e = Delta c (C_pl - C_pg) T_Gamma (end of Sec. 3.4.1).
+ *
+ * Conventions
+ *   - All array arguments are DEVICE pointers owned by the caller; the
+ *     library allocates nothing on these calls.  Scalars are host values.
+ *   - Cell arrays: double[nz][ny][nx], x fastest (no ghost cells; boundary
+ *     conditions are applied by index mapping).
+ *   - Face arrays of axis x: double[nz][ny][nx+1]; y: double[nz][ny+1][nx];
+ *     z: double[nz+1][ny][nx]; face f lies between cells f-1 and f and
+ *     holds the face-normal velocity (positive along +axis).  On a periodic
+ *     axis face n is face 0 (the stored face-n value is not read).
+ *   - PLIC plane of a mixed cell in its local unit cube (origin at the low
+ *     corner): liquid is {x : m.x <= alpha}, m points from liquid into gas,
+ *     |m_x| + |m_y| + |m_z| = 1.  Mixed cells: eps < c < 1 - eps.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream).  Host-side argument errors return VOF_EINVAL before
+ *     anything is launched; launch failures return VOF_ECUDA.  Conditions
+ *     detected inside kernels (a face CFL number above 1) set a sticky
+ *     device status read by vof_get_device_status().
+ *   - Out-of-place: input and output arrays of one call must not overlap.
+ */
+#ifndef VOFGB_H
+#define VOFGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VOF_API __attribute__((visibility("default")))
+#else
+#define VOF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VOF_OK = 0,
+  VOF_EINVAL = 1,  /* bad argument (null pointer, size, aliasing) */
+  VOF_ECUDA = 2,   /* a CUDA call failed; see vof_last_cuda_error() */
+  VOF_ECFL = 3     /* device status: |u| dt / h > 1 on some face */
+} vof_status;
+
+typedef struct {
+  int nx, ny, nz;     /* interior cells per axis (>= 1) */
+  int bc[3];          /* per axis x, y, z: 0 periodic, 1 zero-gradient */
+  double h;           /* cell size (> 0) */
+  double Cp_l, Cp_g;  /* volumetric heat capacities rho c_p of liquid, gas (> 0) */
+  double T_sat;       /* interface temperature T_Gamma (Sec. 3.2: T_sat(p_sys)) */
+  double eps_mixed;   /* mixed-cell threshold eps (Sec. 3.1: 1e-12) */
+} vof_grid;
+
+/* Number of doubles vof_step() writes to `sums`. */
+#define VOF_NSUMS 6
+
+/*
+ * PLIC reconstruction (Sec. 3.2): for every mixed cell the MYC normal m
+ * (Aulisa et al. 2007; centred-columns candidate kept unless its dominant
+ * component exceeds the Youngs normal's) and the plane constant alpha with
+ * V(m, alpha) = c (analytic inversion, Scardovelli & Zaleski 2000).
+ *   c      [N]     volume fractions (read)
+ *   m      [3][N]  SoA normal components (written; 0 for pure cells)
+ *   alpha  [N]     plane constants (written; 0 for pure cells)
+ *   mixed  [N]     1 for mixed cells, 0 otherwise (written)
+ */
+VOF_API vof_status vof_reconstruct(const vof_grid* g, const double* c, double* m, double* alpha, uint8_t* mixed,
+                           void* stream);
+
+/*
+ * One direction sweep of Step 1 (Sec. 3.3.1) along x, y or z with the
+ * energy fluxed in tandem (Sec. 3.4.1).  With a = u dt / h on each face, the
+ * donor is the upwind cell; the face VOF flux F is the liquid volume of the
+ * donor slab of width |a| next to the face (PLIC geometry for mixed donors,
+ * c |a| for pure ones), the face temperature T_f is WENO5 of T = e / C_p(c)
+ * (Shu 2009), and G = T_f (C_pl F + C_pg (a - F)) is the fluxed energy.
+ * Each cell then takes (Weymouth-Yue dilatation terms)
+ *   c' = c + (F_l - cc a_l) - (F_r - cc a_r),  clamped to [0, 1]
+ *   e' = e + (G_l - Theta a_l) - (G_r - Theta a_r)
+ * with cc = [c^n > 1/2] and Theta = C_p(cc) T^n frozen at the start of the
+ * time step.
+ *   c_in, e_in    [N] state before the sweep (e_in may be NULL: VOF only)
+ *   c_out, e_out  [N] state after the sweep (must not overlap the inputs;
+ *                 e_out ignored when e_in is NULL)
+ *   u_face        face velocities of this axis (layout above)
+ *   dt            time step; a = u dt / h
+ *   state [N] (uint8, in/out) and theta [N] (double, in/out): the frozen
+ *     step-start data.  state bit0 = the cell changed earlier in this step,
+ *     bit1 = its cc; theta holds its Theta.  A cell with bit0 clear takes
+ *     cc and Theta from its current (c, e).  Zero `state` before the first
+ *     sweep of every time step; the sweep marks the cells it changes.
+ *     state may be NULL only for a single sweep from a step start.
+ *     The VOF-only form (e_in NULL) reads state but does not write it.
+ *   flux_out      face array (nullable): receives F of every face
+ *   diag          device double[1] (nullable): clipped volume is ADDED
+ *                 (atomically; last bits depend on block order)
+ */
+VOF_API vof_status vof_advect_sweep_x(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                              double* e_out, const double* u_face, double dt, uint8_t* state, double* theta,
+                              double* flux_out, double* diag, void* stream);
+VOF_API vof_status vof_advect_sweep_y(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                              double* e_out, const double* v_face, double dt, uint8_t* state, double* theta,
+                              double* flux_out, double* diag, void* stream);
+VOF_API vof_status vof_advect_sweep_z(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                              double* e_out, const double* w_face, double dt, uint8_t* state, double* theta,
+                              double* flux_out, double* diag, void* stream);
+
+/*
+ * Unfused energy sweep (Sec. 3.4.1, Eq. disc_et_adv): e' from the face VOF
+ * fluxes F exported by a VOF-only sweep of the same axis.  T is taken from
+ * (c_before, e_in).  Paired with vof_advect_sweep_*(e_in = NULL) it gives
+ * the same e_out, state and theta bit for bit as the fused sweep.
+ *   axis 0/1/2; c_before, c_after [N] VOF field before/after the sweep;
+ *   e_in, e_out [N]; flux_F, u_face: face arrays of the axis;
+ *   state/theta as for the sweep (updated for cells whose c or e changed).
+ */
+VOF_API vof_status energy_advect_consistent(const vof_grid* g, int axis, const double* c_before, const double* c_after,
+                                    const double* e_in, double* e_out, const double* flux_F, const double* u_face,
+                                    double dt, uint8_t* state, double* theta, void* stream);
+
+/*
+ * Step 2, the phase-change shift (Sec. 3.3.2): every mixed cell moves its
+ * plane along its normal by dd cells (Delta d = -(mdot / rho_l) dt / h):
+ * alpha* = alpha + |m|_2 dd capped to the cell, c = V(m, alpha*).  The
+ * movement a cap cuts off continues in the neighbours the interface moves
+ * into: a pure cell of the receding phase takes the largest volume swept in
+ * it by the shifted plane of an adjacent mixed cell extended into it.  Every
+ * changed cell gets e += Delta c (C_pl - C_pg) T_sat.
+ *   c_in, e_in [N] -> c_out, e_out [N] (no overlap)
+ *   dd [N] per-cell shift in cell units (nullable: dd_uniform everywhere)
+ *   state [N] (nullable): zeroed for the next time step
+ *   diag device double[5] (nullable), ADDED atomically:
+ *     {sum Delta c, volume clamped away in receiving cells, sum Delta e,
+ *      sum c_out, sum e_out}
+ */
+VOF_API vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                                  double* e_out, const double* dd, double dd_uniform, uint8_t* state, double* diag,
+                                  void* stream);
+
+/*
+ * One full time step on the caller's stream: zero the frozen state, three
+ * sweeps in Strang-alternated order (x,y,z on even step_index, z,y,x on odd),
+ * then the shift; c and e are updated in place (ping-pong through the
+ * workspace, so the result lands back in c and e).
+ *   u, v, w        face velocities
+ *   dd, dd_uniform as for vof_phase_change_shift
+ *   sums           device double[VOF_NSUMS] (nullable), OVERWRITTEN with
+ *                  {sum c, sum e (after the step), clipped volume of the
+ *                   sweeps, shift sum Delta c, shift clamped volume,
+ *                   shift sum Delta e}, reduced in a fixed order
+ *                  (deterministic).
+ *   workspace      device buffer of at least vof_step_workspace_bytes(g)
+ *                  bytes, 256-byte aligned, caller-owned, not shared with
+ *                  concurrent calls.
+ */
+VOF_API size_t vof_step_workspace_bytes(const vof_grid* g);
+VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, const double* v, const double* w,
+                    double dt, long step_index, const double* dd, double dd_uniform, double* sums,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* Sticky device status (synchronises the device): VOF_OK or VOF_ECFL; reading clears it. */
+VOF_API vof_status vof_get_device_status(void);
+/* Message for a status code (static string). */
+VOF_API const char* vof_status_string(int status);
+/* The cudaError_t of the last call that returned VOF_ECUDA. */
+VOF_API int vof_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOFGB_H */

@@ -1,0 +1,240 @@
+"""GB300 (sm_103a) library for the hot path of Malan et al.,
+"A Geometric VOF Method for Interface Resolved Phase Change and Conservative
+Thermal Energy Advection" (arXiv:2001.03477): PLIC reconstruction, the
+direction-split geometric VOF sweeps with the thermal energy fluxed in tandem
+(Sec. 3.3.1, 3.4.1) and the phase-change interface shift (Sec. 3.3.2).
+
+This module is a thin ctypes binding over the C ABI in include/vofgb.h
+(libvofgb.so, built in-tree by `build.py`).  It only marshals arguments:
+every step of the path runs in the library's CUDA kernels.  Tensors must be
+contiguous CUDA tensors (float64 fields, uint8 state); calls are queued on
+torch's current CUDA stream.  There is no CPU fallback: if the library is
+not built, or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvofgb.so")
+
+VOF_OK, VOF_EINVAL, VOF_ECUDA, VOF_ECFL = 0, 1, 2, 3
+VOF_NSUMS = 6
+
+
+class VofError(RuntimeError):
+    def __init__(self, name, status, lib=None):
+        msg = f"{name}: status {status}"
+        if lib is not None:
+            msg += f" ({lib.vof_status_string(status).decode()})"
+            if status == VOF_ECUDA:
+                msg += f", cudaError {lib.vof_last_cuda_error()}"
+        super().__init__(msg)
+        self.status = status
+
+
+class _CGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3),
+                ("h", ctypes.c_double), ("Cp_l", ctypes.c_double), ("Cp_g", ctypes.c_double),
+                ("T_sat", ctypes.c_double), ("eps_mixed", ctypes.c_double)]
+
+
+@dataclass
+class Grid:
+    """Uniform grid and phase properties (vof_grid in include/vofgb.h)."""
+    nx: int
+    ny: int
+    nz: int
+    bc: tuple = (0, 0, 0)
+    h: float = 1.0
+    Cp_l: float = 1.0
+    Cp_g: float = 1.0
+    T_sat: float = 0.0
+    eps_mixed: float = 1e-12
+    _c: _CGrid = field(default=None, repr=False, compare=False)
+
+    def c_struct(self):
+        g = _CGrid()
+        g.nx, g.ny, g.nz = int(self.nx), int(self.ny), int(self.nz)
+        for d in range(3):
+            g.bc[d] = int(self.bc[d])
+        g.h, g.Cp_l, g.Cp_g = float(self.h), float(self.Cp_l), float(self.Cp_g)
+        g.T_sat, g.eps_mixed = float(self.T_sat), float(self.eps_mixed)
+        return g
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz
+
+    def face_shape(self, axis):
+        nz, ny, nx = self.shape
+        return [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][axis]
+
+
+_lib = None
+
+
+def lib():
+    """Load libvofgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libvofgb.so is not built ({LIB_PATH}); run paper_2001_03477_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, I, L_, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_size_t
+        G = ctypes.POINTER(_CGrid)
+        sig = {
+            "vof_reconstruct": [G, P, P, P, P, P],
+            "vof_advect_sweep_x": [G, P, P, P, P, P, D, P, P, P, P, P],
+            "vof_advect_sweep_y": [G, P, P, P, P, P, D, P, P, P, P, P],
+            "vof_advect_sweep_z": [G, P, P, P, P, P, D, P, P, P, P, P],
+            "energy_advect_consistent": [G, I, P, P, P, P, P, P, D, P, P, P],
+            "vof_phase_change_shift": [G, P, P, P, P, P, D, P, P, P],
+            "vof_step": [G, P, P, P, P, P, D, L_, P, D, P, P, S, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.vof_step_workspace_bytes.argtypes = [G]
+        L.vof_step_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_get_device_status.argtypes = []
+        L.vof_get_device_status.restype = ctypes.c_int
+        L.vof_status_string.argtypes = [ctypes.c_int]
+        L.vof_status_string.restype = ctypes.c_char_p
+        L.vof_last_cuda_error.argtypes = []
+        L.vof_last_cuda_error.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(name, status):
+    if status != VOF_OK:
+        raise VofError(name, status, lib())
+
+
+def _f64():
+    import torch
+    return torch.float64
+
+
+def _u8():
+    import torch
+    return torch.uint8
+
+
+def vof_reconstruct(g: Grid, c, m, alpha, mixed, stream=None):
+    cg = g.c_struct()
+    _check("vof_reconstruct", lib().vof_reconstruct(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(m, _f64(), "m"),
+                                                    _ptr(alpha, _f64(), "alpha"), _ptr(mixed, _u8(), "mixed"),
+                                                    _stream(stream)))
+
+
+def _sweep(name, g, c_in, e_in, c_out, e_out, uf, dt, state, theta, flux_out, diag, stream):
+    cg = g.c_struct()
+    fn = getattr(lib(), name)
+    _check(name, fn(ctypes.byref(cg), _ptr(c_in, _f64(), "c_in"), _ptr(e_in, _f64(), "e_in"),
+                    _ptr(c_out, _f64(), "c_out"), _ptr(e_out, _f64(), "e_out"), _ptr(uf, _f64(), "face"),
+                    float(dt), _ptr(state, _u8(), "state"), _ptr(theta, _f64(), "theta"),
+                    _ptr(flux_out, _f64(), "flux_out"), _ptr(diag, _f64(), "diag"), _stream(stream)))
+
+
+def vof_advect_sweep_x(g, c_in, e_in, c_out, e_out, u_face, dt, state=None, theta=None, flux_out=None, diag=None,
+                       stream=None):
+    _sweep("vof_advect_sweep_x", g, c_in, e_in, c_out, e_out, u_face, dt, state, theta, flux_out, diag, stream)
+
+
+def vof_advect_sweep_y(g, c_in, e_in, c_out, e_out, v_face, dt, state=None, theta=None, flux_out=None, diag=None,
+                       stream=None):
+    _sweep("vof_advect_sweep_y", g, c_in, e_in, c_out, e_out, v_face, dt, state, theta, flux_out, diag, stream)
+
+
+def vof_advect_sweep_z(g, c_in, e_in, c_out, e_out, w_face, dt, state=None, theta=None, flux_out=None, diag=None,
+                       stream=None):
+    _sweep("vof_advect_sweep_z", g, c_in, e_in, c_out, e_out, w_face, dt, state, theta, flux_out, diag, stream)
+
+
+SWEEPS = (vof_advect_sweep_x, vof_advect_sweep_y, vof_advect_sweep_z)
+
+
+def energy_advect_consistent(g, axis, c_before, c_after, e_in, e_out, flux_F, u_face, dt, state=None, theta=None,
+                             stream=None):
+    cg = g.c_struct()
+    _check("energy_advect_consistent",
+           lib().energy_advect_consistent(ctypes.byref(cg), int(axis), _ptr(c_before, _f64(), "c_before"),
+                                          _ptr(c_after, _f64(), "c_after"), _ptr(e_in, _f64(), "e_in"),
+                                          _ptr(e_out, _f64(), "e_out"), _ptr(flux_F, _f64(), "flux_F"),
+                                          _ptr(u_face, _f64(), "u_face"), float(dt), _ptr(state, _u8(), "state"),
+                                          _ptr(theta, _f64(), "theta"), _stream(stream)))
+
+
+def vof_phase_change_shift(g, c_in, e_in, c_out, e_out, dd=None, dd_uniform=0.0, state=None, diag=None,
+                           stream=None):
+    cg = g.c_struct()
+    _check("vof_phase_change_shift",
+           lib().vof_phase_change_shift(ctypes.byref(cg), _ptr(c_in, _f64(), "c_in"), _ptr(e_in, _f64(), "e_in"),
+                                        _ptr(c_out, _f64(), "c_out"), _ptr(e_out, _f64(), "e_out"),
+                                        _ptr(dd, _f64(), "dd"), float(dd_uniform), _ptr(state, _u8(), "state"),
+                                        _ptr(diag, _f64(), "diag"), _stream(stream)))
+
+
+def vof_step_workspace_bytes(g: Grid) -> int:
+    cg = g.c_struct()
+    return int(lib().vof_step_workspace_bytes(ctypes.byref(cg)))
+
+
+def vof_step(g, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, sums=None, workspace=None, stream=None):
+    cg = g.c_struct()
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("vof_step",
+           lib().vof_step(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(e, _f64(), "e"), _ptr(u, _f64(), "u"),
+                          _ptr(v, _f64(), "v"), _ptr(w, _f64(), "w"), float(dt), int(step_index),
+                          _ptr(dd, _f64(), "dd"), float(dd_uniform), _ptr(sums, _f64(), "sums"),
+                          _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes), _stream(stream)))
+
+
+def vof_get_device_status() -> int:
+    return int(lib().vof_get_device_status())
+
+
+class Stepper:
+    """Owns the workspace of vof_step for one grid (allocated through torch)."""
+
+    def __init__(self, g: Grid, device="cuda"):
+        import torch
+        self.g = g
+        nb = vof_step_workspace_bytes(g)
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.sums = torch.zeros(VOF_NSUMS, dtype=torch.float64, device=device)
+
+    def step(self, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, stream=None):
+        vof_step(self.g, c, e, u, v, w, dt, step_index, dd, dd_uniform, self.sums, self.workspace, stream)
+        return self.sums

@@ -1,0 +1,257 @@
+// vof_api.cu -- C ABI of the library (declared in include/vofgb.h): argument
+// checks, parameter marshalling and the stream-ordered time step.
+#include <cstring>
+#include <mutex>
+
+#include "../../include/vofgb.h"
+#include "vof_launch.h"
+
+namespace vofgb {
+
+__device__ int g_vof_status;
+
+static thread_local int t_last_cuda = 0;
+
+int* device_status_ptr() {
+  static std::mutex mu;
+  static int* ptrs[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_vof_status) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int*>(p);
+  }
+  return ptrs[dev];
+}
+
+static bool grid_ok(const vof_grid* g) {
+  if (!g) return false;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return false;
+  if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return false;
+  for (int d = 0; d < 3; ++d)
+    if (g->bc[d] != 0 && g->bc[d] != 1) return false;
+  if (!(g->h > 0.0) || !(g->Cp_l > 0.0) || !(g->Cp_g > 0.0)) return false;
+  if (!(g->eps_mixed >= 0.0 && g->eps_mixed < 0.5)) return false;
+  return true;
+}
+
+static GridDev to_dev(const vof_grid* g, double dt) {
+  GridDev d;
+  d.n[0] = g->nx; d.n[1] = g->ny; d.n[2] = g->nz;
+  d.bc[0] = g->bc[0]; d.bc[1] = g->bc[1]; d.bc[2] = g->bc[2];
+  d.lam = dt / g->h;
+  d.Cp_l = g->Cp_l; d.Cp_g = g->Cp_g; d.T_sat = g->T_sat; d.eps = g->eps_mixed;
+  return d;
+}
+
+static size_t cells(const vof_grid* g) { return (size_t)g->nx * g->ny * g->nz; }
+
+static size_t face_count(const vof_grid* g, int axis) {
+  size_t nx = g->nx, ny = g->ny, nz = g->nz;
+  if (axis == 0) return nz * ny * (nx + 1);
+  if (axis == 1) return nz * (ny + 1) * nx;
+  return (nz + 1) * ny * nx;
+}
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b) return false;
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+static vof_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return VOF_OK;
+  t_last_cuda = (int)e;
+  return VOF_ECUDA;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace vofgb
+
+using namespace vofgb;
+
+extern "C" {
+
+vof_status vof_reconstruct(const vof_grid* g, const double* c, double* m, double* alpha, uint8_t* mixed,
+                           void* stream) {
+  if (!grid_ok(g) || !c || !m || !alpha || !mixed) return VOF_EINVAL;
+  size_t N = cells(g);
+  if (overlap(c, N * 8, m, 3 * N * 8) || overlap(c, N * 8, alpha, N * 8) || overlap(c, N * 8, mixed, N))
+    return VOF_EINVAL;
+  return cuda_status(launch_reconstruct(to_dev(g, 0.0), c, m, alpha, mixed, (cudaStream_t)stream));
+}
+
+static vof_status sweep_common(int axis, const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                               double* e_out, const double* uf, double dt, uint8_t* state, double* theta,
+                               double* flux_out, double* diag, void* stream) {
+  if (!grid_ok(g) || !c_in || !c_out || !uf) return VOF_EINVAL;
+  if (e_in && (!e_out || (state && !theta))) return VOF_EINVAL;
+  if (!(dt >= 0.0)) return VOF_EINVAL;
+  size_t N = cells(g), B = N * 8;
+  if (overlap(c_in, B, c_out, B)) return VOF_EINVAL;
+  if (e_in && (overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) || overlap(e_in, B, c_out, B) ||
+               overlap(c_out, B, e_out, B)))
+    return VOF_EINVAL;
+  if (flux_out && (overlap(flux_out, face_count(g, axis) * 8, c_out, B) ||
+                   (e_out && overlap(flux_out, face_count(g, axis) * 8, e_out, B))))
+    return VOF_EINVAL;
+  SumOut so{nullptr, 1, diag};
+  return cuda_status(launch_sweep(axis, to_dev(g, dt), c_in, e_in, c_out, e_in ? e_out : nullptr, uf, state, theta,
+                                  flux_out, so, (cudaStream_t)stream));
+}
+
+vof_status vof_advect_sweep_x(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                              double* e_out, const double* u_face, double dt, uint8_t* state, double* theta,
+                              double* flux_out, double* diag, void* stream) {
+  return sweep_common(0, g, c_in, e_in, c_out, e_out, u_face, dt, state, theta, flux_out, diag, stream);
+}
+vof_status vof_advect_sweep_y(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                              double* e_out, const double* v_face, double dt, uint8_t* state, double* theta,
+                              double* flux_out, double* diag, void* stream) {
+  return sweep_common(1, g, c_in, e_in, c_out, e_out, v_face, dt, state, theta, flux_out, diag, stream);
+}
+vof_status vof_advect_sweep_z(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                              double* e_out, const double* w_face, double dt, uint8_t* state, double* theta,
+                              double* flux_out, double* diag, void* stream) {
+  return sweep_common(2, g, c_in, e_in, c_out, e_out, w_face, dt, state, theta, flux_out, diag, stream);
+}
+
+vof_status energy_advect_consistent(const vof_grid* g, int axis, const double* c_before, const double* c_after,
+                                    const double* e_in, double* e_out, const double* flux_F, const double* u_face,
+                                    double dt, uint8_t* state, double* theta, void* stream) {
+  if (!grid_ok(g) || axis < 0 || axis > 2 || !c_before || !c_after || !e_in || !e_out || !flux_F || !u_face)
+    return VOF_EINVAL;
+  if (state && !theta) return VOF_EINVAL;
+  if (!(dt >= 0.0)) return VOF_EINVAL;
+  size_t B = cells(g) * 8;
+  if (overlap(e_in, B, e_out, B) || overlap(c_before, B, e_out, B) || overlap(c_after, B, e_out, B)) return VOF_EINVAL;
+  return cuda_status(launch_energy(axis, to_dev(g, dt), c_before, c_after, e_in, e_out, flux_F, u_face, state, theta,
+                                   (cudaStream_t)stream));
+}
+
+vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
+                                  double* e_out, const double* dd, double dd_uniform, uint8_t* state, double* diag,
+                                  void* stream) {
+  if (!grid_ok(g) || !c_in || !e_in || !c_out || !e_out) return VOF_EINVAL;
+  size_t B = cells(g) * 8;
+  if (overlap(c_in, B, c_out, B) || overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) ||
+      overlap(e_in, B, c_out, B) || overlap(c_out, B, e_out, B))
+    return VOF_EINVAL;
+  SumOut so{nullptr, 5, diag};
+  return cuda_status(
+      launch_shift(to_dev(g, 0.0), c_in, e_in, c_out, e_out, dd, dd_uniform, state, so, (cudaStream_t)stream));
+}
+
+// workspace layout: c2 | e2 | theta | state | partials (3 sweeps x 1, shift x 5)
+struct StepLayout {
+  size_t off_c2, off_e2, off_th, off_st, off_ps, off_sh, total;
+  int nb_sw[3], nb_sh;
+};
+
+static StepLayout step_layout(const vof_grid* g) {
+  StepLayout L;
+  GridDev d = to_dev(g, 0.0);
+  size_t N = cells(g);
+  L.off_c2 = 0;
+  L.off_e2 = L.off_c2 + align256(N * 8);
+  L.off_th = L.off_e2 + align256(N * 8);
+  L.off_st = L.off_th + align256(N * 8);
+  L.off_ps = L.off_st + align256(N);
+  size_t nsw = 0;
+  for (int a = 0; a < 3; ++a) {
+    L.nb_sw[a] = sweep_blocks(a, d);
+    nsw += (size_t)L.nb_sw[a];
+  }
+  L.nb_sh = shift_blocks(d);
+  L.off_sh = L.off_ps + align256(nsw * 8);
+  L.total = L.off_sh + align256((size_t)L.nb_sh * 5 * 8);
+  return L;
+}
+
+size_t vof_step_workspace_bytes(const vof_grid* g) {
+  if (!grid_ok(g)) return 0;
+  return step_layout(g).total;
+}
+
+vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, const double* v, const double* w,
+                    double dt, long step_index, const double* dd, double dd_uniform, double* sums, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+  if (!grid_ok(g) || !c || !e || !u || !v || !w || !workspace) return VOF_EINVAL;
+  if (!(dt >= 0.0) || step_index < 0) return VOF_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
+  StepLayout L = step_layout(g);
+  if (workspace_bytes < L.total) return VOF_EINVAL;
+  size_t N = cells(g), B = N * 8;
+  if (overlap(c, B, e, B) || overlap(c, B, workspace, L.total) || overlap(e, B, workspace, L.total))
+    return VOF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = static_cast<char*>(workspace);
+  double* c2 = reinterpret_cast<double*>(ws + L.off_c2);
+  double* e2 = reinterpret_cast<double*>(ws + L.off_e2);
+  double* th = reinterpret_cast<double*>(ws + L.off_th);
+  uint8_t* state = reinterpret_cast<uint8_t*>(ws + L.off_st);
+  double* ps = reinterpret_cast<double*>(ws + L.off_ps);
+  double* psh = reinterpret_cast<double*>(ws + L.off_sh);
+  GridDev d = to_dev(g, dt);
+  const double* uf[3] = {u, v, w};
+  cudaError_t err = cudaMemsetAsync(state, 0, N, st);
+  if (err != cudaSuccess) return cuda_status(err);
+  double* src_c = c;
+  double* src_e = e;
+  double* dst_c = c2;
+  double* dst_e = e2;
+  size_t poff = 0;
+  int order[3];
+  for (int s = 0; s < 3; ++s) order[s] = (step_index % 2 == 0) ? s : 2 - s;
+  for (int s = 0; s < 3; ++s) {
+    int ax = order[s];
+    SumOut so{ps + poff, 1, nullptr};
+    err = launch_sweep(ax, d, src_c, src_e, dst_c, dst_e, uf[ax], state, th, nullptr, so, st);
+    if (err != cudaSuccess) return cuda_status(err);
+    poff += (size_t)L.nb_sw[ax];
+    double* tc = src_c; src_c = dst_c; dst_c = tc;
+    double* te = src_e; src_e = dst_e; dst_e = te;
+  }
+  // after 3 sweeps the state sits in the workspace; the shift writes back
+  SumOut so{psh, 5, nullptr};
+  err = launch_shift(d, src_c, src_e, c, e, dd, dd_uniform, nullptr, so, st);
+  if (err != cudaSuccess) return cuda_status(err);
+  if (sums) {
+    // sums[0..1] = sum c, sum e; sums[2] = clip; sums[3..5] = shift diagnostics
+    err = launch_reduce(psh, L.nb_sh, 5, 3, 2, sums, st);
+    if (err == cudaSuccess) err = launch_reduce(ps, (int)poff, 1, 0, 1, sums + 2, st);
+    if (err == cudaSuccess) err = launch_reduce(psh, L.nb_sh, 5, 0, 3, sums + 3, st);
+    if (err != cudaSuccess) return cuda_status(err);
+  }
+  return VOF_OK;
+}
+
+vof_status vof_get_device_status(void) {
+  int* p = device_status_ptr();
+  if (!p) return VOF_ECUDA;
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, p, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  int z = 0;
+  e = cudaMemcpy(p, &z, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
+  return (h & DEV_CFL) ? VOF_ECFL : VOF_OK;
+}
+
+const char* vof_status_string(int status) {
+  switch (status) {
+    case VOF_OK: return "ok";
+    case VOF_EINVAL: return "invalid argument";
+    case VOF_ECUDA: return "CUDA error";
+    case VOF_ECFL: return "face CFL number above 1";
+    default: return "unknown status";
+  }
+}
+
+int vof_last_cuda_error(void) { return t_last_cuda; }
+
+}  // extern "C"

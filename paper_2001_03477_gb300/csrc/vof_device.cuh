@@ -1,0 +1,335 @@
+// vof_device.cuh -- device-side PLIC geometry, MYC normal and WENO5 face
+// value for the GB300 library (sm_103a).  Method: Malan et al.,
+// arXiv:2001.03477, Sec. 3.2 (PLIC: MYC normal, plane constant from the
+// volume), Sec. 3.3 (geometric face fluxes), Sec. 3.4.1 (WENO5 face
+// temperature).
+//
+// The library is compiled with -fmad=false: every expression below rounds
+// each operation separately, in the order written, so that discrete
+// decisions (which normal candidate wins, which cells are mixed, which
+// face value shortcut applies) are taken on exactly the same numbers on any
+// path that evaluates them.  Where a fused multiply-add is wanted it is
+// written as fma().
+#pragma once
+#include <cstdint>
+
+namespace vofgb {
+
+// ---------------------------------------------------------------------------
+// Problem description passed to kernels by value
+// ---------------------------------------------------------------------------
+struct GridDev {
+  int n[3];      // nx, ny, nz
+  int bc[3];     // 0 periodic, 1 zero-gradient
+  double lam;    // dt / h
+  double Cp_l, Cp_g, T_sat, eps;
+};
+
+__device__ __forceinline__ int map_idx(int i, int n, int bc) {
+  if (bc == 0) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+__device__ __forceinline__ double heat_cap(double Cp_l, double Cp_g, double c) {
+  return Cp_l * c + Cp_g * (1.0 - c);
+}
+
+__device__ __forceinline__ bool is_mixed(double c, double eps) { return c > eps && c < 1.0 - eps; }
+
+// ---------------------------------------------------------------------------
+// Volume below a plane in the unit cube (Scardovelli & Zaleski 2000)
+// ---------------------------------------------------------------------------
+// sorted 0 <= m1 <= m2 <= m3, sum 1, 0 < a <= 1/2: inclusion-exclusion of the
+// cube's corner terms, branch by branch, with the (a-m2)^3 and (a-m3)^3
+// corrections kept bounded by m1 so nothing cancels catastrophically.
+__device__ __forceinline__ double vol_low(double m1, double m2, double m3, double a) {
+  double m12 = m1 + m2;
+  if (a < m1) return a * a * a / (6.0 * m1 * m2 * m3);
+  double v2 = a * (a - m1) / (2.0 * m2 * m3) + m1 * m1 / (6.0 * m2 * m3);
+  if (a < m2) return v2;
+  double t2 = a - m2;
+  double v3 = v2 - t2 * t2 * t2 / (6.0 * m1 * m2 * m3);
+  double top = m12 < m3 ? m12 : m3;
+  if (a < top) return v3;
+  if (m12 <= m3) return (2.0 * a - m12) / (2.0 * m3);
+  double t3 = a - m3;
+  return v3 - t3 * t3 * t3 / (6.0 * m1 * m2 * m3);
+}
+
+__device__ __forceinline__ void sort3(double& a, double& b, double& c) {
+  double t;
+  if (a > b) { t = a; a = b; b = t; }
+  if (b > c) { t = b; b = c; c = t; }
+  if (a > b) { t = a; a = b; b = t; }
+}
+
+// m >= 0, sum 1
+__device__ __forceinline__ double vol_pos(double m0, double m1, double m2, double a) {
+  if (a <= 0.0) return 0.0;
+  if (a >= 1.0) return 1.0;
+  sort3(m0, m1, m2);
+  if (a <= 0.5) return vol_low(m0, m1, m2, a);
+  return 1.0 - vol_low(m0, m1, m2, 1.0 - a);
+}
+
+struct Mirror {
+  double mp[3];  // |m| / l1
+  double sh;     // alpha_mirror = alpha + sh
+  double l1;
+};
+
+__device__ __forceinline__ Mirror mirror_normalise(double m0, double m1, double m2) {
+  Mirror r;
+  double sh = 0.0;
+  double a0, a1, a2;
+  if (m0 < 0.0) { a0 = -m0; sh -= m0; } else a0 = m0;
+  if (m1 < 0.0) { a1 = -m1; sh -= m1; } else a1 = m1;
+  if (m2 < 0.0) { a2 = -m2; sh -= m2; } else a2 = m2;
+  double s = a0 + a1 + a2;
+  r.sh = sh;
+  r.l1 = s;
+  if (s > 0.0) { a0 /= s; a1 /= s; a2 /= s; }
+  r.mp[0] = a0; r.mp[1] = a1; r.mp[2] = a2;
+  return r;
+}
+
+// liquid fraction of {x in [0,1]^3 : m.x <= alpha}, any m
+__device__ __forceinline__ double volume(double m0, double m1, double m2, double alpha) {
+  Mirror r = mirror_normalise(m0, m1, m2);
+  if (r.l1 == 0.0) return alpha >= 0.0 ? 1.0 : 0.0;
+  return vol_pos(r.mp[0], r.mp[1], r.mp[2], (alpha + r.sh) / r.l1);
+}
+
+// derivative dV/da on the same branches (for the Newton polish)
+__device__ __forceinline__ double dvol_low(double m1, double m2, double m3, double a) {
+  double m12 = m1 + m2;
+  if (a < m1) return a * a / (2.0 * m1 * m2 * m3);
+  double d2 = (2.0 * a - m1) / (2.0 * m2 * m3);
+  if (a < m2) return d2;
+  double t2 = a - m2;
+  double d3 = d2 - t2 * t2 / (2.0 * m1 * m2 * m3);
+  double top = m12 < m3 ? m12 : m3;
+  if (a < top) return d3;
+  if (m12 <= m3) return 1.0 / m3;
+  double t3 = a - m3;
+  return d3 - t3 * t3 / (2.0 * m1 * m2 * m3);
+}
+
+// Plane constant for sorted m (sum 1) and 0 < c <= 1/2, analytic per branch
+// (Scardovelli & Zaleski 2000): cube root, quadratic, linear, or the
+// trigonometric root of the branch cubic; then one safeguarded Newton step.
+__device__ __forceinline__ double alpha_low(double m1, double m2, double m3, double c) {
+  double m12 = m1 + m2;
+  double P6 = 6.0 * m1 * m2 * m3;
+  double V1 = (m1 > 0.0) ? m1 * m1 / (6.0 * m2 * m3) : 0.0;
+  double V2 = V1 + (m2 - m1) / (2.0 * m3);
+  double a, lo, hi;
+  if (c < V1) {
+    a = cbrt(P6 * c);
+    lo = 0.0; hi = m1;
+  } else if (c < V2) {
+    double disc = 2.0 * m2 * m3 * c - m1 * m1 / 12.0;
+    a = 0.5 * m1 + sqrt(disc > 0.0 ? disc : 0.0);
+    lo = m1; hi = m2;
+  } else {
+    bool lin = (m12 <= m3);
+    double Vt = lin ? m12 / (2.0 * m3) : vol_low(m1, m2, m3, m3);
+    if (c < Vt) {
+      // a^3 - 3 m12 a^2 + 3 (m1^2 + m2^2) a - (m1^3 + m2^3 - 6 P c) = 0
+      double a2 = -3.0 * m12, a1 = 3.0 * (m1 * m1 + m2 * m2);
+      double a0 = -(m1 * m1 * m1 + m2 * m2 * m2 - P6 * c);
+      lo = m2; hi = lin ? m12 : m3;
+      double p = a1 - a2 * a2 / 3.0;
+      double q = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
+      double best = 0.5 * (lo + hi);
+      if (p < 0.0) {
+        double r = 2.0 * sqrt(-p / 3.0);
+        double arg = 3.0 * q / (p * r);
+        arg = arg > 1.0 ? 1.0 : (arg < -1.0 ? -1.0 : arg);
+        double th = acos(arg) / 3.0;
+        double bd = 1e300;
+        for (int k = 0; k < 3; ++k) {
+          double t = r * cos(th - 2.0943951023931957 * k) - a2 / 3.0;
+          double d = t < lo ? lo - t : (t > hi ? t - hi : 0.0);
+          if (d < bd) { bd = d; best = t; }
+        }
+      }
+      a = best;
+    } else if (lin) {
+      a = m3 * c + 0.5 * m12;
+      lo = m12; hi = 0.5;
+    } else {
+      // a^3 - 1.5 a^2 + 1.5 S2 a - 0.5 (S3 - 6 P c) = 0
+      double S2 = m1 * m1 + m2 * m2 + m3 * m3;
+      double S3 = m1 * m1 * m1 + m2 * m2 * m2 + m3 * m3 * m3;
+      double a2 = -1.5, a1 = 1.5 * S2, a0 = -0.5 * (S3 - P6 * c);
+      lo = m3; hi = 0.5;
+      double p = a1 - a2 * a2 / 3.0;
+      double q = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
+      double best = 0.5 * (lo + hi);
+      if (p < 0.0) {
+        double r = 2.0 * sqrt(-p / 3.0);
+        double arg = 3.0 * q / (p * r);
+        arg = arg > 1.0 ? 1.0 : (arg < -1.0 ? -1.0 : arg);
+        double th = acos(arg) / 3.0;
+        double bd = 1e300;
+        for (int k = 0; k < 3; ++k) {
+          double t = r * cos(th - 2.0943951023931957 * k) - a2 / 3.0;
+          double d = t < lo ? lo - t : (t > hi ? t - hi : 0.0);
+          if (d < bd) { bd = d; best = t; }
+        }
+      }
+      a = best;
+    }
+  }
+  a = a < lo ? lo : (a > hi ? hi : a);
+  // Newton polish on the branch polynomial (safeguarded to the bracket)
+  for (int it = 0; it < 2; ++it) {
+    double f = vol_low(m1, m2, m3, a) - c;
+    double d = dvol_low(m1, m2, m3, a);
+    if (!(d > 0.0)) break;
+    double an = a - f / d;
+    if (!(an >= lo && an <= hi)) break;
+    a = an;
+  }
+  return a;
+}
+
+// alpha with volume(m, alpha) = c for any m (mirror, normalise, invert,
+// undo): the same outer steps as the volume function.
+__device__ __forceinline__ double plane_alpha(double m0, double m1, double m2, double c) {
+  Mirror r = mirror_normalise(m0, m1, m2);
+  if (r.l1 == 0.0) return 0.0;
+  if (c <= 0.0) return 0.0 - r.sh;
+  if (c >= 1.0) return r.l1 - r.sh;
+  double s0 = r.mp[0], s1 = r.mp[1], s2 = r.mp[2];
+  sort3(s0, s1, s2);
+  double am;
+  if (c <= 0.5) am = alpha_low(s0, s1, s2, c);
+  else am = 1.0 - alpha_low(s0, s1, s2, 1.0 - c);
+  return am * r.l1 - r.sh;
+}
+
+// liquid volume (cell units) in the slab x_axis in [x0, x0+delta]
+__device__ __forceinline__ double slab_volume(const double m[3], double alpha, int axis, double x0, double delta) {
+  if (delta <= 0.0) return 0.0;
+  double mm0 = m[0], mm1 = m[1], mm2 = m[2];
+  double ma = m[axis];
+  if (axis == 0) mm0 = ma * delta;
+  else if (axis == 1) mm1 = ma * delta;
+  else mm2 = ma * delta;
+  double a2 = alpha - ma * x0;
+  return delta * volume(mm0, mm1, mm2, a2);
+}
+
+// ---------------------------------------------------------------------------
+// MYC normal (Aulisa et al. 2007): stencil s[(dz*3+dy)*3+dx], offsets 0..2
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sax(const double* s, int d, int r, int p, int q) {
+  // value at offset r along d, p along t1, q along t2 (t1 < t2 the other axes)
+  int o0, o1, o2;
+  if (d == 0) { o0 = r; o1 = p; o2 = q; }
+  else if (d == 1) { o1 = r; o0 = p; o2 = q; }
+  else { o2 = r; o0 = p; o1 = q; }
+  return s[((o2 + 1) * 3 + (o1 + 1)) * 3 + (o0 + 1)];
+}
+
+__device__ __forceinline__ void youngs_normal(const double* s, double m[3]) {
+  const double w[3] = {1.0, 2.0, 1.0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double g = 0.0;
+#pragma unroll
+    for (int q = -1; q <= 1; ++q)
+#pragma unroll
+      for (int p = -1; p <= 1; ++p) {
+        double diff = sax(s, d, 1, p, q) - sax(s, d, -1, p, q);
+        g = g + (w[p + 1] * w[q + 1]) * diff;
+      }
+    m[d] = -g;
+  }
+  double l1 = fabs(m[0]) + fabs(m[1]) + fabs(m[2]);
+  if (l1 > 0.0) { m[0] /= l1; m[1] /= l1; m[2] /= l1; }
+  else { m[0] = 1.0; m[1] = 0.0; m[2] = 0.0; }
+}
+
+__device__ __forceinline__ void cc_candidate(const double* s, int d, double m[3]) {
+  double h[3][3];
+#pragma unroll
+  for (int q = -1; q <= 1; ++q)
+#pragma unroll
+    for (int p = -1; p <= 1; ++p) {
+      double col = sax(s, d, -1, p, q);
+      col = col + sax(s, d, 0, p, q);
+      col = col + sax(s, d, 1, p, q);
+      h[p + 1][q + 1] = col;
+    }
+  double lower = 0.0, upper = 0.0;
+#pragma unroll
+  for (int q = -1; q <= 1; ++q)
+#pragma unroll
+    for (int p = -1; p <= 1; ++p) {
+      lower = lower + sax(s, d, -1, p, q);
+      upper = upper + sax(s, d, 1, p, q);
+    }
+  double sg = (lower >= upper) ? 1.0 : -1.0;
+  double a1 = -(h[2][1] - h[0][1]) * 0.5;
+  double a2 = -(h[1][2] - h[1][0]) * 0.5;
+  double l1 = fabs(a1) + fabs(a2) + 1.0;
+  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  m[t1] = a1 / l1;
+  m[t2] = a2 / l1;
+  m[d] = sg / l1;
+}
+
+// Best centred-columns candidate (largest own-axis component, lowest axis on
+// ties), kept unless its dominant component exceeds the Youngs normal's, in
+// which case Youngs is taken.
+__device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
+  double best[3];
+  int bd = 0;
+  cc_candidate(s, 0, best);
+#pragma unroll
+  for (int d = 1; d < 3; ++d) {
+    double cand[3];
+    cc_candidate(s, d, cand);
+    if (fabs(cand[d]) > fabs(best[bd])) {
+      best[0] = cand[0]; best[1] = cand[1]; best[2] = cand[2];
+      bd = d;
+    }
+  }
+  double y[3];
+  youngs_normal(s, y);
+  double ymax = fabs(y[0]);
+  if (fabs(y[1]) > ymax) ymax = fabs(y[1]);
+  if (fabs(y[2]) > ymax) ymax = fabs(y[2]);
+  double cmax = fabs(best[bd]);
+  if (cmax <= ymax) { m[0] = best[0]; m[1] = best[1]; m[2] = best[2]; }
+  else { m[0] = y[0]; m[1] = y[1]; m[2] = y[2]; }
+}
+
+// ---------------------------------------------------------------------------
+// WENO5 face value (Jiang-Shu weights, eps 1e-6), upwind-ordered stencil
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double weno5(double vm2, double vm1, double v0, double vp1, double vp2) {
+  if (vm2 == v0 && vm1 == v0 && vp1 == v0 && vp2 == v0) return v0;
+  const double epsw = 1e-6;
+  double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+  double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+  double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+  double d0 = vm2 - 2.0 * vm1 + v0, e0 = vm2 - 4.0 * vm1 + 3.0 * v0;
+  double d1 = vm1 - 2.0 * v0 + vp1, e1 = vm1 - vp1;
+  double d2 = v0 - 2.0 * vp1 + vp2, e2 = 3.0 * v0 - 4.0 * vp1 + vp2;
+  double b0 = (13.0 / 12.0) * d0 * d0 + 0.25 * e0 * e0;
+  double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
+  double b2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
+  double a0 = 0.1 / ((epsw + b0) * (epsw + b0));
+  double a1 = 0.6 / ((epsw + b1) * (epsw + b1));
+  double a2 = 0.3 / ((epsw + b2) * (epsw + b2));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+}  // namespace vofgb

@@ -141,7 +141,10 @@ def radial_faces(shape, h, centre, strength, r_cut):
     nz, ny, nx = shape
     c = np.asarray(centre, dtype=np.float64)
     out = []
-    for axis in range(3):
+    # a centred source in a cubic box: y and z faces are the x faces with
+    # the axes permuted (same solid angles), so compute x faces only
+    sym = (nx == ny == nz) and np.allclose(c, c[0]) and abs(c[0] - 0.5 * nx * h) < 1e-15
+    for axis in range(1 if sym else 3):
         fs = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][axis]
         kk, jj, ii = np.meshgrid(np.arange(fs[0]), np.arange(fs[1]), np.arange(fs[2]), indexing="ij")
         # low corner of the face in physical coordinates
@@ -159,6 +162,10 @@ def radial_faces(shape, h, centre, strength, r_cut):
         vel = strength * om / (h * h)
         vel = np.where(rc < r_cut, 0.0, vel)
         out.append(np.ascontiguousarray(vel))
+    if sym:
+        u = out[0]
+        out.append(np.ascontiguousarray(np.swapaxes(u, 1, 2)))   # v[k][f][i] = u[k][i][f]
+        out.append(np.ascontiguousarray(np.transpose(u, (2, 1, 0))))  # w[f][j][i] = u[i][j][f]
     return tuple(out)
 
 

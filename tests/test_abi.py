@@ -1,0 +1,82 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point
+declared in include/vofgb.h, and rejects bad arguments on the host before
+launching anything (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2001_03477_gb300 import build
+    build.build()
+    import paper_2001_03477_gb300 as P
+    return P.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "vofgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:VOF_API\s+)?(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_lists_the_hot_path():
+    names = declared_functions()
+    for n in ("vof_reconstruct", "vof_advect_sweep_x", "vof_advect_sweep_y", "vof_advect_sweep_z",
+              "vof_phase_change_shift", "energy_advect_consistent", "vof_step", "vof_step_workspace_bytes"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_host_validation_without_gpu(lib):
+    import paper_2001_03477_gb300 as P
+    g = P.Grid(8, 8, 8, (0, 0, 0), 1.0, 2.0, 1.0, 0.0)
+    cg = g.c_struct()
+    nul = ctypes.c_void_p(0)
+    # null arrays
+    assert lib.vof_reconstruct(ctypes.byref(cg), nul, nul, nul, nul, nul) == P.VOF_EINVAL
+    assert lib.vof_advect_sweep_x(ctypes.byref(cg), nul, nul, nul, nul, nul, 0.1, nul, nul, nul, nul,
+                                  nul) == P.VOF_EINVAL
+    # aliasing input and output
+    fake = ctypes.c_void_p(1 << 40)
+    assert lib.vof_advect_sweep_y(ctypes.byref(cg), fake, nul, fake, nul, ctypes.c_void_p(1 << 41), 0.1, nul, nul,
+                                  nul, nul, nul) == P.VOF_EINVAL
+    # bad grid
+    bad = P.Grid(0, 8, 8).c_struct()
+    assert lib.vof_step_workspace_bytes(ctypes.byref(bad)) == 0
+    bad2 = P.Grid(8, 8, 8, (0, 2, 0)).c_struct()
+    assert lib.vof_reconstruct(ctypes.byref(bad2), fake, fake, fake, fake, nul) == P.VOF_EINVAL
+    # negative dt, misaligned workspace
+    assert lib.vof_step(ctypes.byref(cg), fake, ctypes.c_void_p(2 << 40), fake, fake, fake, -1.0, 0, nul, 0.0, nul,
+                        ctypes.c_void_p(3 << 40), 1 << 30, nul) == P.VOF_EINVAL
+    assert lib.vof_step(ctypes.byref(cg), fake, ctypes.c_void_p(2 << 40), fake, fake, fake, 0.1, 0, nul, 0.0, nul,
+                        ctypes.c_void_p((3 << 40) + 8), 1 << 30, nul) == P.VOF_EINVAL
+    # workspace too small
+    assert lib.vof_step(ctypes.byref(cg), fake, ctypes.c_void_p(2 << 40), fake, fake, fake, 0.1, 0, nul, 0.0, nul,
+                        ctypes.c_void_p(3 << 40), 16, nul) == P.VOF_EINVAL
+    assert lib.vof_status_string(P.VOF_ECFL).decode() == "face CFL number above 1"
+
+
+def test_workspace_size_scales(lib):
+    import paper_2001_03477_gb300 as P
+    a = P.vof_step_workspace_bytes(P.Grid(32, 32, 32))
+    b = P.vof_step_workspace_bytes(P.Grid(64, 64, 64))
+    assert a >= 32 ** 3 * 25 and b >= 64 ** 3 * 25 and b > 7 * a
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    import torch
+    import paper_2001_03477_gb300 as P
+    g = P.Grid(4, 4, 4)
+    c = torch.zeros(4, 4, 4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        P.vof_reconstruct(g, c, c, c, c)

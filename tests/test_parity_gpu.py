@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU
+oracle, element by element on the same seeded inputs.
+
+Tolerances (FP64 form): volume fractions 1e-12 absolute per cell,
+temperature 1e-11 relative per cell, totals 1e-13 relative.  Discrete
+results (mixed-cell flags, MYC normals, which are built from the same
+separately rounded operations on both sides) must be bit-identical.
+Sizes span several CTA tiles with ragged tails in every direction, both
+boundary conditions, a grid smaller than one tile, and the full 256^3
+bubble-growth workload the benchmark times.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_03477_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C_TOL = 1e-12
+T_TOL = 1e-11
+SUM_TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_03477_gb300 import build
+    build.build()
+    import paper_2001_03477_gb300 as P
+    return P
+
+
+def dev(a, dtype=None):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype=dtype or torch.float64)
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def ogrid(g):
+    return O.Grid(g.nx, g.ny, g.nz, g.bc, g.h, g.Cp_l, g.Cp_g, g.T_sat, g.eps_mixed)
+
+
+def case(name):
+    """(Grid, c, e, (u, v, w), dt, dd)"""
+    import paper_2001_03477_gb300 as P
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    if name == "sphere32":
+        wl = W.translating_sphere(n=32, nsub=16)
+        g = P.Grid(32, 32, 32, wl.bc, wl.h, wl.Cp_l, wl.Cp_g, wl.T_sat)
+        # T = 1 in the liquid, 0 in the gas, plus a smooth perturbation so
+        # that WENO5 works on non-constant data
+        zc = (np.arange(32) + 0.5) * wl.h
+        Z, Y, X = np.meshgrid(zc, zc, zc, indexing="ij")
+        T = 1.0 + 0.2 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+        e = (wl.Cp_l * wl.c + wl.Cp_g * (1 - wl.c)) * T
+        return g, wl.c, e, (wl.u, wl.v, wl.w), wl.dt, wl.dd_uniform
+    if name == "deform_ragged":
+        nx, ny, nz = 37, 29, 21
+        h = 1.0 / 32
+        g = P.Grid(nx, ny, nz, (1, 1, 1), h, 1000.0, 1.0, 1.0)
+        c = W.ellipsoid_fractions((nz, ny, nx), h, (0.55, 0.45, 0.33), (0.3, 0.22, 0.15),
+                                  rot=np.linalg.qr(rng.normal(size=(3, 3)))[0], nsub=12)
+        u, v, w = W.deformation_faces((nz, ny, nx), h, 0.4)
+        T = 1.0 + 0.1 * rng.random((nz, ny, nx))
+        e = (1000.0 * c + (1 - c)) * T
+        return g, c, e, (u, v, w), 0.2 * h / 2.0, -0.02
+    if name == "tiny_periodic":
+        nx, ny, nz = 5, 3, 2
+        g = P.Grid(nx, ny, nz, (0, 0, 0), 0.2, 3.0, 1.0, 0.5)
+        c = rng.random((nz, ny, nx))
+        c[c < 0.2] = 0.0
+        c[c > 0.8] = 1.0
+        u = rng.uniform(-1, 1, (nz, ny, nx + 1))
+        v = rng.uniform(-1, 1, (nz, ny + 1, nx))
+        w = rng.uniform(-1, 1, (nz + 1, ny, nx))
+        T = 0.5 + rng.random((nz, ny, nx))
+        e = (3.0 * c + (1 - c)) * T
+        return g, c, e, (u, v, w), 0.05, 0.03
+    raise KeyError(name)
+
+
+CASES = ["sphere32", "deform_ragged", "tiny_periodic"]
+
+
+def temperature(g, c, e):
+    return e / (g.Cp_l * c + g.Cp_g * (1.0 - c))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_reconstruct(P, name):
+    import torch
+    g, c, e, _, _, _ = case(name)
+    N = g.cells
+    cd = dev(c)
+    m = torch.empty((3,) + g.shape, dtype=torch.float64, device="cuda")
+    al = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    mx = torch.empty(g.shape, dtype=torch.uint8, device="cuda")
+    P.vof_reconstruct(g, cd, m, al, mx)
+    mo, alo, mxo = O.reconstruct(ogrid(g), c)
+    assert np.array_equal(host(mx), mxo)
+    assert np.array_equal(host(m), mo)
+    alg = host(al)
+    for k, j, i in np.argwhere(mxo):
+        mm = mo[:, k, j, i]
+        assert abs(O.volume(mm, alg[k, j, i]) - c[k, j, i]) < 1e-14
+        if O.plane_area(mm, alo[k, j, i]) > 1e-3:
+            assert abs(alg[k, j, i] - alo[k, j, i]) < 1e-12
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sweep(P, name, axis):
+    import torch
+    g, c, e, vel, dt, _ = case(name)
+    og = ogrid(g)
+    cc, th = O.frozen(og, c, e)
+    co, eo, clip, Fo, Go = O.sweep(og, axis, c, e, vel[axis], dt, cc, th, want_flux=True)
+    cd, ed, uf = dev(c), dev(e), dev(vel[axis])
+    c2 = torch.empty_like(cd); e2 = torch.empty_like(ed)
+    state = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+    theta = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    flux = torch.zeros(g.face_shape(axis), dtype=torch.float64, device="cuda")
+    diag = torch.zeros(1, dtype=torch.float64, device="cuda")
+    P.SWEEPS[axis](g, cd, ed, c2, e2, uf, dt, state, theta, flux, diag)
+    cg, eg = host(c2), host(e2)
+    assert np.abs(cg - co).max() <= C_TOL
+    To, Tg = temperature(g, co, eo), temperature(g, cg, eg)
+    assert (np.abs(Tg - To) / np.maximum(np.abs(To), 1e-300)).max() <= T_TOL
+    Fg = host(flux)
+    # periodic axes: face n is a copy of face 0 on both sides
+    assert np.abs(Fg - Fo).max() <= C_TOL
+    assert abs(host(diag)[0] - clip) <= C_TOL
+    # state marks exactly the cells whose c or e changed, with their cc/Theta
+    st = host(state)
+    changed = (cg != c) | (eg != e)
+    assert np.array_equal(st & 1, changed.astype(np.uint8))
+    assert np.array_equal((st >> 1) & 1 == 1, (cc == 1) & changed)
+    thg = host(theta)
+    assert np.array_equal(thg[changed], th[changed])
+
+    # unfused: VOF-only sweep + consistent energy update == fused, bitwise
+    c3 = torch.empty_like(cd); e3 = torch.empty_like(ed)
+    state2 = torch.zeros_like(state); theta2 = torch.zeros_like(theta)
+    flux2 = torch.zeros_like(flux)
+    P.SWEEPS[axis](g, cd, None, c3, None, uf, dt, state2, theta2, flux2, None)
+    P.energy_advect_consistent(g, axis, cd, c3, ed, e3, flux2, uf, dt, state2, theta2)
+    assert torch.equal(c3, c2) and torch.equal(e3, e2)
+    assert torch.equal(flux2, flux) and torch.equal(state2, state) and torch.equal(theta2, theta)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_shift(P, name):
+    import torch
+    g, c, e, _, _, dd = case(name)
+    og = ogrid(g)
+    for ddv, ddarr in ((dd, None), (0.0, np.random.default_rng(7).uniform(-0.05, 0.05, g.shape))):
+        co, eo, dg = O.phase_shift(og, c, e, dd=ddarr, dd_uniform=ddv)
+        cd, ed = dev(c), dev(e)
+        c2 = torch.empty_like(cd); e2 = torch.empty_like(ed)
+        diag = torch.zeros(5, dtype=torch.float64, device="cuda")
+        P.vof_phase_change_shift(g, cd, ed, c2, e2, dev(ddarr) if ddarr is not None else None, ddv, None, diag)
+        cg, eg = host(c2), host(e2)
+        assert np.abs(cg - co).max() <= C_TOL
+        To, Tg = temperature(g, co, eo), temperature(g, cg, eg)
+        assert (np.abs(Tg - To) / np.abs(To)).max() <= T_TOL
+        d = host(diag)
+        assert abs(d[0] - dg[0]) <= 1e-11
+        assert abs(d[1] - dg[1]) <= 1e-11
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step(P, name):
+    import torch
+    g, c, e, (u, v, w), dt, dd = case(name)
+    og = ogrid(g)
+    st = P.Stepper(g)
+    cd, ed = dev(c), dev(e)
+    ud, vd, wd = dev(u), dev(v), dev(w)
+    co, eo = c, e
+    for s in range(2):
+        co, eo, so = O.step(og, co, eo, u, v, w, dt, s, dd_uniform=dd)
+        sg = host(st.step(cd, ed, ud, vd, wd, dt, s, dd_uniform=dd)).copy()
+        cg, eg = host(cd), host(ed)
+        assert np.abs(cg - co).max() <= C_TOL
+        To, Tg = temperature(g, co, eo), temperature(g, cg, eg)
+        assert (np.abs(Tg - To) / np.abs(To)).max() <= T_TOL
+        assert abs(sg[0] - so[0]) <= SUM_TOL * abs(so[0])
+        assert abs(sg[1] - so[1]) <= SUM_TOL * abs(so[1])
+        for k in (2, 3, 4, 5):
+            assert abs(sg[k] - so[k]) <= 1e-12 * max(1.0, abs(so[1]) if k == 5 else 1.0)
+
+
+def test_multi_step_totals_and_shape(P):
+    """Eight steps of the translating sphere: per-cell agreement stays at
+    round-off level and the totals agree to 1e-13."""
+    g, c, e, (u, v, w), dt, dd = case("sphere32")
+    og = ogrid(g)
+    co, eo, so = O.run(og, c, e, u, v, w, dt, 0, 8, dd_uniform=dd)
+    st = P.Stepper(g)
+    cd, ed = dev(c), dev(e)
+    ud, vd, wd = dev(u), dev(v), dev(w)
+    for s in range(8):
+        sg = st.step(cd, ed, ud, vd, wd, dt, s, dd_uniform=dd)
+    sg = host(sg)
+    cg, eg = host(cd), host(ed)
+    assert np.abs(cg - co).max() <= 1e-11
+    assert abs(sg[0] - so[0]) <= SUM_TOL * abs(so[0])
+    assert abs(sg[1] - so[1]) <= SUM_TOL * abs(so[1])
+
+
+def test_uniform_temperature_gpu(P):
+    """T = T_Gamma everywhere stays uniform through sweeps and shift with a
+    heat-capacity ratio of 3236 (Sec. 3.4.1)."""
+    import paper_2001_03477_gb300 as PP
+    n = 48
+    h = 1.0 / n
+    g = PP.Grid(n, n, n, (1, 1, 1), h, 3236.3, 1.0, 1.0)
+    c = W.sphere_fractions((n, n, n), h, (0.35, 0.35, 0.35), 0.15, nsub=12)
+    u, v, w = W.deformation_faces((n, n, n), h, 0.2)
+    e = 3236.3 * c + (1 - c)
+    st = P.Stepper(g)
+    cd, ed = dev(c), dev(e)
+    for s in range(6):
+        st.step(cd, ed, dev(u), dev(v), dev(w), 0.25 * h / 2, s, dd_uniform=-0.01)
+    cg, eg = host(cd), host(ed)
+    T = eg / (3236.3 * cg + (1 - cg))
+    assert np.abs(T - 1.0).max() < 1e-13
+
+
+def test_cfl_status(P):
+    import torch
+    import paper_2001_03477_gb300 as PP
+    g = PP.Grid(8, 8, 8, (0, 0, 0), 1.0, 2.0, 1.0, 0.0)
+    c = np.full((8, 8, 8), 0.5)
+    cd = dev(c)
+    out = torch.empty_like(cd)
+    uf = dev(np.full((8, 8, 9), 1.5))  # |a| = 1.5
+    PP.vof_get_device_status()  # clear
+    PP.vof_advect_sweep_x(g, cd, None, out, None, uf, 1.0)
+    assert PP.vof_get_device_status() == PP.VOF_ECFL
+    assert PP.vof_get_device_status() == PP.VOF_OK
+
+
+def test_full_size_bubble_step(P):
+    """The benchmark's workload (256^3 bubble growth, launch configuration
+    of the timed step): one full step element by element against the
+    oracle."""
+    wl = W.bubble_growth(n=256, nsub=8)
+    import paper_2001_03477_gb300 as PP
+    g = PP.Grid(256, 256, 256, wl.bc, wl.h, wl.Cp_l, wl.Cp_g, wl.T_sat)
+    og = ogrid(g)
+    co, eo, so = O.step(og, wl.c, wl.e, wl.u, wl.v, wl.w, wl.dt, 0, dd_uniform=wl.dd_uniform)
+    st = P.Stepper(g)
+    cd, ed = dev(wl.c), dev(wl.e)
+    sg = host(st.step(cd, ed, dev(wl.u), dev(wl.v), dev(wl.w), wl.dt, 0, dd_uniform=wl.dd_uniform))
+    cg, eg = host(cd), host(ed)
+    assert np.abs(cg - co).max() <= C_TOL
+    To, Tg = temperature(g, co, eo), temperature(g, cg, eg)
+    assert (np.abs(Tg - To) / np.abs(To)).max() <= T_TOL
+    assert abs(sg[0] - so[0]) <= SUM_TOL * abs(so[0])
+    assert abs(sg[1] - so[1]) <= SUM_TOL * abs(so[1])
