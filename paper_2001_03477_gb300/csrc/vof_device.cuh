@@ -23,7 +23,30 @@ struct GridDev {
   int bc[3];     // 0 periodic, 1 zero-gradient
   double lam;    // dt / h
   double Cp_l, Cp_g, T_sat, eps;
+  long long eps_bits;     // bit pattern of eps
+  long long one_m_eps;    // bit pattern of 1 - eps
 };
+
+// ---------------------------------------------------------------------------
+// Comparisons on the integer pipe.  On this part FP64 compares issue on the
+// FP64 unit (1/64 of the FP32 rate); the bit-pattern forms below give the
+// same answer as the IEEE comparison for every non-NaN operand (and the same
+// decision for the mixed-cell test with NaN), so decisions agree with the
+// oracle's double compares.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// a == b (IEEE: +0 == -0)
+__device__ __forceinline__ bool deq(double a, double b) {
+  unsigned long long x = (unsigned long long)dbits(a), y = (unsigned long long)dbits(b);
+  return x == y || ((x | y) << 1) == 0ull;
+}
+__device__ __forceinline__ bool dnz(double a) { return (((unsigned long long)dbits(a)) << 1) != 0ull; }
+__device__ __forceinline__ bool dgt0(double a) { return dbits(a) > 0; }
+__device__ __forceinline__ bool dlt0(double a) { return dbits(a) < 0 && dnz(a); }
+// a > 1.0
+__device__ __forceinline__ bool dgt1(double a) { return dbits(a) > 0x3FF0000000000000LL; }
+// a > 0.5
+__device__ __forceinline__ bool dgthalf(double a) { return dbits(a) > 0x3FE0000000000000LL; }
 
 __device__ __forceinline__ int map_idx(int i, int n, int bc) {
   if (bc == 0) {
@@ -38,6 +61,12 @@ __device__ __forceinline__ double heat_cap(double Cp_l, double Cp_g, double c) {
 }
 
 __device__ __forceinline__ bool is_mixed(double c, double eps) { return c > eps && c < 1.0 - eps; }
+// the same test on the integer pipe (eps >= 0)
+__device__ __forceinline__ bool is_mixed_b(double c, const GridDev& g) {
+  long long b = dbits(c);
+  return b > g.eps_bits && b < g.one_m_eps;
+}
+__device__ __forceinline__ bool is_full_b(double c, const GridDev& g) { return dbits(c) >= g.one_m_eps; }
 
 // ---------------------------------------------------------------------------
 // Volume below a plane in the unit cube (Scardovelli & Zaleski 2000)
@@ -186,16 +215,23 @@ __device__ __forceinline__ double alpha_low(double m1, double m2, double m3, dou
     }
   }
   a = a < lo ? lo : (a > hi ? hi : a);
-  // Newton polish on the branch polynomial (safeguarded to the bracket)
-  for (int it = 0; it < 2; ++it) {
-    double f = vol_low(m1, m2, m3, a) - c;
-    double d = dvol_low(m1, m2, m3, a);
-    if (!(d > 0.0)) break;
-    double an = a - f / d;
-    if (!(an >= lo && an <= hi)) break;
+  // polish: Newton on the monotone volume, kept inside a shrinking bracket
+  // (a bisection step whenever Newton would leave it); at most 8 steps
+  // and the best point seen is returned
+  double blo = lo, bhi = hi, best = a, bestf = 1e300;
+  for (int it = 0; it < 8; ++it) {
+    const double f = vol_low(m1, m2, m3, a) - c;
+    if (fabs(f) < bestf) { bestf = fabs(f); best = a; }
+    if (f == 0.0) break;
+    if (f < 0.0) blo = a; else bhi = a;
+    const double d = dvol_low(m1, m2, m3, a);
+    double an = (d > 0.0) ? a - f / d : a;
+    if (an == a) break;  // converged to the last bit
+    if (!(an >= blo && an <= bhi)) an = 0.5 * (blo + bhi);
+    if (an == a) break;
     a = an;
   }
-  return a;
+  return best;
 }
 
 // alpha with volume(m, alpha) = c for any m (mirror, normalise, invert,
@@ -210,6 +246,30 @@ __device__ __forceinline__ double plane_alpha(double m0, double m1, double m2, d
   double am;
   if (c <= 0.5) am = alpha_low(s0, s1, s2, c);
   else am = 1.0 - alpha_low(s0, s1, s2, 1.0 - c);
+  return am * r.l1 - r.sh;
+}
+
+// The same plane constant by bisection on the monotone volume, step for
+// step the plain algorithm (interval [0,1] of the mirrored normalised plane,
+// halving until the bracket is two adjacent doubles, then the end whose
+// volume is closer to c).  Used where alpha(c) is ill-conditioned (c within
+// 1e-3 of 0 or 1) and the plane is extrapolated into neighbouring cells,
+// which would amplify the last-bit differences of any other inversion.
+static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, double m2, double c) {
+  Mirror r = mirror_normalise(m0, m1, m2);
+  if (r.l1 == 0.0) return 0.0;
+  if (c <= 0.0) return 0.0 - r.sh;
+  if (c >= 1.0) return r.l1 - r.sh;
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = lo + 0.5 * (hi - lo);
+    if (!(mid > lo && mid < hi)) break;
+    if (vol_pos(r.mp[0], r.mp[1], r.mp[2], mid) < c) lo = mid;
+    else hi = mid;
+  }
+  double vl = fabs(vol_pos(r.mp[0], r.mp[1], r.mp[2], lo) - c);
+  double vh = fabs(vol_pos(r.mp[0], r.mp[1], r.mp[2], hi) - c);
+  double am = (vh < vl) ? hi : lo;
   return am * r.l1 - r.sh;
 }
 
@@ -315,21 +375,25 @@ __device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
 // WENO5 face value (Jiang-Shu weights, eps 1e-6), upwind-ordered stencil
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double weno5(double vm2, double vm1, double v0, double vp1, double vp2) {
-  if (vm2 == v0 && vm1 == v0 && vp1 == v0 && vp2 == v0) return v0;
+  if (deq(vm2, v0) && deq(vm1, v0) && deq(vp1, v0) && deq(vp2, v0)) return v0;
+  // Jiang-Shu weights alpha_k = d_k / (eps + beta_k)^2 written over a common
+  // denominator: T_f = sum d_k q_k prod_{j!=k} s_j / sum d_k prod_{j!=k} s_j,
+  // s_j = (eps + beta_j)^2, and the 1/6 of the q_k folded into the end --
+  // one division instead of four (the FP64 unit is the scarce resource).
   const double epsw = 1e-6;
-  double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
-  double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
-  double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
-  double d0 = vm2 - 2.0 * vm1 + v0, e0 = vm2 - 4.0 * vm1 + 3.0 * v0;
-  double d1 = vm1 - 2.0 * v0 + vp1, e1 = vm1 - vp1;
-  double d2 = v0 - 2.0 * vp1 + vp2, e2 = 3.0 * v0 - 4.0 * vp1 + vp2;
-  double b0 = (13.0 / 12.0) * d0 * d0 + 0.25 * e0 * e0;
-  double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
-  double b2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
-  double a0 = 0.1 / ((epsw + b0) * (epsw + b0));
-  double a1 = 0.6 / ((epsw + b1) * (epsw + b1));
-  double a2 = 0.3 / ((epsw + b2) * (epsw + b2));
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  const double q0 = fma(2.0, vm2, fma(-7.0, vm1, 11.0 * v0));
+  const double q1 = fma(-1.0, vm1, fma(5.0, v0, 2.0 * vp1));
+  const double q2 = fma(2.0, v0, fma(5.0, vp1, -vp2));
+  const double d0 = vm2 - 2.0 * vm1 + v0, e0 = fma(-4.0, vm1, vm2) + 3.0 * v0;
+  const double d1 = vm1 - 2.0 * v0 + vp1, e1 = vm1 - vp1;
+  const double d2 = v0 - 2.0 * vp1 + vp2, e2 = fma(3.0, v0, fma(-4.0, vp1, vp2));
+  const double b0 = fma(13.0 / 12.0 * d0, d0, 0.25 * e0 * e0);
+  const double b1 = fma(13.0 / 12.0 * d1, d1, 0.25 * e1 * e1);
+  const double b2 = fma(13.0 / 12.0 * d2, d2, 0.25 * e2 * e2);
+  const double s0 = (epsw + b0) * (epsw + b0), s1 = (epsw + b1) * (epsw + b1), s2 = (epsw + b2) * (epsw + b2);
+  const double w0 = 0.1 * (s1 * s2), w1 = 0.6 * (s0 * s2), w2 = 0.3 * (s0 * s1);
+  const double num = fma(w0, q0, fma(w1, q1, w2 * q2));
+  return num / (6.0 * (w0 + w1 + w2));
 }
 
 }  // namespace vofgb

@@ -86,10 +86,25 @@ def case(name):
         T = 0.5 + rng.random((nz, ny, nx))
         e = (3.0 * c + (1 - c)) * T
         return g, c, e, (u, v, w), 0.05, 0.03
+    if name == "multi_segment":
+        # several segments along every sweep axis, ragged in all three
+        nx, ny, nz = 300, 70, 130
+        h = 1.0 / 128
+        g = P.Grid(nx, ny, nz, (1, 0, 0), h, 4000.0, 1.2, 2.0)
+        c = W.ellipsoid_fractions((nz, ny, nx), h, (1.2, 0.27, 0.5), (0.9, 0.2, 0.35),
+                                  rot=np.linalg.qr(rng.normal(size=(3, 3)))[0], nsub=8)
+        u, v, w = W.deformation_faces((nz, ny, nx), h, 0.1)
+        zc = (np.arange(nz) + 0.5) * h
+        yc = (np.arange(ny) + 0.5) * h
+        xc = (np.arange(nx) + 0.5) * h
+        Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+        T = 2.0 + 0.3 * np.tanh((X - 1.1) / 0.05) * np.cos(3 * Y)  # uniform away from a layer
+        e = (4000.0 * c + 1.2 * (1 - c)) * T
+        return g, c, e, (u, v, w), 0.2 * h / 2.0, -0.015
     raise KeyError(name)
 
 
-CASES = ["sphere32", "deform_ragged", "tiny_periodic"]
+CASES = ["sphere32", "deform_ragged", "tiny_periodic", "multi_segment"]
 
 
 def temperature(g, c, e):
@@ -144,7 +159,7 @@ def test_sweep(P, name, axis):
     st = host(state)
     changed = (cg != c) | (eg != e)
     assert np.array_equal(st & 1, changed.astype(np.uint8))
-    assert np.array_equal((st >> 1) & 1 == 1, (cc == 1) & changed)
+    assert np.array_equal(((st >> 1) & 1) == 1, (cc == 1) & changed)
     thg = host(theta)
     assert np.array_equal(thg[changed], th[changed])
 
@@ -180,15 +195,17 @@ def test_shift(P, name):
 
 @pytest.mark.parametrize("name", CASES)
 def test_step(P, name):
+    """Full steps (sweep order xyz, then zyx) from the same input on both
+    sides: the second step starts from the oracle's first-step state."""
     import torch
     g, c, e, (u, v, w), dt, dd = case(name)
     og = ogrid(g)
     st = P.Stepper(g)
-    cd, ed = dev(c), dev(e)
     ud, vd, wd = dev(u), dev(v), dev(w)
-    co, eo = c, e
+    ci, ei = c, e
     for s in range(2):
-        co, eo, so = O.step(og, co, eo, u, v, w, dt, s, dd_uniform=dd)
+        co, eo, so = O.step(og, ci, ei, u, v, w, dt, s, dd_uniform=dd)
+        cd, ed = dev(ci), dev(ei)
         sg = host(st.step(cd, ed, ud, vd, wd, dt, s, dd_uniform=dd)).copy()
         cg, eg = host(cd), host(ed)
         assert np.abs(cg - co).max() <= C_TOL
@@ -196,13 +213,19 @@ def test_step(P, name):
         assert (np.abs(Tg - To) / np.abs(To)).max() <= T_TOL
         assert abs(sg[0] - so[0]) <= SUM_TOL * abs(so[0])
         assert abs(sg[1] - so[1]) <= SUM_TOL * abs(so[1])
+        # diagnostics (clipped volume, shift sums): sums of per-cell terms
+        # that agree to ~1e-16, so compared relative to their size
         for k in (2, 3, 4, 5):
-            assert abs(sg[k] - so[k]) <= 1e-12 * max(1.0, abs(so[1]) if k == 5 else 1.0)
+            assert abs(sg[k] - so[k]) <= 1e-12 * max(1.0, abs(so[k]))
+        ci, ei = co, eo
 
 
 def test_multi_step_totals_and_shape(P):
-    """Eight steps of the translating sphere: per-cell agreement stays at
-    round-off level and the totals agree to 1e-13."""
+    """Eight steps of the translating sphere, each side from its own previous
+    state.  Round-off differences can move a cell across the mixed threshold
+    eps = 1e-12 (mixed cells shift their plane, pure ones do not), which
+    changes that cell by about eps; per-cell agreement is therefore checked
+    at 10 eps after several steps, the totals at 1e-13."""
     g, c, e, (u, v, w), dt, dd = case("sphere32")
     og = ogrid(g)
     co, eo, so = O.run(og, c, e, u, v, w, dt, 0, 8, dd_uniform=dd)
