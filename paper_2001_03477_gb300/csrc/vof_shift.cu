@@ -21,7 +21,7 @@ __device__ __forceinline__ bool same_bits_dev(double a, double b) { return dbits
 
 template <int K>
 __device__ __forceinline__ void block_sums_sh(double (&v)[K], SumOut out, int block_lin) {
-  __shared__ double red[K][kShThreads / 32];
+  __shared__ double red[K][kShThreads / 32];  // up to 8 warps
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -36,20 +36,23 @@ __device__ __forceinline__ void block_sums_sh(double (&v)[K], SumOut out, int bl
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int w = 0; w < kShThreads / 32; ++w) s += red[k][w];
+      const int nw = (int)(blockDim.x * blockDim.y * blockDim.z) / 32;
+      for (int w = 0; w < nw; ++w) s += red[k][w];
       if (out.partials) out.partials[(size_t)block_lin * out.stride + k] = s;
       else if (out.diag) atomicAdd(out.diag + k, s);
     }
   }
 }
 
-// Shift kernel: a CTA owns a 32 x 8 column of cells and walks kShSegZ planes
+// Shift kernel: a CTA owns a 32 x kShTY column of cells and walks kShSegZ planes
 // along z.  Shared-memory rings hold c of planes z..z+2 (halo 2 in x and y)
 // and the plane data (m, alpha, |m|_2 dd) of the moving mixed cells of
 // planes z-1..z+1 (halo 1); each thread then settles its cell of plane z.
-constexpr int kShSegZ = 32;
-constexpr int kRX = kShBX + 4, kRY = 8 + 4;   // c plane with halo 2
-constexpr int kPX = kShBX + 2, kPY = 8 + 2;   // plane-data region with halo 1
+constexpr int kShSegZ = 8;    // short z segments and small CTAs: the FP64 work of
+constexpr int kShTY = 4;      // the interface is spread over many CTAs
+constexpr int kShT = 32 * kShTY;
+constexpr int kRX = kShBX + 4, kRY = kShTY + 4;   // c plane with halo 2
+constexpr int kPX = kShBX + 2, kPY = kShTY + 2;   // plane-data region with halo 1
 constexpr int kRP = kRX * kRY, kPP = kPX * kPY;
 
 struct ShiftSmem {
@@ -126,14 +129,14 @@ __device__ __noinline__ double extended_sweep(GridDev g, const double* pm, const
   return best;
 }
 
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(kShT, 4)
 k_shift(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
         double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, SumOut sums) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ShiftSmem& S = *reinterpret_cast<ShiftSmem*>(smem_raw);
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-  const int x0 = blockIdx.x * kShBX, y0 = blockIdx.y * 8;
+  const int x0 = blockIdx.x * kShBX, y0 = blockIdx.y * kShTY;
   const int z0 = blockIdx.z * kShSegZ, z1 = min(z0 + kShSegZ, nz);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool cell_ok = gx < nx && gy < ny;
@@ -141,7 +144,7 @@ k_shift(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 
   auto load_plane = [&](int z, int slot) {
     const int zz = map_idx(z, nz, g.bc[2]);
-    for (int q = tid; q < kRP; q += 256) {
+    for (int q = tid; q < kRP; q += kShT) {
       const int lx = q % kRX, ly = q / kRX;
       const int xx = map_idx(x0 + lx - 2, nx, g.bc[0]);
       const int yy = map_idx(y0 + ly - 2, ny, g.bc[1]);
@@ -153,7 +156,7 @@ k_shift(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
     const int sl = ((z % 3) + 3) % 3;
     const int sm1 = ((z - 1) % 3 + 3) % 3, sp1 = ((z + 1) % 3 + 3) % 3;
     int any = 0;
-    for (int q = tid; q < kPP; q += 256) {
+    for (int q = tid; q < kPP; q += kShT) {
       const int px = q % kPX, py = q / kPX;
       const int rq = (py + 1) * kRX + (px + 1);
       const double ct = S.c[sl][rq];
@@ -297,7 +300,7 @@ static dim3 sh_grid(const GridDev& g) {
 }
 
 static dim3 shm_grid(const GridDev& g) {
-  return dim3((g.n[0] + kShBX - 1) / kShBX, (g.n[1] + 7) / 8, (g.n[2] + kShSegZ - 1) / kShSegZ);
+  return dim3((g.n[0] + kShBX - 1) / kShBX, (g.n[1] + kShTY - 1) / kShTY, (g.n[2] + kShSegZ - 1) / kShSegZ);
 }
 
 int shift_blocks(const GridDev& g) {
@@ -316,7 +319,7 @@ cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_i
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
-  k_shift<<<shm_grid(g), dim3(kShBX, 8), smem, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sums);
+  k_shift<<<shm_grid(g), dim3(kShBX, kShTY), smem, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sums);
   cudaError_t err = cudaGetLastError();
   if (err == cudaSuccess && state)
     err = cudaMemsetAsync(state, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);

@@ -28,31 +28,6 @@ struct SweepTile<2> { static constexpr int BX = 32, BY = 1, BZ = 8; };
 
 constexpr int kThreads = 256;
 
-// block sum of up to 4 values into partials/diag
-template <int K>
-__device__ __forceinline__ void block_sums(double (&v)[K], SumOut out, int block_lin) {
-  __shared__ double red[K][kThreads / 32];
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) red[k][warp] = x;
-  }
-  __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += red[k][w];
-      if (out.partials) out.partials[(size_t)block_lin * out.stride + k] = s;
-      else if (out.diag) atomicAdd(out.diag + k, s);
-    }
-  }
-}
-
 __device__ __forceinline__ size_t face_index(int ax, int f, int i, int j, int k, int nx, int ny) {
   // f along ax; (i,j,k) cell coordinates for the other two axes
   if (ax == 0) return ((size_t)k * ny + j) * (nx + 1) + f;
@@ -61,16 +36,13 @@ __device__ __forceinline__ size_t face_index(int ax, int f, int i, int j, int k,
 }
 
 // ---------------------------------------------------------------------------
-// Marching sweeps.  A thread (sweeps along y and z) or a warp (sweep along x)
-// walks along the sweep axis through a segment of one grid line, holding a
-// window of 8 cells (c, e, T) in registers.  A cell is a no-op -- its c and e
-// come out bit-identical -- when the 7 cells around it along the axis have
-// the same (c, e) bits, c is exactly 0 or 1 and the cell has not changed
-// earlier in the step (then both donors are pure with the same c, F = c a,
-// both face temperatures are T, and (G - Theta a) vanishes exactly on both
-// faces).  No-op cells cost no FP64 work; face fluxes are evaluated only
-// where an adjacent cell is not a no-op; T = e / C_p(c) is divided only where
-// (c, e) differs from the previous cell of the line.
+// No-op cells.  A cell's c and e come out bit-identical when the 7 cells
+// around it along the sweep axis have the same (c, e) bits, c is exactly 0 or
+// 1 and the cell has not changed earlier in the step: both donors are then
+// pure with the same c, F = c a, both face temperatures equal T, and
+// (G - Theta a) vanishes exactly on both faces.  No-op cells cost no FP64
+// work; face fluxes are evaluated only next to non-no-op cells and
+// T = e / C_p(c) only where such a face needs it.
 // ---------------------------------------------------------------------------
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -111,9 +83,16 @@ __device__ __noinline__ double mixed_donor_flux(GridDev g, const double* __restr
   return dgt0(a) ? vol : -vol;
 }
 
-// energy flux of a face from its upwind-ordered temperature stencil (kept
-// out of line: it runs only on faces next to non-trivial cells)
-__device__ __noinline__ double energy_flux(const GridDev& g, double Fv, double a, double t0, double t1, double t2,
+// energy flux G = T_f (C_pl F + C_pg (a - F)) with T_f = WENO5 of the
+// upwind-ordered stencil (out of line: only faces next to non-no-op cells)
+__device__ __noinline__ double face_energy_flux(double Cp_l, double Cp_g, double Fv, double a, double t0, double t1,
+                                                double t2, double t3, double t4) {
+  const double Tf = weno5(t0, t1, t2, t3, t4);
+  return (Tf * Cp_l) * Fv + (Tf * Cp_g) * (a - Fv);
+}
+
+// energy flux of a face from its upwind-ordered temperature stencil
+__device__ __forceinline__ double energy_flux(const GridDev& g, double Fv, double a, double t0, double t1, double t2,
                                               double t3, double t4) {
   double Tf = weno5(t0, t1, t2, t3, t4);
   return (Tf * g.Cp_l) * Fv + (Tf * g.Cp_g) * (a - Fv);
@@ -121,7 +100,7 @@ __device__ __noinline__ double energy_flux(const GridDev& g, double Fv, double a
 
 // WY update of one cell from its two faces; returns the clipped volume
 template <bool ENERGY>
-__device__ __noinline__ double update_cell(const GridDev& g, size_t id, double c, double e, double T, uint8_t stv,
+__device__ __forceinline__ double update_cell(const GridDev& g, size_t id, double c, double e, double T, uint8_t stv,
                                               double Fl, double Gl, double al, double Fr, double Gr, double ar,
                                               double* __restrict__ c_out, double* __restrict__ e_out,
                                               uint8_t* __restrict__ state, double* __restrict__ theta) {
@@ -148,8 +127,9 @@ __device__ __noinline__ double update_cell(const GridDev& g, size_t id, double c
 
 template <int NV>
 __device__ __forceinline__ void block_reduce_out(double (&v)[NV], SumOut out) {
-  __shared__ double red[NV][8];
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  __shared__ double red[NV][8];  // up to 8 warps per CTA (256 threads)
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nwarps = (int)(blockDim.x * blockDim.y * blockDim.z) >> 5;
   const int lane = tid & 31, warp = tid >> 5;
   const int block_lin = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 #pragma unroll
@@ -169,259 +149,211 @@ __device__ __forceinline__ void block_reduce_out(double (&v)[NV], SumOut out) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += red[k][w];
+      for (int w = 0; w < nwarps; ++w) s += red[k][w];
       if (out.partials) out.partials[(size_t)block_lin * out.stride + k] = s;
       else if (out.diag && dnz(s)) atomicAdd(out.diag + k, s);
     }
   }
 }
 
-constexpr int kSegCol = 32;   // cells per thread along y / z
-constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
+// Tile sweep: one thread per cell.  A CTA stages c and e of its tile plus a
+// halo of 4 cells along the sweep axis (no transverse halo: the 27-cell MYC
+// stencil of a mixed donor is read from global memory, which only the few
+// interface faces need).  Phases, separated by barriers:
+//   1. no-op flags of the tile cells and of the first halo cell on each side
+//      (7-cell window along the axis has equal (c, e) bits, c is 0 or 1, the
+//      cell has not changed earlier in the step);
+//   2. T = e / C_p(c) only for cells within 3 of a non-no-op cell;
+//   3. face fluxes only for faces next to a non-no-op cell;
+//   4. cell updates; no-op cells are copied.
+template <int AX>
+struct TileShape;
+template <>
+struct TileShape<0> { static constexpr int X = 64, Y = 4, Z = 1; };
+template <>
+struct TileShape<1> { static constexpr int X = 16, Y = 16, Z = 1; };
+template <>
+struct TileShape<2> { static constexpr int X = 16, Y = 1, Z = 16; };
 
-// Sweep along y (AX = 1) or z (AX = 2): block = 32 lanes along x x 8 warps
-// along the remaining axis; each thread walks kSegCol cells of its line.
-// While face k is processed the window holds c, e of cells k-1..k+3
-// (wc[0..4]) and T of cells k-3..k+3 (wT[0..6]).
+constexpr int kHalo = 4;
+static_assert(TileShape<0>::X * TileShape<0>::Y * TileShape<0>::Z == 256, "256 threads per sweep CTA");
+static_assert(TileShape<1>::X * TileShape<1>::Y * TileShape<1>::Z == 256, "256 threads per sweep CTA");
+static_assert(TileShape<2>::X * TileShape<2>::Y * TileShape<2>::Z == 256, "256 threads per sweep CTA");
+
 template <int AX, bool ENERGY>
-__global__ void __launch_bounds__(256, 2)
-k_sweep_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-            double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
-            double* __restrict__ theta, double* __restrict__ flux_out, SumOut sums, int* __restrict__ status) {
+__global__ void __launch_bounds__(256, 3)
+k_sweep_tile(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+             double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
+             double* __restrict__ theta, double* __restrict__ flux_out, SumOut sums, int* __restrict__ status) {
+  constexpr int TX = TileShape<AX>::X, TY = TileShape<AX>::Y, TZ = TileShape<AX>::Z;
+  constexpr int TA = AX == 0 ? TX : (AX == 1 ? TY : TZ);  // tile length along the axis
+  constexpr int TT = (TX * TY * TZ) / TA;                  // transverse cells of the tile
+  constexpr int HL = TA + 2 * kHalo;                       // staged length along the axis
+  constexpr int NH = HL * TT;
+  constexpr int NFL = TA + 1;                              // faces per line
+  constexpr int NF = NFL * TT;
+  constexpr int FL = TA + 2;                               // flagged positions per line: -1 .. TA
+  __shared__ double sc[NH];
+  __shared__ double se[ENERGY ? NH : 1];
+  __shared__ double sT[ENERGY ? NH : 1];
+  __shared__ uint8_t snoop[FL * TT];
+  __shared__ double sF[NF];
+  __shared__ double sG[ENERGY ? NF : 1];
+  __shared__ double sA[NF];
+
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int n_ax = AX == 1 ? ny : nz;
-  const int n_t = AX == 1 ? nz : ny;
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int t = blockIdx.y * 8 + threadIdx.y;
-  const int s0 = blockIdx.z * kSegCol;
-  const int s1 = min(s0 + kSegCol, n_ax);
-  const bool act = (x < nx) && (t < n_t);
+  const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  double clip = 0.0;
-  if (act) {
-    const size_t stride = AX == 1 ? (size_t)nx : (size_t)nx * ny;
-    const size_t cbase = AX == 1 ? (size_t)t * ny * nx + x : (size_t)t * nx + x;
-    const size_t fstride = stride;
-    const size_t fbase = AX == 1 ? (size_t)t * (ny + 1) * nx + x : (size_t)t * nx + x;
-    double wc[5], we[5], wT[7];
-    int run = 0;
-    double pc = 0.0, pe = 0.0, pT = 0.0;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int a0 = AX == 0 ? x0 : (AX == 1 ? y0 : z0);
+  const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+  // transverse line index t in [0, TT) <-> (tile coords of the two other axes)
+  auto line_coords = [&](int t, int pos, int& gx, int& gy, int& gz) {
+    if (AX == 0) { gx = x0 + pos; gy = y0 + t % TY; gz = z0 + t / TY; }
+    else if (AX == 1) { gx = x0 + t % TX; gy = y0 + pos; gz = z0 + t / TX; }
+    else { gx = x0 + t % TX; gy = y0 + t / TX; gz = z0 + pos; }
+  };
+  auto line_ok = [&](int t) {
+    int gx, gy, gz;
+    line_coords(t, 0, gx, gy, gz);
+    return (AX == 0 || gx < nx) && (AX == 1 || gy < ny) && (AX == 2 || gz < nz);
+  };
+  // staged index of (line t, position p in [-kHalo, TA + kHalo)) -- lines are
+  // contiguous along the axis for AX = 0 and interleaved otherwise so that a
+  // warp's loads stay coalesced along x
+  auto hidx = [&](int t, int p) { return AX == 0 ? t * HL + (p + kHalo) : (p + kHalo) * TT + t; };
+
+  // 1. stage c, e
+  for (int q = tid; q < NH; q += 256) {
+    int t, p;
+    if (AX == 0) { t = q / HL; p = q % HL - kHalo; }
+    else { p = q / TT - kHalo; t = q % TT; }
+    int gx, gy, gz;
+    line_coords(t, p, gx, gy, gz);
+    const int xx = map_idx(gx, nx, g.bc[0]), yy = map_idx(gy, ny, g.bc[1]), zz = map_idx(gz, nz, g.bc[2]);
+    const size_t id = ((size_t)zz * ny + yy) * nx + xx;
+    sc[q] = __ldg(c_in + id);
+    if (ENERGY) se[q] = __ldg(e_in + id);
+  }
+  __syncthreads();
+  // 2. no-op flags of positions -1 .. TA
+  for (int q = tid; q < FL * TT; q += 256) {
+    const int t = q / FL, p = q % FL - 1;
+    int gx, gy, gz;
+    line_coords(t, p, gx, gy, gz);
+    const int ga = a0 + p;
+    bool noop;
+    if (!line_ok(t) || (bca != 0 && (ga < 0 || ga >= n_ax))) {
+      noop = true;  // not a cell of the grid: needs no face
+    } else {
+      const int h0 = hidx(t, p);
+      const double c0 = sc[h0];
+      noop = is01(c0);
+      if (noop) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const size_t id = cbase + stride * map_idx(s0 - 4 + i, n_ax, bca);
-      const double cv = __ldg(c_in + id);
-      const double ev = ENERGY ? __ldg(e_in + id) : 0.0;
-      const bool same = i > 0 && same_bits(cv, pc) && (!ENERGY || same_bits(ev, pe));
-      const double Tv = ENERGY ? (same ? pT : ev / heat_cap(g.Cp_l, g.Cp_g, cv)) : 0.0;
-      if (i >= 3) { wc[i - 3] = cv; we[i - 3] = ev; }
-      if (i >= 1) wT[i - 1] = Tv;
-      run = same ? run + 1 : 1;
-      pc = cv; pe = ev; pT = Tv;
-    }
-    double Fp = 0.0, Gp = 0.0, ap = 0.0;
-    bool noop_prev = true;
-    uint8_t st_prev = 0;
-    double nc, ne = 0.0;
-    {
-      const size_t id = cbase + stride * map_idx(s0 + 4, n_ax, bca);
-      nc = __ldg(c_in + id);
-      if (ENERGY) ne = __ldg(e_in + id);
-    }
-    double nu = __ldg(uf + fbase + fstride * ((bca == 0 && s0 == n_ax) ? 0 : s0));
-    uint8_t nst = (state && s0 < s1) ? state[cbase + stride * s0] : (uint8_t)0;
-    for (int k = s0; k <= s1; ++k) {
-      const bool inner = k < s1;
-      const double a = nu * g.lam;
-      const uint8_t st_cur = nst;
-      const double tc = nc, te = ne;
-      if (inner) {
-        const size_t id = cbase + stride * map_idx(k + 5, n_ax, bca);
-        nc = __ldg(c_in + id);
-        if (ENERGY) ne = __ldg(e_in + id);
-        const int f1 = k + 1;
-        nu = __ldg(uf + fbase + fstride * ((bca == 0 && f1 == n_ax) ? 0 : f1));
-        nst = (state && k + 1 < s1) ? state[cbase + stride * (k + 1)] : (uint8_t)0;
+        for (int d = -3; d <= 3; ++d) {
+          const int hd = hidx(t, p + d);
+          noop = noop && same_bits(sc[hd], c0) && (!ENERGY || same_bits(se[hd], se[h0]));
+        }
       }
-      // cell k is a no-op when cells k-3..k+3 agree, c_k is 0 or 1 and the
-      // cell is still clean
-      const bool noop_cur = inner && run >= 7 && is01(wc[1]) && !(st_cur & 1);
-      const bool need = flux_out || (k > s0 && !noop_prev) || (inner && !noop_cur);
-      double F = 0.0, G = 0.0;
-      if (need && dnz(a)) {
+      if (noop && state) {
+        const int xx = map_idx(gx, nx, g.bc[0]), yy = map_idx(gy, ny, g.bc[1]), zz = map_idx(gz, nz, g.bc[2]);
+        noop = !(state[((size_t)zz * ny + yy) * nx + xx] & 1);
+      }
+    }
+    snoop[q] = noop ? 1 : 0;
+  }
+  __syncthreads();
+  // 3. T where some cell within 3 positions is not a no-op
+  if (ENERGY) {
+    for (int q = tid; q < NH; q += 256) {
+      int t, p;
+      if (AX == 0) { t = q / HL; p = q % HL - kHalo; }
+      else { p = q / TT - kHalo; t = q % TT; }
+      bool need = false;
+#pragma unroll
+      for (int d = -3; d <= 3; ++d) {
+        const int pp = p + d;
+        if (pp >= -1 && pp <= TA) need = need || !snoop[t * FL + pp + 1];
+      }
+      if (need) sT[q] = se[q] / heat_cap(g.Cp_l, g.Cp_g, sc[q]);
+    }
+  }
+  __syncthreads();
+  // 4. faces f = 0..TA of each line (face f between positions f-1 and f)
+  for (int q = tid; q < NF; q += 256) {
+    const int t = q / NFL, f = q % NFL;
+    double Fv = 0.0, Gv = 0.0, a = 0.0;
+    const int gfa = a0 + f;
+    const bool need = line_ok(t) && gfa <= n_ax && (flux_out || !snoop[t * FL + f] || !snoop[t * FL + f + 1]);
+    if (need) {
+      int gx, gy, gz;
+      line_coords(t, f, gx, gy, gz);
+      const int fr = (bca == 0 && gfa == n_ax) ? 0 : gfa;
+      size_t fid;
+      if (AX == 0) fid = ((size_t)gz * ny + gy) * (nx + 1) + fr;
+      else if (AX == 1) fid = ((size_t)gz * (ny + 1) + fr) * nx + gx;
+      else fid = ((size_t)fr * ny + gy) * nx + gx;
+      a = __ldg(uf + fid) * g.lam;
+      if (dnz(a)) {
         const bool pos = dgt0(a);
-        const double cd = pos ? wc[0] : wc[1];
+        const int pd = pos ? f - 1 : f;  // donor position
+        const double cd = sc[hidx(t, pd)];
         if (is_mixed_b(cd, g)) {
-          const int ds = map_idx(pos ? k - 1 : k, n_ax, bca);
-          F = mixed_donor_flux(g, c_in, AX, x, AX == 1 ? ds : t, AX == 2 ? ds : t, cd, a, status);
+          int dx, dy, dz;
+          line_coords(t, pd, dx, dy, dz);
+          Fv = mixed_donor_flux(g, c_in, AX, map_idx(dx, nx, g.bc[0]), map_idx(dy, ny, g.bc[1]),
+                                map_idx(dz, nz, g.bc[2]), cd, a, status);
         } else {
-          F = cd * a;
+          Fv = cd * a;
         }
         if (ENERGY) {
-          G = pos ? energy_flux(g, F, a, wT[0], wT[1], wT[2], wT[3], wT[4])
-                  : energy_flux(g, F, a, wT[5], wT[4], wT[3], wT[2], wT[1]);
+          double v[5];
+#pragma unroll
+          for (int r = -2; r <= 2; ++r) v[r + 2] = sT[hidx(t, pd + (pos ? r : -r))];
+          Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, v[0], v[1], v[2], v[3], v[4]);
         }
       }
-      if (flux_out && (inner || k == n_ax)) flux_out[fbase + fstride * k] = F;
-      if (k > s0) {
-        const size_t id = cbase + stride * (k - 1);
-        if (noop_prev) {
-          c_out[id] = wc[0];
-          if (ENERGY) e_out[id] = we[0];
-        } else {
-          clip += update_cell<ENERGY>(g, id, wc[0], we[0], wT[2], st_prev, Fp, Gp, ap, F, G, a, c_out, e_out, state,
-                                      theta);
-        }
-      }
-      Fp = F; Gp = G; ap = a;
-      noop_prev = noop_cur;
-      st_prev = st_cur;
-      if (inner) {
-        // shift the window and append cell k + 4
-        const bool same = same_bits(tc, wc[4]) && (!ENERGY || same_bits(te, we[4]));
-        const double tT = ENERGY ? (same ? wT[6] : te / heat_cap(g.Cp_l, g.Cp_g, tc)) : 0.0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { wc[i] = wc[i + 1]; we[i] = we[i + 1]; }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) wT[i] = wT[i + 1];
-        wc[4] = tc; we[4] = te; wT[6] = tT;
-        run = same ? run + 1 : 1;
+      if (flux_out && (f < TA || gfa == n_ax)) {
+        size_t fo;
+        if (AX == 0) fo = ((size_t)gz * ny + gy) * (nx + 1) + gfa;
+        else if (AX == 1) fo = ((size_t)gz * (ny + 1) + gfa) * nx + gx;
+        else fo = ((size_t)gfa * ny + gy) * nx + gx;
+        flux_out[fo] = Fv;
       }
     }
+    sF[q] = Fv;
+    sA[q] = a;
+    if (ENERGY) sG[q] = Gv;
   }
-  double v[1] = {clip};
-  block_reduce_out<1>(v, sums);
-}
-
-// value at lane + d (d in [-4, 4]) of the concatenated chunks P | C | N
-__device__ __forceinline__ double lane_get(double vP, double vC, double vN, int lane, int d) {
-  const int idx = lane + d;
-  const int src = idx & 31;
-  const double a = __shfl_sync(kFull, vP, src);
-  const double b = __shfl_sync(kFull, vC, src);
-  const double c = __shfl_sync(kFull, vN, src);
-  return idx < 0 ? a : (idx < 32 ? b : c);
-}
-
-// Sweep along x: each warp walks a row segment of kSegRow cells in chunks of
-// 32 (lane = cell), neighbours across lanes by shuffles and ballot masks.
-template <bool ENERGY>
-__global__ void __launch_bounds__(256, 2)
-k_sweep_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-            double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
-            double* __restrict__ theta, double* __restrict__ flux_out, SumOut sums, int* __restrict__ status) {
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int lane = threadIdx.x;
-  const int row = blockIdx.y * 8 + threadIdx.y;  // row = z * ny + y
-  const int x0 = blockIdx.x * kSegRow;
-  const int x1 = min(x0 + kSegRow, nx);
-  const bool rowok = row < ny * nz;
-  const int ry = rowok ? row % ny : 0, rz = rowok ? row / ny : 0;
-  const size_t rbase = ((size_t)rz * ny + ry) * nx;
-  const size_t fbase = ((size_t)rz * ny + ry) * (nx + 1);
-  const int bcx = g.bc[0];
+  __syncthreads();
+  // 5. cells
   double clip = 0.0;
-  if (rowok) {
-    auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
-    auto lde = [&](int X) { return ENERGY ? __ldg(e_in + rbase + map_idx(X, nx, bcx)) : 0.0; };
-    auto ldst = [&](int X) -> uint8_t { return (state && X >= x0 && X < x1) ? state[rbase + X] : (uint8_t)0; };
-    // chunks: P = cells base-32.., C = base.., N = base+32..; start with C = chunk -1
-    int base = x0 - 32;
-    double cP = ldc(base - 32 + lane), eP = lde(base - 32 + lane);
-    double cC = ldc(base + lane), eC = lde(base + lane);
-    double cN = ldc(base + 32 + lane), eN = lde(base + 32 + lane);
-    uint8_t sC = ldst(base + lane), sN = ldst(base + 32 + lane);
-    auto eqmask = [&](double cprev_last, double eprev_last, double cc, double ee) -> unsigned {
-      double cl = __shfl_up_sync(kFull, cc, 1), el = __shfl_up_sync(kFull, ee, 1);
-      if (lane == 0) { cl = cprev_last; el = eprev_last; }
-      return __ballot_sync(kFull, same_bits(cc, cl) && (!ENERGY || same_bits(ee, el)));
-    };
-    unsigned eqP = eqmask(cP, eP, cP, eP);  // lane-0 bit of the first chunk is never used
-    unsigned eqC = eqmask(__shfl_sync(kFull, cP, 31), __shfl_sync(kFull, eP, 31), cC, eC);
-    unsigned eqN = eqmask(__shfl_sync(kFull, cC, 31), __shfl_sync(kFull, eC, 31), cN, eN);
-    // carried right face of the previous chunk's lane 31
-    double Fc = 0.0, Gc = 0.0, ac = 0.0;
-    for (; base < x1; base += 32) {
-      // prefetch chunk N+1
-      const int bn = base + 64;
-      const double cNN = ldc(bn + lane), eNN = lde(bn + lane);
-      const uint8_t sNN = ldst(bn + lane);
-      const int f = base + lane + 1;  // right face of this lane's cell
-      const bool fok = f >= x0 && f <= x1;
-      const double u = fok ? __ldg(uf + fbase + ((bcx == 0 && f == nx) ? 0 : f)) : 0.0;
-      const double a = u * g.lam;
-      const bool cell_ok = base + lane >= x0 && base + lane < x1;
-      // no-op masks: uniform over [l-3, l+3] needs eq bits at l-2..l+3
-      const unsigned long long M1 = ((unsigned long long)eqC << 32) | eqP;
-      const unsigned long long M2 = ((unsigned long long)eqN << 32) | eqC;
-      const bool uni = lane >= 2 ? (((M2 >> (lane - 2)) & 0x3Full) == 0x3Full)
-                                 : (((M1 >> (32 + lane - 2)) & 0x3Full) == 0x3Full);
-      const bool noopC = uni && is01(cC) && !(sC & 1);
-      const bool uniN0 = ((M2 >> 30) & 0x3Full) == 0x3Full;
-      const double cN0 = __shfl_sync(kFull, cN, 0);
-      const uint8_t sN0 = (uint8_t)__shfl_sync(kFull, (int)sN, 0);
-      const bool noopN0 = uniN0 && is01(cN0) && !(sN0 & 1);
-      const int noop_next = __shfl_down_sync(kFull, (int)noopC, 1);  // every lane takes part
-      const bool noopR = lane < 31 ? (bool)noop_next : noopN0;
-      // right face needed by this cell (inside the segment) or the next one
-      const bool next_ok = f < x1;
-      const bool need = fok && (flux_out || (cell_ok && !noopC) || (next_ok && !noopR));
-      double F = 0.0, G = 0.0;
-      const unsigned needm = __ballot_sync(kFull, need && dnz(a));
-      if (needm) {
-        double TP = 0.0, TC = 0.0, TN = 0.0;
-        if (ENERGY) {
-          TP = eP / heat_cap(g.Cp_l, g.Cp_g, cP);
-          TC = eC / heat_cap(g.Cp_l, g.Cp_g, cC);
-          TN = eN / heat_cap(g.Cp_l, g.Cp_g, cN);
-        }
-        const double cR = lane_get(cP, cC, cN, lane, 1);
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
-        const bool pos = dgt0(a);
-        if (ENERGY) {
-          const double Tm2 = lane_get(TP, TC, TN, lane, -2), Tm1 = lane_get(TP, TC, TN, lane, -1);
-          const double T1 = lane_get(TP, TC, TN, lane, 1), T2 = lane_get(TP, TC, TN, lane, 2);
-          const double T3 = lane_get(TP, TC, TN, lane, 3);
-          if (pos) { t0 = Tm2; t1 = Tm1; t2 = TC; t3 = T1; t4 = T2; }
-          else { t0 = T3; t1 = T2; t2 = T1; t3 = TC; t4 = Tm1; }
-        }
-        if ((needm >> lane) & 1u) {
-          const double cd = pos ? cC : cR;
-          if (is_mixed_b(cd, g)) {
-            const int dx = pos ? base + lane : base + lane + 1;
-            F = mixed_donor_flux(g, c_in, 0, map_idx(dx, nx, bcx), ry, rz, cd, a, status);
-          } else {
-            F = cd * a;
-          }
-          if (ENERGY) G = energy_flux(g, F, a, t0, t1, t2, t3, t4);
-        }
+  {
+    const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    if (gx < nx && gy < ny && gz < nz) {
+      const int p = AX == 0 ? lx : (AX == 1 ? ly : lz);
+      const int t = AX == 0 ? ly + TY * lz : (AX == 1 ? lx + TX * lz : lx + TX * ly);
+      const size_t id = ((size_t)gz * ny + gy) * nx + gx;
+      const int h = hidx(t, p);
+      const double c = sc[h];
+      const double e = ENERGY ? se[h] : 0.0;
+      if (snoop[t * FL + p + 1]) {
+        c_out[id] = c;
+        if (ENERGY) e_out[id] = e;
+      } else {
+        const int qa = t * NFL + p, qb = qa + 1;
+        const uint8_t stv = state ? state[id] : (uint8_t)0;
+        clip = update_cell<ENERGY>(g, id, c, e, ENERGY ? sT[h] : 0.0, stv, sF[qa], ENERGY ? sG[qa] : 0.0, sA[qa],
+                                   sF[qb], ENERGY ? sG[qb] : 0.0, sA[qb], c_out, e_out, state, theta);
       }
-      if (flux_out && fok && (f < x1 || f == nx)) flux_out[fbase + f] = F;
-      // left face = right face of the lane to the left (lane 0: carried)
-      double Fl = __shfl_up_sync(kFull, F, 1), Gl = __shfl_up_sync(kFull, G, 1), al = __shfl_up_sync(kFull, a, 1);
-      if (lane == 0) { Fl = Fc; Gl = Gc; al = ac; }
-      Fc = __shfl_sync(kFull, F, 31); Gc = __shfl_sync(kFull, G, 31); ac = __shfl_sync(kFull, a, 31);
-      if (cell_ok) {
-        const size_t id = rbase + base + lane;
-        if (noopC) {
-          c_out[id] = cC;
-          if (ENERGY) e_out[id] = eC;
-        } else {
-          const double TC = ENERGY ? eC / heat_cap(g.Cp_l, g.Cp_g, cC) : 0.0;
-          clip += update_cell<ENERGY>(g, id, cC, eC, TC, sC, Fl, Gl, al, F, G, a, c_out, e_out, state, theta);
-        }
-      }
-      // rotate chunks
-      const double c31 = __shfl_sync(kFull, cN, 31), e31 = __shfl_sync(kFull, eN, 31);
-      const unsigned eqNN = eqmask(c31, e31, cNN, eNN);
-      cP = cC; eP = eC;
-      cC = cN; eC = eN; sC = sN;
-      cN = cNN; eN = eNN; sN = sNN;
-      eqP = eqC; eqC = eqN; eqN = eqNN;
     }
   }
   double v[1] = {clip};
   block_reduce_out<1>(v, sums);
 }
+
 // Energy update from given face VOF fluxes (the unfused form).
 template <int AX>
 __global__ void __launch_bounds__(kThreads)
@@ -520,47 +452,41 @@ static dim3 sweep_block() {
   return dim3(SweepTile<AX>::BX, SweepTile<AX>::BY, SweepTile<AX>::BZ);
 }
 
-static dim3 col_grid(int axis, const GridDev& g) {
-  const int n_ax = g.n[axis], n_t = axis == 1 ? g.n[2] : g.n[1];
-  return dim3((g.n[0] + 31) / 32, (n_t + 7) / 8, (n_ax + kSegCol - 1) / kSegCol);
+template <int AX>
+static dim3 tile_grid(const GridDev& g) {
+  using S = TileShape<AX>;
+  return dim3((g.n[0] + S::X - 1) / S::X, (g.n[1] + S::Y - 1) / S::Y, (g.n[2] + S::Z - 1) / S::Z);
 }
 
-static dim3 row_grid(const GridDev& g) {
-  return dim3((g.n[0] + kSegRow - 1) / kSegRow, (g.n[1] * g.n[2] + 7) / 8, 1);
+template <int AX>
+static dim3 tile_block() {
+  return dim3(TileShape<AX>::X, TileShape<AX>::Y, TileShape<AX>::Z);
 }
 
 int sweep_blocks(int axis, const GridDev& g) {
-  dim3 gr = axis == 0 ? row_grid(g) : col_grid(axis, g);
+  dim3 gr = axis == 0 ? tile_grid<0>(g) : (axis == 1 ? tile_grid<1>(g) : tile_grid<2>(g));
   return (int)(gr.x * gr.y * gr.z);
+}
+
+template <int AX>
+static void launch_tile(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
+                        const double* uf, uint8_t* state, double* theta, double* flux_out, SumOut sums,
+                        int* status, cudaStream_t st) {
+  if (e_in)
+    k_sweep_tile<AX, true><<<tile_grid<AX>(g), tile_block<AX>(), 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state,
+                                                                           theta, flux_out, sums, status);
+  else
+    k_sweep_tile<AX, false><<<tile_grid<AX>(g), tile_block<AX>(), 0, st>>>(g, c_in, nullptr, c_out, nullptr, uf,
+                                                                            state, theta, flux_out, sums, status);
 }
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
                          SumOut sums, cudaStream_t st) {
   int* status = device_status_ptr();
-  const dim3 blk(32, 8);
-  if (axis == 0) {
-    if (e_in)
-      k_sweep_row<true><<<row_grid(g), blk, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums,
-                                                      status);
-    else
-      k_sweep_row<false><<<row_grid(g), blk, 0, st>>>(g, c_in, nullptr, c_out, nullptr, uf, state, theta, flux_out,
-                                                       sums, status);
-  } else if (axis == 1) {
-    if (e_in)
-      k_sweep_col<1, true><<<col_grid(1, g), blk, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out,
-                                                            sums, status);
-    else
-      k_sweep_col<1, false><<<col_grid(1, g), blk, 0, st>>>(g, c_in, nullptr, c_out, nullptr, uf, state, theta,
-                                                             flux_out, sums, status);
-  } else {
-    if (e_in)
-      k_sweep_col<2, true><<<col_grid(2, g), blk, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out,
-                                                            sums, status);
-    else
-      k_sweep_col<2, false><<<col_grid(2, g), blk, 0, st>>>(g, c_in, nullptr, c_out, nullptr, uf, state, theta,
-                                                             flux_out, sums, status);
-  }
+  if (axis == 0) launch_tile<0>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums, status, st);
+  else if (axis == 1) launch_tile<1>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums, status, st);
+  else launch_tile<2>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums, status, st);
   return cudaGetLastError();
 }
 
