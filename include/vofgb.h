@@ -171,6 +171,30 @@ VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const doubl
                     double dt, long step_index, const double* dd, double dd_uniform, double* sums,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * A time step that allocates nothing (the paper has no counterpart; this is
+ * for callers that cannot allocate device memory when they step -- code in a
+ * host callback or an error path where the allocator must not be entered,
+ * embedders whose device memory is reserved up front by their own pool, small
+ * tools without an allocator).  Same arguments and results as vof_step(),
+ * minus the workspace: the scratch space is one fixed 24 MiB array that every
+ * GPU loading the library keeps until the process exits.
+ *   - grids above VOF_NOALLOC_MAX_CELLS cells return VOF_EINVAL, nothing
+ *     launched;
+ *   - all calls on a device share the array: calls whose kernels overlap on
+ *     the GPU race (order them on one stream or synchronise in between);
+ *   - the array keeps the previous call's contents; the step clears what must
+ *     start at zero itself;
+ *   - the first call on a device looks up the array's address with that
+ *     device current; make it before any stream capture on the device.
+ * vof_noalloc_scratch_bytes() returns the size of the array.
+ */
+#define VOF_NOALLOC_MAX_CELLS 262144L
+VOF_API size_t vof_noalloc_scratch_bytes(void);
+VOF_API vof_status vof_step_noalloc(const vof_grid* g, double* c, double* e, const double* u, const double* v,
+                                    const double* w, double dt, long step_index, const double* dd, double dd_uniform,
+                                    double* sums, void* stream);
+
 /* Sticky device status (synchronises the device): VOF_OK or VOF_ECFL; reading clears it. */
 VOF_API vof_status vof_get_device_status(void);
 /* Message for a status code (static string). */

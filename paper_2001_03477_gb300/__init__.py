@@ -102,6 +102,10 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        L.vof_step_noalloc.argtypes = [G, P, P, P, P, P, D, L_, P, D, P, P]
+        L.vof_step_noalloc.restype = ctypes.c_int
+        L.vof_noalloc_scratch_bytes.argtypes = []
+        L.vof_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.vof_step_workspace_bytes.argtypes = [G]
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_get_device_status.argtypes = []
@@ -218,6 +222,23 @@ def vof_step(g, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, sums=Non
                           _ptr(v, _f64(), "v"), _ptr(w, _f64(), "w"), float(dt), int(step_index),
                           _ptr(dd, _f64(), "dd"), float(dd_uniform), _ptr(sums, _f64(), "sums"),
                           _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes), _stream(stream)))
+
+
+def vof_step_noalloc(g, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, sums=None, stream=None):
+    """vof_step without a workspace, for callers that cannot allocate device
+    memory while they step: the scratch lives in the library's fixed array
+    (grids up to VOF_NOALLOC_MAX_CELLS = 64^3 cells).  Calls that overlap on
+    the GPU share that array and race; the first call on a device must come
+    before any stream capture on it."""
+    cg = g.c_struct()
+    _check("vof_step_noalloc",
+           lib().vof_step_noalloc(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(e, _f64(), "e"),
+                                  _ptr(u, _f64(), "u"), _ptr(v, _f64(), "v"), _ptr(w, _f64(), "w"), float(dt),
+                                  int(step_index), _ptr(dd, _f64(), "dd"), float(dd_uniform),
+                                  _ptr(sums, _f64(), "sums"), _stream(stream)))
+
+
+VOF_NOALLOC_MAX_CELLS = 262144
 
 
 def vof_get_device_status() -> int:
