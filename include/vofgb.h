@@ -107,16 +107,23 @@ VOF_API vof_status vof_reconstruct(const vof_grid* g, const double* c, double* m
  *   flux_out      face array (nullable): receives F of every face
  *   diag          device double[1] (nullable): clipped volume is ADDED
  *                 (atomically; last bits depend on block order)
+ *   workspace     device scratch of at least vof_sweep_workspace_bytes(g)
+ *                 bytes, 256-byte aligned, caller-owned, not overlapping the
+ *                 fields and not shared with concurrent calls
  */
+VOF_API size_t vof_sweep_workspace_bytes(const vof_grid* g);
 VOF_API vof_status vof_advect_sweep_x(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
-                              double* e_out, const double* u_face, double dt, uint8_t* state, double* theta,
-                              double* flux_out, double* diag, void* stream);
+                                      double* e_out, const double* u_face, double dt, uint8_t* state,
+                                      double* theta, double* flux_out, double* diag, void* workspace,
+                                      size_t workspace_bytes, void* stream);
 VOF_API vof_status vof_advect_sweep_y(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
-                              double* e_out, const double* v_face, double dt, uint8_t* state, double* theta,
-                              double* flux_out, double* diag, void* stream);
+                                      double* e_out, const double* v_face, double dt, uint8_t* state,
+                                      double* theta, double* flux_out, double* diag, void* workspace,
+                                      size_t workspace_bytes, void* stream);
 VOF_API vof_status vof_advect_sweep_z(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
-                              double* e_out, const double* w_face, double dt, uint8_t* state, double* theta,
-                              double* flux_out, double* diag, void* stream);
+                                      double* e_out, const double* w_face, double dt, uint8_t* state,
+                                      double* theta, double* flux_out, double* diag, void* workspace,
+                                      size_t workspace_bytes, void* stream);
 
 /*
  * Unfused energy sweep (Sec. 3.4.1, Eq. disc_et_adv): e' from the face VOF
@@ -179,8 +186,9 @@ VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const doubl
  * tools without an allocator).  Same arguments and results as vof_step(),
  * minus the workspace: the scratch space is one fixed 24 MiB array that every
  * GPU loading the library keeps until the process exits.
- *   - grids above VOF_NOALLOC_MAX_CELLS cells return VOF_EINVAL, nothing
- *     launched;
+ *   - grids above VOF_NOALLOC_MAX_CELLS cells, or whose step workspace
+ *     (vof_step_workspace_bytes) exceeds the array -- only grids narrower
+ *     than 32 cells in x can -- return VOF_EINVAL, nothing launched;
  *   - all calls on a device share the array: calls whose kernels overlap on
  *     the GPU race (order them on one stream or synchronise in between);
  *   - the array keeps the previous call's contents; the step clears what must

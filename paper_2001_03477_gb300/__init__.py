@@ -91,9 +91,9 @@ def lib():
         G = ctypes.POINTER(_CGrid)
         sig = {
             "vof_reconstruct": [G, P, P, P, P, P],
-            "vof_advect_sweep_x": [G, P, P, P, P, P, D, P, P, P, P, P],
-            "vof_advect_sweep_y": [G, P, P, P, P, P, D, P, P, P, P, P],
-            "vof_advect_sweep_z": [G, P, P, P, P, P, D, P, P, P, P, P],
+            "vof_advect_sweep_x": [G, P, P, P, P, P, D, P, P, P, P, P, S, P],
+            "vof_advect_sweep_y": [G, P, P, P, P, P, D, P, P, P, P, P, S, P],
+            "vof_advect_sweep_z": [G, P, P, P, P, P, D, P, P, P, P, P, S, P],
             "energy_advect_consistent": [G, I, P, P, P, P, P, P, D, P, P, P],
             "vof_phase_change_shift": [G, P, P, P, P, P, D, P, P, P],
             "vof_step": [G, P, P, P, P, P, D, L_, P, D, P, P, S, P],
@@ -106,6 +106,8 @@ def lib():
         L.vof_step_noalloc.restype = ctypes.c_int
         L.vof_noalloc_scratch_bytes.argtypes = []
         L.vof_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.vof_sweep_workspace_bytes.argtypes = [G]
+        L.vof_sweep_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_workspace_bytes.argtypes = [G]
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_get_device_status.argtypes = []
@@ -161,28 +163,54 @@ def vof_reconstruct(g: Grid, c, m, alpha, mixed, stream=None):
                                                     _stream(stream)))
 
 
-def _sweep(name, g, c_in, e_in, c_out, e_out, uf, dt, state, theta, flux_out, diag, stream):
+def vof_sweep_workspace_bytes(g: Grid) -> int:
+    cg = g.c_struct()
+    return int(lib().vof_sweep_workspace_bytes(ctypes.byref(cg)))
+
+
+_ws_cache = {}
+
+
+def sweep_workspace(g: Grid, device=None):
+    """A cached scratch buffer (torch allocation) for the stand-alone sweeps."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    nb = vof_sweep_workspace_bytes(g)
+    key = (dev, nb)
+    if key not in _ws_cache:
+        _ws_cache[key] = torch.empty(nb, dtype=torch.uint8, device=dev)
+    return _ws_cache[key]
+
+
+def _sweep(name, g, c_in, e_in, c_out, e_out, uf, dt, state, theta, flux_out, diag, workspace, stream):
     cg = g.c_struct()
     fn = getattr(lib(), name)
+    if workspace is None:
+        workspace = sweep_workspace(g, c_in.device)
+    nbytes = workspace.numel() * workspace.element_size()
     _check(name, fn(ctypes.byref(cg), _ptr(c_in, _f64(), "c_in"), _ptr(e_in, _f64(), "e_in"),
                     _ptr(c_out, _f64(), "c_out"), _ptr(e_out, _f64(), "e_out"), _ptr(uf, _f64(), "face"),
                     float(dt), _ptr(state, _u8(), "state"), _ptr(theta, _f64(), "theta"),
-                    _ptr(flux_out, _f64(), "flux_out"), _ptr(diag, _f64(), "diag"), _stream(stream)))
+                    _ptr(flux_out, _f64(), "flux_out"), _ptr(diag, _f64(), "diag"),
+                    _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes), _stream(stream)))
 
 
 def vof_advect_sweep_x(g, c_in, e_in, c_out, e_out, u_face, dt, state=None, theta=None, flux_out=None, diag=None,
-                       stream=None):
-    _sweep("vof_advect_sweep_x", g, c_in, e_in, c_out, e_out, u_face, dt, state, theta, flux_out, diag, stream)
+                       workspace=None, stream=None):
+    _sweep("vof_advect_sweep_x", g, c_in, e_in, c_out, e_out, u_face, dt, state, theta, flux_out, diag, workspace,
+           stream)
 
 
 def vof_advect_sweep_y(g, c_in, e_in, c_out, e_out, v_face, dt, state=None, theta=None, flux_out=None, diag=None,
-                       stream=None):
-    _sweep("vof_advect_sweep_y", g, c_in, e_in, c_out, e_out, v_face, dt, state, theta, flux_out, diag, stream)
+                       workspace=None, stream=None):
+    _sweep("vof_advect_sweep_y", g, c_in, e_in, c_out, e_out, v_face, dt, state, theta, flux_out, diag, workspace,
+           stream)
 
 
 def vof_advect_sweep_z(g, c_in, e_in, c_out, e_out, w_face, dt, state=None, theta=None, flux_out=None, diag=None,
-                       stream=None):
-    _sweep("vof_advect_sweep_z", g, c_in, e_in, c_out, e_out, w_face, dt, state, theta, flux_out, diag, stream)
+                       workspace=None, stream=None):
+    _sweep("vof_advect_sweep_z", g, c_in, e_in, c_out, e_out, w_face, dt, state, theta, flux_out, diag, workspace,
+           stream)
 
 
 SWEEPS = (vof_advect_sweep_x, vof_advect_sweep_y, vof_advect_sweep_z)

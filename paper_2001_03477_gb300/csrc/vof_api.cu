@@ -88,12 +88,22 @@ vof_status vof_reconstruct(const vof_grid* g, const double* c, double* m, double
   return cuda_status(launch_reconstruct(to_dev(g, 0.0), c, m, alpha, mixed, (cudaStream_t)stream));
 }
 
+size_t vof_sweep_workspace_bytes(const vof_grid* g) {
+  if (!grid_ok(g)) return 0;
+  return sweep_scratch_bytes(to_dev(g, 0.0));
+}
+
 static vof_status sweep_common(int axis, const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
                                double* e_out, const double* uf, double dt, uint8_t* state, double* theta,
-                               double* flux_out, double* diag, void* stream) {
-  if (!grid_ok(g) || !c_in || !c_out || !uf) return VOF_EINVAL;
+                               double* flux_out, double* diag, void* workspace, size_t workspace_bytes,
+                               void* stream) {
+  if (!grid_ok(g) || !c_in || !c_out || !uf || !workspace) return VOF_EINVAL;
   if (e_in && (!e_out || (state && !theta))) return VOF_EINVAL;
   if (!(dt >= 0.0)) return VOF_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
+  const GridDev d = to_dev(g, dt);
+  const size_t need = sweep_scratch_bytes(d);
+  if (workspace_bytes < need) return VOF_EINVAL;
   size_t N = cells(g), B = N * 8;
   if (overlap(c_in, B, c_out, B)) return VOF_EINVAL;
   if (e_in && (overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) || overlap(e_in, B, c_out, B) ||
@@ -102,25 +112,34 @@ static vof_status sweep_common(int axis, const vof_grid* g, const double* c_in, 
   if (flux_out && (overlap(flux_out, face_count(g, axis) * 8, c_out, B) ||
                    (e_out && overlap(flux_out, face_count(g, axis) * 8, e_out, B))))
     return VOF_EINVAL;
-  SumOut so{nullptr, 1, diag};
-  return cuda_status(launch_sweep(axis, to_dev(g, dt), c_in, e_in, c_out, e_in ? e_out : nullptr, uf, state, theta,
-                                  flux_out, so, (cudaStream_t)stream));
+  if (overlap(workspace, need, c_in, B) || overlap(workspace, need, c_out, B) ||
+      (e_in && (overlap(workspace, need, e_in, B) || overlap(workspace, need, e_out, B))))
+    return VOF_EINVAL;
+  SweepScratch sc = carve_sweep_scratch(axis, d, workspace, nullptr, diag);
+  return cuda_status(launch_sweep(axis, d, c_in, e_in, c_out, e_in ? e_out : nullptr, uf, state, theta, flux_out, sc,
+                                  (cudaStream_t)stream));
 }
 
 vof_status vof_advect_sweep_x(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
                               double* e_out, const double* u_face, double dt, uint8_t* state, double* theta,
-                              double* flux_out, double* diag, void* stream) {
-  return sweep_common(0, g, c_in, e_in, c_out, e_out, u_face, dt, state, theta, flux_out, diag, stream);
+                              double* flux_out, double* diag, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  return sweep_common(0, g, c_in, e_in, c_out, e_out, u_face, dt, state, theta, flux_out, diag, workspace,
+                      workspace_bytes, stream);
 }
 vof_status vof_advect_sweep_y(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
                               double* e_out, const double* v_face, double dt, uint8_t* state, double* theta,
-                              double* flux_out, double* diag, void* stream) {
-  return sweep_common(1, g, c_in, e_in, c_out, e_out, v_face, dt, state, theta, flux_out, diag, stream);
+                              double* flux_out, double* diag, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  return sweep_common(1, g, c_in, e_in, c_out, e_out, v_face, dt, state, theta, flux_out, diag, workspace,
+                      workspace_bytes, stream);
 }
 vof_status vof_advect_sweep_z(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
                               double* e_out, const double* w_face, double dt, uint8_t* state, double* theta,
-                              double* flux_out, double* diag, void* stream) {
-  return sweep_common(2, g, c_in, e_in, c_out, e_out, w_face, dt, state, theta, flux_out, diag, stream);
+                              double* flux_out, double* diag, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  return sweep_common(2, g, c_in, e_in, c_out, e_out, w_face, dt, state, theta, flux_out, diag, workspace,
+                      workspace_bytes, stream);
 }
 
 vof_status energy_advect_consistent(const vof_grid* g, int axis, const double* c_before, const double* c_after,
@@ -150,8 +169,9 @@ vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const d
 }
 
 // workspace layout: c2 | e2 | theta | state | partials (3 sweeps x 1, shift x 5)
+// | sweep scratch (reused by the three sweeps)
 struct StepLayout {
-  size_t off_c2, off_e2, off_th, off_st, off_ps, off_sh, total;
+  size_t off_c2, off_e2, off_th, off_st, off_ps, off_sh, off_sw, total;
   int nb_sw[3], nb_sh;
 };
 
@@ -171,7 +191,8 @@ static StepLayout step_layout(const vof_grid* g) {
   }
   L.nb_sh = shift_blocks(d);
   L.off_sh = L.off_ps + align256(nsw * 8);
-  L.total = L.off_sh + align256((size_t)L.nb_sh * 5 * 8);
+  L.off_sw = L.off_sh + align256((size_t)L.nb_sh * 5 * 8);
+  L.total = L.off_sw + align256(sweep_scratch_bytes(d));
   return L;
 }
 
@@ -212,8 +233,8 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
   for (int s = 0; s < 3; ++s) order[s] = (step_index % 2 == 0) ? s : 2 - s;
   for (int s = 0; s < 3; ++s) {
     int ax = order[s];
-    SumOut so{ps + poff, 1, nullptr};
-    err = launch_sweep(ax, d, src_c, src_e, dst_c, dst_e, uf[ax], state, th, nullptr, so, st);
+    SweepScratch sc = carve_sweep_scratch(ax, d, ws + L.off_sw, ps + poff, nullptr);
+    err = launch_sweep(ax, d, src_c, src_e, dst_c, dst_e, uf[ax], state, th, nullptr, sc, st);
     if (err != cudaSuccess) return cuda_status(err);
     poff += (size_t)L.nb_sw[ax];
     double* tc = src_c; src_c = dst_c; dst_c = tc;

@@ -19,12 +19,38 @@ struct SumOut {
   double* diag;
 };
 
+// Scratch of one sweep (kernel A -> kernel B): T of the cells whose (c, e)
+// differs from the previous cell of their line, the per-warp lists of cells
+// that are not no-ops with their counts, and per-CTA partial sums of the
+// clipped volume (or, when partial is null, atomics into diag).
+struct SweepScratch {
+  double* T;
+  uint32_t* list;
+  int* count;
+  double* partial;
+  double* diag;
+  uint32_t* mlist;  // per-warp lists of mixed cells
+  int* mcount;
+  double* plane;    // [N][4]: m0, m1, m2, alpha of the listed mixed cells
+};
+
+struct SweepPlan {
+  dim3 gridA, blockA;
+  int cap;          // list capacity per warp of kernel A
+  long long nsub;   // number of lists (warps of kernel A)
+  unsigned gridB;   // CTAs of kernel B (8 lists each)
+};
+
+SweepPlan sweep_plan(int axis, const GridDev& g);
+size_t sweep_scratch_bytes(const GridDev& g);
+SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* partials, double* diag);
+
 int sweep_blocks(int axis, const GridDev& g);
 int shift_blocks(const GridDev& g);
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
-                         SumOut sums, cudaStream_t st);
+                         SweepScratch sc, cudaStream_t st);
 
 cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, const double* c_after,
                           const double* e_in, double* e_out, const double* F, const double* uf, uint8_t* state,

@@ -12,8 +12,10 @@
 // fixed array in device memory that the library reserves when it is loaded.
 //
 // Limits and rules for callers:
-//   * the grid may have at most VOF_NOALLOC_MAX_CELLS cells (64^3); larger
-//     grids are rejected with VOF_EINVAL before anything is launched;
+//   * the grid may have at most VOF_NOALLOC_MAX_CELLS cells (64^3), and its
+//     step workspace must fit the array (it does for every such grid at
+//     least 32 cells wide in x; much thinner grids need more list space);
+//     other grids are rejected with VOF_EINVAL before anything is launched;
 //   * every GPU on which the library is loaded holds the array (24 MiB)
 //     until the process exits;
 //   * all calls share the one array per device: two calls whose kernels

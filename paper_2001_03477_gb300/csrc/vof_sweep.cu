@@ -3,16 +3,23 @@
 // with the Weymouth-Yue split scheme, and Sec. 3.4.1 Eq. disc_et_adv), plus
 // the unfused energy update from exported VOF fluxes.
 //
-// One CTA owns a tile of cells.  c is staged in shared memory with a halo of
-// 3 cells along the sweep axis and 1 across (MYC stencils of the donor
-// cells), T = e / C_p(c) with a halo of 3 along the sweep axis (WENO5).
-// Each face of the tile is evaluated once (geometry only when its donor is
-// mixed), then every cell applies
+// Every cell applies
 //   c <- c + (F_l - cc a_l) - (F_r - cc a_r)
 //   e <- e + (G_l - Theta a_l) - (G_r - Theta a_r),
-//   G = (T_f C_pl) F + (T_f C_pg) (a - F),
+//   G = (T_f C_pl) F + (T_f C_pg) (a - F),  T_f = WENO5 of T = e / C_p(c),
 // with cc = [c^n > 1/2] and Theta = C_p(cc) T^n frozen at the start of the
 // step (see the `state` convention in include/vofgb.h).
+//
+// Two kernels per sweep:
+//   A (stream): walks the grid lines, copies the cells that provably do not
+//     change (no-op cells, below) straight to the output, stores T for every
+//     cell whose (c, e) differs from the previous cell of its line, and lists
+//     the remaining cells per warp in a fixed order;
+//   B (active cells): one warp per list, one listed cell per lane; rebuilds
+//     the cell's 7-cell T stencil, evaluates its two faces (PLIC geometry for
+//     a mixed donor, WENO5) and updates c, e and the frozen state.
+// The bulk of the grid then costs a load and a store at HBM speed, and the
+// FP64 work (the scarce unit on this part) runs in full warps.
 #include "vof_launch.h"
 
 namespace vofgb {
@@ -40,9 +47,7 @@ __device__ __forceinline__ size_t face_index(int ax, int f, int i, int j, int k,
 // around it along the sweep axis have the same (c, e) bits, c is exactly 0 or
 // 1 and the cell has not changed earlier in the step: both donors are then
 // pure with the same c, F = c a, both face temperatures equal T, and
-// (G - Theta a) vanishes exactly on both faces.  No-op cells cost no FP64
-// work; face fluxes are evaluated only next to non-no-op cells and
-// T = e / C_p(c) only where such a face needs it.
+// (G - Theta a) vanishes exactly on both faces.
 // ---------------------------------------------------------------------------
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -156,202 +161,304 @@ __device__ __forceinline__ void block_reduce_out(double (&v)[NV], SumOut out) {
   }
 }
 
-// Tile sweep: one thread per cell.  A CTA stages c and e of its tile plus a
-// halo of 4 cells along the sweep axis (no transverse halo: the 27-cell MYC
-// stencil of a mixed donor is read from global memory, which only the few
-// interface faces need).  Phases, separated by barriers:
-//   1. no-op flags of the tile cells and of the first halo cell on each side
-//      (7-cell window along the axis has equal (c, e) bits, c is 0 or 1, the
-//      cell has not changed earlier in the step);
-//   2. T = e / C_p(c) only for cells within 3 of a non-no-op cell;
-//   3. face fluxes only for faces next to a non-no-op cell;
-//   4. cell updates; no-op cells are copied.
-template <int AX>
-struct TileShape;
-template <>
-struct TileShape<0> { static constexpr int X = 64, Y = 4, Z = 1; };
-template <>
-struct TileShape<1> { static constexpr int X = 16, Y = 16, Z = 1; };
-template <>
-struct TileShape<2> { static constexpr int X = 16, Y = 1, Z = 16; };
 
-constexpr int kHalo = 4;
-static_assert(TileShape<0>::X * TileShape<0>::Y * TileShape<0>::Z == 256, "256 threads per sweep CTA");
-static_assert(TileShape<1>::X * TileShape<1>::Y * TileShape<1>::Z == 256, "256 threads per sweep CTA");
-static_assert(TileShape<2>::X * TileShape<2>::Y * TileShape<2>::Z == 256, "256 threads per sweep CTA");
+// ---------------------------------------------------------------------------
+// Kernel A for the sweeps along y (AX = 1) and z (AX = 2): a warp owns 32
+// consecutive x at one position of the remaining axis and walks kSegA cells
+// along the sweep axis; each lane keeps a run length of equal (c, e) cells.
+// ---------------------------------------------------------------------------
+constexpr int kSegA = 32;     // cells per lane along y / z
+constexpr int kWarpsA = 8;    // warps per CTA of kernel A
+constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
 
 template <int AX, bool ENERGY>
-__global__ void __launch_bounds__(256, 3)
-k_sweep_tile(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-             double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
-             double* __restrict__ theta, double* __restrict__ flux_out, SumOut sums, int* __restrict__ status) {
-  constexpr int TX = TileShape<AX>::X, TY = TileShape<AX>::Y, TZ = TileShape<AX>::Z;
-  constexpr int TA = AX == 0 ? TX : (AX == 1 ? TY : TZ);  // tile length along the axis
-  constexpr int TT = (TX * TY * TZ) / TA;                  // transverse cells of the tile
-  constexpr int HL = TA + 2 * kHalo;                       // staged length along the axis
-  constexpr int NH = HL * TT;
-  constexpr int NFL = TA + 1;                              // faces per line
-  constexpr int NF = NFL * TT;
-  constexpr int FL = TA + 2;                               // flagged positions per line: -1 .. TA
-  __shared__ double sc[NH];
-  __shared__ double se[ENERGY ? NH : 1];
-  __shared__ double sT[ENERGY ? NH : 1];
-  __shared__ uint8_t snoop[FL * TT];
-  __shared__ double sF[NF];
-  __shared__ double sG[ENERGY ? NF : 1];
-  __shared__ double sA[NF];
+__global__ void __launch_bounds__(32 * kWarpsA)
+k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all) {
+  const int nx = g.n[0], ny = g.n[1];
+  const int n_ax = g.n[AX];
+  const int n_t = AX == 1 ? g.n[2] : g.n[1];
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int x = blockIdx.x * 32 + lane;
+  const int t = blockIdx.y * kWarpsA + warp;
+  const int s0 = blockIdx.z * kSegA, s1 = min(s0 + kSegA, n_ax);
+  const bool act = x < nx && t < n_t;
+  const int xs = act ? x : 0, ts = act ? t : 0;
+  const int bca = g.bc[AX];
+  const size_t stride = AX == 1 ? (size_t)nx : (size_t)nx * ny;
+  const size_t cbase = AX == 1 ? (size_t)ts * ny * nx + xs : (size_t)ts * nx + xs;
+  const size_t sub = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * kWarpsA * gridDim.x + (size_t)warp * gridDim.x +
+                     blockIdx.x;
+  uint32_t* list = sc.list + sub * (size_t)(32 * kSegA);
+  uint32_t* mlist = sc.mlist + sub * (size_t)(32 * kSegA);
+  int nlist = 0, nmixed = 0;
+  // window: cells k .. k+3 (c, e), run = equal cells ending at k+3, and
+  // whether cells k and k-1 differ from their predecessors
+  double wc[4], we[4];
+  int run = 0;
+  bool dif[4];
+  double pc = 0.0, pe = 0.0;
+#pragma unroll
+  for (int i = -4; i < 4; ++i) {
+    const size_t id = cbase + stride * map_idx(s0 + i, n_ax, bca);
+    const double cv = __ldg(c_in + id);
+    const double ev = ENERGY ? __ldg(e_in + id) : 0.0;
+    const bool same = i > -4 && same_bits(cv, pc) && (!ENERGY || same_bits(ev, pe));
+    run = same ? run + 1 : 1;
+    if (i >= 0) { wc[i] = cv; we[i] = ev; dif[i] = !same; }
+    pc = cv; pe = ev;
+  }
+  for (int k = s0; k < s1; ++k) {
+    // prefetch cell k + 4
+    const size_t idn = cbase + stride * map_idx(k + 4, n_ax, bca);
+    const double cn = __ldg(c_in + idn);
+    const double en = ENERGY ? __ldg(e_in + idn) : 0.0;
+    const size_t id = cbase + stride * k;
+    const uint8_t stv = (act && state) ? state[id] : (uint8_t)0;
+    // cells k-3..k+3 equal <=> run (ending at k+3) >= 7
+    const bool noop = act && !force_all && run >= 7 && is01(wc[0]) && !(stv & 1);
+    if (act) {
+      if (noop) {
+        c_out[id] = wc[0];
+        if (ENERGY) e_out[id] = we[0];
+      }
+      if (ENERGY && dif[0]) sc.T[id] = we[0] / heat_cap(g.Cp_l, g.Cp_g, wc[0]);
+    }
+    const bool listed = act && !noop;
+    const unsigned m = __ballot_sync(kFull, listed);
+    if (listed) list[nlist + __popc(m & ((1u << lane) - 1u))] = (uint32_t)id;
+    nlist += __popc(m);
+    const bool mixed = act && is_mixed_b(wc[0], g);
+    const unsigned mm = __ballot_sync(kFull, mixed);
+    if (mixed) mlist[nmixed + __popc(mm & ((1u << lane) - 1u))] = (uint32_t)id;
+    nmixed += __popc(mm);
+    // shift the window
+    const bool same = same_bits(cn, wc[3]) && (!ENERGY || same_bits(en, we[3]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { wc[i] = wc[i + 1]; we[i] = we[i + 1]; dif[i] = dif[i + 1]; }
+    wc[3] = cn; we[3] = en; dif[3] = !same;
+    run = same ? run + 1 : 1;
+  }
+  if (lane == 0) {
+    sc.count[sub] = nlist;
+    sc.mcount[sub] = nmixed;
+  }
+}
 
+// ---------------------------------------------------------------------------
+// Kernel A for the sweep along x: a warp owns kSegRow cells of one row and
+// walks them in chunks of 32 (lane = cell); equality with the previous cell
+// is a ballot mask, so "cells l-3..l+3 equal" is a 6-bit window test.
+// ---------------------------------------------------------------------------
+template <bool ENERGY>
+__global__ void __launch_bounds__(256)
+k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int row = blockIdx.y * 8 + warp;  // row = z * ny + y
+  const int x0 = blockIdx.x * kSegRow, x1 = min(x0 + kSegRow, nx);
+  const bool rowok = row < ny * nz;
+  const size_t rbase = (size_t)(rowok ? row : 0) * nx;
+  const int bcx = g.bc[0];
+  const size_t sub = (size_t)row * gridDim.x + blockIdx.x;
+  if (!rowok) {  // whole warp: empty lists
+    if (lane == 0) {
+      sc.count[sub] = 0;
+      sc.mcount[sub] = 0;
+    }
+    return;
+  }
+  uint32_t* list = sc.list + sub * (size_t)kSegRow;
+  uint32_t* mlist = sc.mlist + sub * (size_t)kSegRow;
+  int nlist = 0, nmixed = 0;
+  auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
+  auto lde = [&](int X) { return ENERGY ? __ldg(e_in + rbase + map_idx(X, nx, bcx)) : 0.0; };
+  auto eqmask = [&](double cprev, double eprev, double cc, double ee) -> unsigned {
+    double cl = __shfl_up_sync(kFull, cc, 1), el = __shfl_up_sync(kFull, ee, 1);
+    if (lane == 0) { cl = cprev; el = eprev; }
+    return __ballot_sync(kFull, same_bits(cc, cl) && (!ENERGY || same_bits(ee, el)));
+  };
+  // chunks P (base-32), C (base), N (base+32)
+  int base = x0;
+  double cP = ldc(base - 32 + lane), eP = lde(base - 32 + lane);
+  double cC = ldc(base + lane), eC = lde(base + lane);
+  double cN = ldc(base + 32 + lane), eN = lde(base + 32 + lane);
+  const double cPP = ldc(base - 33), ePP = lde(base - 33);
+  unsigned eqP = eqmask(cPP, ePP, cP, eP);
+  unsigned eqC = eqmask(__shfl_sync(kFull, cP, 31), __shfl_sync(kFull, eP, 31), cC, eC);
+  unsigned eqN = eqmask(__shfl_sync(kFull, cC, 31), __shfl_sync(kFull, eC, 31), cN, eN);
+  for (; base < x1; base += 32) {
+    const double cNN = ldc(base + 64 + lane), eNN = lde(base + 64 + lane);
+    const int X = base + lane;
+    const bool cell_ok = X < x1;
+    const uint8_t stv = (cell_ok && state) ? state[rbase + X] : (uint8_t)0;
+    const unsigned long long M1 = ((unsigned long long)eqC << 32) | eqP;
+    const unsigned long long M2 = ((unsigned long long)eqN << 32) | eqC;
+    // cells X-3..X+3 equal <=> eq bits of X-2..X+3
+    const bool uni = lane >= 2 ? (((M2 >> (lane - 2)) & 0x3Full) == 0x3Full)
+                               : (((M1 >> (32 + lane - 2)) & 0x3Full) == 0x3Full);
+    const bool noop = cell_ok && !force_all && uni && is01(cC) && !(stv & 1);
+    if (cell_ok) {
+      if (noop) {
+        c_out[rbase + X] = cC;
+        if (ENERGY) e_out[rbase + X] = eC;
+      }
+      if (ENERGY && !((eqC >> lane) & 1u)) sc.T[rbase + X] = eC / heat_cap(g.Cp_l, g.Cp_g, cC);
+    }
+    const bool listed = cell_ok && !noop;
+    const unsigned m = __ballot_sync(kFull, listed);
+    if (listed) list[nlist + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(rbase + X);
+    nlist += __popc(m);
+    const bool mixed = cell_ok && is_mixed_b(cC, g);
+    const unsigned mm = __ballot_sync(kFull, mixed);
+    if (mixed) mlist[nmixed + __popc(mm & ((1u << lane) - 1u))] = (uint32_t)(rbase + X);
+    nmixed += __popc(mm);
+    const double c31 = __shfl_sync(kFull, cN, 31), e31 = __shfl_sync(kFull, eN, 31);
+    const unsigned eqNN = eqmask(c31, e31, cNN, eNN);
+    cP = cC; eP = eC;
+    cC = cN; eC = eN;
+    cN = cNN; eN = eNN;
+    eqP = eqC; eqC = eqN; eqN = eqNN;
+  }
+  if (lane == 0) {
+    sc.count[sub] = nlist;
+    sc.mcount[sub] = nmixed;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel M: the PLIC plane (MYC normal + plane constant) of every mixed cell,
+// once per sweep, one mixed cell per lane; stored per cell for kernel B.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc, int nsub, int cap) {
+  const int lane = threadIdx.x & 31;
+  const int sub = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (sub >= nsub) return;
+  const int cnt = sc.mcount[sub];
+  const uint32_t* mlist = sc.mlist + (size_t)sub * cap;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  for (int i = lane; i < cnt; i += 32) {
+    const size_t id = mlist[i];
+    const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+    double s[27];
+#pragma unroll
+    for (int oz = 0; oz < 3; ++oz) {
+      const int zz = map_idx(z + oz - 1, nz, g.bc[2]);
+#pragma unroll
+      for (int oy = 0; oy < 3; ++oy) {
+        const int yy = map_idx(y + oy - 1, ny, g.bc[1]);
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+          const int xx = map_idx(x + ox - 1, nx, g.bc[0]);
+          s[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_at(g, xx, yy, zz));
+        }
+      }
+    }
+    double m[3];
+    myc_normal(s, m);
+    const double al = plane_alpha(m[0], m[1], m[2], s[13]);
+    double4 pl;
+    pl.x = m[0]; pl.y = m[1]; pl.z = m[2]; pl.w = al;
+    reinterpret_cast<double4*>(sc.plane)[id] = pl;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel B: one warp per kernel-A list, one listed cell per lane.
+// ---------------------------------------------------------------------------
+template <int AX, bool ENERGY>
+__global__ void __launch_bounds__(256, 2)
+k_active(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+         double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
+         double* __restrict__ theta, double* __restrict__ flux_out, SweepScratch sc, int nsub, int cap,
+         int* __restrict__ status) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-  const int a0 = AX == 0 ? x0 : (AX == 1 ? y0 : z0);
-  const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
-  // transverse line index t in [0, TT) <-> (tile coords of the two other axes)
-  auto line_coords = [&](int t, int pos, int& gx, int& gy, int& gz) {
-    if (AX == 0) { gx = x0 + pos; gy = y0 + t % TY; gz = z0 + t / TY; }
-    else if (AX == 1) { gx = x0 + t % TX; gy = y0 + pos; gz = z0 + t / TX; }
-    else { gx = x0 + t % TX; gy = y0 + t / TX; gz = z0 + pos; }
-  };
-  auto line_ok = [&](int t) {
-    int gx, gy, gz;
-    line_coords(t, 0, gx, gy, gz);
-    return (AX == 0 || gx < nx) && (AX == 1 || gy < ny) && (AX == 2 || gz < nz);
-  };
-  // staged index of (line t, position p in [-kHalo, TA + kHalo)) -- lines are
-  // contiguous along the axis for AX = 0 and interleaved otherwise so that a
-  // warp's loads stay coalesced along x
-  auto hidx = [&](int t, int p) { return AX == 0 ? t * HL + (p + kHalo) : (p + kHalo) * TT + t; };
-
-  // 1. stage c, e
-  for (int q = tid; q < NH; q += 256) {
-    int t, p;
-    if (AX == 0) { t = q / HL; p = q % HL - kHalo; }
-    else { p = q / TT - kHalo; t = q % TT; }
-    int gx, gy, gz;
-    line_coords(t, p, gx, gy, gz);
-    const int xx = map_idx(gx, nx, g.bc[0]), yy = map_idx(gy, ny, g.bc[1]), zz = map_idx(gz, nz, g.bc[2]);
-    const size_t id = ((size_t)zz * ny + yy) * nx + xx;
-    sc[q] = __ldg(c_in + id);
-    if (ENERGY) se[q] = __ldg(e_in + id);
-  }
-  __syncthreads();
-  // 2. no-op flags of positions -1 .. TA
-  for (int q = tid; q < FL * TT; q += 256) {
-    const int t = q / FL, p = q % FL - 1;
-    int gx, gy, gz;
-    line_coords(t, p, gx, gy, gz);
-    const int ga = a0 + p;
-    bool noop;
-    if (!line_ok(t) || (bca != 0 && (ga < 0 || ga >= n_ax))) {
-      noop = true;  // not a cell of the grid: needs no face
-    } else {
-      const int h0 = hidx(t, p);
-      const double c0 = sc[h0];
-      noop = is01(c0);
-      if (noop) {
-#pragma unroll
-        for (int d = -3; d <= 3; ++d) {
-          const int hd = hidx(t, p + d);
-          noop = noop && same_bits(sc[hd], c0) && (!ENERGY || same_bits(se[hd], se[h0]));
-        }
-      }
-      if (noop && state) {
-        const int xx = map_idx(gx, nx, g.bc[0]), yy = map_idx(gy, ny, g.bc[1]), zz = map_idx(gz, nz, g.bc[2]);
-        noop = !(state[((size_t)zz * ny + yy) * nx + xx] & 1);
-      }
-    }
-    snoop[q] = noop ? 1 : 0;
-  }
-  __syncthreads();
-  // 3. T where some cell within 3 positions is not a no-op
-  if (ENERGY) {
-    for (int q = tid; q < NH; q += 256) {
-      int t, p;
-      if (AX == 0) { t = q / HL; p = q % HL - kHalo; }
-      else { p = q / TT - kHalo; t = q % TT; }
-      bool need = false;
-#pragma unroll
-      for (int d = -3; d <= 3; ++d) {
-        const int pp = p + d;
-        if (pp >= -1 && pp <= TA) need = need || !snoop[t * FL + pp + 1];
-      }
-      if (need) sT[q] = se[q] / heat_cap(g.Cp_l, g.Cp_g, sc[q]);
-    }
-  }
-  __syncthreads();
-  // 4. faces f = 0..TA of each line (face f between positions f-1 and f)
-  for (int q = tid; q < NF; q += 256) {
-    const int t = q / NFL, f = q % NFL;
-    double Fv = 0.0, Gv = 0.0, a = 0.0;
-    const int gfa = a0 + f;
-    const bool need = line_ok(t) && gfa <= n_ax && (flux_out || !snoop[t * FL + f] || !snoop[t * FL + f + 1]);
-    if (need) {
-      int gx, gy, gz;
-      line_coords(t, f, gx, gy, gz);
-      const int fr = (bca == 0 && gfa == n_ax) ? 0 : gfa;
-      size_t fid;
-      if (AX == 0) fid = ((size_t)gz * ny + gy) * (nx + 1) + fr;
-      else if (AX == 1) fid = ((size_t)gz * (ny + 1) + fr) * nx + gx;
-      else fid = ((size_t)fr * ny + gy) * nx + gx;
-      a = __ldg(uf + fid) * g.lam;
-      if (dnz(a)) {
-        const bool pos = dgt0(a);
-        const int pd = pos ? f - 1 : f;  // donor position
-        const double cd = sc[hidx(t, pd)];
-        if (is_mixed_b(cd, g)) {
-          int dx, dy, dz;
-          line_coords(t, pd, dx, dy, dz);
-          Fv = mixed_donor_flux(g, c_in, AX, map_idx(dx, nx, g.bc[0]), map_idx(dy, ny, g.bc[1]),
-                                map_idx(dz, nz, g.bc[2]), cd, a, status);
-        } else {
-          Fv = cd * a;
-        }
-        if (ENERGY) {
-          double v[5];
-#pragma unroll
-          for (int r = -2; r <= 2; ++r) v[r + 2] = sT[hidx(t, pd + (pos ? r : -r))];
-          Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, v[0], v[1], v[2], v[3], v[4]);
-        }
-      }
-      if (flux_out && (f < TA || gfa == n_ax)) {
-        size_t fo;
-        if (AX == 0) fo = ((size_t)gz * ny + gy) * (nx + 1) + gfa;
-        else if (AX == 1) fo = ((size_t)gz * (ny + 1) + gfa) * nx + gx;
-        else fo = ((size_t)gfa * ny + gy) * nx + gx;
-        flux_out[fo] = Fv;
-      }
-    }
-    sF[q] = Fv;
-    sA[q] = a;
-    if (ENERGY) sG[q] = Gv;
-  }
-  __syncthreads();
-  // 5. cells
+  const int lane = threadIdx.x & 31;
+  const int sub = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   double clip = 0.0;
-  {
-    const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
-    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    if (gx < nx && gy < ny && gz < nz) {
-      const int p = AX == 0 ? lx : (AX == 1 ? ly : lz);
-      const int t = AX == 0 ? ly + TY * lz : (AX == 1 ? lx + TX * lz : lx + TX * ly);
-      const size_t id = ((size_t)gz * ny + gy) * nx + gx;
-      const int h = hidx(t, p);
-      const double c = sc[h];
-      const double e = ENERGY ? se[h] : 0.0;
-      if (snoop[t * FL + p + 1]) {
-        c_out[id] = c;
-        if (ENERGY) e_out[id] = e;
-      } else {
-        const int qa = t * NFL + p, qb = qa + 1;
-        const uint8_t stv = state ? state[id] : (uint8_t)0;
-        clip = update_cell<ENERGY>(g, id, c, e, ENERGY ? sT[h] : 0.0, stv, sF[qa], ENERGY ? sG[qa] : 0.0, sA[qa],
-                                   sF[qb], ENERGY ? sG[qb] : 0.0, sA[qb], c_out, e_out, state, theta);
+  if (sub < nsub) {
+    const int cnt = sc.count[sub];
+    const uint32_t* list = sc.list + (size_t)sub * cap;
+    for (int i = lane; i < cnt; i += 32) {
+      const size_t id = list[i];
+      const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+      const int k = AX == 0 ? x : (AX == 1 ? y : z);
+      const size_t stride = AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny);
+      const size_t lbase = id - stride * k;  // cell index of position 0 of this line
+      // (c, e) of cells k-4..k+3 and T of k-3..k+3 (run starts read back,
+      // others equal to their predecessor; the first is divided if needed)
+      double cw[8], ew[8], Tw[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t jd = lbase + stride * map_idx(k - 4 + j, n_ax, bca);
+        cw[j] = __ldg(c_in + jd);
+        ew[j] = ENERGY ? __ldg(e_in + jd) : 0.0;
+        if (ENERGY && j >= 1) {
+          const bool dif = !(same_bits(cw[j], cw[j - 1]) && same_bits(ew[j], ew[j - 1]));
+          Tw[j] = dif ? sc.T[jd] : (j == 1 ? ew[j] / heat_cap(g.Cp_l, g.Cp_g, cw[j]) : Tw[j - 1]);
+        }
       }
+      double F[2], G[2], A[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int f = k + side;  // face between cells f-1 and f
+        const int fr = (bca == 0 && f == n_ax) ? 0 : f;
+        size_t fid;
+        if (AX == 0) fid = ((size_t)z * ny + y) * (nx + 1) + fr;
+        else if (AX == 1) fid = ((size_t)z * (ny + 1) + fr) * nx + x;
+        else fid = ((size_t)fr * ny + y) * nx + x;
+        const double a = __ldg(uf + fid) * g.lam;
+        double Fv = 0.0, Gv = 0.0;
+        if (dnz(a)) {
+          const bool pos = dgt0(a);
+          // donor = cell k-1+side (a > 0) or k+side (a < 0); window index
+          // 3+side or 4+side -- constant indices keep the window in registers
+          const double cd = pos ? cw[3 + side] : cw[4 + side];
+          if (is_mixed_b(cd, g)) {
+            const int dk = map_idx(pos ? k - 1 + side : k + side, n_ax, bca);
+            const size_t did = lbase + stride * dk;
+            const double4 pl = reinterpret_cast<const double4*>(sc.plane)[did];
+            const double mv[3] = {pl.x, pl.y, pl.z};
+            const double da = fabs(a);
+            if (da > 1.0 && status) atomicOr(status, DEV_CFL);
+            const double vol = slab_volume(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
+            Fv = pos ? vol : -vol;
+          } else {
+            Fv = cd * a;
+          }
+          if (ENERGY) {
+            // upwind-ordered stencil around the donor
+            const double t0 = pos ? Tw[1 + side] : Tw[6 + side];
+            const double t1 = pos ? Tw[2 + side] : Tw[5 + side];
+            const double t2 = pos ? Tw[3 + side] : Tw[4 + side];
+            const double t3 = pos ? Tw[4 + side] : Tw[3 + side];
+            const double t4 = pos ? Tw[5 + side] : Tw[2 + side];
+            Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, t0, t1, t2, t3, t4);
+          }
+        }
+        F[side] = Fv; G[side] = Gv; A[side] = a;
+      }
+      if (flux_out) {
+        // faces are listed with the cell on their + side; the last face of a
+        // line goes with the last cell
+        size_t fo;
+        if (AX == 0) fo = ((size_t)z * ny + y) * (nx + 1) + k;
+        else if (AX == 1) fo = ((size_t)z * (ny + 1) + k) * nx + x;
+        else fo = ((size_t)k * ny + y) * nx + x;
+        flux_out[fo] = F[0];
+        if (k == n_ax - 1) flux_out[fo + (AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny))] = F[1];
+      }
+      const uint8_t stv = state ? state[id] : (uint8_t)0;
+      clip += update_cell<ENERGY>(g, id, cw[4], ew[4], Tw[4], stv, F[0], G[0], A[0], F[1], G[1], A[1], c_out,
+                                  e_out, state, theta);
     }
   }
   double v[1] = {clip};
-  block_reduce_out<1>(v, sums);
+  block_reduce_out<1>(v, SumOut{sc.partial, 1, sc.diag});
 }
 
 // Energy update from given face VOF fluxes (the unfused form).
@@ -452,41 +559,99 @@ static dim3 sweep_block() {
   return dim3(SweepTile<AX>::BX, SweepTile<AX>::BY, SweepTile<AX>::BZ);
 }
 
-template <int AX>
-static dim3 tile_grid(const GridDev& g) {
-  using S = TileShape<AX>;
-  return dim3((g.n[0] + S::X - 1) / S::X, (g.n[1] + S::Y - 1) / S::Y, (g.n[2] + S::Z - 1) / S::Z);
+
+// ---------------------------------------------------------------------------
+// Launch plans
+// ---------------------------------------------------------------------------
+SweepPlan sweep_plan(int axis, const GridDev& g) {
+  SweepPlan p;
+  if (axis == 0) {
+    p.gridA = dim3((g.n[0] + kSegRow - 1) / kSegRow, (g.n[1] * g.n[2] + 7) / 8, 1);
+    p.blockA = dim3(32, 8, 1);
+    p.cap = kSegRow;
+    p.nsub = (long long)p.gridA.x * p.gridA.y * 8;
+  } else {
+    const int n_t = axis == 1 ? g.n[2] : g.n[1];
+    p.gridA = dim3((g.n[0] + 31) / 32, (n_t + kWarpsA - 1) / kWarpsA, (g.n[axis] + kSegA - 1) / kSegA);
+    p.blockA = dim3(32, kWarpsA, 1);
+    p.cap = 32 * kSegA;
+    p.nsub = (long long)p.gridA.x * p.gridA.y * p.gridA.z * kWarpsA;
+  }
+  p.gridB = (unsigned)((p.nsub + 7) / 8);
+  return p;
 }
 
-template <int AX>
-static dim3 tile_block() {
-  return dim3(TileShape<AX>::X, TileShape<AX>::Y, TileShape<AX>::Z);
+size_t sweep_scratch_bytes(const GridDev& g) {
+  size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  size_t best = 0;
+  for (int a = 0; a < 3; ++a) {
+    SweepPlan p = sweep_plan(a, g);
+    size_t b = 0;
+    b += (N * 8 + 255) & ~(size_t)255;                                    // T
+    b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // lists
+    b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;                       // counts
+    b += ((size_t)p.gridB * 8 + 255) & ~(size_t)255;                      // partials
+    b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // mixed lists
+    b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;                       // mixed counts
+    b += (N * 32 + 255) & ~(size_t)255;                                   // planes
+    best = b > best ? b : best;
+  }
+  return best;
 }
 
-int sweep_blocks(int axis, const GridDev& g) {
-  dim3 gr = axis == 0 ? tile_grid<0>(g) : (axis == 1 ? tile_grid<1>(g) : tile_grid<2>(g));
-  return (int)(gr.x * gr.y * gr.z);
+SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* partials, double* diag) {
+  size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  SweepPlan p = sweep_plan(axis, g);
+  char* b = static_cast<char*>(ws);
+  SweepScratch s;
+  s.T = reinterpret_cast<double*>(b);
+  b += (N * 8 + 255) & ~(size_t)255;
+  s.list = reinterpret_cast<uint32_t*>(b);
+  b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;
+  s.count = reinterpret_cast<int*>(b);
+  b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;
+  s.partial = partials ? partials : (diag ? nullptr : reinterpret_cast<double*>(b));
+  b += ((size_t)p.gridB * 8 + 255) & ~(size_t)255;
+  s.mlist = reinterpret_cast<uint32_t*>(b);
+  b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;
+  s.mcount = reinterpret_cast<int*>(b);
+  b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;
+  s.plane = reinterpret_cast<double*>(b);
+  s.diag = diag;
+  return s;
 }
 
-template <int AX>
-static void launch_tile(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
-                        const double* uf, uint8_t* state, double* theta, double* flux_out, SumOut sums,
-                        int* status, cudaStream_t st) {
-  if (e_in)
-    k_sweep_tile<AX, true><<<tile_grid<AX>(g), tile_block<AX>(), 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state,
-                                                                           theta, flux_out, sums, status);
+int sweep_blocks(int axis, const GridDev& g) { return (int)sweep_plan(axis, g).gridB; }
+
+template <int AX, bool ENERGY>
+static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
+                      double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
+                      SweepScratch sc, int* status, cudaStream_t st) {
+  if (AX == 0)
+    k_stream_row<ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc, flux_out != nullptr);
   else
-    k_sweep_tile<AX, false><<<tile_grid<AX>(g), tile_block<AX>(), 0, st>>>(g, c_in, nullptr, c_out, nullptr, uf,
-                                                                            state, theta, flux_out, sums, status);
+    k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
+                                                                          flux_out != nullptr);
+  k_planes<<<p.gridB, 256, 0, st>>>(g, c_in, sc, (int)p.nsub, p.cap);
+  k_active<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc,
+                                                 (int)p.nsub, p.cap, status);
 }
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
-                         SumOut sums, cudaStream_t st) {
+                         SweepScratch sc, cudaStream_t st) {
   int* status = device_status_ptr();
-  if (axis == 0) launch_tile<0>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums, status, st);
-  else if (axis == 1) launch_tile<1>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums, status, st);
-  else launch_tile<2>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sums, status, st);
+  const SweepPlan p = sweep_plan(axis, g);
+  if (e_in) {
+    if (axis == 0) launch_ab<0, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
+    else if (axis == 1) launch_ab<1, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
+    else launch_ab<2, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
+  } else {
+    if (axis == 0) launch_ab<0, false>(p, g, c_in, nullptr, c_out, nullptr, uf, state, theta, flux_out, sc, status, st);
+    else if (axis == 1)
+      launch_ab<1, false>(p, g, c_in, nullptr, c_out, nullptr, uf, state, theta, flux_out, sc, status, st);
+    else launch_ab<2, false>(p, g, c_in, nullptr, c_out, nullptr, uf, state, theta, flux_out, sc, status, st);
+  }
   return cudaGetLastError();
 }
 

@@ -44,12 +44,19 @@ def test_host_validation_without_gpu(lib):
     nul = ctypes.c_void_p(0)
     # null arrays
     assert lib.vof_reconstruct(ctypes.byref(cg), nul, nul, nul, nul, nul) == P.VOF_EINVAL
-    assert lib.vof_advect_sweep_x(ctypes.byref(cg), nul, nul, nul, nul, nul, 0.1, nul, nul, nul, nul,
+    assert lib.vof_advect_sweep_x(ctypes.byref(cg), nul, nul, nul, nul, nul, 0.1, nul, nul, nul, nul, nul, 0,
                                   nul) == P.VOF_EINVAL
     # aliasing input and output
     fake = ctypes.c_void_p(1 << 40)
+    ws = ctypes.c_void_p(5 << 40)
+    big = lib.vof_sweep_workspace_bytes(ctypes.byref(cg))
     assert lib.vof_advect_sweep_y(ctypes.byref(cg), fake, nul, fake, nul, ctypes.c_void_p(1 << 41), 0.1, nul, nul,
-                                  nul, nul, nul) == P.VOF_EINVAL
+                                  nul, nul, ws, big, nul) == P.VOF_EINVAL
+    # sweep workspace missing, too small or misaligned
+    ok_out = ctypes.c_void_p(4 << 40)
+    for w_, nb in ((nul, big), (ws, big - 8), (ctypes.c_void_p((5 << 40) + 16), big)):
+        assert lib.vof_advect_sweep_z(ctypes.byref(cg), fake, nul, ok_out, nul, ctypes.c_void_p(1 << 41), 0.1, nul,
+                                      nul, nul, nul, w_, nb, nul) == P.VOF_EINVAL
     # bad grid
     bad = P.Grid(0, 8, 8).c_struct()
     assert lib.vof_step_workspace_bytes(ctypes.byref(bad)) == 0
@@ -70,7 +77,9 @@ def test_workspace_size_scales(lib):
     import paper_2001_03477_gb300 as P
     a = P.vof_step_workspace_bytes(P.Grid(32, 32, 32))
     b = P.vof_step_workspace_bytes(P.Grid(64, 64, 64))
-    assert a >= 32 ** 3 * 25 and b >= 64 ** 3 * 25 and b > 7 * a
+    assert a >= 32 ** 3 * 25 and b >= 64 ** 3 * 25 and b > 5 * a
+    s = P.vof_sweep_workspace_bytes(P.Grid(64, 64, 64))
+    assert 64 ** 3 * 12 <= s < b
 
 
 def test_binding_refuses_cpu_tensors(lib):
