@@ -152,10 +152,17 @@ VOF_API vof_status energy_advect_consistent(const vof_grid* g, int axis, const d
  *   diag device double[5] (nullable), ADDED atomically:
  *     {sum Delta c, volume clamped away in receiving cells, sum Delta e,
  *      sum c_out, sum e_out}
+ *   workspace: device scratch of at least vof_shift_workspace_bytes(g)
+ *     bytes, 256-byte aligned, overlapping no other argument; owned by the
+ *     caller, contents need not be initialised, busy until the launches on
+ *     `stream` complete.
+ * Returns VOF_EINVAL for a bad grid, null or overlapping arrays, a missing,
+ * short or misaligned workspace; VOF_ECUDA if a launch fails.
  */
+VOF_API size_t vof_shift_workspace_bytes(const vof_grid* g);
 VOF_API vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
                                   double* e_out, const double* dd, double dd_uniform, uint8_t* state, double* diag,
-                                  void* stream);
+                                  void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * One full time step on the caller's stream: zero the frozen state, three
@@ -187,8 +194,9 @@ VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const doubl
  * minus the workspace: the scratch space is one fixed 24 MiB array that every
  * GPU loading the library keeps until the process exits.
  *   - grids above VOF_NOALLOC_MAX_CELLS cells, or whose step workspace
- *     (vof_step_workspace_bytes) exceeds the array -- only grids narrower
- *     than 32 cells in x can -- return VOF_EINVAL, nothing launched;
+ *     (vof_step_workspace_bytes) exceeds the array -- only grids with fewer
+ *     than 8 cells along some axis can -- return VOF_EINVAL, nothing
+ *     launched;
  *   - all calls on a device share the array: calls whose kernels overlap on
  *     the GPU race (order them on one stream or synchronise in between);
  *   - the array keeps the previous call's contents; the step clears what must

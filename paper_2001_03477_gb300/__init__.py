@@ -95,7 +95,7 @@ def lib():
             "vof_advect_sweep_y": [G, P, P, P, P, P, D, P, P, P, P, P, S, P],
             "vof_advect_sweep_z": [G, P, P, P, P, P, D, P, P, P, P, P, S, P],
             "energy_advect_consistent": [G, I, P, P, P, P, P, P, D, P, P, P],
-            "vof_phase_change_shift": [G, P, P, P, P, P, D, P, P, P],
+            "vof_phase_change_shift": [G, P, P, P, P, P, D, P, P, P, S, P],
             "vof_step": [G, P, P, P, P, P, D, L_, P, D, P, P, S, P],
         }
         for name, args in sig.items():
@@ -108,6 +108,8 @@ def lib():
         L.vof_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.vof_sweep_workspace_bytes.argtypes = [G]
         L.vof_sweep_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_shift_workspace_bytes.argtypes = [G]
+        L.vof_shift_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_workspace_bytes.argtypes = [G]
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_get_device_status.argtypes = []
@@ -168,18 +170,31 @@ def vof_sweep_workspace_bytes(g: Grid) -> int:
     return int(lib().vof_sweep_workspace_bytes(ctypes.byref(cg)))
 
 
+def vof_shift_workspace_bytes(g: Grid) -> int:
+    cg = g.c_struct()
+    return int(lib().vof_shift_workspace_bytes(ctypes.byref(cg)))
+
+
 _ws_cache = {}
 
 
-def sweep_workspace(g: Grid, device=None):
-    """A cached scratch buffer (torch allocation) for the stand-alone sweeps."""
+def _cached_workspace(nb, device):
     import torch
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    nb = vof_sweep_workspace_bytes(g)
     key = (dev, nb)
     if key not in _ws_cache:
         _ws_cache[key] = torch.empty(nb, dtype=torch.uint8, device=dev)
     return _ws_cache[key]
+
+
+def sweep_workspace(g: Grid, device=None):
+    """A cached scratch buffer (torch allocation) for the stand-alone sweeps."""
+    return _cached_workspace(vof_sweep_workspace_bytes(g), device)
+
+
+def shift_workspace(g: Grid, device=None):
+    """A cached scratch buffer (torch allocation) for the stand-alone shift."""
+    return _cached_workspace(vof_shift_workspace_bytes(g), device)
 
 
 def _sweep(name, g, c_in, e_in, c_out, e_out, uf, dt, state, theta, flux_out, diag, workspace, stream):
@@ -228,13 +243,17 @@ def energy_advect_consistent(g, axis, c_before, c_after, e_in, e_out, flux_F, u_
 
 
 def vof_phase_change_shift(g, c_in, e_in, c_out, e_out, dd=None, dd_uniform=0.0, state=None, diag=None,
-                           stream=None):
+                           workspace=None, stream=None):
     cg = g.c_struct()
+    if workspace is None:
+        workspace = shift_workspace(g, c_in.device)
+    nbytes = workspace.numel() * workspace.element_size()
     _check("vof_phase_change_shift",
            lib().vof_phase_change_shift(ctypes.byref(cg), _ptr(c_in, _f64(), "c_in"), _ptr(e_in, _f64(), "e_in"),
                                         _ptr(c_out, _f64(), "c_out"), _ptr(e_out, _f64(), "e_out"),
                                         _ptr(dd, _f64(), "dd"), float(dd_uniform), _ptr(state, _u8(), "state"),
-                                        _ptr(diag, _f64(), "diag"), _stream(stream)))
+                                        _ptr(diag, _f64(), "diag"), _ptr(workspace, None, "workspace"),
+                                        ctypes.c_size_t(nbytes), _stream(stream)))
 
 
 def vof_step_workspace_bytes(g: Grid) -> int:

@@ -155,21 +155,34 @@ vof_status energy_advect_consistent(const vof_grid* g, int axis, const double* c
                                    (cudaStream_t)stream));
 }
 
+size_t vof_shift_workspace_bytes(const vof_grid* g) {
+  if (!grid_ok(g)) return 0;
+  return shift_scratch_bytes(to_dev(g, 0.0));
+}
+
 vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const double* e_in, double* c_out,
                                   double* e_out, const double* dd, double dd_uniform, uint8_t* state, double* diag,
-                                  void* stream) {
-  if (!grid_ok(g) || !c_in || !e_in || !c_out || !e_out) return VOF_EINVAL;
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+  if (!grid_ok(g) || !c_in || !e_in || !c_out || !e_out || !workspace) return VOF_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
+  const GridDev d = to_dev(g, 0.0);
+  const size_t need = shift_scratch_bytes(d);
+  if (workspace_bytes < need) return VOF_EINVAL;
   size_t B = cells(g) * 8;
   if (overlap(c_in, B, c_out, B) || overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) ||
       overlap(e_in, B, c_out, B) || overlap(c_out, B, e_out, B))
     return VOF_EINVAL;
+  if (overlap(workspace, need, c_in, B) || overlap(workspace, need, c_out, B) || overlap(workspace, need, e_in, B) ||
+      overlap(workspace, need, e_out, B) || (dd && overlap(workspace, need, dd, B)) ||
+      (state && overlap(workspace, need, state, cells(g))) || (diag && overlap(workspace, need, diag, 5 * 8)))
+    return VOF_EINVAL;
   SumOut so{nullptr, 5, diag};
-  return cuda_status(
-      launch_shift(to_dev(g, 0.0), c_in, e_in, c_out, e_out, dd, dd_uniform, state, so, (cudaStream_t)stream));
+  return cuda_status(launch_shift(d, c_in, e_in, c_out, e_out, dd, dd_uniform, state, carve_shift_scratch(d, workspace),
+                                  so, (cudaStream_t)stream));
 }
 
-// workspace layout: c2 | e2 | theta | state | partials (3 sweeps x 1, shift x 5)
-// | sweep scratch (reused by the three sweeps)
+// workspace layout: c2 | e2 | theta | state | partials (3 sweeps x 1,
+// 3 shift kernels x 5) | scratch (reused by the three sweeps, then the shift)
 struct StepLayout {
   size_t off_c2, off_e2, off_th, off_st, off_ps, off_sh, off_sw, total;
   int nb_sw[3], nb_sh;
@@ -191,8 +204,9 @@ static StepLayout step_layout(const vof_grid* g) {
   }
   L.nb_sh = shift_blocks(d);
   L.off_sh = L.off_ps + align256(nsw * 8);
-  L.off_sw = L.off_sh + align256((size_t)L.nb_sh * 5 * 8);
-  L.total = L.off_sw + align256(sweep_scratch_bytes(d));
+  L.off_sw = L.off_sh + align256((size_t)3 * L.nb_sh * 5 * 8);
+  const size_t sw = sweep_scratch_bytes(d), sh = shift_scratch_bytes(d);
+  L.total = L.off_sw + align256(sw > sh ? sw : sh);
   return L;
 }
 
@@ -242,13 +256,13 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
   }
   // after 3 sweeps the state sits in the workspace; the shift writes back
   SumOut so{psh, 5, nullptr};
-  err = launch_shift(d, src_c, src_e, c, e, dd, dd_uniform, nullptr, so, st);
+  err = launch_shift(d, src_c, src_e, c, e, dd, dd_uniform, nullptr, carve_shift_scratch(d, ws + L.off_sw), so, st);
   if (err != cudaSuccess) return cuda_status(err);
   if (sums) {
     // sums[0..1] = sum c, sum e; sums[2] = clip; sums[3..5] = shift diagnostics
-    err = launch_reduce(psh, L.nb_sh, 5, 3, 2, sums, st);
+    err = launch_reduce(psh, 3 * L.nb_sh, 5, 3, 2, sums, st);
     if (err == cudaSuccess) err = launch_reduce(ps, (int)poff, 1, 0, 1, sums + 2, st);
-    if (err == cudaSuccess) err = launch_reduce(psh, L.nb_sh, 5, 0, 3, sums + 3, st);
+    if (err == cudaSuccess) err = launch_reduce(psh, 3 * L.nb_sh, 5, 0, 3, sums + 3, st);
     if (err != cudaSuccess) return cuda_status(err);
   }
   return VOF_OK;

@@ -46,7 +46,22 @@ size_t sweep_scratch_bytes(const GridDev& g);
 SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* partials, double* diag);
 
 int sweep_blocks(int axis, const GridDev& g);
+
+// Scratch of the shift: per-warp lists of moving mixed cells with their
+// counts, and the plane (m0, m1, m2, alpha) and shift |m|_2 dd of every
+// listed cell, stored densely at the cell's index.
+struct ShiftScratch {
+  uint32_t* list;
+  int* count;
+  double* plane;  // [N][4]
+  double* shift;  // [N]
+};
+
+// CTAs of each of the three shift kernels; their partial sums take
+// 3 * shift_blocks rows of the SumOut
 int shift_blocks(const GridDev& g);
+size_t shift_scratch_bytes(const GridDev& g);
+ShiftScratch carve_shift_scratch(const GridDev& g, void* ws);
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
@@ -57,7 +72,8 @@ cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, co
                           double* theta, cudaStream_t st);
 
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
-                         const double* dd, double dd_uniform, uint8_t* state, SumOut sums, cudaStream_t st);
+                         const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut sums,
+                         cudaStream_t st);
 
 cudaError_t launch_reconstruct(const GridDev& g, const double* c, double* m, double* alpha, uint8_t* mixed,
                                cudaStream_t st);

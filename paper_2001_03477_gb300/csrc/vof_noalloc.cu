@@ -13,8 +13,8 @@
 //
 // Limits and rules for callers:
 //   * the grid may have at most VOF_NOALLOC_MAX_CELLS cells (64^3), and its
-//     step workspace must fit the array (it does for every such grid at
-//     least 32 cells wide in x; much thinner grids need more list space);
+//     step workspace must fit the array (it does for every such grid with
+//     at least 8 cells along each axis; thinner grids need more list space);
 //     other grids are rejected with VOF_EINVAL before anything is launched;
 //   * every GPU on which the library is loaded holds the array (24 MiB)
 //     until the process exits;

@@ -3,14 +3,14 @@
 // alpha^{n+1}) with the energy change Delta e = Delta c (C_pl - C_pg) T_Gamma
 // (end of Sec. 3.4.1), and the stand-alone PLIC reconstruction (Sec. 3.2).
 //
-// Shift, one fused pass: the CTA stages c with a halo of 2, reconstructs the
-// plane (MYC normal + plane constant) of every moving mixed cell of the tile
-// and its 1-cell ring, then each cell of the tile
+// The shift moves every mixed cell's plane along its normal:
 //   * mixed:  alpha* = alpha + |m|_2 dd capped to the cell, c = V(m, alpha*);
 //   * pure, of the receding phase: takes the largest volume swept inside it
 //     by the shifted plane of an adjacent mixed cell extended across the
 //     shared face, edge or corner (the cap's cut-off movement carried on in
 //     the direction the interface moves).
+// Only cells at the interface do work, so the kernels after the first one
+// visit a compact list of the moving mixed cells instead of the grid.
 #include "vof_launch.h"
 
 namespace vofgb {
@@ -44,212 +44,237 @@ __device__ __forceinline__ void block_sums_sh(double (&v)[K], SumOut out, int bl
   }
 }
 
-// Shift kernel: a CTA owns a 32 x kShTY column of cells and walks kShSegZ planes
-// along z.  Shared-memory rings hold c of planes z..z+2 (halo 2 in x and y)
-// and the plane data (m, alpha, |m|_2 dd) of the moving mixed cells of
-// planes z-1..z+1 (halo 1); each thread then settles its cell of plane z.
-constexpr int kShSegZ = 8;    // short z segments and small CTAs: the FP64 work of
-constexpr int kShTY = 4;      // the interface is spread over many CTAs
-constexpr int kShT = 32 * kShTY;
-constexpr int kRX = kShBX + 4, kRY = kShTY + 4;   // c plane with halo 2
-constexpr int kPX = kShBX + 2, kPY = kShTY + 2;   // plane-data region with halo 1
-constexpr int kRP = kRX * kRY, kPP = kPX * kPY;
+// ---------------------------------------------------------------------------
+// Shift in three kernels.
+//   SA (stream): copies c, e to the output, sums them, and lists the moving
+//      mixed cells per warp (256 consecutive cells per warp, fixed order);
+//   SM (planes): per moving mixed cell, the plane (MYC normal, plane
+//      constant -- by bisection when c is within 1e-3 of 0 or 1, where the
+//      plane is extrapolated into neighbours), the shift |m|_2 dd, and the
+//      cell's own shifted volume;
+//   SR (receivers): per moving mixed cell, the pure neighbours of the
+//      receding phase it is the first to reach in the scan order; for each,
+//      the largest volume swept in it by the extended planes of all its
+//      moving mixed neighbours.
+// Sums are per-CTA partials {dc, clamped, de, c, e}.
+// ---------------------------------------------------------------------------
+constexpr int kWarpCells = 256;
 
-struct ShiftSmem {
-  double c[3][kRP];
-  double pd[3][5][kPP];   // m0, m1, m2, alpha, shift
-  int any[3];
-};
-
-// Plane of a moving mixed cell from its 3x3x3 stencil (three shared-memory
-// rows of the c ring, each pointer at the cell's own column): MYC normal,
-// plane constant, shift |m|_2 dd.  Writes m0, m1, m2, alpha at out[0],
-// out[kPP], out[2 kPP], out[3 kPP]; returns the shift.
-__device__ __noinline__ double moving_plane(const double* zm, const double* z0p, const double* zp, double ct,
-                                            double ddv, double* out) {
-  double st[27];
-  const double* rows[3] = {zm, z0p, zp};
-#pragma unroll
-  for (int oz = 0; oz < 3; ++oz)
-#pragma unroll
-    for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-      for (int ox = 0; ox < 3; ++ox) st[(oz * 3 + oy) * 3 + ox] = rows[oz][(oy - 1) * kRX + (ox - 1)];
-  double m[3];
-  myc_normal(st, m);
-  // nearly empty or full cells: alpha(c) is ill-conditioned and this plane
-  // is extrapolated into the neighbours, so take the bisection constant
-  const bool edge = dbits(ct) < 0x3F50624DD2F1A9FCLL /* 1e-3 */ || dbits(ct) > 0x3FEFF7CED916872BLL /* 0.999 */;
-  const double al = edge ? plane_alpha_bisect(m[0], m[1], m[2], ct) : plane_alpha(m[0], m[1], m[2], ct);
-  const double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-  out[0] = m[0];
-  out[kPP] = m[1];
-  out[2 * kPP] = m[2];
-  out[3 * kPP] = al;
-  return mn2 * ddv;
+__device__ __forceinline__ void decode(const GridDev& g, size_t id, int& x, int& y, int& z) {
+  x = (int)(id % (size_t)g.n[0]);
+  const size_t r = id / (size_t)g.n[0];
+  y = (int)(r % (size_t)g.n[1]);
+  z = (int)(r / (size_t)g.n[1]);
 }
 
-// Largest volume swept inside a pure cell by the shifted plane of an
-// adjacent moving mixed cell extended into it (26 neighbours, z outer, x
-// inner; neighbours beyond a zero-gradient boundary do not count).
-// p[0..2]: plane data of planes z-1, z, z+1 (layout [5][kPP]).
-__device__ __noinline__ double extended_sweep(GridDev g, const double* pm, const double* p0, const double* pp, int q,
-                                              int gx, int gy, int z, bool full) {
-  const double* pl[3] = {pm, p0, pp};
-  double best = 0.0;
-  for (int oz = -1; oz <= 1; ++oz) {
-    if (g.bc[2] != 0 && (z + oz < 0 || z + oz >= g.n[2])) continue;
-    const double* P = pl[oz + 1];
-    for (int oy = -1; oy <= 1; ++oy) {
-      if (g.bc[1] != 0 && (gy + oy < 0 || gy + oy >= g.n[1])) continue;
-      for (int ox = -1; ox <= 1; ++ox) {
-        if (!ox && !oy && !oz) continue;
-        if (g.bc[0] != 0 && (gx + ox < 0 || gx + ox >= g.n[0])) continue;
-        const int qn = q + oy * kPX + ox;
-        const double sft = P[4 * kPP + qn];
-        if (!dnz(sft)) continue;
-        if (dlt0(sft) != full) continue;
-        const double m0 = P[qn], m1 = P[kPP + qn], m2 = P[2 * kPP + qn], al = P[3 * kPP + qn];
-        const double shiftv = -((m0 * (double)(-ox) + m1 * (double)(-oy)) + m2 * (double)(-oz));
-        const double a_old = al + shiftv;
-        const double a_new = (al + sft) + shiftv;
-        // the extended plane stays outside this cell (both volumes are
-        // exactly 1, or exactly 0): nothing is swept.  The 1e-9 margin keeps
-        // the test clear of the rounding of the volume function's own test.
-        double lo = 0.0, hi = 0.0;
-        if (m0 < 0.0) lo += m0; else hi += m0;
-        if (m1 < 0.0) lo += m1; else hi += m1;
-        if (m2 < 0.0) lo += m2; else hi += m2;
-        if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
-        const double sw = volume(m0, m1, m2, a_new) - volume(m0, m1, m2, a_old);
-        if (fabs(sw) > fabs(best)) best = sw;
-      }
+__device__ __forceinline__ size_t cell_id(const GridDev& g, int x, int y, int z) {
+  return ((size_t)z * g.n[1] + y) * g.n[0] + x;
+}
+
+__global__ void __launch_bounds__(256)
+k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
+               SumOut sums) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const int lane = threadIdx.x & 31;
+  const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  uint32_t* list = sc.list + w * kWarpCells;
+  int n = 0;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const bool uni_moving = dnz(dd_uniform);
+  for (int it = 0; it < kWarpCells / 32; ++it) {
+    const size_t id = w * kWarpCells + (size_t)it * 32 + lane;
+    const bool ok = id < N;
+    double c = 0.0, e = 0.0;
+    if (ok) {
+      c = __ldg(c_in + id);
+      e = __ldg(e_in + id);
+      c_out[id] = c;
+      e_out[id] = e;
+      acc[3] += c;
+      acc[4] += e;
     }
+    bool moving = ok && is_mixed_b(c, g);
+    if (moving) moving = dd ? dnz(__ldg(dd + id)) : uni_moving;
+    const unsigned m = __ballot_sync(0xffffffffu, moving);
+    if (moving) list[n + __popc(m & ((1u << lane) - 1u))] = (uint32_t)id;
+    n += __popc(m);
   }
-  return best;
+  if (lane == 0) sc.count[w] = n;
+  block_sums_sh<5>(acc, sums, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kShT, 4)
-k_shift(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-        double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, SumOut sums) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ShiftSmem& S = *reinterpret_cast<ShiftSmem*>(smem_raw);
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-  const int x0 = blockIdx.x * kShBX, y0 = blockIdx.y * kShTY;
-  const int z0 = blockIdx.z * kShSegZ, z1 = min(z0 + kShSegZ, nz);
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool cell_ok = gx < nx && gy < ny;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // sum dc, unplaced, sum de, sum c, sum e
-
-  auto load_plane = [&](int z, int slot) {
-    const int zz = map_idx(z, nz, g.bc[2]);
-    for (int q = tid; q < kRP; q += kShT) {
-      const int lx = q % kRX, ly = q / kRX;
-      const int xx = map_idx(x0 + lx - 2, nx, g.bc[0]);
-      const int yy = map_idx(y0 + ly - 2, ny, g.bc[1]);
-      S.c[slot][q] = __ldg(c_in + ((size_t)zz * ny + yy) * nx + xx);
-    }
-  };
-  // plane data of plane z (ring slot z % 3) from c planes z-1, z, z+1
-  auto plane_data = [&](int z) {
-    const int sl = ((z % 3) + 3) % 3;
-    const int sm1 = ((z - 1) % 3 + 3) % 3, sp1 = ((z + 1) % 3 + 3) % 3;
-    int any = 0;
-    for (int q = tid; q < kPP; q += kShT) {
-      const int px = q % kPX, py = q / kPX;
-      const int rq = (py + 1) * kRX + (px + 1);
-      const double ct = S.c[sl][rq];
-      double sft = 0.0;
-      if (is_mixed_b(ct, g)) {
-        double ddv = dd_uniform;
-        if (dd) {
-          const int xx = map_idx(x0 + px - 1, nx, g.bc[0]);
-          const int yy = map_idx(y0 + py - 1, ny, g.bc[1]);
-          const int zz = map_idx(z, nz, g.bc[2]);
-          ddv = __ldg(dd + ((size_t)zz * ny + yy) * nx + xx);
-        }
-        if (dnz(ddv)) {
-          sft = moving_plane(S.c[sm1] + rq, S.c[sl] + rq, S.c[sp1] + rq, ct, ddv, &S.pd[sl][0][q]);
-          any = 1;
+__global__ void __launch_bounds__(256)
+k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
+               long long nwarps, SumOut sums) {
+  const int lane = threadIdx.x & 31;
+  const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if ((long long)w < nwarps) {
+    const int cnt = sc.count[w];
+    const uint32_t* list = sc.list + w * kWarpCells;
+    for (int i = lane; i < cnt; i += 32) {
+      const size_t id = list[i];
+      int x, y, z;
+      decode(g, id, x, y, z);
+      double st[27];
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz) {
+        const int zz = map_idx(z + oz - 1, g.n[2], g.bc[2]);
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+          const int yy = map_idx(y + oy - 1, g.n[1], g.bc[1]);
+#pragma unroll
+          for (int ox = 0; ox < 3; ++ox) {
+            const int xx = map_idx(x + ox - 1, g.n[0], g.bc[0]);
+            st[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_id(g, xx, yy, zz));
+          }
         }
       }
-      S.pd[sl][4][q] = sft;
-    }
-    if (__any_sync(0xffffffffu, any) && (tid & 31) == 0) atomicOr(&S.any[sl], 1);
-  };
-
-  // prologue: c planes z0-1, z0, z0+1 and plane data of z0-1 (needs z0-2)
-  if (tid < 3) S.any[tid] = 0;
-  load_plane(z0 - 2, ((z0 - 2) % 3 + 3) % 3);
-  load_plane(z0 - 1, ((z0 - 1) % 3 + 3) % 3);
-  load_plane(z0, ((z0) % 3 + 3) % 3);
-  __syncthreads();
-  plane_data(z0 - 1);
-  __syncthreads();
-  // now the slot of z0-2 is free: load z0+1, then plane data of z0
-  load_plane(z0 + 1, ((z0 + 1) % 3 + 3) % 3);
-  __syncthreads();
-  plane_data(z0);
-  __syncthreads();
-
-  for (int z = z0; z < z1; ++z) {
-    // own cell's energy, issued before the plane work to hide its latency
-    const size_t id = ((size_t)z * ny + gy) * nx + gx;
-    const double ev = cell_ok ? __ldg(e_in + id) : 0.0;
-    // c of plane z+2 replaces plane z-1; plane data of z+1 replaces z-2
-    const int sz2 = ((z + 2) % 3 + 3) % 3;
-    if (tid == 0) S.any[((z + 1) % 3 + 3) % 3] = 0;
-    load_plane(z + 2, sz2);
-    __syncthreads();
-    plane_data(z + 1);
-    __syncthreads();
-    if (cell_ok) {
-      const int sl = ((z % 3) + 3) % 3;
-      const int q = (ty + 1) * kPX + (tx + 1);
-      const double ct = S.c[sl][(ty + 2) * kRX + (tx + 2)];
-      double cn = ct;
-      if (is_mixed_b(ct, g)) {
-        const double sft = S.pd[sl][4][q];
-        if (dnz(sft)) {
-          const double m0 = S.pd[sl][0][q], m1 = S.pd[sl][1][q], m2 = S.pd[sl][2][q], al = S.pd[sl][3][q];
-          double lo = 0.0, hi = 0.0;
-          if (m0 < 0.0) lo += m0; else hi += m0;
-          if (m1 < 0.0) lo += m1; else hi += m1;
-          if (m2 < 0.0) lo += m2; else hi += m2;
-          double ast = al + sft;
-          if (ast < lo) ast = lo;
-          if (ast > hi) ast = hi;
-          cn = volume(m0, m1, m2, ast);
-        }
-      } else if (S.any[0] | S.any[1] | S.any[2]) {
-        const bool full = is_full_b(ct, g);
-        const double* pl[3] = {&S.pd[((z - 1) % 3 + 3) % 3][0][0], &S.pd[((z % 3) + 3) % 3][0][0],
-                               &S.pd[((z + 1) % 3 + 3) % 3][0][0]};
-        const double best = extended_sweep(g, pl[0], pl[1], pl[2], q, gx, gy, z, full);
-        if (dnz(best)) {
-          const double v = ct + best;
-          const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
-          if (!deq(v, vc)) acc[1] += v - vc;
-          cn = vc;
-        }
-      }
-      double en = ev;
+      const double ct = st[13];
+      double m[3];
+      myc_normal(st, m);
+      const bool edge = dbits(ct) < 0x3F50624DD2F1A9FCLL /* 1e-3 */ || dbits(ct) > 0x3FEFF7CED916872BLL /* 0.999 */;
+      const double al = edge ? plane_alpha_bisect(m[0], m[1], m[2], ct) : plane_alpha(m[0], m[1], m[2], ct);
+      const double ddv = dd ? __ldg(dd + id) : dd_uniform;
+      const double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+      const double sft = mn2 * ddv;
+      double4 pl;
+      pl.x = m[0]; pl.y = m[1]; pl.z = m[2]; pl.w = al;
+      reinterpret_cast<double4*>(sc.plane)[id] = pl;
+      sc.shift[id] = sft;
+      // own shift, capped to the cell
+      double lo = 0.0, hi = 0.0;
+      if (m[0] < 0.0) lo += m[0]; else hi += m[0];
+      if (m[1] < 0.0) lo += m[1]; else hi += m[1];
+      if (m[2] < 0.0) lo += m[2]; else hi += m[2];
+      double ast = al + sft;
+      if (ast < lo) ast = lo;
+      if (ast > hi) ast = hi;
+      const double cn = volume(m[0], m[1], m[2], ast);
       if (!same_bits_dev(cn, ct)) {
         const double dc = cn - ct;
         const double de = dc * (g.Cp_l - g.Cp_g) * g.T_sat;
-        en = ev + de;
+        c_out[id] = cn;
+        e_out[id] = __ldg(e_in + id) + de;
         acc[0] += dc;
         acc[2] += de;
+        acc[3] += dc;  // sum c_out = sum c_in + sum dc
+        acc[4] += de;
       }
-      c_out[id] = cn;
-      e_out[id] = en;
-      acc[3] += cn;
-      acc[4] += en;
     }
-    __syncthreads();
   }
-  block_sums_sh<5>(acc, sums, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+  block_sums_sh<5>(acc, sums, blockIdx.x);
+}
+
+// moving mixed cell whose shift has the sign that reaches a receiver of this kind
+__device__ __forceinline__ bool reaches(const GridDev& g, const double* __restrict__ c_in,
+                                        const double* __restrict__ dd, double dd_uniform, size_t q, bool full) {
+  if (!is_mixed_b(__ldg(c_in + q), g)) return false;
+  const double ddv = dd ? __ldg(dd + q) : dd_uniform;
+  return dnz(ddv) && (dlt0(ddv) == full);
+}
+
+__global__ void __launch_bounds__(256)
+k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in,
+                  double* __restrict__ c_out, double* __restrict__ e_out, const double* __restrict__ dd,
+                  double dd_uniform, ShiftScratch sc, long long nwarps, SumOut sums) {
+  const int lane = threadIdx.x & 31;
+  const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if ((long long)w < nwarps) {
+    const int cnt = sc.count[w];
+    const uint32_t* list = sc.list + w * kWarpCells;
+    for (int i = lane; i < cnt; i += 32) {
+      const size_t qid = list[i];
+      int qx, qy, qz;
+      decode(g, qid, qx, qy, qz);
+      const double qdd = dd ? __ldg(dd + qid) : dd_uniform;
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            if (!ox && !oy && !oz) continue;
+            int px = qx + ox, py = qy + oy, pz = qz + oz;
+            if (g.bc[0] != 0 && (px < 0 || px >= nx)) continue;
+            if (g.bc[1] != 0 && (py < 0 || py >= ny)) continue;
+            if (g.bc[2] != 0 && (pz < 0 || pz >= nz)) continue;
+            px = map_idx(px, nx, g.bc[0]);
+            py = map_idx(py, ny, g.bc[1]);
+            pz = map_idx(pz, nz, g.bc[2]);
+            const size_t pid = cell_id(g, px, py, pz);
+            const double cp = __ldg(c_in + pid);
+            if (is_mixed_b(cp, g)) continue;
+            const bool full = is_full_b(cp, g);
+            if (dlt0(qdd) != full) continue;
+            // this receiver is settled by its first reaching neighbour offset
+            // in the scan order (z outer, x inner), which must be the offset
+            // back to this cell (on periodic axes of 1 or 2 cells several
+            // offsets lead to the same cell; only one of them settles it)
+            int first = -1;
+            for (int rz = -1; rz <= 1 && first < 0; ++rz)
+              for (int ry = -1; ry <= 1 && first < 0; ++ry)
+                for (int rx = -1; rx <= 1 && first < 0; ++rx) {
+                  if (!rx && !ry && !rz) continue;
+                  int sx = px + rx, sy = py + ry, sz = pz + rz;
+                  if (g.bc[0] != 0 && (sx < 0 || sx >= nx)) continue;
+                  if (g.bc[1] != 0 && (sy < 0 || sy >= ny)) continue;
+                  if (g.bc[2] != 0 && (sz < 0 || sz >= nz)) continue;
+                  const size_t sid =
+                      cell_id(g, map_idx(sx, nx, g.bc[0]), map_idx(sy, ny, g.bc[1]), map_idx(sz, nz, g.bc[2]));
+                  if (reaches(g, c_in, dd, dd_uniform, sid, full)) first = ((rz + 1) * 3 + (ry + 1)) * 3 + (rx + 1);
+                }
+            if (first != ((1 - oz) * 3 + (1 - oy)) * 3 + (1 - ox)) continue;
+            // settle the receiver: largest sweep over its reaching neighbours
+            double best = 0.0;
+            for (int rz = -1; rz <= 1; ++rz)
+              for (int ry = -1; ry <= 1; ++ry)
+                for (int rx = -1; rx <= 1; ++rx) {
+                  if (!rx && !ry && !rz) continue;
+                  int sx = px + rx, sy = py + ry, sz = pz + rz;
+                  if (g.bc[0] != 0 && (sx < 0 || sx >= nx)) continue;
+                  if (g.bc[1] != 0 && (sy < 0 || sy >= ny)) continue;
+                  if (g.bc[2] != 0 && (sz < 0 || sz >= nz)) continue;
+                  const size_t sid =
+                      cell_id(g, map_idx(sx, nx, g.bc[0]), map_idx(sy, ny, g.bc[1]), map_idx(sz, nz, g.bc[2]));
+                  if (!reaches(g, c_in, dd, dd_uniform, sid, full)) continue;
+                  const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
+                  const double sft = sc.shift[sid];
+                  const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
+                  // the receiver sits at offset -(rx, ry, rz) from the source
+                  const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
+                  const double a_old = al + shiftv;
+                  const double a_new = (al + sft) + shiftv;
+                  double lo = 0.0, hi = 0.0;
+                  if (m0 < 0.0) lo += m0; else hi += m0;
+                  if (m1 < 0.0) lo += m1; else hi += m1;
+                  if (m2 < 0.0) lo += m2; else hi += m2;
+                  // the extended plane stays outside the receiver: both
+                  // volumes are exactly 1 (or 0); the margin clears rounding
+                  if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
+                  const double sw = volume(m0, m1, m2, a_new) - volume(m0, m1, m2, a_old);
+                  if (fabs(sw) > fabs(best)) best = sw;
+                }
+            if (dnz(best)) {
+              const double v = cp + best;
+              const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
+              if (!deq(v, vc)) acc[1] += v - vc;
+              if (!same_bits_dev(vc, cp)) {
+                const double dc = vc - cp;
+                const double de = dc * (g.Cp_l - g.Cp_g) * g.T_sat;
+                c_out[pid] = vc;
+                e_out[pid] = __ldg(e_in + pid) + de;
+                acc[0] += dc;
+                acc[2] += de;
+                acc[3] += dc;
+                acc[4] += de;
+              }
+            }
+          }
+    }
+  }
+  block_sums_sh<5>(acc, sums, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kShThreads)
@@ -299,27 +324,54 @@ static dim3 sh_grid(const GridDev& g) {
   return dim3((g.n[0] + kShBX - 1) / kShBX, (g.n[1] + kShBY - 1) / kShBY, (g.n[2] + kShBZ - 1) / kShBZ);
 }
 
-static dim3 shm_grid(const GridDev& g) {
-  return dim3((g.n[0] + kShBX - 1) / kShBX, (g.n[1] + kShTY - 1) / kShTY, (g.n[2] + kShSegZ - 1) / kShSegZ);
+static long long shift_warps(const GridDev& g) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  return (long long)((N + kWarpCells - 1) / kWarpCells);
 }
 
-int shift_blocks(const GridDev& g) {
-  dim3 gr = shm_grid(g);
-  return (int)(gr.x * gr.y * gr.z);
+// CTAs of each shift kernel (8 warps of 256 cells)
+int shift_blocks(const GridDev& g) { return (int)((shift_warps(g) + 7) / 8); }
+
+size_t shift_scratch_bytes(const GridDev& g) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const size_t nw = (size_t)shift_warps(g);
+  size_t b = 0;
+  b += (nw * kWarpCells * 4 + 255) & ~(size_t)255;  // lists
+  b += (nw * 4 + 255) & ~(size_t)255;               // counts
+  b += (N * 32 + 255) & ~(size_t)255;               // planes
+  b += (N * 8 + 255) & ~(size_t)255;                // shifts
+  return b;
+}
+
+ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const size_t nw = (size_t)shift_warps(g);
+  char* b = static_cast<char*>(ws);
+  ShiftScratch s;
+  s.list = reinterpret_cast<uint32_t*>(b);
+  b += (nw * kWarpCells * 4 + 255) & ~(size_t)255;
+  s.count = reinterpret_cast<int*>(b);
+  b += (nw * 4 + 255) & ~(size_t)255;
+  s.plane = reinterpret_cast<double*>(b);
+  b += (N * 32 + 255) & ~(size_t)255;
+  s.shift = reinterpret_cast<double*>(b);
+  return s;
 }
 
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
-                         const double* dd, double dd_uniform, uint8_t* state, SumOut sums, cudaStream_t st) {
-  static bool attr_done[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const size_t smem = sizeof(ShiftSmem);
-  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done[dev] = true;
+                         const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut sums,
+                         cudaStream_t st) {
+  const long long nw = shift_warps(g);
+  const unsigned nb = (unsigned)((nw + 7) / 8);
+  // the three kernels write partials to consecutive regions of nb CTAs
+  SumOut s0 = sums, s1 = sums, s2 = sums;
+  if (sums.partials) {
+    s1.partials = sums.partials + (size_t)nb * sums.stride;
+    s2.partials = sums.partials + (size_t)2 * nb * sums.stride;
   }
-  k_shift<<<shm_grid(g), dim3(kShBX, kShTY), smem, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sums);
+  k_shift_stream<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, s0);
+  k_shift_planes<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, nw, s1);
+  k_shift_receivers<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, nw, s2);
   cudaError_t err = cudaGetLastError();
   if (err == cudaSuccess && state)
     err = cudaMemsetAsync(state, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);

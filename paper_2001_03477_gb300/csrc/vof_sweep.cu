@@ -174,7 +174,8 @@ constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
 template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(32 * kWarpsA)
 k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all) {
+             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
+             int cap) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int n_t = AX == 1 ? g.n[2] : g.n[1];
@@ -189,8 +190,8 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
   const size_t cbase = AX == 1 ? (size_t)ts * ny * nx + xs : (size_t)ts * nx + xs;
   const size_t sub = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * kWarpsA * gridDim.x + (size_t)warp * gridDim.x +
                      blockIdx.x;
-  uint32_t* list = sc.list + sub * (size_t)(32 * kSegA);
-  uint32_t* mlist = sc.mlist + sub * (size_t)(32 * kSegA);
+  uint32_t* list = sc.list + sub * (size_t)cap;
+  uint32_t* mlist = sc.mlist + sub * (size_t)cap;
   int nlist = 0, nmixed = 0;
   // window: cells k .. k+3 (c, e), run = equal cells ending at k+3, and
   // whether cells k and k-1 differ from their predecessors
@@ -253,7 +254,8 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
 template <bool ENERGY>
 __global__ void __launch_bounds__(256)
 k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all) {
+             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
+             int cap) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int row = blockIdx.y * 8 + warp;  // row = z * ny + y
@@ -269,8 +271,8 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
     }
     return;
   }
-  uint32_t* list = sc.list + sub * (size_t)kSegRow;
-  uint32_t* mlist = sc.mlist + sub * (size_t)kSegRow;
+  uint32_t* list = sc.list + sub * (size_t)cap;
+  uint32_t* mlist = sc.mlist + sub * (size_t)cap;
   int nlist = 0, nmixed = 0;
   auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
   auto lde = [&](int X) { return ENERGY ? __ldg(e_in + rbase + map_idx(X, nx, bcx)) : 0.0; };
@@ -568,13 +570,13 @@ SweepPlan sweep_plan(int axis, const GridDev& g) {
   if (axis == 0) {
     p.gridA = dim3((g.n[0] + kSegRow - 1) / kSegRow, (g.n[1] * g.n[2] + 7) / 8, 1);
     p.blockA = dim3(32, 8, 1);
-    p.cap = kSegRow;
+    p.cap = g.n[0] < kSegRow ? g.n[0] : kSegRow;  // cells a warp covers
     p.nsub = (long long)p.gridA.x * p.gridA.y * 8;
   } else {
     const int n_t = axis == 1 ? g.n[2] : g.n[1];
     p.gridA = dim3((g.n[0] + 31) / 32, (n_t + kWarpsA - 1) / kWarpsA, (g.n[axis] + kSegA - 1) / kSegA);
     p.blockA = dim3(32, kWarpsA, 1);
-    p.cap = 32 * kSegA;
+    p.cap = (g.n[0] < 32 ? g.n[0] : 32) * (g.n[axis] < kSegA ? g.n[axis] : kSegA);
     p.nsub = (long long)p.gridA.x * p.gridA.y * p.gridA.z * kWarpsA;
   }
   p.gridB = (unsigned)((p.nsub + 7) / 8);
@@ -628,10 +630,11 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
                       double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
                       SweepScratch sc, int* status, cudaStream_t st) {
   if (AX == 0)
-    k_stream_row<ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc, flux_out != nullptr);
+    k_stream_row<ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc, flux_out != nullptr,
+                                                        p.cap);
   else
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
-                                                                          flux_out != nullptr);
+                                                                          flux_out != nullptr, p.cap);
   k_planes<<<p.gridB, 256, 0, st>>>(g, c_in, sc, (int)p.nsub, p.cap);
   k_active<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc,
                                                  (int)p.nsub, p.cap, status);

@@ -70,6 +70,12 @@ def test_host_validation_without_gpu(lib):
     # workspace too small
     assert lib.vof_step(ctypes.byref(cg), fake, ctypes.c_void_p(2 << 40), fake, fake, fake, 0.1, 0, nul, 0.0, nul,
                         ctypes.c_void_p(3 << 40), 16, nul) == P.VOF_EINVAL
+    # shift workspace missing, too small, misaligned or overlapping an output
+    shb = lib.vof_shift_workspace_bytes(ctypes.byref(cg))
+    ce, eo = ctypes.c_void_p(2 << 40), ctypes.c_void_p(6 << 40)
+    for w_, nb in ((nul, shb), (ws, shb - 8), (ctypes.c_void_p((5 << 40) + 16), shb), (ok_out, shb)):
+        assert lib.vof_phase_change_shift(ctypes.byref(cg), fake, ce, ok_out, eo, nul, 0.01, nul, nul, w_, nb,
+                                          nul) == P.VOF_EINVAL
     assert lib.vof_status_string(P.VOF_ECFL).decode() == "face CFL number above 1"
 
 
@@ -80,6 +86,9 @@ def test_workspace_size_scales(lib):
     assert a >= 32 ** 3 * 25 and b >= 64 ** 3 * 25 and b > 5 * a
     s = P.vof_sweep_workspace_bytes(P.Grid(64, 64, 64))
     assert 64 ** 3 * 12 <= s < b
+    # planes (32 B) and shifts (8 B) of every cell, plus the lists
+    sh = P.vof_shift_workspace_bytes(P.Grid(64, 64, 64))
+    assert 64 ** 3 * 44 <= sh < b
 
 
 def test_binding_refuses_cpu_tensors(lib):

@@ -11,6 +11,8 @@ bubble-growth workload the benchmark times.
 """
 import zlib
 
+import math
+
 import numpy as np
 import pytest
 
@@ -191,6 +193,10 @@ def test_shift(P, name):
         d = host(diag)
         assert abs(d[0] - dg[0]) <= 1e-11
         assert abs(d[1] - dg[1]) <= 1e-11
+        assert abs(d[2] - dg[2]) <= 1e-12 * max(1.0, abs(dg[2]))
+        # sums of the outputs (added by the three shift kernels)
+        assert abs(d[3] - math.fsum(co.ravel())) <= 1e-13 * max(1.0, abs(math.fsum(co.ravel())))
+        assert abs(d[4] - math.fsum(eo.ravel())) <= 1e-12 * max(1.0, abs(math.fsum(eo.ravel())))
 
 
 @pytest.mark.parametrize("name", CASES)
