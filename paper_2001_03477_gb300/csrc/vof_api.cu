@@ -182,7 +182,7 @@ vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const d
 }
 
 // workspace layout: c2 | e2 | theta | state | partials (3 sweeps x 1,
-// 3 shift kernels x 5) | scratch (reused by the three sweeps, then the shift)
+// 2 shift kernels x 5) | scratch (reused by the three sweeps, then the shift)
 struct StepLayout {
   size_t off_c2, off_e2, off_th, off_st, off_ps, off_sh, off_sw, total;
   int nb_sw[3], nb_sh;
@@ -204,7 +204,7 @@ static StepLayout step_layout(const vof_grid* g) {
   }
   L.nb_sh = shift_blocks(d);
   L.off_sh = L.off_ps + align256(nsw * 8);
-  L.off_sw = L.off_sh + align256((size_t)3 * L.nb_sh * 5 * 8);
+  L.off_sw = L.off_sh + align256((size_t)kShiftPartialSets * L.nb_sh * 5 * 8);
   const size_t sw = sweep_scratch_bytes(d), sh = shift_scratch_bytes(d);
   L.total = L.off_sw + align256(sw > sh ? sw : sh);
   return L;
@@ -260,9 +260,9 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
   if (err != cudaSuccess) return cuda_status(err);
   if (sums) {
     // sums[0..1] = sum c, sum e; sums[2] = clip; sums[3..5] = shift diagnostics
-    err = launch_reduce(psh, 3 * L.nb_sh, 5, 3, 2, sums, st);
+    err = launch_reduce(psh, kShiftPartialSets * L.nb_sh, 5, 3, 2, sums, st);
     if (err == cudaSuccess) err = launch_reduce(ps, (int)poff, 1, 0, 1, sums + 2, st);
-    if (err == cudaSuccess) err = launch_reduce(psh, 3 * L.nb_sh, 5, 0, 3, sums + 3, st);
+    if (err == cudaSuccess) err = launch_reduce(psh, kShiftPartialSets * L.nb_sh, 5, 0, 3, sums + 3, st);
     if (err != cudaSuccess) return cuda_status(err);
   }
   return VOF_OK;

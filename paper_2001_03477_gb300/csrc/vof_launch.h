@@ -29,8 +29,9 @@ struct SweepScratch {
   int* count;
   double* partial;
   double* diag;
-  uint32_t* mlist;  // per-warp lists of mixed cells
-  int* mcount;
+  uint32_t* mlist;  // per-warp staging lists of mixed cells
+  int* gcount;      // number of mixed cells (zeroed before kernel A)
+  uint32_t* gmix;   // grid-wide list of mixed cells, in no fixed order
   double* plane;    // [N][4]: m0, m1, m2, alpha of the listed mixed cells
 };
 
@@ -48,17 +49,25 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* p
 int sweep_blocks(int axis, const GridDev& g);
 
 // Scratch of the shift: per-warp lists of moving mixed cells with their
-// counts, and the plane (m0, m1, m2, alpha) and shift |m|_2 dd of every
-// listed cell, stored densely at the cell's index.
+// counts (fixed order), a grid-wide list of the same cells and one of the
+// receivers (no fixed order) with their counters, and per cell: the plane
+// (m0, m1, m2, alpha) and shift |m|_2 dd of a moving mixed cell, the mask of
+// receivers it settles, and the volume swept into a receiver.
 struct ShiftScratch {
   uint32_t* list;
   int* count;
+  int* counters;  // [0] non-edge cells, [1] edge cells, [2] receivers
+  uint32_t* gmix; // non-edge cells from the front, edge cells from the back
+  uint32_t* recv;
   double* plane;  // [N][4]
   double* shift;  // [N]
+  double* sweep;  // [N]
+  uint32_t* own;  // [N]
 };
 
-// CTAs of each of the three shift kernels; their partial sums take
-// 3 * shift_blocks rows of the SumOut
+// CTAs of the shift's stream and sums kernels; their partial sums take
+// kShiftPartialSets * shift_blocks rows of the SumOut
+constexpr int kShiftPartialSets = 2;
 int shift_blocks(const GridDev& g);
 size_t shift_scratch_bytes(const GridDev& g);
 ShiftScratch carve_shift_scratch(const GridDev& g, void* ws);

@@ -45,20 +45,27 @@ __device__ __forceinline__ void block_sums_sh(double (&v)[K], SumOut out, int bl
 }
 
 // ---------------------------------------------------------------------------
-// Shift in three kernels.
-//   SA (stream): copies c, e to the output, sums them, and lists the moving
-//      mixed cells per warp (256 consecutive cells per warp, fixed order);
-//   SM (planes): per moving mixed cell, the plane (MYC normal, plane
-//      constant -- by bisection when c is within 1e-3 of 0 or 1, where the
-//      plane is extrapolated into neighbours), the shift |m|_2 dd, and the
-//      cell's own shifted volume;
-//   SR (receivers): per moving mixed cell, the pure neighbours of the
-//      receding phase it is the first to reach in the scan order; for each,
-//      the largest volume swept in it by the extended planes of all its
-//      moving mixed neighbours.
-// Sums are per-CTA partials {dc, clamped, de, c, e}.
+// Shift in four kernels.
+//   stream:    copies c, e to the output and sums them; lists the moving
+//              mixed cells per warp (256 consecutive cells per warp, fixed
+//              order) and appends them to a grid-wide list, cells with c
+//              within 1e-3 of 0 or 1 ("edge" cells, whose plane constant
+//              takes the bisection) at its back, the others at its front;
+//   planes:    one moving mixed cell per thread over the grid-wide list:
+//              plane (MYC normal + plane constant), shift |m|_2 dd, the
+//              cell's own shifted volume, and the receivers it settles --
+//              pure neighbours of the receding phase whose first reaching
+//              neighbour (scan order z outer, x inner) it is;
+//   receivers: one receiver per thread: the largest volume swept in it by
+//              the extended planes of its reaching neighbours;
+//   sums:      per warp list in fixed order, the changes of every moving
+//              cell and of the receivers it settled, so the sums do not
+//              depend on the order of the grid-wide lists.
 // ---------------------------------------------------------------------------
 constexpr int kWarpCells = 256;
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kListThreads = 128;     // planes / receivers kernels: CTA size
+constexpr int kListCTAs = 152 * 4;    // and grid (grid-stride loops)
 
 __device__ __forceinline__ void decode(const GridDev& g, size_t id, int& x, int& y, int& z) {
   x = (int)(id % (size_t)g.n[0]);
@@ -71,15 +78,44 @@ __device__ __forceinline__ size_t cell_id(const GridDev& g, int x, int y, int z)
   return ((size_t)z * g.n[1] + y) * g.n[0] + x;
 }
 
+// c within 1e-3 of 0 or 1: alpha(c) is ill-conditioned and the plane is
+// extrapolated into neighbours, so its constant takes the bisection
+__device__ __forceinline__ bool edge_cell(double c) {
+  return dbits(c) < 0x3F50624DD2F1A9FCLL /* 1e-3 */ || dbits(c) > 0x3FEFF7CED916872BLL /* 0.999 */;
+}
+
+// neighbour of (x, y, z) at offset (ox, oy, oz); false beyond a
+// zero-gradient boundary
+__device__ __forceinline__ bool neighbour(const GridDev& g, int x, int y, int z, int ox, int oy, int oz, size_t& id) {
+  int px = x + ox, py = y + oy, pz = z + oz;
+  if (g.bc[0] != 0 && (px < 0 || px >= g.n[0])) return false;
+  if (g.bc[1] != 0 && (py < 0 || py >= g.n[1])) return false;
+  if (g.bc[2] != 0 && (pz < 0 || pz >= g.n[2])) return false;
+  id = cell_id(g, map_idx(px, g.n[0], g.bc[0]), map_idx(py, g.n[1], g.bc[1]), map_idx(pz, g.n[2], g.bc[2]));
+  return true;
+}
+
+// moving mixed cell whose shift has the sign that reaches a receiver of this kind
+__device__ __forceinline__ bool reaches(const GridDev& g, const double* __restrict__ c_in,
+                                        const double* __restrict__ dd, double dd_uniform, size_t q, bool full) {
+  if (!is_mixed_b(__ldg(c_in + q), g)) return false;
+  const double ddv = dd ? __ldg(dd + q) : dd_uniform;
+  return dnz(ddv) && (dlt0(ddv) == full);
+}
+
+// offsets as bit indices: ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1), 0..26
+__device__ __forceinline__ int offset_bit(int ox, int oy, int oz) { return ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1); }
+
 __global__ void __launch_bounds__(256)
 k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
                double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
                SumOut sums) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   uint32_t* list = sc.list + w * kWarpCells;
-  int n = 0;
+  int n = 0, ne = 0;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const bool uni_moving = dnz(dd_uniform);
   for (int it = 0; it < kWarpCells / 32; ++it) {
@@ -96,27 +132,52 @@ k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restr
     }
     bool moving = ok && is_mixed_b(c, g);
     if (moving) moving = dd ? dnz(__ldg(dd + id)) : uni_moving;
-    const unsigned m = __ballot_sync(0xffffffffu, moving);
-    if (moving) list[n + __popc(m & ((1u << lane) - 1u))] = (uint32_t)id;
+    const unsigned m = __ballot_sync(kFullMask, moving);
+    if (moving) list[n + __popc(m & lt)] = (uint32_t)id;
     n += __popc(m);
+    ne += __popc(__ballot_sync(kFullMask, moving && edge_cell(c)));
   }
-  if (lane == 0) sc.count[w] = n;
+  if (lane == 0 && (long long)w * kWarpCells < (long long)N) sc.count[w] = n;
+  if (n > 0) {  // warp-uniform: append to the grid-wide list
+    int bn = 0, be = 0;
+    if (lane == 0) {
+      if (n - ne) bn = atomicAdd(sc.counters + 0, n - ne);
+      if (ne) be = atomicAdd(sc.counters + 1, ne);
+    }
+    bn = __shfl_sync(kFullMask, bn, 0);
+    be = __shfl_sync(kFullMask, be, 0);
+    __syncwarp();
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const int j = j0 + lane;
+      const bool v = j < n;
+      const uint32_t id = v ? list[j] : 0u;
+      const bool edge = v && edge_cell(__ldg(c_in + id));
+      const unsigned me = __ballot_sync(kFullMask, edge), mn = __ballot_sync(kFullMask, v && !edge);
+      if (edge) sc.gmix[N - 1 - (size_t)(be + __popc(me & lt))] = id;
+      else if (v) sc.gmix[bn + __popc(mn & lt)] = id;
+      be += __popc(me);
+      bn += __popc(mn);
+    }
+  }
   block_sums_sh<5>(acc, sums, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kListThreads)
 k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
-               long long nwarps, SumOut sums) {
+               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const int nn = sc.counters[0], ne = sc.counters[1];
   const int lane = threadIdx.x & 31;
-  const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if ((long long)w < nwarps) {
-    const int cnt = sc.count[w];
-    const uint32_t* list = sc.list + w * kWarpCells;
-    for (int i = lane; i < cnt; i += 32) {
-      const size_t id = list[i];
-      int x, y, z;
+  const int total = nn + ne;
+  // whole warps iterate together (the receiver append below is warp-wide)
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
+    const int i = i0 + lane;
+    const bool v = i < total;
+    unsigned own = 0u;
+    int x = 0, y = 0, z = 0;
+    if (v) {
+      const size_t id = i < nn ? sc.gmix[i] : sc.gmix[N - 1 - (size_t)(i - nn)];
       decode(g, id, x, y, z);
       double st[27];
 #pragma unroll
@@ -135,8 +196,7 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
       const double ct = st[13];
       double m[3];
       myc_normal(st, m);
-      const bool edge = dbits(ct) < 0x3F50624DD2F1A9FCLL /* 1e-3 */ || dbits(ct) > 0x3FEFF7CED916872BLL /* 0.999 */;
-      const double al = edge ? plane_alpha_bisect(m[0], m[1], m[2], ct) : plane_alpha(m[0], m[1], m[2], ct);
+      const double al = edge_cell(ct) ? plane_alpha_bisect(m[0], m[1], m[2], ct) : plane_alpha(m[0], m[1], m[2], ct);
       const double ddv = dd ? __ldg(dd + id) : dd_uniform;
       const double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
       const double sft = mn2 * ddv;
@@ -154,126 +214,145 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
       if (ast > hi) ast = hi;
       const double cn = volume(m[0], m[1], m[2], ast);
       if (!same_bits_dev(cn, ct)) {
-        const double dc = cn - ct;
-        const double de = dc * (g.Cp_l - g.Cp_g) * g.T_sat;
         c_out[id] = cn;
-        e_out[id] = __ldg(e_in + id) + de;
-        acc[0] += dc;
-        acc[2] += de;
-        acc[3] += dc;  // sum c_out = sum c_in + sum dc
-        acc[4] += de;
+        e_out[id] = __ldg(e_in + id) + (cn - ct) * (g.Cp_l - g.Cp_g) * g.T_sat;
+      }
+      // receivers this cell settles
+      const bool full = dlt0(ddv);  // the kind of pure cell this shift reaches
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            if (!ox && !oy && !oz) continue;
+            size_t pid;
+            if (!neighbour(g, x, y, z, ox, oy, oz, pid)) continue;
+            const double cp = __ldg(c_in + pid);
+            if (is_mixed_b(cp, g) || is_full_b(cp, g) != full) continue;
+            int px, py, pz;
+            decode(g, pid, px, py, pz);
+            int first = -1;
+            for (int rz = -1; rz <= 1 && first < 0; ++rz)
+              for (int ry = -1; ry <= 1 && first < 0; ++ry)
+                for (int rx = -1; rx <= 1 && first < 0; ++rx) {
+                  if (!rx && !ry && !rz) continue;
+                  size_t sid;
+                  if (!neighbour(g, px, py, pz, rx, ry, rz, sid)) continue;
+                  if (reaches(g, c_in, dd, dd_uniform, sid, full)) first = offset_bit(rx, ry, rz);
+                }
+            // on periodic axes of 1 or 2 cells several offsets lead to the
+            // same cell; only the offset back to this cell settles it
+            if (first == offset_bit(-ox, -oy, -oz)) own |= 1u << offset_bit(ox, oy, oz);
+          }
+      sc.own[id] = own;
+    }
+    // append the settled receivers: one atomic per warp
+    const int k = __popc(own);
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int wtot = __shfl_sync(kFullMask, incl, 31);
+    int base = 0;
+    if (lane == 31 && wtot) base = atomicAdd(sc.counters + 2, wtot);
+    base = __shfl_sync(kFullMask, base, 31) + incl - k;
+    while (own) {
+      const int b = __ffs(own) - 1;
+      own &= own - 1u;
+      const int oz = b / 9 - 1, oy = (b / 3) % 3 - 1, ox = b % 3 - 1;
+      size_t pid = 0;
+      neighbour(g, x, y, z, ox, oy, oz, pid);
+      sc.recv[base++] = (uint32_t)pid;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kListThreads)
+k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in,
+                  double* __restrict__ c_out, double* __restrict__ e_out, const double* __restrict__ dd,
+                  double dd_uniform, ShiftScratch sc) {
+  const int nr = sc.counters[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+    const size_t pid = sc.recv[i];
+    const double cp = __ldg(c_in + pid);
+    const bool full = is_full_b(cp, g);
+    int px, py, pz;
+    decode(g, pid, px, py, pz);
+    double best = 0.0;
+    for (int rz = -1; rz <= 1; ++rz)
+      for (int ry = -1; ry <= 1; ++ry)
+        for (int rx = -1; rx <= 1; ++rx) {
+          if (!rx && !ry && !rz) continue;
+          size_t sid;
+          if (!neighbour(g, px, py, pz, rx, ry, rz, sid)) continue;
+          if (!reaches(g, c_in, dd, dd_uniform, sid, full)) continue;
+          const double sft = sc.shift[sid];
+          if (!dnz(sft)) continue;  // a zero normal does not move
+          const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
+          const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
+          // the receiver sits at offset -(rx, ry, rz) from the source
+          const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
+          const double a_old = al + shiftv;
+          const double a_new = (al + sft) + shiftv;
+          double lo = 0.0, hi = 0.0;
+          if (m0 < 0.0) lo += m0; else hi += m0;
+          if (m1 < 0.0) lo += m1; else hi += m1;
+          if (m2 < 0.0) lo += m2; else hi += m2;
+          // the extended plane stays outside the receiver: both volumes are
+          // exactly 1 (or 0); the margin clears the rounding of that test
+          if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
+          const double sw = volume(m0, m1, m2, a_new) - volume(m0, m1, m2, a_old);
+          if (fabs(sw) > fabs(best)) best = sw;
+        }
+    sc.sweep[pid] = best;
+    if (dnz(best)) {
+      const double v = cp + best;
+      const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
+      if (!same_bits_dev(vc, cp)) {
+        c_out[pid] = vc;
+        e_out[pid] = __ldg(e_in + pid) + (vc - cp) * (g.Cp_l - g.Cp_g) * g.T_sat;
       }
     }
   }
-  block_sums_sh<5>(acc, sums, blockIdx.x);
-}
-
-// moving mixed cell whose shift has the sign that reaches a receiver of this kind
-__device__ __forceinline__ bool reaches(const GridDev& g, const double* __restrict__ c_in,
-                                        const double* __restrict__ dd, double dd_uniform, size_t q, bool full) {
-  if (!is_mixed_b(__ldg(c_in + q), g)) return false;
-  const double ddv = dd ? __ldg(dd + q) : dd_uniform;
-  return dnz(ddv) && (dlt0(ddv) == full);
 }
 
 __global__ void __launch_bounds__(256)
-k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in,
-                  double* __restrict__ c_out, double* __restrict__ e_out, const double* __restrict__ dd,
-                  double dd_uniform, ShiftScratch sc, long long nwarps, SumOut sums) {
+k_shift_sums(GridDev g, const double* __restrict__ c_in, const double* __restrict__ c_out, ShiftScratch sc,
+             long long nwarps, SumOut sums) {
   const int lane = threadIdx.x & 31;
   const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if ((long long)w < nwarps) {
     const int cnt = sc.count[w];
     const uint32_t* list = sc.list + w * kWarpCells;
     for (int i = lane; i < cnt; i += 32) {
       const size_t qid = list[i];
-      int qx, qy, qz;
-      decode(g, qid, qx, qy, qz);
-      const double qdd = dd ? __ldg(dd + qid) : dd_uniform;
-      for (int oz = -1; oz <= 1; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-          for (int ox = -1; ox <= 1; ++ox) {
-            if (!ox && !oy && !oz) continue;
-            int px = qx + ox, py = qy + oy, pz = qz + oz;
-            if (g.bc[0] != 0 && (px < 0 || px >= nx)) continue;
-            if (g.bc[1] != 0 && (py < 0 || py >= ny)) continue;
-            if (g.bc[2] != 0 && (pz < 0 || pz >= nz)) continue;
-            px = map_idx(px, nx, g.bc[0]);
-            py = map_idx(py, ny, g.bc[1]);
-            pz = map_idx(pz, nz, g.bc[2]);
-            const size_t pid = cell_id(g, px, py, pz);
-            const double cp = __ldg(c_in + pid);
-            if (is_mixed_b(cp, g)) continue;
-            const bool full = is_full_b(cp, g);
-            if (dlt0(qdd) != full) continue;
-            // this receiver is settled by its first reaching neighbour offset
-            // in the scan order (z outer, x inner), which must be the offset
-            // back to this cell (on periodic axes of 1 or 2 cells several
-            // offsets lead to the same cell; only one of them settles it)
-            int first = -1;
-            for (int rz = -1; rz <= 1 && first < 0; ++rz)
-              for (int ry = -1; ry <= 1 && first < 0; ++ry)
-                for (int rx = -1; rx <= 1 && first < 0; ++rx) {
-                  if (!rx && !ry && !rz) continue;
-                  int sx = px + rx, sy = py + ry, sz = pz + rz;
-                  if (g.bc[0] != 0 && (sx < 0 || sx >= nx)) continue;
-                  if (g.bc[1] != 0 && (sy < 0 || sy >= ny)) continue;
-                  if (g.bc[2] != 0 && (sz < 0 || sz >= nz)) continue;
-                  const size_t sid =
-                      cell_id(g, map_idx(sx, nx, g.bc[0]), map_idx(sy, ny, g.bc[1]), map_idx(sz, nz, g.bc[2]));
-                  if (reaches(g, c_in, dd, dd_uniform, sid, full)) first = ((rz + 1) * 3 + (ry + 1)) * 3 + (rx + 1);
-                }
-            if (first != ((1 - oz) * 3 + (1 - oy)) * 3 + (1 - ox)) continue;
-            // settle the receiver: largest sweep over its reaching neighbours
-            double best = 0.0;
-            for (int rz = -1; rz <= 1; ++rz)
-              for (int ry = -1; ry <= 1; ++ry)
-                for (int rx = -1; rx <= 1; ++rx) {
-                  if (!rx && !ry && !rz) continue;
-                  int sx = px + rx, sy = py + ry, sz = pz + rz;
-                  if (g.bc[0] != 0 && (sx < 0 || sx >= nx)) continue;
-                  if (g.bc[1] != 0 && (sy < 0 || sy >= ny)) continue;
-                  if (g.bc[2] != 0 && (sz < 0 || sz >= nz)) continue;
-                  const size_t sid =
-                      cell_id(g, map_idx(sx, nx, g.bc[0]), map_idx(sy, ny, g.bc[1]), map_idx(sz, nz, g.bc[2]));
-                  if (!reaches(g, c_in, dd, dd_uniform, sid, full)) continue;
-                  const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
-                  const double sft = sc.shift[sid];
-                  const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
-                  // the receiver sits at offset -(rx, ry, rz) from the source
-                  const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
-                  const double a_old = al + shiftv;
-                  const double a_new = (al + sft) + shiftv;
-                  double lo = 0.0, hi = 0.0;
-                  if (m0 < 0.0) lo += m0; else hi += m0;
-                  if (m1 < 0.0) lo += m1; else hi += m1;
-                  if (m2 < 0.0) lo += m2; else hi += m2;
-                  // the extended plane stays outside the receiver: both
-                  // volumes are exactly 1 (or 0); the margin clears rounding
-                  if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
-                  const double sw = volume(m0, m1, m2, a_new) - volume(m0, m1, m2, a_old);
-                  if (fabs(sw) > fabs(best)) best = sw;
-                }
-            if (dnz(best)) {
-              const double v = cp + best;
-              const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
-              if (!deq(v, vc)) acc[1] += v - vc;
-              if (!same_bits_dev(vc, cp)) {
-                const double dc = vc - cp;
-                const double de = dc * (g.Cp_l - g.Cp_g) * g.T_sat;
-                c_out[pid] = vc;
-                e_out[pid] = __ldg(e_in + pid) + de;
-                acc[0] += dc;
-                acc[2] += de;
-                acc[3] += dc;
-                acc[4] += de;
-              }
-            }
-          }
+      const double dq = c_out[qid] - __ldg(c_in + qid);
+      acc[0] += dq;
+      acc[2] += dq * (g.Cp_l - g.Cp_g) * g.T_sat;
+      unsigned own = sc.own[qid];
+      if (!own) continue;
+      int x, y, z;
+      decode(g, qid, x, y, z);
+      while (own) {
+        const int b = __ffs(own) - 1;
+        own &= own - 1u;
+        size_t pid = 0;
+        neighbour(g, x, y, z, b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1, pid);
+        const double best = sc.sweep[pid];
+        if (!dnz(best)) continue;
+        const double cp = __ldg(c_in + pid);
+        const double v = cp + best;
+        const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
+        if (!deq(v, vc)) acc[1] += v - vc;
+        const double dc = vc - cp;
+        acc[0] += dc;
+        acc[2] += dc * (g.Cp_l - g.Cp_g) * g.T_sat;
+      }
     }
   }
+  acc[3] = acc[0];  // sum c_out = sum c_in + sum dc
+  acc[4] = acc[2];
   block_sums_sh<5>(acc, sums, blockIdx.x);
 }
 
@@ -329,32 +408,39 @@ static long long shift_warps(const GridDev& g) {
   return (long long)((N + kWarpCells - 1) / kWarpCells);
 }
 
-// CTAs of each shift kernel (8 warps of 256 cells)
+// CTAs of the stream and sums kernels (8 warps of 256 cells)
 int shift_blocks(const GridDev& g) { return (int)((shift_warps(g) + 7) / 8); }
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t shift_scratch_bytes(const GridDev& g) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-  const size_t nw = (size_t)shift_warps(g);
-  size_t b = 0;
-  b += (nw * kWarpCells * 4 + 255) & ~(size_t)255;  // lists
-  b += (nw * 4 + 255) & ~(size_t)255;               // counts
-  b += (N * 32 + 255) & ~(size_t)255;               // planes
-  b += (N * 8 + 255) & ~(size_t)255;                // shifts
-  return b;
+  const size_t nw = (size_t)shift_blocks(g) * 8;
+  return al256(nw * kWarpCells * 4)  // per-warp lists
+         + al256(nw * 4)             // counts
+         + 256                       // counters
+         + al256(N * 4)              // grid-wide list of moving cells
+         + al256(N * 4)              // receivers
+         + al256(N * 32)             // planes
+         + al256(N * 8)              // shifts
+         + al256(N * 8)              // sweeps
+         + al256(N * 4);             // settled-receiver masks
 }
 
 ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-  const size_t nw = (size_t)shift_warps(g);
+  const size_t nw = (size_t)shift_blocks(g) * 8;
   char* b = static_cast<char*>(ws);
   ShiftScratch s;
-  s.list = reinterpret_cast<uint32_t*>(b);
-  b += (nw * kWarpCells * 4 + 255) & ~(size_t)255;
-  s.count = reinterpret_cast<int*>(b);
-  b += (nw * 4 + 255) & ~(size_t)255;
-  s.plane = reinterpret_cast<double*>(b);
-  b += (N * 32 + 255) & ~(size_t)255;
-  s.shift = reinterpret_cast<double*>(b);
+  s.list = reinterpret_cast<uint32_t*>(b);   b += al256(nw * kWarpCells * 4);
+  s.count = reinterpret_cast<int*>(b);       b += al256(nw * 4);
+  s.counters = reinterpret_cast<int*>(b);    b += 256;
+  s.gmix = reinterpret_cast<uint32_t*>(b);   b += al256(N * 4);
+  s.recv = reinterpret_cast<uint32_t*>(b);   b += al256(N * 4);
+  s.plane = reinterpret_cast<double*>(b);    b += al256(N * 32);
+  s.shift = reinterpret_cast<double*>(b);    b += al256(N * 8);
+  s.sweep = reinterpret_cast<double*>(b);    b += al256(N * 8);
+  s.own = reinterpret_cast<uint32_t*>(b);
   return s;
 }
 
@@ -362,19 +448,18 @@ cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_i
                          const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut sums,
                          cudaStream_t st) {
   const long long nw = shift_warps(g);
-  const unsigned nb = (unsigned)((nw + 7) / 8);
-  // the three kernels write partials to consecutive regions of nb CTAs
-  SumOut s0 = sums, s1 = sums, s2 = sums;
-  if (sums.partials) {
-    s1.partials = sums.partials + (size_t)nb * sums.stride;
-    s2.partials = sums.partials + (size_t)2 * nb * sums.stride;
-  }
+  const unsigned nb = (unsigned)shift_blocks(g);
+  // the stream and sums kernels write partials to consecutive sets of nb CTAs
+  SumOut s0 = sums, s1 = sums;
+  if (sums.partials) s1.partials = sums.partials + (size_t)nb * sums.stride;
+  cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
+  if (err != cudaSuccess) return err;
   k_shift_stream<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, s0);
-  k_shift_planes<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, nw, s1);
-  k_shift_receivers<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, nw, s2);
-  cudaError_t err = cudaGetLastError();
-  if (err == cudaSuccess && state)
-    err = cudaMemsetAsync(state, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
+  k_shift_planes<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc);
+  k_shift_receivers<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc);
+  k_shift_sums<<<nb, 256, 0, st>>>(g, c_in, c_out, sc, nw, s1);
+  err = cudaGetLastError();
+  if (err == cudaSuccess && state) err = cudaMemsetAsync(state, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
   return err;
 }
 

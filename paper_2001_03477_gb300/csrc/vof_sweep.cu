@@ -170,6 +170,21 @@ __device__ __forceinline__ void block_reduce_out(double (&v)[NV], SumOut out) {
 constexpr int kSegA = 32;     // cells per lane along y / z
 constexpr int kWarpsA = 8;    // warps per CTA of kernel A
 constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
+constexpr int kPlaneThreads = 128;  // kernel M: CTA size; grid kPlaneCTAs
+constexpr int kPlaneCTAs = 152 * 4;
+
+// Appends a warp's mixed cells (staged in its own list) to the grid-wide
+// list of mixed cells: one atomic per warp reserves the slots.  The order of
+// the grid-wide list varies from run to run; nothing that reads it depends
+// on the order.
+__device__ __forceinline__ void append_mixed(const SweepScratch& sc, const uint32_t* mlist, int nmixed, int lane) {
+  if (nmixed == 0) return;  // warp-uniform
+  int base = 0;
+  if (lane == 0) base = atomicAdd(sc.gcount, nmixed);
+  base = __shfl_sync(kFull, base, 0);
+  __syncwarp();
+  for (int i = lane; i < nmixed; i += 32) sc.gmix[base + i] = mlist[i];
+}
 
 template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(32 * kWarpsA)
@@ -240,10 +255,8 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     wc[3] = cn; we[3] = en; dif[3] = !same;
     run = same ? run + 1 : 1;
   }
-  if (lane == 0) {
-    sc.count[sub] = nlist;
-    sc.mcount[sub] = nmixed;
-  }
+  if (lane == 0) sc.count[sub] = nlist;
+  append_mixed(sc, mlist, nmixed, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -264,11 +277,8 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
   const size_t rbase = (size_t)(rowok ? row : 0) * nx;
   const int bcx = g.bc[0];
   const size_t sub = (size_t)row * gridDim.x + blockIdx.x;
-  if (!rowok) {  // whole warp: empty lists
-    if (lane == 0) {
-      sc.count[sub] = 0;
-      sc.mcount[sub] = 0;
-    }
+  if (!rowok) {  // whole warp: empty list
+    if (lane == 0) sc.count[sub] = 0;
     return;
   }
   uint32_t* list = sc.list + sub * (size_t)cap;
@@ -323,26 +333,21 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
     cN = cNN; eN = eNN;
     eqP = eqC; eqC = eqN; eqN = eqNN;
   }
-  if (lane == 0) {
-    sc.count[sub] = nlist;
-    sc.mcount[sub] = nmixed;
-  }
+  if (lane == 0) sc.count[sub] = nlist;
+  append_mixed(sc, mlist, nmixed, lane);
 }
 
 // ---------------------------------------------------------------------------
 // Kernel M: the PLIC plane (MYC normal + plane constant) of every mixed cell,
-// once per sweep, one mixed cell per lane; stored per cell for kernel B.
+// once per sweep, one mixed cell per thread over the grid-wide list (every
+// lane busy); stored per cell for kernel B.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc, int nsub, int cap) {
-  const int lane = threadIdx.x & 31;
-  const int sub = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (sub >= nsub) return;
-  const int cnt = sc.mcount[sub];
-  const uint32_t* mlist = sc.mlist + (size_t)sub * cap;
+__global__ void __launch_bounds__(kPlaneThreads)
+k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  for (int i = lane; i < cnt; i += 32) {
-    const size_t id = mlist[i];
+  const int cnt = *sc.gcount;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const size_t id = sc.gmix[i];
     const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
     double s[27];
 #pragma unroll
@@ -593,8 +598,9 @@ size_t sweep_scratch_bytes(const GridDev& g) {
     b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // lists
     b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;                       // counts
     b += ((size_t)p.gridB * 8 + 255) & ~(size_t)255;                      // partials
-    b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // mixed lists
-    b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;                       // mixed counts
+    b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // mixed lists (staging)
+    b += 256;                                                             // mixed count
+    b += (N * 4 + 255) & ~(size_t)255;                                    // grid-wide mixed list
     b += (N * 32 + 255) & ~(size_t)255;                                   // planes
     best = b > best ? b : best;
   }
@@ -616,8 +622,10 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* p
   b += ((size_t)p.gridB * 8 + 255) & ~(size_t)255;
   s.mlist = reinterpret_cast<uint32_t*>(b);
   b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;
-  s.mcount = reinterpret_cast<int*>(b);
-  b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;
+  s.gcount = reinterpret_cast<int*>(b);
+  b += 256;
+  s.gmix = reinterpret_cast<uint32_t*>(b);
+  b += (N * 4 + 255) & ~(size_t)255;
   s.plane = reinterpret_cast<double*>(b);
   s.diag = diag;
   return s;
@@ -635,7 +643,7 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
   else
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
                                                                           flux_out != nullptr, p.cap);
-  k_planes<<<p.gridB, 256, 0, st>>>(g, c_in, sc, (int)p.nsub, p.cap);
+  k_planes<<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, sc);
   k_active<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc,
                                                  (int)p.nsub, p.cap, status);
 }
@@ -645,6 +653,8 @@ cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const d
                          SweepScratch sc, cudaStream_t st) {
   int* status = device_status_ptr();
   const SweepPlan p = sweep_plan(axis, g);
+  const cudaError_t err = cudaMemsetAsync(sc.gcount, 0, sizeof(int), st);
+  if (err != cudaSuccess) return err;
   if (e_in) {
     if (axis == 0) launch_ab<0, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
     else if (axis == 1) launch_ab<1, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
