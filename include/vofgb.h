@@ -56,7 +56,7 @@ typedef enum {
 } vof_status;
 
 typedef struct {
-  int nx, ny, nz;     /* interior cells per axis (>= 1) */
+  int nx, ny, nz;     /* interior cells per axis (>= 1; nx ny nz < 2^31) */
   int bc[3];          /* per axis x, y, z: 0 periodic, 1 zero-gradient */
   double h;           /* cell size (> 0) */
   double Cp_l, Cp_g;  /* volumetric heat capacities rho c_p of liquid, gas (> 0) */
@@ -191,7 +191,7 @@ VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const doubl
  * host callback or an error path where the allocator must not be entered,
  * embedders whose device memory is reserved up front by their own pool, small
  * tools without an allocator).  Same arguments and results as vof_step(),
- * minus the workspace: the scratch space is one fixed 32 MiB array that every
+ * minus the workspace: the scratch space is one fixed 40 MiB array that every
  * GPU loading the library keeps until the process exits.
  *   - grids above VOF_NOALLOC_MAX_CELLS cells, or whose step workspace
  *     (vof_step_workspace_bytes) exceeds the array -- only grids with fewer

@@ -29,7 +29,8 @@ int* device_status_ptr() {
 static bool grid_ok(const vof_grid* g) {
   if (!g) return false;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1) return false;
-  if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return false;
+  // cell lists hold 32-bit entries (cell index << 1 | face side)
+  if ((long long)g->nx * g->ny * g->nz >= (1LL << 31)) return false;
   for (int d = 0; d < 3; ++d)
     if (g->bc[d] != 0 && g->bc[d] != 1) return false;
   if (!(g->h > 0.0) || !(g->Cp_l > 0.0) || !(g->Cp_g > 0.0)) return false;

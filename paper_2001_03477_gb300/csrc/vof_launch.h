@@ -19,27 +19,34 @@ struct SumOut {
   double* diag;
 };
 
-// Scratch of one sweep (kernel A -> kernel B): T of the cells whose (c, e)
-// differs from the previous cell of their line, the per-warp lists of cells
-// that are not no-ops with their counts, and per-CTA partial sums of the
-// clipped volume (or, when partial is null, atomics into diag).
+// Scratch of one sweep (kernel A -> kernels M, F, U): T of the cells whose
+// (c, e) differs from the previous cell of their line (kernel F adds the
+// listed others), the per-warp lists of cells that are not no-ops with their
+// counts, per-CTA partial sums of the clipped volume (or, when partial is
+// null, atomics into diag), per-warp staging of mixed cells and run ends,
+// the grid-wide lists of mixed cells and of face items with their counters,
+// the planes of the mixed cells and the face fluxes F, G.
 struct SweepScratch {
   double* T;
   uint32_t* list;
   int* count;
   double* partial;
   double* diag;
-  uint32_t* mlist;  // per-warp staging lists of mixed cells
-  int* gcount;      // number of mixed cells (zeroed before kernel A)
-  uint32_t* gmix;   // grid-wide list of mixed cells, in no fixed order
-  double* plane;    // [N][4]: m0, m1, m2, alpha of the listed mixed cells
+  uint32_t* mlist;   // per-warp staging lists of mixed cells
+  uint32_t* rlist;   // per-warp staging lists of run ends
+  int* counters;     // [0] mixed cells, [1] face items (zeroed before kernel A)
+  uint32_t* gmix;    // grid-wide list of mixed cells, in no fixed order
+  uint32_t* gface;   // grid-wide face items (cell << 1 | side), no fixed order
+  double* plane;     // [N][4]: m0, m1, m2, alpha of the listed mixed cells
+  double* F;         // face arrays of the axis (face layout of the velocities)
+  double* G;
 };
 
 struct SweepPlan {
   dim3 gridA, blockA;
   int cap;          // list capacity per warp of kernel A
   long long nsub;   // number of lists (warps of kernel A)
-  unsigned gridB;   // CTAs of kernel B (8 lists each)
+  unsigned gridB;   // CTAs of kernel U (8 lists each)
 };
 
 SweepPlan sweep_plan(int axis, const GridDev& g);

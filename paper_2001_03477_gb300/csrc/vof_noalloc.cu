@@ -16,7 +16,7 @@
 //     step workspace must fit the array (it does for every such grid with
 //     at least 8 cells along each axis; thinner grids need more list space);
 //     other grids are rejected with VOF_EINVAL before anything is launched;
-//   * every GPU on which the library is loaded holds the array (32 MiB)
+//   * every GPU on which the library is loaded holds the array (40 MiB)
 //     until the process exits;
 //   * all calls share the one array per device: two calls whose kernels
 //     overlap on the GPU (different streams, or different host threads on
@@ -37,7 +37,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB
+constexpr size_t kNoAllocBytes = size_t(40) << 20;  // 40 MiB
 
 // the scratch array; in host code this name is only a stand-in for the
 // device symbol, never a usable address

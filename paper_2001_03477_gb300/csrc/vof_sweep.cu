@@ -173,17 +173,26 @@ constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
 constexpr int kPlaneThreads = 128;  // kernel M: CTA size; grid kPlaneCTAs
 constexpr int kPlaneCTAs = 152 * 4;
 
-// Appends a warp's mixed cells (staged in its own list) to the grid-wide
-// list of mixed cells: one atomic per warp reserves the slots.  The order of
-// the grid-wide list varies from run to run; nothing that reads it depends
-// on the order.
-__device__ __forceinline__ void append_mixed(const SweepScratch& sc, const uint32_t* mlist, int nmixed, int lane) {
-  if (nmixed == 0) return;  // warp-uniform
-  int base = 0;
-  if (lane == 0) base = atomicAdd(sc.gcount, nmixed);
-  base = __shfl_sync(kFull, base, 0);
+// Appends a warp's lists (staged in its own slots) to the grid-wide lists:
+// its mixed cells to the list of kernel M, and one face item per listed cell
+// (its left face) and per run end (the right face of a listed cell whose
+// next cell along the axis is not listed) to the list of kernel F.  One
+// atomic per list and warp reserves the slots; the order of the grid-wide
+// lists varies from run to run, and nothing that reads them depends on it.
+__device__ __forceinline__ void append_lists(const SweepScratch& sc, const uint32_t* list, int nlist,
+                                             const uint32_t* mlist, int nmixed, const uint32_t* rlist, int nrun,
+                                             int lane) {
+  int bm = 0, bf = 0;
+  if (lane == 0) {
+    if (nmixed) bm = atomicAdd(sc.counters + 0, nmixed);
+    if (nlist + nrun) bf = atomicAdd(sc.counters + 1, nlist + nrun);
+  }
+  bm = __shfl_sync(kFull, bm, 0);
+  bf = __shfl_sync(kFull, bf, 0);
   __syncwarp();
-  for (int i = lane; i < nmixed; i += 32) sc.gmix[base + i] = mlist[i];
+  for (int i = lane; i < nmixed; i += 32) sc.gmix[bm + i] = mlist[i];
+  for (int i = lane; i < nlist; i += 32) sc.gface[bf + i] = list[i] << 1;
+  for (int i = lane; i < nrun; i += 32) sc.gface[bf + nlist + i] = (rlist[i] << 1) | 1u;
 }
 
 template <int AX, bool ENERGY>
@@ -207,7 +216,10 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
                      blockIdx.x;
   uint32_t* list = sc.list + sub * (size_t)cap;
   uint32_t* mlist = sc.mlist + sub * (size_t)cap;
-  int nlist = 0, nmixed = 0;
+  uint32_t* rlist = sc.rlist + sub * (size_t)cap;
+  const unsigned lt = (1u << lane) - 1u;
+  int nlist = 0, nmixed = 0, nrun = 0;
+  bool prev_listed = false;  // cell k-1 of this segment listed
   // window: cells k .. k+3 (c, e), run = equal cells ending at k+3, and
   // whether cells k and k-1 differ from their predecessors
   double wc[4], we[4];
@@ -242,12 +254,17 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     }
     const bool listed = act && !noop;
     const unsigned m = __ballot_sync(kFull, listed);
-    if (listed) list[nlist + __popc(m & ((1u << lane) - 1u))] = (uint32_t)id;
+    if (listed) list[nlist + __popc(m & lt)] = (uint32_t)id;
     nlist += __popc(m);
     const bool mixed = act && is_mixed_b(wc[0], g);
     const unsigned mm = __ballot_sync(kFull, mixed);
-    if (mixed) mlist[nmixed + __popc(mm & ((1u << lane) - 1u))] = (uint32_t)id;
+    if (mixed) mlist[nmixed + __popc(mm & lt)] = (uint32_t)id;
     nmixed += __popc(mm);
+    const bool rend = prev_listed && !listed;  // cell k-1 ends a run
+    const unsigned mr = __ballot_sync(kFull, rend);
+    if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(id - stride);
+    nrun += __popc(mr);
+    prev_listed = listed;
     // shift the window
     const bool same = same_bits(cn, wc[3]) && (!ENERGY || same_bits(en, we[3]));
 #pragma unroll
@@ -255,8 +272,21 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     wc[3] = cn; we[3] = en; dif[3] = !same;
     run = same ? run + 1 : 1;
   }
+  // the segment's last cell ends a run unless the next cell along the axis
+  // (next segment, or cell 0 across a periodic boundary) is listed; the
+  // window now holds cells s1 .. s1+3
+  bool next_listed = false;
+  if (s1 < n_ax || bca == 0) {
+    const size_t idn = cbase + stride * map_idx(s1, n_ax, bca);
+    const uint8_t stn = (act && state) ? state[idn] : (uint8_t)0;
+    next_listed = act && !(!force_all && run >= 7 && is01(wc[0]) && !(stn & 1));
+  }
+  const bool rend = prev_listed && !next_listed;
+  const unsigned mr = __ballot_sync(kFull, rend);
+  if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(cbase + stride * (s1 - 1));
+  nrun += __popc(mr);
   if (lane == 0) sc.count[sub] = nlist;
-  append_mixed(sc, mlist, nmixed, lane);
+  append_lists(sc, list, nlist, mlist, nmixed, rlist, nrun, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,7 +313,9 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
   }
   uint32_t* list = sc.list + sub * (size_t)cap;
   uint32_t* mlist = sc.mlist + sub * (size_t)cap;
-  int nlist = 0, nmixed = 0;
+  uint32_t* rlist = sc.rlist + sub * (size_t)cap;
+  const unsigned lt = (1u << lane) - 1u;
+  int nlist = 0, nmixed = 0, nrun = 0;
   auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
   auto lde = [&](int X) { return ENERGY ? __ldg(e_in + rbase + map_idx(X, nx, bcx)) : 0.0; };
   auto eqmask = [&](double cprev, double eprev, double cc, double ee) -> unsigned {
@@ -320,12 +352,26 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
     }
     const bool listed = cell_ok && !noop;
     const unsigned m = __ballot_sync(kFull, listed);
-    if (listed) list[nlist + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(rbase + X);
+    if (listed) list[nlist + __popc(m & lt)] = (uint32_t)(rbase + X);
     nlist += __popc(m);
     const bool mixed = cell_ok && is_mixed_b(cC, g);
     const unsigned mm = __ballot_sync(kFull, mixed);
-    if (mixed) mlist[nmixed + __popc(mm & ((1u << lane) - 1u))] = (uint32_t)(rbase + X);
+    if (mixed) mlist[nmixed + __popc(mm & lt)] = (uint32_t)(rbase + X);
     nmixed += __popc(mm);
+    // is cell X+1 listed?  (lane 31: the next chunk's first cell; past the
+    // segment end the next segment's first cell, or cell 0 across a
+    // periodic boundary; none past a zero-gradient boundary)
+    const bool uni_n = lane >= 1 ? (((M2 >> (lane - 1)) & 0x3Full) == 0x3Full) : (((M1 >> 31) & 0x3Full) == 0x3Full);
+    const double c_dn = __shfl_down_sync(kFull, cC, 1), c_n0 = __shfl_sync(kFull, cN, 0);
+    const double c_next = lane == 31 ? c_n0 : c_dn;
+    const int Xn = X + 1;
+    const bool in_line = Xn < nx || bcx == 0;
+    const uint8_t stn = (listed && in_line && state) ? state[rbase + map_idx(Xn, nx, bcx)] : (uint8_t)0;
+    const bool next_listed = in_line && !(!force_all && uni_n && is01(c_next) && !(stn & 1));
+    const bool rend = listed && !next_listed;
+    const unsigned mr = __ballot_sync(kFull, rend);
+    if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(rbase + X);
+    nrun += __popc(mr);
     const double c31 = __shfl_sync(kFull, cN, 31), e31 = __shfl_sync(kFull, eN, 31);
     const unsigned eqNN = eqmask(c31, e31, cNN, eNN);
     cP = cC; eP = eC;
@@ -334,7 +380,7 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
     eqP = eqC; eqC = eqN; eqN = eqNN;
   }
   if (lane == 0) sc.count[sub] = nlist;
-  append_mixed(sc, mlist, nmixed, lane);
+  append_lists(sc, list, nlist, mlist, nmixed, rlist, nrun, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,7 +391,7 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
 __global__ void __launch_bounds__(kPlaneThreads)
 k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int cnt = *sc.gcount;
+  const int cnt = sc.counters[0];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
     const size_t id = sc.gmix[i];
     const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
@@ -373,15 +419,108 @@ k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc) {
 }
 
 // ---------------------------------------------------------------------------
-// Kernel B: one warp per kernel-A list, one listed cell per lane.
+// Kernel F: one face per thread over the grid-wide face list -- the left face
+// of every listed cell and the right face of every run end, so each face is
+// evaluated once.  VOF flux F (PLIC slab of a mixed donor, c a of a pure
+// one) and energy flux G (WENO5 face temperature) go to per-face scratch.
+// A listed cell's left-face item also stores the cell's T where kernel A
+// did not (cells equal to their predecessor); nothing reads those entries
+// in this kernel, which only reads T of cells that differ from their
+// predecessor.
+// ---------------------------------------------------------------------------
+constexpr int kFaceThreads = 128;
+constexpr int kFaceCTAs = 152 * 8;
+
+template <int AX>
+__device__ __forceinline__ size_t face_of(const GridDev& g, int f, int x, int y, int z) {
+  if (AX == 0) return ((size_t)z * g.n[1] + y) * (g.n[0] + 1) + f;
+  if (AX == 1) return ((size_t)z * (g.n[1] + 1) + f) * g.n[0] + x;
+  return ((size_t)f * g.n[1] + y) * g.n[0] + x;
+}
+
+template <int AX, bool ENERGY>
+__global__ void __launch_bounds__(kFaceThreads)
+k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, const double* __restrict__ uf,
+        double* __restrict__ flux_out, SweepScratch sc, int* __restrict__ status) {
+  const int nx = g.n[0], ny = g.n[1];
+  const int n_ax = g.n[AX];
+  const int bca = g.bc[AX];
+  const int cnt = sc.counters[1];
+  const size_t stride = AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t item = sc.gface[i];
+    const size_t id = item >> 1;
+    const int side = (int)(item & 1u);
+    const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+    const int k = AX == 0 ? x : (AX == 1 ? y : z);
+    const size_t lbase = id - stride * k;  // cell index of position 0 of this line
+    const int f = k + side;                // face between cells f-1 and f
+    // (c, e) of cells f-4..f+2 and T of f-3..f+2 (cells that differ from
+    // their predecessor read back, others equal to it; the first divided)
+    double cw[7], ew[7], Tw[7];
+    bool dif4 = true;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const size_t jd = lbase + stride * map_idx(f - 4 + j, n_ax, bca);
+      cw[j] = __ldg(c_in + jd);
+      ew[j] = ENERGY ? __ldg(e_in + jd) : 0.0;
+      if (ENERGY && j >= 1) {
+        const bool dif = !(same_bits(cw[j], cw[j - 1]) && same_bits(ew[j], ew[j - 1]));
+        Tw[j] = dif ? sc.T[jd] : (j == 1 ? ew[j] / heat_cap(g.Cp_l, g.Cp_g, cw[j]) : Tw[j - 1]);
+        if (j == 4) dif4 = dif;
+      }
+    }
+    const int fr = (bca == 0 && f == n_ax) ? 0 : f;
+    const size_t fid = face_of<AX>(g, fr, x, y, z);
+    const double a = __ldg(uf + fid) * g.lam;
+    double Fv = 0.0, Gv = 0.0;
+    if (dnz(a)) {
+      const bool pos = dgt0(a);
+      const double cd = pos ? cw[3] : cw[4];  // donor f-1 (a > 0) or f (a < 0)
+      if (is_mixed_b(cd, g)) {
+        const size_t did = lbase + stride * map_idx(pos ? f - 1 : f, n_ax, bca);
+        const double4 pl = reinterpret_cast<const double4*>(sc.plane)[did];
+        const double mv[3] = {pl.x, pl.y, pl.z};
+        const double da = fabs(a);
+        if (da > 1.0 && status) atomicOr(status, DEV_CFL);
+        const double vol = slab_volume(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
+        Fv = pos ? vol : -vol;
+      } else {
+        Fv = cd * a;
+      }
+      if (ENERGY) {
+        // upwind-ordered stencil around the donor
+        const double t0 = pos ? Tw[1] : Tw[6];
+        const double t1 = pos ? Tw[2] : Tw[5];
+        const double t2 = pos ? Tw[3] : Tw[4];
+        const double t3 = pos ? Tw[4] : Tw[3];
+        const double t4 = pos ? Tw[5] : Tw[2];
+        Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, t0, t1, t2, t3, t4);
+      }
+    }
+    sc.F[fid] = Fv;
+    if (ENERGY) sc.G[fid] = Gv;
+    if (ENERGY && side == 0 && !dif4) sc.T[id] = Tw[4];
+    if (flux_out) {
+      // every face of the line, the periodic face n_ax (= face 0) included
+      flux_out[face_of<AX>(g, f, x, y, z)] = Fv;
+      if (bca == 0 && f == 0) flux_out[face_of<AX>(g, n_ax, x, y, z)] = Fv;
+      if (bca == 0 && f == n_ax) flux_out[face_of<AX>(g, 0, x, y, z)] = Fv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel U: one warp per kernel-A list (fixed order, so the clipped-volume
+// sums are reproducible), one listed cell per lane: the WY update from the
+// two face fluxes.
 // ---------------------------------------------------------------------------
 template <int AX, bool ENERGY>
-__global__ void __launch_bounds__(256, 2)
-k_active(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+__global__ void __launch_bounds__(256)
+k_update(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
          double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
-         double* __restrict__ theta, double* __restrict__ flux_out, SweepScratch sc, int nsub, int cap,
-         int* __restrict__ status) {
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+         double* __restrict__ theta, SweepScratch sc, int nsub, int cap) {
+  const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
   const int lane = threadIdx.x & 31;
@@ -394,74 +533,16 @@ k_active(GridDev g, const double* __restrict__ c_in, const double* __restrict__ 
       const size_t id = list[i];
       const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
       const int k = AX == 0 ? x : (AX == 1 ? y : z);
-      const size_t stride = AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny);
-      const size_t lbase = id - stride * k;  // cell index of position 0 of this line
-      // (c, e) of cells k-4..k+3 and T of k-3..k+3 (run starts read back,
-      // others equal to their predecessor; the first is divided if needed)
-      double cw[8], ew[8], Tw[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const size_t jd = lbase + stride * map_idx(k - 4 + j, n_ax, bca);
-        cw[j] = __ldg(c_in + jd);
-        ew[j] = ENERGY ? __ldg(e_in + jd) : 0.0;
-        if (ENERGY && j >= 1) {
-          const bool dif = !(same_bits(cw[j], cw[j - 1]) && same_bits(ew[j], ew[j - 1]));
-          Tw[j] = dif ? sc.T[jd] : (j == 1 ? ew[j] / heat_cap(g.Cp_l, g.Cp_g, cw[j]) : Tw[j - 1]);
-        }
-      }
-      double F[2], G[2], A[2];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int f = k + side;  // face between cells f-1 and f
-        const int fr = (bca == 0 && f == n_ax) ? 0 : f;
-        size_t fid;
-        if (AX == 0) fid = ((size_t)z * ny + y) * (nx + 1) + fr;
-        else if (AX == 1) fid = ((size_t)z * (ny + 1) + fr) * nx + x;
-        else fid = ((size_t)fr * ny + y) * nx + x;
-        const double a = __ldg(uf + fid) * g.lam;
-        double Fv = 0.0, Gv = 0.0;
-        if (dnz(a)) {
-          const bool pos = dgt0(a);
-          // donor = cell k-1+side (a > 0) or k+side (a < 0); window index
-          // 3+side or 4+side -- constant indices keep the window in registers
-          const double cd = pos ? cw[3 + side] : cw[4 + side];
-          if (is_mixed_b(cd, g)) {
-            const int dk = map_idx(pos ? k - 1 + side : k + side, n_ax, bca);
-            const size_t did = lbase + stride * dk;
-            const double4 pl = reinterpret_cast<const double4*>(sc.plane)[did];
-            const double mv[3] = {pl.x, pl.y, pl.z};
-            const double da = fabs(a);
-            if (da > 1.0 && status) atomicOr(status, DEV_CFL);
-            const double vol = slab_volume(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
-            Fv = pos ? vol : -vol;
-          } else {
-            Fv = cd * a;
-          }
-          if (ENERGY) {
-            // upwind-ordered stencil around the donor
-            const double t0 = pos ? Tw[1 + side] : Tw[6 + side];
-            const double t1 = pos ? Tw[2 + side] : Tw[5 + side];
-            const double t2 = pos ? Tw[3 + side] : Tw[4 + side];
-            const double t3 = pos ? Tw[4 + side] : Tw[3 + side];
-            const double t4 = pos ? Tw[5 + side] : Tw[2 + side];
-            Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, t0, t1, t2, t3, t4);
-          }
-        }
-        F[side] = Fv; G[side] = Gv; A[side] = a;
-      }
-      if (flux_out) {
-        // faces are listed with the cell on their + side; the last face of a
-        // line goes with the last cell
-        size_t fo;
-        if (AX == 0) fo = ((size_t)z * ny + y) * (nx + 1) + k;
-        else if (AX == 1) fo = ((size_t)z * (ny + 1) + k) * nx + x;
-        else fo = ((size_t)k * ny + y) * nx + x;
-        flux_out[fo] = F[0];
-        if (k == n_ax - 1) flux_out[fo + (AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny))] = F[1];
-      }
+      const int f1 = (bca == 0 && k + 1 == n_ax) ? 0 : k + 1;
+      const size_t fl = face_of<AX>(g, k, x, y, z), fr = face_of<AX>(g, f1, x, y, z);
+      const double al = __ldg(uf + fl) * g.lam, ar = __ldg(uf + fr) * g.lam;
+      const double Fl = sc.F[fl], Fr = sc.F[fr];
+      const double Gl = ENERGY ? sc.G[fl] : 0.0, Gr = ENERGY ? sc.G[fr] : 0.0;
+      const double c = __ldg(c_in + id);
+      const double e = ENERGY ? __ldg(e_in + id) : 0.0;
+      const double T = ENERGY ? sc.T[id] : 0.0;
       const uint8_t stv = state ? state[id] : (uint8_t)0;
-      clip += update_cell<ENERGY>(g, id, cw[4], ew[4], Tw[4], stv, F[0], G[0], A[0], F[1], G[1], A[1], c_out,
-                                  e_out, state, theta);
+      clip += update_cell<ENERGY>(g, id, c, e, T, stv, Fl, Gl, al, Fr, Gr, ar, c_out, e_out, state, theta);
     }
   }
   double v[1] = {clip};
@@ -588,45 +669,59 @@ SweepPlan sweep_plan(int axis, const GridDev& g) {
   return p;
 }
 
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// faces of the axis with the most: N + lines
+static size_t max_faces(const GridDev& g) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  size_t lines = 0;
+  for (int a = 0; a < 3; ++a) {
+    const size_t l = N / (size_t)g.n[a];
+    lines = l > lines ? l : lines;
+  }
+  return N + lines;
+}
+
 size_t sweep_scratch_bytes(const GridDev& g) {
-  size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   size_t best = 0;
   for (int a = 0; a < 3; ++a) {
     SweepPlan p = sweep_plan(a, g);
     size_t b = 0;
-    b += (N * 8 + 255) & ~(size_t)255;                                    // T
-    b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // lists
-    b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;                       // counts
-    b += ((size_t)p.gridB * 8 + 255) & ~(size_t)255;                      // partials
-    b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;               // mixed lists (staging)
-    b += 256;                                                             // mixed count
-    b += (N * 4 + 255) & ~(size_t)255;                                    // grid-wide mixed list
-    b += (N * 32 + 255) & ~(size_t)255;                                   // planes
+    b += al256(N * 8);                          // T
+    b += al256((size_t)p.nsub * p.cap * 4);     // lists
+    b += al256((size_t)p.nsub * 4);             // counts
+    b += al256((size_t)p.gridB * 8);            // partials
+    b += al256((size_t)p.nsub * p.cap * 4);     // mixed lists (staging)
+    b += al256((size_t)p.nsub * p.cap * 4);     // run ends (staging)
+    b += 256;                                   // counters
+    b += al256(N * 4);                          // grid-wide mixed list
+    b += al256(2 * N * 4);                      // grid-wide face list
+    b += al256(N * 32);                         // planes
+    b += 2 * al256(max_faces(g) * 8);           // face fluxes F, G
     best = b > best ? b : best;
   }
   return best;
 }
 
 SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* partials, double* diag) {
-  size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   SweepPlan p = sweep_plan(axis, g);
   char* b = static_cast<char*>(ws);
   SweepScratch s;
-  s.T = reinterpret_cast<double*>(b);
-  b += (N * 8 + 255) & ~(size_t)255;
-  s.list = reinterpret_cast<uint32_t*>(b);
-  b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;
-  s.count = reinterpret_cast<int*>(b);
-  b += ((size_t)p.nsub * 4 + 255) & ~(size_t)255;
+  s.T = reinterpret_cast<double*>(b);           b += al256(N * 8);
+  s.list = reinterpret_cast<uint32_t*>(b);      b += al256((size_t)p.nsub * p.cap * 4);
+  s.count = reinterpret_cast<int*>(b);          b += al256((size_t)p.nsub * 4);
   s.partial = partials ? partials : (diag ? nullptr : reinterpret_cast<double*>(b));
-  b += ((size_t)p.gridB * 8 + 255) & ~(size_t)255;
-  s.mlist = reinterpret_cast<uint32_t*>(b);
-  b += ((size_t)p.nsub * p.cap * 4 + 255) & ~(size_t)255;
-  s.gcount = reinterpret_cast<int*>(b);
-  b += 256;
-  s.gmix = reinterpret_cast<uint32_t*>(b);
-  b += (N * 4 + 255) & ~(size_t)255;
-  s.plane = reinterpret_cast<double*>(b);
+  b += al256((size_t)p.gridB * 8);
+  s.mlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
+  s.rlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
+  s.counters = reinterpret_cast<int*>(b);       b += 256;
+  s.gmix = reinterpret_cast<uint32_t*>(b);      b += al256(N * 4);
+  s.gface = reinterpret_cast<uint32_t*>(b);     b += al256(2 * N * 4);
+  s.plane = reinterpret_cast<double*>(b);       b += al256(N * 32);
+  s.F = reinterpret_cast<double*>(b);           b += al256(max_faces(g) * 8);
+  s.G = reinterpret_cast<double*>(b);
   s.diag = diag;
   return s;
 }
@@ -644,8 +739,9 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
                                                                           flux_out != nullptr, p.cap);
   k_planes<<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, sc);
-  k_active<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc,
-                                                 (int)p.nsub, p.cap, status);
+  k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
+  k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,
+                                                 p.cap);
 }
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
@@ -653,7 +749,7 @@ cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const d
                          SweepScratch sc, cudaStream_t st) {
   int* status = device_status_ptr();
   const SweepPlan p = sweep_plan(axis, g);
-  const cudaError_t err = cudaMemsetAsync(sc.gcount, 0, sizeof(int), st);
+  const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 2 * sizeof(int), st);
   if (err != cudaSuccess) return err;
   if (e_in) {
     if (axis == 0) launch_ab<0, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
