@@ -39,7 +39,6 @@ N_CELLS = 256
 SWEEP_BYTES_PER_CELL = 8 + 8 + 8 + 1 + 8 + 8
 # per step: 3 sweeps + zeroing the state (1 B) + shift (read c, e; write c, e)
 STEP_BYTES_PER_CELL = 3 * SWEEP_BYTES_PER_CELL + 1 + 32
-MY_KERNELS_PER_STEP = 7  # 3 sweeps, 1 shift, 3 reductions
 
 
 def dist_env():
@@ -186,35 +185,25 @@ def run_gpu(args):
     cells = wl.cells
     value = cells * args.steps * world / (ms * 1e-3) / 1e9
 
-    # ---- per-kernel durations (same launch configuration) ------------------
-    # the three sweeps and the shift launched one by one through the C ABI,
-    # each bracketed by CUDA events on the launching stream
-    c2, e2 = torch.empty_like(c), torch.empty_like(e)
-    state = torch.zeros(wl.shape, dtype=torch.uint8, device=dev)
-    theta = torch.zeros(wl.shape, dtype=torch.float64, device=dev)
-    reps = max(3, min(args.steps, 50))
-    names = ["sweep_x", "sweep_y", "sweep_z", "shift"]
-    evs = {k: [] for k in names}
+    # ---- per-launch durations of the same step ----------------------------
+    # the library records a CUDA event on the launching stream after each of
+    # its launches (vof_profile_begin/end); durations are per step, averaged
+    # over `reps` steps run right after the timed region
+    reps = max(3, min(args.steps, 20))
     barrier()
+    P.vof_profile_begin(stream)
     for r in range(reps):
-        for k, fn, uf in (("sweep_x", P.vof_advect_sweep_x, u), ("sweep_y", P.vof_advect_sweep_y, v),
-                          ("sweep_z", P.vof_advect_sweep_z, w)):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn(g, c, e, c2, e2, uf, wl.dt, state, theta)
-            b.record(stream)
-            evs[k].append((a, b))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        P.vof_phase_change_shift(g, c, e, c2, e2, None, wl.dd_uniform)
-        b.record(stream)
-        evs["shift"].append((a, b))
+        st.step(c, e, u, v, w, wl.dt, args.warmup + args.steps + r, dd_uniform=wl.dd_uniform)
+    launches = P.vof_profile_end()
     barrier()
-    kern_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in evs[k]])) for k in names}
-    sweep_ms = float(np.mean([kern_ms["sweep_x"], kern_ms["sweep_y"], kern_ms["sweep_z"]]))
+    kern_ms = {}
+    for name, t in launches:
+        kern_ms[name] = kern_ms.get(name, 0.0) + t / reps
+    kernels_per_step = sum(1 for name, _ in launches if "memset" not in name) // reps
     peak, peak_kind = measured_peak_gbs()
+    sweep_ms = 0.0
     sweep_bytes = SWEEP_BYTES_PER_CELL * cells
-    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    achieved = 0.0
     traffic = sweep_traffic_from_profile()
 
     # ---- end to end through the public API with host buffers ---------------
@@ -264,10 +253,10 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": "k_sweep (x/y/z mean)", "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes_per_launch": sweep_bytes},
-            "kernel_ms": {k: round(v_, 5) for k, v_ in kern_ms.items()},
+            "kernel_ms": {k: round(v_, 5) for k, v_ in sorted(kern_ms.items(), key=lambda kv: -kv[1])},
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": P.VOF_NSUMS * 8},
-            "gpu_launches": MY_KERNELS_PER_STEP * args.steps,
+            "gpu_launches": kernels_per_step * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "final_sums": [float(x) for x in sums],
@@ -336,9 +325,8 @@ def run_reference(args):
 
 
 def kernels_once():
-    """One launch of each hot-path kernel on the benchmark workload (the
-    three sweeps and the shift, through the C ABI): the target of the
-    committed ncu captures."""
+    """One time step (vof_step, the benchmark's launch configuration) on
+    the benchmark workload: the target of the committed ncu captures."""
     import torch
     import paper_2001_03477_gb300 as P
     from paper_2001_03477_gb300 import build
@@ -349,14 +337,10 @@ def kernels_once():
     c = torch.from_numpy(wl.c).to(dev)
     e = torch.from_numpy(wl.e).to(dev)
     u, v, w = (torch.from_numpy(a).to(dev) for a in (wl.u, wl.v, wl.w))
-    c2, e2 = torch.empty_like(c), torch.empty_like(e)
-    state = torch.zeros(wl.shape, dtype=torch.uint8, device=dev)
-    theta = torch.zeros(wl.shape, dtype=torch.float64, device=dev)
-    for fn, uf in ((P.vof_advect_sweep_x, u), (P.vof_advect_sweep_y, v), (P.vof_advect_sweep_z, w)):
-        fn(g, c, e, c2, e2, uf, wl.dt, state, theta)
-    P.vof_phase_change_shift(g, c, e, c2, e2, None, wl.dd_uniform)
+    st = P.Stepper(g, device=dev)
+    st.step(c, e, u, v, w, wl.dt, 0, dd_uniform=wl.dd_uniform)
     torch.cuda.synchronize()
-    print("kernels-once ok")
+    print("kernels-once ok", [float(x) for x in st.sums.cpu()])
 
 
 def main():

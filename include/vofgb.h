@@ -211,6 +211,20 @@ VOF_API vof_status vof_step_noalloc(const vof_grid* g, double* c, double* e, con
                                     const double* w, double dt, long step_index, const double* dd, double dd_uniform,
                                     double* sums, void* stream);
 
+/*
+ * Per-launch timing (instrumentation; the paper has no counterpart).
+ * vof_profile_begin(stream) records a start event on `stream`; until
+ * vof_profile_end() every kernel or memset the library launches is followed
+ * by an event on its stream.  vof_profile_end() waits for the last event,
+ * writes up to max_entries launch durations in milliseconds (time from the
+ * previous event, so each includes the gap before its launch) and the
+ * launches' names (static strings owned by the library), and returns the
+ * number of launches recorded (-1 if no profile was open or CUDA failed).
+ * Profile one stream at a time.  VOF_EINVAL if a profile is already open.
+ */
+VOF_API vof_status vof_profile_begin(void* stream);
+VOF_API int vof_profile_end(float* ms, const char** names, int max_entries);
+
 /* Sticky device status (synchronises the device): VOF_OK or VOF_ECFL; reading clears it. */
 VOF_API vof_status vof_get_device_status(void);
 /* Message for a status code (static string). */

@@ -112,6 +112,10 @@ def lib():
         L.vof_shift_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_workspace_bytes.argtypes = [G]
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_profile_begin.argtypes = [P]
+        L.vof_profile_begin.restype = ctypes.c_int
+        L.vof_profile_end.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
+        L.vof_profile_end.restype = ctypes.c_int
         L.vof_get_device_status.argtypes = []
         L.vof_get_device_status.restype = ctypes.c_int
         L.vof_status_string.argtypes = [ctypes.c_int]
@@ -290,6 +294,20 @@ VOF_NOALLOC_MAX_CELLS = 262144
 
 def vof_get_device_status() -> int:
     return int(lib().vof_get_device_status())
+
+
+def vof_profile_begin(stream=None):
+    _check("vof_profile_begin", lib().vof_profile_begin(_stream(stream)))
+
+
+def vof_profile_end(max_entries=4096):
+    """[(launch name, ms)] of the library launches since vof_profile_begin."""
+    ms = (ctypes.c_float * max_entries)()
+    names = (ctypes.c_char_p * max_entries)()
+    n = int(lib().vof_profile_end(ms, names, max_entries))
+    if n < 0:
+        raise VofError("vof_profile_end", VOF_ECUDA, lib())
+    return [(names[i].decode(), float(ms[i])) for i in range(min(n, max_entries))]
 
 
 class Stepper:

@@ -106,17 +106,23 @@ static vof_status sweep_common(int axis, const vof_grid* g, const double* c_in, 
   const size_t need = sweep_scratch_bytes(d);
   if (workspace_bytes < need) return VOF_EINVAL;
   size_t N = cells(g), B = N * 8;
-  if (overlap(c_in, B, c_out, B)) return VOF_EINVAL;
-  if (e_in && (overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) || overlap(e_in, B, c_out, B) ||
-               overlap(c_out, B, e_out, B)))
-    return VOF_EINVAL;
+  // either fully in place (c_out == c_in and e_out == e_in) or no overlap
+  const bool inplace = c_out == c_in && (!e_in || e_out == e_in);
+  if (!inplace) {
+    if (overlap(c_in, B, c_out, B)) return VOF_EINVAL;
+    if (e_in && (overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) || overlap(e_in, B, c_out, B)))
+      return VOF_EINVAL;
+  }
+  if (e_in && (overlap(c_out, B, e_out, B) || overlap(c_in, B, e_in, B))) return VOF_EINVAL;
   if (flux_out && (overlap(flux_out, face_count(g, axis) * 8, c_out, B) ||
                    (e_out && overlap(flux_out, face_count(g, axis) * 8, e_out, B))))
     return VOF_EINVAL;
   if (overlap(workspace, need, c_in, B) || overlap(workspace, need, c_out, B) ||
       (e_in && (overlap(workspace, need, e_in, B) || overlap(workspace, need, e_out, B))))
     return VOF_EINVAL;
-  SweepScratch sc = carve_sweep_scratch(axis, d, workspace, nullptr, diag);
+  // stand-alone sweep: diag[0] += clipped volume
+  static const signed char kMap[kNSums] = {-1, -1, 0, -1, -1, -1};
+  SweepScratch sc = carve_sweep_scratch(axis, d, workspace, sums_to_diag(diag, kMap));
   return cuda_status(launch_sweep(axis, d, c_in, e_in, c_out, e_in ? e_out : nullptr, uf, state, theta, flux_out, sc,
                                   (cudaStream_t)stream));
 }
@@ -170,42 +176,53 @@ vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const d
   const size_t need = shift_scratch_bytes(d);
   if (workspace_bytes < need) return VOF_EINVAL;
   size_t B = cells(g) * 8;
-  if (overlap(c_in, B, c_out, B) || overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) ||
-      overlap(e_in, B, c_out, B) || overlap(c_out, B, e_out, B))
+  // either fully in place (c_out == c_in and e_out == e_in) or no overlap
+  const bool inplace = c_out == c_in && e_out == e_in;
+  if (!inplace && (overlap(c_in, B, c_out, B) || overlap(e_in, B, e_out, B) || overlap(c_in, B, e_out, B) ||
+                   overlap(e_in, B, c_out, B)))
     return VOF_EINVAL;
+  if (overlap(c_out, B, e_out, B) || overlap(c_in, B, e_in, B)) return VOF_EINVAL;
   if (overlap(workspace, need, c_in, B) || overlap(workspace, need, c_out, B) || overlap(workspace, need, e_in, B) ||
       overlap(workspace, need, e_out, B) || (dd && overlap(workspace, need, dd, B)) ||
       (state && overlap(workspace, need, state, cells(g))) || (diag && overlap(workspace, need, diag, 5 * 8)))
     return VOF_EINVAL;
-  SumOut so{nullptr, 5, diag};
+  // diag = {sum dc, clamped, sum de, sum c_out, sum e_out}
+  static const signed char kMap[kNSums] = {3, 4, -1, 0, 1, 2};
+  const SumOut so = sums_to_diag(diag, kMap);
   return cuda_status(launch_shift(d, c_in, e_in, c_out, e_out, dd, dd_uniform, state, carve_shift_scratch(d, workspace),
-                                  so, (cudaStream_t)stream));
+                                  so, so, (cudaStream_t)stream));
 }
 
-// workspace layout: c2 | e2 | theta | state | partials (3 sweeps x 1,
-// 2 shift kernels x 5) | scratch (reused by the three sweeps, then the shift)
+// workspace layout: theta | state | sum rows (tile pass, the three sweeps'
+// update kernels, the shift's sums kernel; kNSums doubles per CTA) |
+// reduction scratch | tiles |
+// scratch (reused by the three sweeps, then the shift).  The sweeps and the
+// shift all run in place on c and e; the tile pass sums c and e at the start
+// and every later kernel adds the changes it makes, so one fixed-order
+// reduction of all rows gives the sums at the end of the step.
 struct StepLayout {
-  size_t off_c2, off_e2, off_th, off_st, off_ps, off_sh, off_sw, total;
-  int nb_sw[3], nb_sh;
+  size_t off_th, off_st, off_rows, off_red, off_tiles, off_sw, total;
+  int nb_tiles, nb_sw[3], nb_sh, nrows;
 };
 
 static StepLayout step_layout(const vof_grid* g) {
   StepLayout L;
   GridDev d = to_dev(g, 0.0);
   size_t N = cells(g);
-  L.off_c2 = 0;
-  L.off_e2 = L.off_c2 + align256(N * 8);
-  L.off_th = L.off_e2 + align256(N * 8);
+  L.off_th = 0;
   L.off_st = L.off_th + align256(N * 8);
-  L.off_ps = L.off_st + align256(N);
-  size_t nsw = 0;
+  L.off_rows = L.off_st + align256(N);
+  L.nb_tiles = tile_blocks(d);
+  L.nrows = L.nb_tiles;
   for (int a = 0; a < 3; ++a) {
     L.nb_sw[a] = sweep_blocks(a, d);
-    nsw += (size_t)L.nb_sw[a];
+    L.nrows += L.nb_sw[a];
   }
-  L.nb_sh = shift_blocks(d);
-  L.off_sh = L.off_ps + align256(nsw * 8);
-  L.off_sw = L.off_sh + align256((size_t)kShiftPartialSets * L.nb_sh * 5 * 8);
+  L.nb_sh = shift_sum_blocks(d);
+  L.nrows += L.nb_sh;
+  L.off_red = L.off_rows + align256((size_t)L.nrows * kNSums * 8);
+  L.off_tiles = L.off_red + align256(reduce_scratch_bytes());
+  L.off_sw = L.off_tiles + align256(tile_scratch_bytes(d));
   const size_t sw = sweep_scratch_bytes(d), sh = shift_scratch_bytes(d);
   L.total = L.off_sw + align256(sw > sh ? sw : sh);
   return L;
@@ -229,41 +246,45 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
     return VOF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = static_cast<char*>(workspace);
-  double* c2 = reinterpret_cast<double*>(ws + L.off_c2);
-  double* e2 = reinterpret_cast<double*>(ws + L.off_e2);
   double* th = reinterpret_cast<double*>(ws + L.off_th);
   uint8_t* state = reinterpret_cast<uint8_t*>(ws + L.off_st);
-  double* ps = reinterpret_cast<double*>(ws + L.off_ps);
-  double* psh = reinterpret_cast<double*>(ws + L.off_sh);
+  double* rows = reinterpret_cast<double*>(ws + L.off_rows);
   GridDev d = to_dev(g, dt);
   const double* uf[3] = {u, v, w};
   cudaError_t err = cudaMemsetAsync(state, 0, N, st);
   if (err != cudaSuccess) return cuda_status(err);
-  double* src_c = c;
-  double* src_e = e;
-  double* dst_c = c2;
-  double* dst_e = e2;
-  size_t poff = 0;
-  int order[3];
-  for (int s = 0; s < 3; ++s) order[s] = (step_index % 2 == 0) ? s : 2 - s;
-  for (int s = 0; s < 3; ++s) {
-    int ax = order[s];
-    SweepScratch sc = carve_sweep_scratch(ax, d, ws + L.off_sw, ps + poff, nullptr);
-    err = launch_sweep(ax, d, src_c, src_e, dst_c, dst_e, uf[ax], state, th, nullptr, sc, st);
-    if (err != cudaSuccess) return cuda_status(err);
-    poff += (size_t)L.nb_sw[ax];
-    double* tc = src_c; src_c = dst_c; dst_c = tc;
-    double* te = src_e; src_e = dst_e; dst_e = te;
-  }
-  // after 3 sweeps the state sits in the workspace; the shift writes back
-  SumOut so{psh, 5, nullptr};
-  err = launch_shift(d, src_c, src_e, c, e, dd, dd_uniform, nullptr, carve_shift_scratch(d, ws + L.off_sw), so, st);
+  prof_mark("step.memset_state", st);
+  // tile pass: quiet tiles and the sums of c, e at the start of the step
+  const TileScratch ts = carve_tile_scratch(d, ws + L.off_tiles);
+  size_t r = 0;
+  err = launch_tiles(d, c, e, ts, sums_to_partials(rows, kNSums), st);
   if (err != cudaSuccess) return cuda_status(err);
+  r += (size_t)L.nb_tiles;
+  TileMap tm{nullptr, {0, 0, 0}};
+  if (tiles_usable(d)) {
+    tm.quiet = ts.quiet;
+    tile_counts(d, tm.nt);
+  }
+  for (int s = 0; s < 3; ++s) {
+    const int ax = (step_index % 2 == 0) ? s : 2 - s;
+    SweepScratch sc = carve_sweep_scratch(ax, d, ws + L.off_sw, sums_to_partials(rows + r * kNSums, kNSums));
+    sc.tiles = tm;
+    err = launch_sweep(ax, d, c, e, c, e, uf[ax], state, th, nullptr, sc, st);
+    if (err != cudaSuccess) return cuda_status(err);
+    r += (size_t)L.nb_sw[ax];
+  }
+  ShiftScratch shs = carve_shift_scratch(d, ws + L.off_sw);
+  shs.tiles = tm;
+  const SumOut none = sums_to_partials(nullptr, kNSums);
+  err = launch_shift(d, c, e, c, e, dd, dd_uniform, nullptr, shs, none, sums_to_partials(rows + r * kNSums, kNSums),
+                     st);
+  if (err != cudaSuccess) return cuda_status(err);
+  r += (size_t)L.nb_sh;
   if (sums) {
     // sums[0..1] = sum c, sum e; sums[2] = clip; sums[3..5] = shift diagnostics
-    err = launch_reduce(psh, kShiftPartialSets * L.nb_sh, 5, 3, 2, sums, st);
-    if (err == cudaSuccess) err = launch_reduce(ps, (int)poff, 1, 0, 1, sums + 2, st);
-    if (err == cudaSuccess) err = launch_reduce(psh, kShiftPartialSets * L.nb_sh, 5, 0, 3, sums + 3, st);
+    ReduceJobs jobs{};
+    jobs.job[0] = ReduceJob{rows, (int)r, kNSums, 0, kNSums, sums};
+    err = launch_reduce(jobs, 1, reinterpret_cast<double*>(ws + L.off_red), st);
     if (err != cudaSuccess) return cuda_status(err);
   }
   return VOF_OK;

@@ -10,13 +10,43 @@
 
 namespace vofgb {
 
-// Per-block partial sums: a kernel either writes its block's partials to
-// `partials[block * stride + k]` (deterministic, reduced later in a fixed
-// order) or, when partials == nullptr, adds them to `diag[k]` with atomics.
+// Sums.  Every kernel that sums produces one row of kNSums values per CTA,
+// in one layout:
+//   [kSumC] sum of c contributions   [kSumE] sum of e contributions
+//   [kSumClip] clipped volume of the sweeps
+//   [kSumShDc] shift: sum Delta c    [kSumUnpl] shift: volume clamped away
+//   [kSumShDe] shift: sum Delta e
+// and either writes it to partials[block * stride] (deterministic, reduced
+// later in a fixed order) or, when partials == nullptr, adds each value k
+// with map[k] >= 0 to diag[map[k]] with an atomic (nothing when diag is
+// null too).
+enum { kSumC = 0, kSumE, kSumClip, kSumShDc, kSumUnpl, kSumShDe, kNSums };
 struct SumOut {
   double* partials;
   int stride;
   double* diag;
+  signed char map[kNSums];
+};
+inline SumOut sums_to_partials(double* p, int stride) {
+  SumOut s{p, stride, nullptr, {-1, -1, -1, -1, -1, -1}};
+  return s;
+}
+inline SumOut sums_to_diag(double* diag, const signed char (&map)[kNSums]) {
+  SumOut s{nullptr, kNSums, diag, {map[0], map[1], map[2], map[3], map[4], map[5]}};
+  return s;
+}
+
+// Quiet tiles: 8^3 tiles whose cells, with a 3-cell halo, all hold the same
+// (c, e) bits with c exactly 0 or 1 at the start of a time step.  No cell of
+// such a tile changes in any of the step's three sweeps (each sweep's 7-cell
+// window stays inside the uniform box, and the cells of the box outside the
+// tile that the earlier sweeps' windows reach are themselves no-ops), and none
+// is mixed when the shift runs, so the streaming kernels of an in-place step
+// skip them.  quiet == nullptr: no tile is skipped.
+constexpr int kTile = 8;
+struct TileMap {
+  const uint8_t* quiet;
+  int nt[3];  // tiles per axis
 };
 
 // Scratch of one sweep (kernel A -> kernels M, F, U): T of the cells whose
@@ -30,8 +60,8 @@ struct SweepScratch {
   double* T;
   uint32_t* list;
   int* count;
-  double* partial;
-  double* diag;
+  SumOut sums;       // per-CTA sums of kernel U: Delta c, Delta e, clipped volume
+  TileMap tiles;     // quiet tiles (in-place steps only)
   uint32_t* mlist;   // per-warp staging lists of mixed cells
   uint32_t* rlist;   // per-warp staging lists of run ends
   int* counters;     // [0] mixed cells, [1] face items (zeroed before kernel A)
@@ -51,15 +81,16 @@ struct SweepPlan {
 
 SweepPlan sweep_plan(int axis, const GridDev& g);
 size_t sweep_scratch_bytes(const GridDev& g);
-SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* partials, double* diag);
+SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, SumOut sums);
 
 int sweep_blocks(int axis, const GridDev& g);
 
 // Scratch of the shift: per-warp lists of moving mixed cells with their
-// counts (fixed order), a grid-wide list of the same cells and one of the
-// receivers (no fixed order) with their counters, and per cell: the plane
-// (m0, m1, m2, alpha) and shift |m|_2 dd of a moving mixed cell, the mask of
-// receivers it settles, and the volume swept into a receiver.
+// counts (fixed order; a warp owns up to 256 cells of one x row), a
+// grid-wide list of the same cells and one of the receivers (no fixed order)
+// with their counters, and per cell: the plane (m0, m1, m2, alpha), shift
+// |m|_2 dd and shifted volume of a moving mixed cell, the mask of receivers
+// it settles, and the volume swept into a receiver.
 struct ShiftScratch {
   uint32_t* list;
   int* count;
@@ -69,15 +100,34 @@ struct ShiftScratch {
   double* plane;  // [N][4]
   double* shift;  // [N]
   double* sweep;  // [N]
+  double* cnew;   // [N] shifted volume of a moving mixed cell
   uint32_t* own;  // [N]
+  TileMap tiles;  // quiet tiles (in-place steps only)
 };
 
-// CTAs of the shift's stream and sums kernels; their partial sums take
-// kShiftPartialSets * shift_blocks rows of the SumOut
-constexpr int kShiftPartialSets = 2;
-int shift_blocks(const GridDev& g);
+// The shift's kernels: stream (lists; out of place also copies; sums c, e
+// when `stream_sums` is given) and sums (applies and sums the changes).
+// sum_blocks: CTAs of the sums kernel (rows it writes to its SumOut).
+int shift_sum_blocks(const GridDev& g);
+int shift_stream_blocks(const GridDev& g);
 size_t shift_scratch_bytes(const GridDev& g);
 ShiftScratch carve_shift_scratch(const GridDev& g, void* ws);
+
+// Tiles: per-tile uniform flag and values, then the quiet map; the tile
+// pass also sums c and e over the grid (per-CTA rows).
+struct TileScratch {
+  uint8_t* uni;
+  double* vc;
+  double* ve;
+  uint8_t* quiet;
+};
+void tile_counts(const GridDev& g, int nt[3]);
+bool tiles_usable(const GridDev& g);
+int tile_blocks(const GridDev& g);
+size_t tile_scratch_bytes(const GridDev& g);
+TileScratch carve_tile_scratch(const GridDev& g, void* ws);
+cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, TileScratch ts, SumOut sums,
+                         cudaStream_t st);
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
@@ -88,17 +138,29 @@ cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, co
                           double* theta, cudaStream_t st);
 
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
-                         const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut sums,
-                         cudaStream_t st);
+                         const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut stream_sums,
+                         SumOut sums, cudaStream_t st);
 
 cudaError_t launch_reconstruct(const GridDev& g, const double* c, double* m, double* alpha, uint8_t* mixed,
                                cudaStream_t st);
 
-cudaError_t launch_reduce(const double* partials, int nblocks, int stride, int k0, int nk, double* out,
-                          cudaStream_t st);
+// out[k] = sum over b < nblocks of partials[b * stride + k0 + k], k < nk
+struct ReduceJob {
+  const double* partials;
+  int nblocks, stride, k0, nk;
+  double* out;
+};
+constexpr int kMaxReduceJobs = 4;
+constexpr int kMaxReduceK = 8;      // outputs per job at most
+constexpr int kReduceCTAs = 152;    // first-level CTAs per job
+struct ReduceJobs {
+  ReduceJob job[kMaxReduceJobs];
+};
+size_t reduce_scratch_bytes();
+cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st);
 
-cudaError_t launch_sum_fields(const GridDev& g, const double* c, const double* e, double* partials,
-                              int* nblocks_out, cudaStream_t st);
+// per-launch timing (vof_profile_begin/end): records an event after a launch
+void prof_mark(const char* name, cudaStream_t st);
 
 // sticky device status word (iteration caps, CFL > 1): bit flags
 enum : int { DEV_CFL = 1 };

@@ -12,6 +12,7 @@
 // Only cells at the interface do work, so the kernels after the first one
 // visit a compact list of the moving mixed cells instead of the grid.
 #include "vof_launch.h"
+#include "vof_sums.cuh"
 
 namespace vofgb {
 
@@ -19,36 +20,12 @@ constexpr int kShBX = 32, kShBY = 4, kShBZ = 2, kShThreads = kShBX * kShBY * kSh
 
 __device__ __forceinline__ bool same_bits_dev(double a, double b) { return dbits(a) == dbits(b); }
 
-template <int K>
-__device__ __forceinline__ void block_sums_sh(double (&v)[K], SumOut out, int block_lin) {
-  __shared__ double red[K][kShThreads / 32];  // up to 8 warps
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) red[k][warp] = x;
-  }
-  __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      const int nw = (int)(blockDim.x * blockDim.y * blockDim.z) / 32;
-      for (int w = 0; w < nw; ++w) s += red[k][w];
-      if (out.partials) out.partials[(size_t)block_lin * out.stride + k] = s;
-      else if (out.diag) atomicAdd(out.diag + k, s);
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Shift in four kernels.
-//   stream:    copies c, e to the output and sums them; lists the moving
-//              mixed cells per warp (256 consecutive cells per warp, fixed
-//              order) and appends them to a grid-wide list, cells with c
+//   stream:    (out of place: copies c, e to the output; stand-alone: sums
+//              c, e) lists the moving mixed cells per warp (up to 256 cells
+//              of one x row per warp, fixed order) and appends them to a
+//              grid-wide list, cells with c
 //              within 1e-3 of 0 or 1 ("edge" cells, whose plane constant
 //              takes the bisection) at its back, the others at its front;
 //   planes:    one moving mixed cell per thread over the grid-wide list:
@@ -58,9 +35,11 @@ __device__ __forceinline__ void block_sums_sh(double (&v)[K], SumOut out, int bl
 //              neighbour (scan order z outer, x inner) it is;
 //   receivers: one receiver per thread: the largest volume swept in it by
 //              the extended planes of its reaching neighbours;
-//   sums:      per warp list in fixed order, the changes of every moving
-//              cell and of the receivers it settled, so the sums do not
-//              depend on the order of the grid-wide lists.
+//   sums:      per warp list in fixed order, applies and sums the changes
+//              of every moving cell and of the receivers it settled, so the
+//              sums do not depend on the order of the grid-wide lists.
+// Only the last kernel writes c and e, and each cell it writes is touched by
+// one thread, so the shift may run in place (c_out == c_in, e_out == e_in).
 // ---------------------------------------------------------------------------
 constexpr int kWarpCells = 256;
 constexpr unsigned kFullMask = 0xffffffffu;
@@ -109,35 +88,59 @@ __device__ __forceinline__ int offset_bit(int ox, int oy, int oz) { return ((oz 
 __global__ void __launch_bounds__(256)
 k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
                double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
-               SumOut sums) {
+               SumOut sums, int copy) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-  const int lane = threadIdx.x & 31;
+  const int nx = g.n[0], ny = g.n[1];
+  const int lane = threadIdx.x, warp = threadIdx.y;
   const unsigned lt = (1u << lane) - 1u;
-  const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  uint32_t* list = sc.list + w * kWarpCells;
-  int n = 0, ne = 0;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const bool uni_moving = dnz(dd_uniform);
-  for (int it = 0; it < kWarpCells / 32; ++it) {
-    const size_t id = w * kWarpCells + (size_t)it * 32 + lane;
-    const bool ok = id < N;
-    double c = 0.0, e = 0.0;
-    if (ok) {
-      c = __ldg(c_in + id);
-      e = __ldg(e_in + id);
-      c_out[id] = c;
-      e_out[id] = e;
-      acc[3] += c;
-      acc[4] += e;
-    }
-    bool moving = ok && is_mixed_b(c, g);
-    if (moving) moving = dd ? dnz(__ldg(dd + id)) : uni_moving;
-    const unsigned m = __ballot_sync(kFullMask, moving);
-    if (moving) list[n + __popc(m & lt)] = (uint32_t)id;
-    n += __popc(m);
-    ne += __popc(__ballot_sync(kFullMask, moving && edge_cell(c)));
+  const int row = blockIdx.x * 8 + warp;  // row = z * ny + y (grid x: rows, grid y: segments)
+  const bool rowok = row < ny * g.n[2];
+  const int x0 = blockIdx.y * kWarpCells, x1 = min(x0 + kWarpCells, nx);
+  const size_t rbase = (size_t)(rowok ? row : 0) * nx;
+  const size_t w = (size_t)row * gridDim.y + blockIdx.y;  // list of this warp
+  const int cap = nx < kWarpCells ? nx : kWarpCells;
+  uint32_t* list = sc.list + w * cap;
+  const bool do_sums = sums.partials || sums.diag;
+  // quiet tiles of the row segment (in place only): bit l = tile l quiet
+  unsigned qmask = 0u;
+  if (sc.tiles.quiet && !copy && !do_sums && rowok) {
+    const int txi = (x0 >> 3) + lane;
+    const int y = row % ny, z = row / ny;
+    const bool q = txi * kTile < x1 &&
+                   sc.tiles.quiet[((size_t)(z >> 3) * sc.tiles.nt[1] + (y >> 3)) * sc.tiles.nt[0] + txi] != 0;
+    qmask = __ballot_sync(kFullMask, q);
   }
-  if (lane == 0 && (long long)w * kWarpCells < (long long)N) sc.count[w] = n;
+  int n = 0, ne = 0;
+  double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const bool uni_moving = dnz(dd_uniform);
+  if (rowok) {
+    for (int it = 0; it < kWarpCells / 32 && x0 + 32 * it < x1; ++it) {
+      if (((qmask >> (4 * it)) & 0xFu) == 0xFu) continue;  // four quiet tiles: no mixed cell
+      const int X = x0 + 32 * it + lane;
+      const bool ok = X < x1;
+      const size_t id = rbase + X;
+      double c = 0.0;
+      if (ok) {
+        c = __ldg(c_in + id);
+        if (copy || do_sums) {
+          const double e = __ldg(e_in + id);
+          if (copy) {  // out of place: every cell starts as a copy
+            c_out[id] = c;
+            e_out[id] = e;
+          }
+          v[kSumC] += c;
+          v[kSumE] += e;
+        }
+      }
+      bool moving = ok && is_mixed_b(c, g);
+      if (moving) moving = dd ? dnz(__ldg(dd + id)) : uni_moving;
+      const unsigned m = __ballot_sync(kFullMask, moving);
+      if (moving) list[n + __popc(m & lt)] = (uint32_t)id;
+      n += __popc(m);
+      ne += __popc(__ballot_sync(kFullMask, moving && edge_cell(c)));
+    }
+    if (lane == 0) sc.count[w] = n;
+  }
   if (n > 0) {  // warp-uniform: append to the grid-wide list
     int bn = 0, be = 0;
     if (lane == 0) {
@@ -149,22 +152,22 @@ k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restr
     __syncwarp();
     for (int j0 = 0; j0 < n; j0 += 32) {
       const int j = j0 + lane;
-      const bool v = j < n;
-      const uint32_t id = v ? list[j] : 0u;
-      const bool edge = v && edge_cell(__ldg(c_in + id));
-      const unsigned me = __ballot_sync(kFullMask, edge), mn = __ballot_sync(kFullMask, v && !edge);
+      const bool vv = j < n;
+      const uint32_t id = vv ? list[j] : 0u;
+      const bool edge = vv && edge_cell(__ldg(c_in + id));
+      const unsigned me = __ballot_sync(kFullMask, edge), mn = __ballot_sync(kFullMask, vv && !edge);
       if (edge) sc.gmix[N - 1 - (size_t)(be + __popc(me & lt))] = id;
-      else if (v) sc.gmix[bn + __popc(mn & lt)] = id;
+      else if (vv) sc.gmix[bn + __popc(mn & lt)] = id;
       be += __popc(me);
       bn += __popc(mn);
     }
   }
-  block_sums_sh<5>(acc, sums, blockIdx.x);
+  block_sums(v, sums, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
 __global__ void __launch_bounds__(kListThreads)
-k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc) {
+k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
+               ShiftScratch sc) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int nn = sc.counters[0], ne = sc.counters[1];
   const int lane = threadIdx.x & 31;
@@ -212,11 +215,7 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
       double ast = al + sft;
       if (ast < lo) ast = lo;
       if (ast > hi) ast = hi;
-      const double cn = volume(m[0], m[1], m[2], ast);
-      if (!same_bits_dev(cn, ct)) {
-        c_out[id] = cn;
-        e_out[id] = __ldg(e_in + id) + (cn - ct) * (g.Cp_l - g.Cp_g) * g.T_sat;
-      }
+      sc.cnew[id] = volume(m[0], m[1], m[2], ast);  // applied by the sums kernel
       // receivers this cell settles
       const bool full = dlt0(ddv);  // the kind of pure cell this shift reaches
       for (int oz = -1; oz <= 1; ++oz)
@@ -268,9 +267,8 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
 }
 
 __global__ void __launch_bounds__(kListThreads)
-k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in,
-                  double* __restrict__ c_out, double* __restrict__ e_out, const double* __restrict__ dd,
-                  double dd_uniform, ShiftScratch sc) {
+k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
+                  ShiftScratch sc) {
   const int nr = sc.counters[2];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
     const size_t pid = sc.recv[i];
@@ -304,32 +302,35 @@ k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __re
           const double sw = volume(m0, m1, m2, a_new) - volume(m0, m1, m2, a_old);
           if (fabs(sw) > fabs(best)) best = sw;
         }
-    sc.sweep[pid] = best;
-    if (dnz(best)) {
-      const double v = cp + best;
-      const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
-      if (!same_bits_dev(vc, cp)) {
-        c_out[pid] = vc;
-        e_out[pid] = __ldg(e_in + pid) + (vc - cp) * (g.Cp_l - g.Cp_g) * g.T_sat;
-      }
-    }
+    sc.sweep[pid] = best;  // applied by the sums kernel
   }
 }
 
+// Applies the new values (moving cells and the receivers they settle) and
+// sums the changes, per warp list in fixed order.  Every cell it writes is
+// read and written by one thread only, so it may work in place.
 __global__ void __launch_bounds__(256)
-k_shift_sums(GridDev g, const double* __restrict__ c_in, const double* __restrict__ c_out, ShiftScratch sc,
+k_shift_sums(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out, ShiftScratch sc,
              long long nwarps, SumOut sums) {
   const int lane = threadIdx.x & 31;
   const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int cap = g.n[0] < kWarpCells ? g.n[0] : kWarpCells;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // dc, clamped, de
   if ((long long)w < nwarps) {
     const int cnt = sc.count[w];
-    const uint32_t* list = sc.list + w * kWarpCells;
+    const uint32_t* list = sc.list + w * cap;
     for (int i = lane; i < cnt; i += 32) {
       const size_t qid = list[i];
-      const double dq = c_out[qid] - __ldg(c_in + qid);
-      acc[0] += dq;
-      acc[2] += dq * (g.Cp_l - g.Cp_g) * g.T_sat;
+      const double ct = c_in[qid], cn = sc.cnew[qid];
+      if (!same_bits_dev(cn, ct)) {
+        const double dc = cn - ct;
+        const double de = dc * (g.Cp_l - g.Cp_g) * g.T_sat;
+        const double eq = e_in[qid];
+        c_out[qid] = cn;
+        e_out[qid] = eq + de;
+        acc[0] += dc;
+        acc[2] += de;
+      }
       unsigned own = sc.own[qid];
       if (!own) continue;
       int x, y, z;
@@ -341,19 +342,30 @@ k_shift_sums(GridDev g, const double* __restrict__ c_in, const double* __restric
         neighbour(g, x, y, z, b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1, pid);
         const double best = sc.sweep[pid];
         if (!dnz(best)) continue;
-        const double cp = __ldg(c_in + pid);
+        const double cp = c_in[pid];
         const double v = cp + best;
         const double vc = dlt0(v) ? 0.0 : (dgt1(v) ? 1.0 : v);
         if (!deq(v, vc)) acc[1] += v - vc;
-        const double dc = vc - cp;
-        acc[0] += dc;
-        acc[2] += dc * (g.Cp_l - g.Cp_g) * g.T_sat;
+        if (!same_bits_dev(vc, cp)) {
+          const double dc = vc - cp;
+          const double de = dc * (g.Cp_l - g.Cp_g) * g.T_sat;
+          const double ep = e_in[pid];
+          c_out[pid] = vc;
+          e_out[pid] = ep + de;
+          acc[0] += dc;
+          acc[2] += de;
+        }
       }
     }
   }
-  acc[3] = acc[0];  // sum c_out = sum c_in + sum dc
-  acc[4] = acc[2];
-  block_sums_sh<5>(acc, sums, blockIdx.x);
+  double v[kNSums];
+  v[kSumC] = acc[0];  // sum c_out = sum c_in + sum dc
+  v[kSumE] = acc[2];
+  v[kSumClip] = 0.0;
+  v[kSumShDc] = acc[0];
+  v[kSumUnpl] = acc[1];
+  v[kSumShDe] = acc[2];
+  block_sums(v, sums, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kShThreads)
@@ -403,36 +415,47 @@ static dim3 sh_grid(const GridDev& g) {
   return dim3((g.n[0] + kShBX - 1) / kShBX, (g.n[1] + kShBY - 1) / kShBY, (g.n[2] + kShBZ - 1) / kShBZ);
 }
 
+// one list per x-row segment of up to kWarpCells cells
 static long long shift_warps(const GridDev& g) {
-  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-  return (long long)((N + kWarpCells - 1) / kWarpCells);
+  return (long long)((g.n[0] + kWarpCells - 1) / kWarpCells) * g.n[1] * g.n[2];
 }
 
-// CTAs of the stream and sums kernels (8 warps of 256 cells)
-int shift_blocks(const GridDev& g) { return (int)((shift_warps(g) + 7) / 8); }
+int shift_sum_blocks(const GridDev& g) { return (int)((shift_warps(g) + 7) / 8); }
+
+static dim3 shift_stream_grid(const GridDev& g) {
+  return dim3((unsigned)((g.n[1] * g.n[2] + 7) / 8), (unsigned)((g.n[0] + kWarpCells - 1) / kWarpCells), 1);
+}
+
+int shift_stream_blocks(const GridDev& g) {
+  const dim3 d = shift_stream_grid(g);
+  return (int)(d.x * d.y);
+}
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t shift_scratch_bytes(const GridDev& g) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-  const size_t nw = (size_t)shift_blocks(g) * 8;
-  return al256(nw * kWarpCells * 4)  // per-warp lists
-         + al256(nw * 4)             // counts
-         + 256                       // counters
-         + al256(N * 4)              // grid-wide list of moving cells
-         + al256(N * 4)              // receivers
-         + al256(N * 32)             // planes
-         + al256(N * 8)              // shifts
-         + al256(N * 8)              // sweeps
-         + al256(N * 4);             // settled-receiver masks
+  const size_t nw = (size_t)shift_warps(g);
+  const size_t cap = g.n[0] < kWarpCells ? g.n[0] : kWarpCells;
+  return al256(nw * cap * 4)  // per-warp lists
+         + al256(nw * 4)      // counts
+         + 256                // counters
+         + al256(N * 4)       // grid-wide list of moving cells
+         + al256(N * 4)       // receivers
+         + al256(N * 32)      // planes
+         + al256(N * 8)       // shifts
+         + al256(N * 8)       // sweeps
+         + al256(N * 8)       // new c of moving cells
+         + al256(N * 4);      // settled-receiver masks
 }
 
 ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
-  const size_t nw = (size_t)shift_blocks(g) * 8;
+  const size_t nw = (size_t)shift_warps(g);
+  const size_t cap = g.n[0] < kWarpCells ? g.n[0] : kWarpCells;
   char* b = static_cast<char*>(ws);
   ShiftScratch s;
-  s.list = reinterpret_cast<uint32_t*>(b);   b += al256(nw * kWarpCells * 4);
+  s.list = reinterpret_cast<uint32_t*>(b);   b += al256(nw * cap * 4);
   s.count = reinterpret_cast<int*>(b);       b += al256(nw * 4);
   s.counters = reinterpret_cast<int*>(b);    b += 256;
   s.gmix = reinterpret_cast<uint32_t*>(b);   b += al256(N * 4);
@@ -440,56 +463,99 @@ ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   s.plane = reinterpret_cast<double*>(b);    b += al256(N * 32);
   s.shift = reinterpret_cast<double*>(b);    b += al256(N * 8);
   s.sweep = reinterpret_cast<double*>(b);    b += al256(N * 8);
+  s.cnew = reinterpret_cast<double*>(b);     b += al256(N * 8);
   s.own = reinterpret_cast<uint32_t*>(b);
+  s.tiles = TileMap{nullptr, {0, 0, 0}};
   return s;
 }
 
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
-                         const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut sums,
-                         cudaStream_t st) {
+                         const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut stream_sums,
+                         SumOut sums, cudaStream_t st) {
   const long long nw = shift_warps(g);
-  const unsigned nb = (unsigned)shift_blocks(g);
-  // the stream and sums kernels write partials to consecutive sets of nb CTAs
-  SumOut s0 = sums, s1 = sums;
-  if (sums.partials) s1.partials = sums.partials + (size_t)nb * sums.stride;
   cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
   if (err != cudaSuccess) return err;
-  k_shift_stream<<<nb, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, s0);
-  k_shift_planes<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc);
-  k_shift_receivers<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc);
-  k_shift_sums<<<nb, 256, 0, st>>>(g, c_in, c_out, sc, nw, s1);
+  prof_mark("shift.memset", st);
+  k_shift_stream<<<shift_stream_grid(g), dim3(32, 8), 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc,
+                                                               stream_sums, c_out != c_in);
+  prof_mark("shift.stream", st);
+  k_shift_planes<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
+  prof_mark("shift.planes", st);
+  k_shift_receivers<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
+  prof_mark("shift.receivers", st);
+  k_shift_sums<<<shift_sum_blocks(g), 256, 0, st>>>(g, c_in, e_in, c_out, e_out, sc, nw, sums);
+  prof_mark("shift.sums", st);
   err = cudaGetLastError();
-  if (err == cudaSuccess && state) err = cudaMemsetAsync(state, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
+  if (err == cudaSuccess && state) {
+    err = cudaMemsetAsync(state, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
+    prof_mark("shift.memset_state", st);
+  }
   return err;
 }
 
 cudaError_t launch_reconstruct(const GridDev& g, const double* c, double* m, double* alpha, uint8_t* mixed,
                                cudaStream_t st) {
   k_reconstruct<<<sh_grid(g), dim3(kShBX, kShBY, kShBZ), 0, st>>>(g, c, m, alpha, mixed);
+  prof_mark("reconstruct", st);
   return cudaGetLastError();
 }
 
 // Deterministic reduction of per-block partials: one CTA, fixed order.
-__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ partials, int nblocks, int stride, int k0,
-                                                int nk, double* __restrict__ out) {
-  __shared__ double red[256];
-  for (int k = 0; k < nk; ++k) {
+// Fixed-order reduction of per-CTA partial sums in two levels: kReduceCTAs
+// CTAs each sum a fixed contiguous range of rows (one row per thread, then a
+// shared-memory tree) into scratch, then one CTA per job sums those partials
+// the same way.  The order depends only on the sizes, so the sums are
+// identical run to run.
+constexpr int kReduceThreads = 256;
+
+__device__ __forceinline__ double tree_sum(double x, double* red) {
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_reduce1(ReduceJobs jobs, double* __restrict__ scratch) {
+  __shared__ double red[kReduceThreads];
+  const ReduceJob J = jobs.job[blockIdx.y];
+  const int chunk = (J.nblocks + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * chunk, b1 = min(b0 + chunk, J.nblocks);
+  for (int k = 0; k < J.nk; ++k) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * stride + k0 + k];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = red[0];
-    __syncthreads();
+    for (int b = b0 + threadIdx.x; b < b1; b += kReduceThreads) s += J.partials[(size_t)b * J.stride + J.k0 + k];
+    const double t = tree_sum(s, red);
+    if (threadIdx.x == 0) scratch[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kMaxReduceK + k] = t;
   }
 }
 
-cudaError_t launch_reduce(const double* partials, int nblocks, int stride, int k0, int nk, double* out,
-                          cudaStream_t st) {
-  k_reduce<<<1, 256, 0, st>>>(partials, nblocks, stride, k0, nk, out);
+__global__ void __launch_bounds__(kReduceThreads) k_reduce2(ReduceJobs jobs, const double* __restrict__ scratch,
+                                                            int nparts) {
+  __shared__ double red[kReduceThreads];
+  const ReduceJob J = jobs.job[blockIdx.x];
+  for (int k = 0; k < J.nk; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kReduceThreads)
+      s += scratch[((size_t)blockIdx.x * nparts + b) * kMaxReduceK + k];
+    const double t = tree_sum(s, red);
+    if (threadIdx.x == 0) J.out[k] = t;
+  }
+}
+
+size_t reduce_scratch_bytes() { return (size_t)kMaxReduceJobs * kReduceCTAs * kMaxReduceK * sizeof(double); }
+
+cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st) {
+  if (njobs <= 0 || njobs > kMaxReduceJobs) return cudaErrorInvalidValue;
+  for (int j = 0; j < njobs; ++j)
+    if (jobs.job[j].nk > kMaxReduceK) return cudaErrorInvalidValue;
+  k_reduce1<<<dim3(kReduceCTAs, njobs), kReduceThreads, 0, st>>>(jobs, scratch);
+  prof_mark("reduce.1", st);
+  k_reduce2<<<njobs, kReduceThreads, 0, st>>>(jobs, scratch, kReduceCTAs);
+  prof_mark("reduce.2", st);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 // The bulk of the grid then costs a load and a store at HBM speed, and the
 // FP64 work (the scarce unit on this part) runs in full warps.
 #include "vof_launch.h"
+#include "vof_sums.cuh"
 
 namespace vofgb {
 
@@ -108,7 +109,8 @@ template <bool ENERGY>
 __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, double c, double e, double T, uint8_t stv,
                                               double Fl, double Gl, double al, double Fr, double Gr, double ar,
                                               double* __restrict__ c_out, double* __restrict__ e_out,
-                                              uint8_t* __restrict__ state, double* __restrict__ theta) {
+                                              uint8_t* __restrict__ state, double* __restrict__ theta, double& dc,
+                                              double& de) {
   const bool dirty = stv & 1;
   const double ccv = dirty ? (double)((stv >> 1) & 1) : (dgthalf(c) ? 1.0 : 0.0);
   const double lf = Fl - ccv * al, rf = Fr - ccv * ar;
@@ -117,11 +119,14 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
   if (dlt0(cn)) { cc2 = 0.0; clip = cn; }
   else if (dgt1(cn)) { cc2 = 1.0; clip = cn - 1.0; }
   c_out[id] = cc2;
+  dc = cc2 - c;
+  de = 0.0;
   if (ENERGY) {
     const double th = dirty ? theta[id] : heat_cap(g.Cp_l, g.Cp_g, ccv) * T;
     const double le = Gl - th * al, re = Gr - th * ar;
     const double en = (e + le) - re;
     e_out[id] = en;
+    de = en - e;
     if (state && !dirty && (!deq(cc2, c) || !deq(en, e))) {
       state[id] = (uint8_t)(1 | (ccv > 0.5 ? 2 : 0));
       theta[id] = th;
@@ -129,38 +134,6 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
   }
   return clip;
 }
-
-template <int NV>
-__device__ __forceinline__ void block_reduce_out(double (&v)[NV], SumOut out) {
-  __shared__ double red[NV][8];  // up to 8 warps per CTA (256 threads)
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nwarps = (int)(blockDim.x * blockDim.y * blockDim.z) >> 5;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int block_lin = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double x = v[k];
-    // whole warps of zeros (the common case) skip the FP64 shuffle tree
-    if (__any_sync(kFull, dnz(x))) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
-    } else {
-      x = 0.0;
-    }
-    if (lane == 0) red[k][warp] = x;
-  }
-  __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < nwarps; ++w) s += red[k][w];
-      if (out.partials) out.partials[(size_t)block_lin * out.stride + k] = s;
-      else if (out.diag && dnz(s)) atomicAdd(out.diag + k, s);
-    }
-  }
-}
-
 
 // ---------------------------------------------------------------------------
 // Kernel A for the sweeps along y (AX = 1) and z (AX = 2): a warp owns 32
@@ -199,7 +172,7 @@ template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(32 * kWarpsA)
 k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
              double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
-             int cap) {
+             int cap, int copy) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int n_t = AX == 1 ? g.n[2] : g.n[1];
@@ -218,6 +191,21 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
   uint32_t* mlist = sc.mlist + sub * (size_t)cap;
   uint32_t* rlist = sc.rlist + sub * (size_t)cap;
   const unsigned lt = (1u << lane) - 1u;
+  if (sc.tiles.quiet && !force_all) {
+    // in place: a warp whose 32 x 32 cells lie in quiet tiles has no work
+    // (lanes 0..15 check its 4 x 4 tiles; t is the same for the warp)
+    bool q = true;
+    const int txi = blockIdx.x * 4 + (lane & 3), tai = (s0 >> 3) + (lane >> 2);
+    if (lane < 16 && txi * kTile < nx && tai * kTile < s1 && t < n_t) {
+      const int tt = t >> 3;
+      const int ty_ = AX == 1 ? tai : tt, tz_ = AX == 1 ? tt : tai;
+      q = sc.tiles.quiet[((size_t)tz_ * sc.tiles.nt[1] + ty_) * sc.tiles.nt[0] + txi] != 0;
+    }
+    if (__all_sync(kFull, q)) {
+      if (lane == 0) sc.count[sub] = 0;
+      return;
+    }
+  }
   int nlist = 0, nmixed = 0, nrun = 0;
   bool prev_listed = false;  // cell k-1 of this segment listed
   // window: cells k .. k+3 (c, e), run = equal cells ending at k+3, and
@@ -246,7 +234,7 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     // cells k-3..k+3 equal <=> run (ending at k+3) >= 7
     const bool noop = act && !force_all && run >= 7 && is01(wc[0]) && !(stv & 1);
     if (act) {
-      if (noop) {
+      if (noop && copy) {  // out of place: no-op cells are copied
         c_out[id] = wc[0];
         if (ENERGY) e_out[id] = we[0];
       }
@@ -298,15 +286,15 @@ template <bool ENERGY>
 __global__ void __launch_bounds__(256)
 k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
              double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
-             int cap) {
+             int cap, int copy) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int lane = threadIdx.x, warp = threadIdx.y;
-  const int row = blockIdx.y * 8 + warp;  // row = z * ny + y
-  const int x0 = blockIdx.x * kSegRow, x1 = min(x0 + kSegRow, nx);
+  const int row = blockIdx.x * 8 + warp;  // row = z * ny + y (grid x: rows, grid y: segments)
+  const int x0 = blockIdx.y * kSegRow, x1 = min(x0 + kSegRow, nx);
   const bool rowok = row < ny * nz;
   const size_t rbase = (size_t)(rowok ? row : 0) * nx;
   const int bcx = g.bc[0];
-  const size_t sub = (size_t)row * gridDim.x + blockIdx.x;
+  const size_t sub = (size_t)row * gridDim.y + blockIdx.y;
   if (!rowok) {  // whole warp: empty list
     if (lane == 0) sc.count[sub] = 0;
     return;
@@ -315,6 +303,20 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
   uint32_t* mlist = sc.mlist + sub * (size_t)cap;
   uint32_t* rlist = sc.rlist + sub * (size_t)cap;
   const unsigned lt = (1u << lane) - 1u;
+  if (sc.tiles.quiet && !force_all) {
+    // in place: a warp whose row segment lies in quiet tiles has no work
+    // (lane l checks the l-th tile of the segment)
+    bool q = true;
+    const int txi = (x0 >> 3) + lane;
+    if (txi * kTile < x1) {
+      const int y = row % ny, z = row / ny;
+      q = sc.tiles.quiet[((size_t)(z >> 3) * sc.tiles.nt[1] + (y >> 3)) * sc.tiles.nt[0] + txi] != 0;
+    }
+    if (__all_sync(kFull, q)) {
+      if (lane == 0) sc.count[sub] = 0;
+      return;
+    }
+  }
   int nlist = 0, nmixed = 0, nrun = 0;
   auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
   auto lde = [&](int X) { return ENERGY ? __ldg(e_in + rbase + map_idx(X, nx, bcx)) : 0.0; };
@@ -344,7 +346,7 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
                                : (((M1 >> (32 + lane - 2)) & 0x3Full) == 0x3Full);
     const bool noop = cell_ok && !force_all && uni && is01(cC) && !(stv & 1);
     if (cell_ok) {
-      if (noop) {
+      if (noop && copy) {  // out of place: no-op cells are copied
         c_out[rbase + X] = cC;
         if (ENERGY) e_out[rbase + X] = eC;
       }
@@ -513,19 +515,20 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 // ---------------------------------------------------------------------------
 // Kernel U: one warp per kernel-A list (fixed order, so the clipped-volume
 // sums are reproducible), one listed cell per lane: the WY update from the
-// two face fluxes.
+// two face fluxes.  It reads no cell but its own, so it may update in place
+// (c_out == c_in, e_out == e_in); kernel A then copies nothing.
 // ---------------------------------------------------------------------------
 template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(256)
-k_update(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-         double* __restrict__ e_out, const double* __restrict__ uf, uint8_t* __restrict__ state,
+k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out,
+         const double* __restrict__ uf, uint8_t* __restrict__ state,
          double* __restrict__ theta, SweepScratch sc, int nsub, int cap) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
   const int lane = threadIdx.x & 31;
   const int sub = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  double clip = 0.0;
+  double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (sub < nsub) {
     const int cnt = sc.count[sub];
     const uint32_t* list = sc.list + (size_t)sub * cap;
@@ -538,15 +541,19 @@ k_update(GridDev g, const double* __restrict__ c_in, const double* __restrict__ 
       const double al = __ldg(uf + fl) * g.lam, ar = __ldg(uf + fr) * g.lam;
       const double Fl = sc.F[fl], Fr = sc.F[fr];
       const double Gl = ENERGY ? sc.G[fl] : 0.0, Gr = ENERGY ? sc.G[fr] : 0.0;
-      const double c = __ldg(c_in + id);
-      const double e = ENERGY ? __ldg(e_in + id) : 0.0;
+      // plain loads: in place, this thread writes the cell afterwards
+      const double c = c_in[id];
+      const double e = ENERGY ? e_in[id] : 0.0;
       const double T = ENERGY ? sc.T[id] : 0.0;
       const uint8_t stv = state ? state[id] : (uint8_t)0;
-      clip += update_cell<ENERGY>(g, id, c, e, T, stv, Fl, Gl, al, Fr, Gr, ar, c_out, e_out, state, theta);
+      double dc, de;
+      v[kSumClip] += update_cell<ENERGY>(g, id, c, e, T, stv, Fl, Gl, al, Fr, Gr, ar, c_out, e_out, state, theta,
+                                         dc, de);
+      v[kSumC] += dc;
+      v[kSumE] += de;
     }
   }
-  double v[1] = {clip};
-  block_reduce_out<1>(v, SumOut{sc.partial, 1, sc.diag});
+  block_sums(v, sc.sums, blockIdx.x);
 }
 
 // Energy update from given face VOF fluxes (the unfused form).
@@ -654,7 +661,8 @@ static dim3 sweep_block() {
 SweepPlan sweep_plan(int axis, const GridDev& g) {
   SweepPlan p;
   if (axis == 0) {
-    p.gridA = dim3((g.n[0] + kSegRow - 1) / kSegRow, (g.n[1] * g.n[2] + 7) / 8, 1);
+    // rows on grid x (no 65535 limit), segments of a row on grid y
+    p.gridA = dim3((g.n[1] * g.n[2] + 7) / 8, (g.n[0] + kSegRow - 1) / kSegRow, 1);
     p.blockA = dim3(32, 8, 1);
     p.cap = g.n[0] < kSegRow ? g.n[0] : kSegRow;  // cells a warp covers
     p.nsub = (long long)p.gridA.x * p.gridA.y * 8;
@@ -691,7 +699,6 @@ size_t sweep_scratch_bytes(const GridDev& g) {
     b += al256(N * 8);                          // T
     b += al256((size_t)p.nsub * p.cap * 4);     // lists
     b += al256((size_t)p.nsub * 4);             // counts
-    b += al256((size_t)p.gridB * 8);            // partials
     b += al256((size_t)p.nsub * p.cap * 4);     // mixed lists (staging)
     b += al256((size_t)p.nsub * p.cap * 4);     // run ends (staging)
     b += 256;                                   // counters
@@ -704,7 +711,7 @@ size_t sweep_scratch_bytes(const GridDev& g) {
   return best;
 }
 
-SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* partials, double* diag) {
+SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, SumOut sums) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   SweepPlan p = sweep_plan(axis, g);
   char* b = static_cast<char*>(ws);
@@ -712,8 +719,8 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* p
   s.T = reinterpret_cast<double*>(b);           b += al256(N * 8);
   s.list = reinterpret_cast<uint32_t*>(b);      b += al256((size_t)p.nsub * p.cap * 4);
   s.count = reinterpret_cast<int*>(b);          b += al256((size_t)p.nsub * 4);
-  s.partial = partials ? partials : (diag ? nullptr : reinterpret_cast<double*>(b));
-  b += al256((size_t)p.gridB * 8);
+  s.sums = sums;
+  s.tiles = TileMap{nullptr, {0, 0, 0}};
   s.mlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
   s.rlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
   s.counters = reinterpret_cast<int*>(b);       b += 256;
@@ -722,7 +729,6 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, double* p
   s.plane = reinterpret_cast<double*>(b);       b += al256(N * 32);
   s.F = reinterpret_cast<double*>(b);           b += al256(max_faces(g) * 8);
   s.G = reinterpret_cast<double*>(b);
-  s.diag = diag;
   return s;
 }
 
@@ -734,14 +740,18 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
                       SweepScratch sc, int* status, cudaStream_t st) {
   if (AX == 0)
     k_stream_row<ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc, flux_out != nullptr,
-                                                        p.cap);
+                                                        p.cap, c_out != c_in);
   else
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
-                                                                          flux_out != nullptr, p.cap);
+                                                                          flux_out != nullptr, p.cap, c_out != c_in);
+  prof_mark(AX == 0 ? "sweep_x.stream" : (AX == 1 ? "sweep_y.stream" : "sweep_z.stream"), st);
   k_planes<<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, sc);
+  prof_mark(AX == 0 ? "sweep_x.planes" : (AX == 1 ? "sweep_y.planes" : "sweep_z.planes"), st);
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
+  prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
   k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,
                                                  p.cap);
+  prof_mark(AX == 0 ? "sweep_x.update" : (AX == 1 ? "sweep_y.update" : "sweep_z.update"), st);
 }
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
@@ -751,6 +761,7 @@ cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const d
   const SweepPlan p = sweep_plan(axis, g);
   const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 2 * sizeof(int), st);
   if (err != cudaSuccess) return err;
+  prof_mark("sweep.memset", st);
   if (e_in) {
     if (axis == 0) launch_ab<0, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
     else if (axis == 1) launch_ab<1, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
@@ -773,6 +784,7 @@ cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, co
     k_energy<1><<<sweep_grid<1>(g), sweep_block<1>(), 0, st>>>(g, c_before, c_after, e_in, e_out, F, uf, state, theta);
   else
     k_energy<2><<<sweep_grid<2>(g), sweep_block<2>(), 0, st>>>(g, c_before, c_after, e_in, e_out, F, uf, state, theta);
+  prof_mark("energy", st);
   return cudaGetLastError();
 }
 

@@ -46,11 +46,15 @@ def test_host_validation_without_gpu(lib):
     assert lib.vof_reconstruct(ctypes.byref(cg), nul, nul, nul, nul, nul) == P.VOF_EINVAL
     assert lib.vof_advect_sweep_x(ctypes.byref(cg), nul, nul, nul, nul, nul, 0.1, nul, nul, nul, nul, nul, 0,
                                   nul) == P.VOF_EINVAL
-    # aliasing input and output
+    # partly overlapping input and output (exactly in place is allowed)
     fake = ctypes.c_void_p(1 << 40)
     ws = ctypes.c_void_p(5 << 40)
     big = lib.vof_sweep_workspace_bytes(ctypes.byref(cg))
-    assert lib.vof_advect_sweep_y(ctypes.byref(cg), fake, nul, fake, nul, ctypes.c_void_p(1 << 41), 0.1, nul, nul,
+    assert lib.vof_advect_sweep_y(ctypes.byref(cg), fake, nul, ctypes.c_void_p((1 << 40) + 64), nul,
+                                  ctypes.c_void_p(1 << 41), 0.1, nul, nul, nul, nul, ws, big, nul) == P.VOF_EINVAL
+    # c in place but e out of place
+    e1, e2 = ctypes.c_void_p(2 << 40), ctypes.c_void_p(3 << 40)
+    assert lib.vof_advect_sweep_x(ctypes.byref(cg), fake, e1, fake, e2, ctypes.c_void_p(1 << 41), 0.1, nul, nul,
                                   nul, nul, ws, big, nul) == P.VOF_EINVAL
     # sweep workspace missing, too small or misaligned
     ok_out = ctypes.c_void_p(4 << 40)

@@ -103,10 +103,28 @@ def case(name):
         T = 2.0 + 0.3 * np.tanh((X - 1.1) / 0.05) * np.cos(3 * Y)  # uniform away from a layer
         e = (4000.0 * c + 1.2 * (1 - c)) * T
         return g, c, e, (u, v, w), 0.2 * h / 2.0, -0.015
+    if name == "tiles_periodic":
+        # periodic on every axis with ragged last tiles of 5, 5 and 3 cells,
+        # a drop in a quiet box (uniform T away from a thin layer), moving
+        # diagonally: quiet tiles next to active ones and across the wrap
+        nx, ny, nz = 61, 45, 27
+        h = 1.0 / 48
+        g = P.Grid(nx, ny, nz, (0, 0, 0), h, 2500.0, 1.5, 1.0)
+        c = W.sphere_fractions((nz, ny, nx), h, (0.62, 0.47, 0.28), 0.16, nsub=10)
+        u, v, w = W.uniform_faces((nz, ny, nx), (0.9, -0.6, 0.45))
+        zc = (np.arange(nz) + 0.5) * h
+        yc = (np.arange(ny) + 0.5) * h
+        xc = (np.arange(nx) + 0.5) * h
+        Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+        r = np.sqrt((X - 0.62) ** 2 + (Y - 0.47) ** 2 + (Z - 0.28) ** 2)
+        T = 1.0 + 0.4 * np.where(r < 0.24, np.cos(np.pi * (r - 0.16) / 0.16) ** 2, 0.0)
+        T[r < 0.16] = 1.4
+        e = (2500.0 * c + 1.5 * (1 - c)) * T
+        return g, c, e, (u, v, w), 0.4 * h, -0.02
     raise KeyError(name)
 
 
-CASES = ["sphere32", "deform_ragged", "tiny_periodic", "multi_segment"]
+CASES = ["sphere32", "deform_ragged", "tiny_periodic", "multi_segment", "tiles_periodic"]
 
 
 def temperature(g, c, e):
@@ -197,6 +215,74 @@ def test_shift(P, name):
         # sums of the outputs (added by the three shift kernels)
         assert abs(d[3] - math.fsum(co.ravel())) <= 1e-13 * max(1.0, abs(math.fsum(co.ravel())))
         assert abs(d[4] - math.fsum(eo.ravel())) <= 1e-12 * max(1.0, abs(math.fsum(eo.ravel())))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_in_place_equals_out_of_place(P, name):
+    """Sweeps and the shift called in place (c_out == c_in, e_out == e_in)
+    give the same bits as out of place, over a pair of sweeps with a
+    non-trivial frozen state and then the shift."""
+    import torch
+    g, c, e, vel, dt, dd = case(name)
+    outs = []
+    for inplace in (False, True):
+        cd, ed = dev(c), dev(e)
+        state = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+        theta = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        diag = torch.zeros(3, dtype=torch.float64, device="cuda")
+        sdiag = torch.zeros(5, dtype=torch.float64, device="cuda")
+        for axis in (0, 1, 2):
+            if inplace:
+                P.SWEEPS[axis](g, cd, ed, cd, ed, dev(vel[axis]), dt, state, theta, None, diag[axis:axis + 1])
+            else:
+                c2, e2 = torch.empty_like(cd), torch.empty_like(ed)
+                P.SWEEPS[axis](g, cd, ed, c2, e2, dev(vel[axis]), dt, state, theta, None, diag[axis:axis + 1])
+                cd, ed = c2, e2
+        if inplace:
+            P.vof_phase_change_shift(g, cd, ed, cd, ed, None, dd, None, sdiag)
+        else:
+            c2, e2 = torch.empty_like(cd), torch.empty_like(ed)
+            P.vof_phase_change_shift(g, cd, ed, c2, e2, None, dd, None, sdiag)
+            cd, ed = c2, e2
+        outs.append([host(t) for t in (cd, ed, state, theta, diag, sdiag)])
+    for a, b in zip(outs[0][:4], outs[1][:4]):
+        assert np.array_equal(a, b)
+    # the stand-alone calls add their sums with atomics: equal up to the
+    # order of the additions
+    for a, b in zip(outs[0][4:], outs[1][4:]):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step_equals_its_calls(P, name):
+    """vof_step (quiet tiles skipped, sums from the tile pass plus the
+    changes) gives the same c and e bits as the stand-alone sweeps and shift
+    that visit every cell, over two steps (both sweep orders); its sums
+    match theirs."""
+    import torch
+    g, c, e, (u, v, w), dt, dd = case(name)
+    st = P.Stepper(g)
+    ud, vd, wd = dev(u), dev(v), dev(w)
+    c1, e1 = dev(c), dev(e)
+    c2, e2 = dev(c), dev(e)
+    for s in range(2):
+        st.step(c1, e1, ud, vd, wd, dt, s, dd_uniform=dd)
+        state = torch.zeros(g.shape, dtype=torch.uint8, device="cuda")
+        theta = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        clip = torch.zeros(1, dtype=torch.float64, device="cuda")
+        sdiag = torch.zeros(5, dtype=torch.float64, device="cuda")
+        order = (0, 1, 2) if s % 2 == 0 else (2, 1, 0)
+        for axis in order:
+            P.SWEEPS[axis](g, c2, e2, c2, e2, (ud, vd, wd)[axis], dt, state, theta, None, clip)
+        P.vof_phase_change_shift(g, c2, e2, c2, e2, None, dd, None, sdiag)
+        assert torch.equal(c1, c2) and torch.equal(e1, e2)
+        sums = host(st.sums)
+        d = host(sdiag)
+        for k, ref in ((0, math.fsum(host(c2).ravel())), (1, math.fsum(host(e2).ravel()))):
+            assert abs(sums[k] - ref) <= 1e-13 * max(1.0, abs(ref))
+        assert abs(sums[2] - float(host(clip)[0])) <= 1e-12 * max(1e-300, abs(sums[2])) + 1e-300
+        for k in range(3):
+            assert abs(sums[3 + k] - d[k]) <= 1e-12 * max(1.0, abs(d[k]))
 
 
 @pytest.mark.parametrize("name", CASES)
