@@ -62,6 +62,17 @@ __device__ __forceinline__ double heat_cap(double Cp_l, double Cp_g, double c) {
 
 __device__ __forceinline__ bool is_mixed(double c, double eps) { return c > eps && c < 1.0 - eps; }
 // the same test on the integer pipe (eps >= 0)
+// cell coordinates of a cell index (grids hold fewer than 2^31 cells, so
+// 32-bit division suffices; 64-bit division is a long software sequence)
+__device__ __forceinline__ void cell_xyz(const GridDev& g, size_t id, int& x, int& y, int& z) {
+  const uint32_t i = (uint32_t)id, nx = (uint32_t)g.n[0], ny = (uint32_t)g.n[1];
+  const uint32_t r = i / nx;
+  x = (int)(i - r * nx);
+  const uint32_t q = r / ny;
+  y = (int)(r - q * ny);
+  z = (int)q;
+}
+
 __device__ __forceinline__ bool is_mixed_b(double c, const GridDev& g) {
   long long b = dbits(c);
   return b > g.eps_bits && b < g.one_m_eps;

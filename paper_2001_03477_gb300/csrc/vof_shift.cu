@@ -46,12 +46,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kListThreads = 128;     // planes / receivers kernels: CTA size
 constexpr int kListCTAs = 152 * 4;    // and grid (grid-stride loops)
 
-__device__ __forceinline__ void decode(const GridDev& g, size_t id, int& x, int& y, int& z) {
-  x = (int)(id % (size_t)g.n[0]);
-  const size_t r = id / (size_t)g.n[0];
-  y = (int)(r % (size_t)g.n[1]);
-  z = (int)(r / (size_t)g.n[1]);
-}
+__device__ __forceinline__ void decode(const GridDev& g, size_t id, int& x, int& y, int& z) { cell_xyz(g, id, x, y, z); }
 
 __device__ __forceinline__ size_t cell_id(const GridDev& g, int x, int y, int z) {
   return ((size_t)z * g.n[1] + y) * g.n[0] + x;

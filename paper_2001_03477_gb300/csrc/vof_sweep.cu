@@ -10,16 +10,20 @@
 // with cc = [c^n > 1/2] and Theta = C_p(cc) T^n frozen at the start of the
 // step (see the `state` convention in include/vofgb.h).
 //
-// Two kernels per sweep:
-//   A (stream): walks the grid lines, copies the cells that provably do not
-//     change (no-op cells, below) straight to the output, stores T for every
-//     cell whose (c, e) differs from the previous cell of its line, and lists
-//     the remaining cells per warp in a fixed order;
-//   B (active cells): one warp per list, one listed cell per lane; rebuilds
-//     the cell's 7-cell T stencil, evaluates its two faces (PLIC geometry for
-//     a mixed donor, WENO5) and updates c, e and the frozen state.
-// The bulk of the grid then costs a load and a store at HBM speed, and the
-// FP64 work (the scarce unit on this part) runs in full warps.
+// Four kernels per sweep:
+//   A (stream): walks the grid lines (skipping quiet tiles in an in-place
+//     step), copies the cells that provably do not change (no-op cells,
+//     below) to the output when out of place, and lists the other cells per
+//     warp in a fixed order, plus grid-wide lists of the mixed cells and of
+//     the faces to evaluate (left face of every listed cell, right face of
+//     every run end);
+//   M (prep): the PLIC plane of every mixed cell and T of every listed cell;
+//   F (faces): each listed face once: VOF flux (PLIC slab of a mixed donor)
+//     and energy flux (WENO5 face temperature);
+//   U (update): one warp per kernel-A list, one listed cell per lane: c, e
+//     and the frozen state from the two face fluxes.
+// The bulk of the grid costs kernel A's streaming pass, and the FP64 work
+// (the scarce unit on this part) runs lane-dense over compact lists.
 #include "vof_launch.h"
 #include "vof_sums.cuh"
 
@@ -144,7 +148,7 @@ constexpr int kSegA = 32;     // cells per lane along y / z
 constexpr int kWarpsA = 8;    // warps per CTA of kernel A
 constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
 constexpr int kPlaneThreads = 128;  // kernel M: CTA size; grid kPlaneCTAs
-constexpr int kPlaneCTAs = 152 * 4;
+constexpr int kPlaneCTAs = 152 * 8;
 
 // Appends a warp's lists (staged in its own slots) to the grid-wide lists:
 // its mixed cells to the list of kernel M, and one face item per listed cell
@@ -208,11 +212,10 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
   }
   int nlist = 0, nmixed = 0, nrun = 0;
   bool prev_listed = false;  // cell k-1 of this segment listed
-  // window: cells k .. k+3 (c, e), run = equal cells ending at k+3, and
-  // whether cells k and k-1 differ from their predecessors
-  double wc[4], we[4];
+  // window: cells k .. k+3 (c, e) and run = equal cells ending at k+3;
+  // cells k+4 .. k+7 are in flight (prefetch queue pc/pe)
+  double wc[4], we[4], qc[4], qe[4];
   int run = 0;
-  bool dif[4];
   double pc = 0.0, pe = 0.0;
 #pragma unroll
   for (int i = -4; i < 4; ++i) {
@@ -221,24 +224,32 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     const double ev = ENERGY ? __ldg(e_in + id) : 0.0;
     const bool same = i > -4 && same_bits(cv, pc) && (!ENERGY || same_bits(ev, pe));
     run = same ? run + 1 : 1;
-    if (i >= 0) { wc[i] = cv; we[i] = ev; dif[i] = !same; }
+    if (i >= 0) { wc[i] = cv; we[i] = ev; }
     pc = cv; pe = ev;
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const size_t id = cbase + stride * map_idx(s0 + 4 + i, n_ax, bca);
+    qc[i] = __ldg(c_in + id);
+    qe[i] = ENERGY ? __ldg(e_in + id) : 0.0;
+  }
   for (int k = s0; k < s1; ++k) {
-    // prefetch cell k + 4
-    const size_t idn = cbase + stride * map_idx(k + 4, n_ax, bca);
-    const double cn = __ldg(c_in + idn);
-    const double en = ENERGY ? __ldg(e_in + idn) : 0.0;
+    // cell k + 4 from the queue; cell k + 8 joins it
+    const double cn = qc[0], en = qe[0];
+    {
+      const size_t idq = cbase + stride * map_idx(k + 8, n_ax, bca);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { qc[i] = qc[i + 1]; qe[i] = qe[i + 1]; }
+      qc[3] = __ldg(c_in + idq);
+      qe[3] = ENERGY ? __ldg(e_in + idq) : 0.0;
+    }
     const size_t id = cbase + stride * k;
     const uint8_t stv = (act && state) ? state[id] : (uint8_t)0;
     // cells k-3..k+3 equal <=> run (ending at k+3) >= 7
     const bool noop = act && !force_all && run >= 7 && is01(wc[0]) && !(stv & 1);
-    if (act) {
-      if (noop && copy) {  // out of place: no-op cells are copied
-        c_out[id] = wc[0];
-        if (ENERGY) e_out[id] = we[0];
-      }
-      if (ENERGY && dif[0]) sc.T[id] = we[0] / heat_cap(g.Cp_l, g.Cp_g, wc[0]);
+    if (act && noop && copy) {  // out of place: no-op cells are copied
+      c_out[id] = wc[0];
+      if (ENERGY) e_out[id] = we[0];
     }
     const bool listed = act && !noop;
     const unsigned m = __ballot_sync(kFull, listed);
@@ -256,8 +267,8 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     // shift the window
     const bool same = same_bits(cn, wc[3]) && (!ENERGY || same_bits(en, we[3]));
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { wc[i] = wc[i + 1]; we[i] = we[i + 1]; dif[i] = dif[i + 1]; }
-    wc[3] = cn; we[3] = en; dif[3] = !same;
+    for (int i = 0; i < 3; ++i) { wc[i] = wc[i + 1]; we[i] = we[i + 1]; }
+    wc[3] = cn; we[3] = en;
     run = same ? run + 1 : 1;
   }
   // the segment's last cell ends a run unless the next cell along the axis
@@ -350,7 +361,6 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
         c_out[rbase + X] = cC;
         if (ENERGY) e_out[rbase + X] = eC;
       }
-      if (ENERGY && !((eqC >> lane) & 1u)) sc.T[rbase + X] = eC / heat_cap(g.Cp_l, g.Cp_g, cC);
     }
     const bool listed = cell_ok && !noop;
     const unsigned m = __ballot_sync(kFull, listed);
@@ -386,17 +396,32 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Kernel M: the PLIC plane (MYC normal + plane constant) of every mixed cell,
-// once per sweep, one mixed cell per thread over the grid-wide list (every
-// lane busy); stored per cell for kernel B.
+// Kernel M: per-cell preparation over the grid-wide lists, one item per
+// thread (every lane busy): first the PLIC plane (MYC normal + plane
+// constant) of every mixed cell, then T = e / C_p(c) of every listed cell
+// (the left-face items of the face list).  The plane items take long and
+// are few; the T items fill the machine around them.  Every cell that
+// differs from its predecessor along the axis is listed (its 7-cell window
+// is not uniform), so after this kernel T is stored for all of those --
+// the only T values kernel F reads back -- and for every listed cell, which
+// kernel U reads.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPlaneThreads)
-k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc) {
+k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int cnt = sc.counters[0];
+  const int nm = sc.counters[0];
+  const int cnt = nm + (e_in ? sc.counters[1] : 0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    if (i >= nm) {
+      const uint32_t item = sc.gface[i - nm];
+      if (item & 1u) continue;  // right-face item: its cell has a left item too
+      const size_t id = item >> 1;
+      sc.T[id] = __ldg(e_in + id) / heat_cap(g.Cp_l, g.Cp_g, __ldg(c_in + id));
+      continue;
+    }
     const size_t id = sc.gmix[i];
-    const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+    int x, y, z;
+    cell_xyz(g, id, x, y, z);
     double s[27];
 #pragma unroll
     for (int oz = 0; oz < 3; ++oz) {
@@ -425,10 +450,8 @@ k_planes(GridDev g, const double* __restrict__ c_in, SweepScratch sc) {
 // of every listed cell and the right face of every run end, so each face is
 // evaluated once.  VOF flux F (PLIC slab of a mixed donor, c a of a pure
 // one) and energy flux G (WENO5 face temperature) go to per-face scratch.
-// A listed cell's left-face item also stores the cell's T where kernel A
-// did not (cells equal to their predecessor); nothing reads those entries
-// in this kernel, which only reads T of cells that differ from their
-// predecessor.
+// T comes from kernel M for window cells that differ from their
+// predecessor; a cell equal to its predecessor has its predecessor's T.
 // ---------------------------------------------------------------------------
 constexpr int kFaceThreads = 128;
 constexpr int kFaceCTAs = 152 * 8;
@@ -453,14 +476,14 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
     const uint32_t item = sc.gface[i];
     const size_t id = item >> 1;
     const int side = (int)(item & 1u);
-    const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+    int x, y, z;
+    cell_xyz(g, id, x, y, z);
     const int k = AX == 0 ? x : (AX == 1 ? y : z);
     const size_t lbase = id - stride * k;  // cell index of position 0 of this line
     const int f = k + side;                // face between cells f-1 and f
     // (c, e) of cells f-4..f+2 and T of f-3..f+2 (cells that differ from
     // their predecessor read back, others equal to it; the first divided)
     double cw[7], ew[7], Tw[7];
-    bool dif4 = true;
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       const size_t jd = lbase + stride * map_idx(f - 4 + j, n_ax, bca);
@@ -469,7 +492,6 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
       if (ENERGY && j >= 1) {
         const bool dif = !(same_bits(cw[j], cw[j - 1]) && same_bits(ew[j], ew[j - 1]));
         Tw[j] = dif ? sc.T[jd] : (j == 1 ? ew[j] / heat_cap(g.Cp_l, g.Cp_g, cw[j]) : Tw[j - 1]);
-        if (j == 4) dif4 = dif;
       }
     }
     const int fr = (bca == 0 && f == n_ax) ? 0 : f;
@@ -502,7 +524,6 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
     }
     sc.F[fid] = Fv;
     if (ENERGY) sc.G[fid] = Gv;
-    if (ENERGY && side == 0 && !dif4) sc.T[id] = Tw[4];
     if (flux_out) {
       // every face of the line, the periodic face n_ax (= face 0) included
       flux_out[face_of<AX>(g, f, x, y, z)] = Fv;
@@ -534,7 +555,8 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
     const uint32_t* list = sc.list + (size_t)sub * cap;
     for (int i = lane; i < cnt; i += 32) {
       const size_t id = list[i];
-      const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+      int x, y, z;
+      cell_xyz(g, id, x, y, z);
       const int k = AX == 0 ? x : (AX == 1 ? y : z);
       const int f1 = (bca == 0 && k + 1 == n_ax) ? 0 : k + 1;
       const size_t fl = face_of<AX>(g, k, x, y, z), fr = face_of<AX>(g, f1, x, y, z);
@@ -745,8 +767,8 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
                                                                           flux_out != nullptr, p.cap, c_out != c_in);
   prof_mark(AX == 0 ? "sweep_x.stream" : (AX == 1 ? "sweep_y.stream" : "sweep_z.stream"), st);
-  k_planes<<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, sc);
-  prof_mark(AX == 0 ? "sweep_x.planes" : (AX == 1 ? "sweep_y.planes" : "sweep_z.planes"), st);
+  k_prep<<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc);
+  prof_mark(AX == 0 ? "sweep_x.prep" : (AX == 1 ? "sweep_y.prep" : "sweep_z.prep"), st);
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
   k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,

@@ -36,16 +36,7 @@ __global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restri
   const int x = blockIdx.x * 32 + tx, y = blockIdx.y * kTile + ty, z0 = blockIdx.z * kTile;
   const int xt = blockIdx.x * 4 + j;
   const bool tile_ok = xt * kTile < nx;
-  // reference cell of each tile: its first cell
-  if (ty == 0 && (tx & 7) == 0 && tile_ok) {
-    const size_t rid = ((size_t)z0 * ny + blockIdx.y * kTile) * nx + (size_t)xt * kTile;
-    ref[j][0] = __ldg(c + rid);
-    ref[j][1] = __ldg(e + rid);
-  }
-  __syncthreads();
-  const double cr = tile_ok ? ref[j][0] : 0.0, er = tile_ok ? ref[j][1] : 0.0;
   double cv[kTile], ev[kTile];
-  bool uniform = true;
   const bool xy_ok = x < nx && y < ny;
 #pragma unroll
   for (int zi = 0; zi < kTile; ++zi) {
@@ -54,8 +45,19 @@ __global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restri
     const size_t id = ((size_t)z * ny + y) * nx + x;
     cv[zi] = ok ? __ldg(c + id) : 0.0;
     ev[zi] = ok ? __ldg(e + id) : 0.0;
-    if (ok) uniform = uniform && same_bits_t(cv[zi], cr) && same_bits_t(ev[zi], er);
   }
+  // reference of each tile: its first cell, which this CTA's thread
+  // (8 j, 0) holds as its first value
+  if (ty == 0 && (tx & 7) == 0 && tile_ok) {
+    ref[j][0] = cv[0];
+    ref[j][1] = ev[0];
+  }
+  __syncthreads();
+  const double cr = tile_ok ? ref[j][0] : 0.0, er = tile_ok ? ref[j][1] : 0.0;
+  bool uniform = true;
+#pragma unroll
+  for (int zi = 0; zi < kTile; ++zi)
+    if (xy_ok && z0 + zi < nz) uniform = uniform && same_bits_t(cv[zi], cr) && same_bits_t(ev[zi], er);
   const unsigned b = __ballot_sync(kFullT, uniform);
   if (tx == 0) uni_w[ty] = b;
   __syncthreads();
