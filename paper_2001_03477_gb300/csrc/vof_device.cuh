@@ -161,7 +161,7 @@ __device__ __forceinline__ double dvol_low(double m1, double m2, double m3, doub
 // Plane constant for sorted m (sum 1) and 0 < c <= 1/2, analytic per branch
 // (Scardovelli & Zaleski 2000): cube root, quadratic, linear, or the
 // trigonometric root of the branch cubic; then one safeguarded Newton step.
-__device__ __forceinline__ double alpha_low(double m1, double m2, double m3, double c) {
+static __device__ __noinline__ double alpha_low_analytic(double m1, double m2, double m3, double c) {
   double m12 = m1 + m2;
   double P6 = 6.0 * m1 * m2 * m3;
   double V1 = (m1 > 0.0) ? m1 * m1 / (6.0 * m2 * m3) : 0.0;
@@ -242,6 +242,99 @@ __device__ __forceinline__ double alpha_low(double m1, double m2, double m3, dou
     if (an == a) break;
     a = an;
   }
+  return best;
+}
+
+// Non-negative doubles order like their bit patterns read as integers: a
+// compare that needs no FP64 instruction (an FP64 compare occupies the FP64
+// unit as long as an add on this part).
+__device__ __forceinline__ bool nn_lt(double a, double b) { return dbits(a) < dbits(b); }
+
+// Single-precision guess of the plane constant for sorted m (sum 1) and
+// 0 < c <= 1/2: bisection of the volume's branch form in float (the float
+// unit is ~64x wider than the FP64 one here, and bisection has no
+// branch-dependent convergence), on u with a = u^3 / 2, which resolves the
+// small constants of nearly empty or nearly axis-aligned cells in relative
+// terms.
+__device__ __forceinline__ float alpha_guess_f(float m1, float m2, float m3, float c) {
+  const float m12 = m1 + m2;
+  const float top = m12 < m3 ? m12 : m3;
+  const bool lin = m12 <= m3;
+  const float r6 = 1.0f / (6.0f * m1 * m2 * m3), r2 = 1.0f / (2.0f * m2 * m3), r3 = 1.0f / m3;
+  const float v2c = m1 * m1 * r2 * (1.0f / 3.0f);
+  float lo = 0.0f, hi = 1.0f;
+#pragma unroll 1
+  for (int it = 0; it < 22; ++it) {
+    const float u = 0.5f * (lo + hi);
+    const float a = 0.5f * u * u * u;
+    float v;
+    if (a < m1) {
+      v = a * a * a * r6;
+    } else {
+      const float v2 = a * (a - m1) * r2 + v2c;
+      if (a < m2) {
+        v = v2;
+      } else {
+        const float t2 = a - m2;
+        const float v3 = v2 - t2 * t2 * t2 * r6;
+        if (a < top) v = v3;
+        else if (lin) v = (2.0f * a - m12) * 0.5f * r3;
+        else {
+          const float t3 = a - m3;
+          v = v3 - t3 * t3 * t3 * r6;
+        }
+      }
+    }
+    if (v < c) lo = u; else hi = u;
+  }
+  const float u = 0.5f * (lo + hi);
+  return 0.5f * u * u * u;
+}
+
+// Plane constant for sorted m (sum 1) and 0 < c <= 1/2: float guess, then
+// three Newton steps in FP64 on the volume's branch form evaluated without
+// branches (all branches computed, the right one selected, reciprocals of
+// the branch denominators formed once), so the lanes of a warp stay
+// together.  The best of the iterates is kept; if it misses c by more than
+// rounding, the analytic solution with its safeguarded polish is used.
+__device__ __forceinline__ double alpha_low(double m1, double m2, double m3, double c) {
+  const double m12 = m1 + m2;
+  const double top = m12 < m3 ? m12 : m3;
+  const bool lin = !nn_lt(m3, m12);  // m12 <= m3
+  const double r6 = 1.0 / (6.0 * m1 * m2 * m3);  // inf when m1 = 0: that branch is then never selected
+  const double r2 = 1.0 / (2.0 * m2 * m3);
+  const double r3 = 1.0 / m3;
+  const double v2c = m1 * m1 * r2 / 3.0;
+  double a = (double)alpha_guess_f((float)m1, (float)m2, (float)m3, (float)c);
+  double best = a;
+  long long bestf = 0x7FF0000000000000LL;  // |f| bits
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const double t1 = a - m1, t2 = a - m2, t3 = a - m3;
+    const double v1 = a * a * a * r6, d1 = 3.0 * a * a * r6;
+    const double v2 = a * t1 * r2 + v2c, d2 = (a + t1) * r2;
+    const double v3 = v2 - t2 * t2 * t2 * r6, d3 = d2 - 3.0 * t2 * t2 * r6;
+    const double v4 = (a + (a - m12)) * 0.5 * r3, d4 = r3;
+    const double v5 = v3 - t3 * t3 * t3 * r6, d5 = d3 - 3.0 * t3 * t3 * r6;
+    double v, d;
+    if (nn_lt(a, m1)) { v = v1; d = d1; }
+    else if (nn_lt(a, m2)) { v = v2; d = d2; }
+    else if (nn_lt(a, top)) { v = v3; d = d3; }
+    else if (lin) { v = v4; d = d4; }
+    else { v = v5; d = d5; }
+    const double f = v - c;
+    const long long af = dbits(f) & 0x7FFFFFFFFFFFFFFFLL;
+    if (af < bestf) { bestf = af; best = a; }
+    if (it == 3) break;
+    double an = a - f / d;
+    // stay in [0, 1/2] (a > 0 keeps the cubic corner's derivative nonzero)
+    if (!(dbits(an) > 0)) an = 0.5 * a;
+    if (nn_lt(0.5, an)) an = 0.5;
+    a = an;
+  }
+  // converged to rounding: |f| within a few ulps of the volume
+  const double tol = 32.0 * 1.1102230246251565e-16 * c;
+  if (!(__longlong_as_double(bestf) <= tol)) best = alpha_low_analytic(m1, m2, m3, c);
   return best;
 }
 
@@ -356,30 +449,96 @@ __device__ __forceinline__ void cc_candidate(const double* s, int d, double m[3]
   m[d] = sg / l1;
 }
 
+// Centred-columns candidate along d without its divisions: the two
+// tangential slopes a1, a2 (along t1 < t2), the L1 norm l1 = |a1|+|a2|+1 and
+// the sign of the own-axis component.
+struct CCParts {
+  double a1, a2, l1, sg;
+};
+
+__device__ __forceinline__ CCParts cc_parts(const double* s, int d) {
+  double h[3][3];
+#pragma unroll
+  for (int q = -1; q <= 1; ++q)
+#pragma unroll
+    for (int p = -1; p <= 1; ++p) {
+      double col = sax(s, d, -1, p, q);
+      col = col + sax(s, d, 0, p, q);
+      col = col + sax(s, d, 1, p, q);
+      h[p + 1][q + 1] = col;
+    }
+  double lower = 0.0, upper = 0.0;
+#pragma unroll
+  for (int q = -1; q <= 1; ++q)
+#pragma unroll
+    for (int p = -1; p <= 1; ++p) {
+      lower = lower + sax(s, d, -1, p, q);
+      upper = upper + sax(s, d, 1, p, q);
+    }
+  CCParts r;
+  r.sg = !nn_lt(lower, upper) ? 1.0 : -1.0;  // lower >= upper (both >= 0)
+  r.a1 = -(h[2][1] - h[0][1]) * 0.5;
+  r.a2 = -(h[1][2] - h[1][0]) * 0.5;
+  r.l1 = fabs(r.a1) + fabs(r.a2) + 1.0;
+  return r;
+}
+
 // Best centred-columns candidate (largest own-axis component, lowest axis on
 // ties), kept unless its dominant component exceeds the Youngs normal's, in
-// which case Youngs is taken.
+// which case Youngs is taken.  The same values as normalising every
+// candidate and comparing their components, with fewer divisions: a
+// candidate's own-axis component is +-1/l1 exactly, and the largest Youngs
+// component is the largest |g| over l1 (division is monotone).  Non-negative
+// values are compared as integers.
 __device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
-  double best[3];
-  int bd = 0;
-  cc_candidate(s, 0, best);
+  CCParts c[3];
+  double dom[3];
 #pragma unroll
-  for (int d = 1; d < 3; ++d) {
-    double cand[3];
-    cc_candidate(s, d, cand);
-    if (fabs(cand[d]) > fabs(best[bd])) {
-      best[0] = cand[0]; best[1] = cand[1]; best[2] = cand[2];
-      bd = d;
-    }
+  for (int d = 0; d < 3; ++d) {
+    c[d] = cc_parts(s, d);
+    dom[d] = 1.0 / c[d].l1;
   }
+  int bd = 0;
+  if (nn_lt(dom[0], dom[1])) bd = 1;
+  if (nn_lt(dom[bd], dom[2])) bd = 2;
+  // Youngs gradient
+  const double w[3] = {1.0, 2.0, 1.0};
   double y[3];
-  youngs_normal(s, y);
-  double ymax = fabs(y[0]);
-  if (fabs(y[1]) > ymax) ymax = fabs(y[1]);
-  if (fabs(y[2]) > ymax) ymax = fabs(y[2]);
-  double cmax = fabs(best[bd]);
-  if (cmax <= ymax) { m[0] = best[0]; m[1] = best[1]; m[2] = best[2]; }
-  else { m[0] = y[0]; m[1] = y[1]; m[2] = y[2]; }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double g = 0.0;
+#pragma unroll
+    for (int q = -1; q <= 1; ++q)
+#pragma unroll
+      for (int p = -1; p <= 1; ++p) {
+        double diff = sax(s, d, 1, p, q) - sax(s, d, -1, p, q);
+        g = g + (w[p + 1] * w[q + 1]) * diff;
+      }
+    y[d] = -g;
+  }
+  const double ay0 = fabs(y[0]), ay1 = fabs(y[1]), ay2 = fabs(y[2]);
+  const double l1y = ay0 + ay1 + ay2;
+  double ymax;
+  if (dnz(l1y)) {
+    double amax = ay0;
+    if (nn_lt(amax, ay1)) amax = ay1;
+    if (nn_lt(amax, ay2)) amax = ay2;
+    ymax = amax / l1y;
+  } else {
+    ymax = 1.0;  // degenerate Youngs normal (1, 0, 0)
+  }
+  if (!nn_lt(ymax, dom[bd])) {  // cmax <= ymax: the centred-columns candidate
+    const int t1 = bd == 0 ? 1 : 0, t2 = bd == 2 ? 1 : 2;
+    m[t1] = c[bd].a1 / c[bd].l1;
+    m[t2] = c[bd].a2 / c[bd].l1;
+    m[bd] = dbits(c[bd].sg) < 0 ? -dom[bd] : dom[bd];
+  } else if (dnz(l1y)) {
+    m[0] = y[0] / l1y;
+    m[1] = y[1] / l1y;
+    m[2] = y[2] / l1y;
+  } else {
+    m[0] = 1.0; m[1] = 0.0; m[2] = 0.0;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -349,7 +349,10 @@ def test_uniform_temperature_gpu(P):
         st.step(cd, ed, dev(u), dev(v), dev(w), 0.25 * h / 2, s, dd_uniform=-0.01)
     cg, eg = host(cd), host(ed)
     T = eg / (3236.3 * cg + (1 - cg))
-    assert np.abs(T - 1.0).max() < 1e-13
+    # exact in exact arithmetic; in FP64 each update of a cell next to the
+    # interface rounds energies of the liquid's size (C_pl T), which is
+    # C_pl / C_pg times a gas cell's: allow 16 such roundings over the run
+    assert np.abs(T - 1.0).max() < 16 * np.finfo(float).eps * 3236.3
 
 
 def test_cfl_status(P):
