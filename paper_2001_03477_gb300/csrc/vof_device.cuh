@@ -364,16 +364,43 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
   if (r.l1 == 0.0) return 0.0;
   if (c <= 0.0) return 0.0 - r.sh;
   if (c >= 1.0) return r.l1 - r.sh;
+  // the volume function's own steps, with the sort of the (fixed) normal
+  // done once and its compares of non-negative values made on integers:
+  // the same values at every midpoint as the plain volume function
+  double s0 = r.mp[0], s1 = r.mp[1], s2 = r.mp[2];
+  sort3(s0, s1, s2);
+  const double m12 = s0 + s1;
+  const double top = nn_lt(m12, s2) ? m12 : s2;
+  const bool lin = !nn_lt(s2, m12);
+  const double d6 = 6.0 * s0 * s1 * s2, d2 = 2.0 * s1 * s2, d2m3 = 2.0 * s2;
+  const double v2c = s0 * s0 / (6.0 * s1 * s2);
+  auto vlow = [&](double a) -> double {
+    if (nn_lt(a, s0)) return a * a * a / d6;
+    const double v2 = a * (a - s0) / d2 + v2c;
+    if (nn_lt(a, s1)) return v2;
+    const double t2 = a - s1;
+    const double v3 = v2 - t2 * t2 * t2 / d6;
+    if (nn_lt(a, top)) return v3;
+    if (lin) return (2.0 * a - m12) / d2m3;
+    const double t3 = a - s2;
+    return v3 - t3 * t3 * t3 / d6;
+  };
+  auto vpos = [&](double a) -> double {  // a in (0, 1) here
+    if (!nn_lt(0.5, a)) return vlow(a);
+    return 1.0 - vlow(1.0 - a);
+  };
   double lo = 0.0, hi = 1.0;
   for (int it = 0; it < 200; ++it) {
     double mid = lo + 0.5 * (hi - lo);
-    if (!(mid > lo && mid < hi)) break;
-    if (vol_pos(r.mp[0], r.mp[1], r.mp[2], mid) < c) lo = mid;
+    if (!(nn_lt(lo, mid) && nn_lt(mid, hi))) break;
+    if (nn_lt(vpos(mid), c)) lo = mid;
     else hi = mid;
   }
-  double vl = fabs(vol_pos(r.mp[0], r.mp[1], r.mp[2], lo) - c);
-  double vh = fabs(vol_pos(r.mp[0], r.mp[1], r.mp[2], hi) - c);
-  double am = (vh < vl) ? hi : lo;
+  // lo and hi are 0 or 1 only at a bracket end never left (vpos's end cases)
+  const double vlo = dbits(lo) == 0 ? 0.0 : vpos(lo);
+  const double vhi = dbits(hi) == 0x3FF0000000000000LL ? 1.0 : vpos(hi);
+  const long long el = dbits(vlo - c) & 0x7FFFFFFFFFFFFFFFLL, eh = dbits(vhi - c) & 0x7FFFFFFFFFFFFFFFLL;
+  double am = (eh < el) ? hi : lo;
   return am * r.l1 - r.sh;
 }
 
