@@ -111,16 +111,43 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def sweep_traffic_from_profile():
-    """DRAM bytes per sweep launch from the committed ncu summary, if it
-    names this kernel build; None otherwise."""
-    path = os.path.join(ROOT, "profiles", "sweep_traffic.json.txt")
+# FP64 flops of one face of kernel F (pure donor; fused multiply-adds count
+# two): a = u lambda (1), F = c a (1), WENO5 face value (3 candidate
+# polynomials 15, 3 smoothness indicators 33, weights and their normalised
+# combination 21, the folded 1/6: 1), G = T_f C_pl F + T_f C_pg (a - F) (6)
+FACE_FLOP = 78
+FACE_SOURCES = ("paper_2001_03477_gb300/csrc/vof_sweep.cu", "paper_2001_03477_gb300/csrc/vof_device.cuh")
+
+
+def sources_sha1(paths):
+    import hashlib
+    h = hashlib.sha1()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def faces_traffic_from_profile():
+    """DRAM bytes per launch of kernel F (k_faces) from the committed ncu
+    summary, if it was taken on the current sources of that kernel; None
+    otherwise."""
+    path = os.path.join(ROOT, "profiles", "k_faces_traffic.json.txt")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["dram_bytes_per_launch_full_size"])
+        if d.get("sources_sha1") != sources_sha1(FACE_SOURCES):
+            return None
+        return float(d["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def fp64_peak_tflops(sm_max_mhz):
+    """FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA
+    lanes-ops per SM per clock x 2 flop, at the maximum SM clock seen."""
+    mhz = sm_max_mhz if sm_max_mhz else 2070.0
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
 def load_workload():
@@ -201,10 +228,14 @@ def run_gpu(args):
         kern_ms[name] = kern_ms.get(name, 0.0) + t / reps
     kernels_per_step = sum(1 for name, _ in launches if "memset" not in name) // reps
     peak, peak_kind = measured_peak_gbs()
-    sweep_ms = 0.0
-    sweep_bytes = SWEEP_BYTES_PER_CELL * cells
-    achieved = 0.0
-    traffic = sweep_traffic_from_profile()
+    counts = P.vof_step_work_counts(g, st.workspace, stream)
+    # the dominant kernel: k_faces (its three launches take the largest share
+    # of the step); FP64-ALU bound: it evaluates every listed face once
+    faces_ms = sum(kern_ms.get(f"sweep_{a}.faces", 0.0) for a in "xyz")
+    faces_per_step = sum(counts["faces"])
+    step_ms_prof = sum(kern_ms.values())
+    fp64_achieved = FACE_FLOP * faces_per_step / (faces_ms * 1e-3) / 1e12 if faces_ms > 0 else 0.0
+    traffic = faces_traffic_from_profile()
 
     # ---- end to end through the public API with host buffers ---------------
     # each step the face velocities of the liquid (produced by the flow
@@ -250,9 +281,17 @@ def run_gpu(args):
                            (wl.c.nbytes + wl.e.nbytes + h2d) / 1e9),
                        "algorithmic_bytes_per_cell_step": STEP_BYTES_PER_CELL,
                        "hbm_roofline_frac_step": round(value / world * STEP_BYTES_PER_CELL / peak, 4)},
-            "roofline": {"bound": "hbm", "kernel": "k_sweep (x/y/z mean)", "achieved": round(achieved, 1),
-                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": traffic, "algorithmic_bytes_per_launch": sweep_bytes},
+            "roofline": {"bound": "alu", "kernel": "k_faces (sweep x, y, z)", "achieved": round(fp64_achieved, 4),
+                         "peak": round(fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None), 4),
+                         "unit": "TFLOP/s",
+                         "frac": round(fp64_achieved / fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None), 4),
+                         "traffic": traffic,
+                         "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x max SM clock",
+                         "flop_per_face": FACE_FLOP, "faces_per_launch": round(faces_per_step / 3),
+                         "ms_per_launch": round(faces_ms / 3, 5),
+                         "share_of_step": round(faces_ms / step_ms_prof, 4) if step_ms_prof > 0 else None,
+                         "hbm_frac_step": round(value / world * STEP_BYTES_PER_CELL / peak, 4), "hbm_peak_gbs": peak},
+            "work_counts": counts,
             "kernel_ms": {k: round(v_, 5) for k, v_ in sorted(kern_ms.items(), key=lambda kv: -kv[1])},
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": P.VOF_NSUMS * 8},

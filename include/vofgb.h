@@ -212,6 +212,18 @@ VOF_API vof_status vof_step_noalloc(const vof_grid* g, double* c, double* e, con
                                     double* sums, void* stream);
 
 /*
+ * Work counts of the last vof_step() run with this workspace
+ * (instrumentation; the paper has no counterpart): counts[VOF_NCOUNTS] =
+ *   {mixed cells, faces evaluated} of the x, y and z sweeps (6 ints),
+ *   {moving mixed cells by the analytic plane constant, by bisection,
+ *    receivers settled} of the shift (3 ints).
+ * Copies them to host memory after the work queued on `stream` (the step's
+ * stream) completes.  VOF_EINVAL for a bad grid or null pointers.
+ */
+#define VOF_NCOUNTS 9
+VOF_API vof_status vof_step_work_counts(const vof_grid* g, const void* workspace, int* counts, void* stream);
+
+/*
  * Per-launch timing (instrumentation; the paper has no counterpart).
  * vof_profile_begin(stream) records a start event on `stream`; until
  * vof_profile_end() every kernel or memset the library launches is followed

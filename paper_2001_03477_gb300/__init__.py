@@ -112,6 +112,8 @@ def lib():
         L.vof_shift_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_workspace_bytes.argtypes = [G]
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_step_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
+        L.vof_step_work_counts.restype = ctypes.c_int
         L.vof_profile_begin.argtypes = [P]
         L.vof_profile_begin.restype = ctypes.c_int
         L.vof_profile_end.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
@@ -294,6 +296,21 @@ VOF_NOALLOC_MAX_CELLS = 262144
 
 def vof_get_device_status() -> int:
     return int(lib().vof_get_device_status())
+
+
+VOF_NCOUNTS = 9
+
+
+def vof_step_work_counts(g, workspace, stream=None):
+    """Work counts of the last vof_step run with `workspace`: dict with the
+    mixed cells and faces of each sweep and the shift's cell counts."""
+    cg = g.c_struct()
+    out = (ctypes.c_int * VOF_NCOUNTS)()
+    _check("vof_step_work_counts", lib().vof_step_work_counts(ctypes.byref(cg), _ptr(workspace, None, "workspace"),
+                                                              out, _stream(stream)))
+    v = list(out)
+    return {"mixed": v[0:6:2], "faces": v[1:6:2], "shift_analytic": v[6], "shift_bisection": v[7],
+            "receivers": v[8]}
 
 
 def vof_profile_begin(stream=None):

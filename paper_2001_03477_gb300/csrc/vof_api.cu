@@ -195,13 +195,13 @@ vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const d
 
 // workspace layout: theta | state | sum rows (tile pass, the three sweeps'
 // update kernels, the shift's sums kernel; kNSums doubles per CTA) |
-// reduction scratch | tiles |
+// reduction scratch | work counts | tiles |
 // scratch (reused by the three sweeps, then the shift).  The sweeps and the
 // shift all run in place on c and e; the tile pass sums c and e at the start
 // and every later kernel adds the changes it makes, so one fixed-order
 // reduction of all rows gives the sums at the end of the step.
 struct StepLayout {
-  size_t off_th, off_st, off_rows, off_red, off_tiles, off_sw, total;
+  size_t off_th, off_st, off_rows, off_red, off_stats, off_tiles, off_sw, total;
   int nb_tiles, nb_sw[3], nb_sh, nrows;
 };
 
@@ -221,7 +221,8 @@ static StepLayout step_layout(const vof_grid* g) {
   L.nb_sh = shift_sum_blocks(d);
   L.nrows += L.nb_sh;
   L.off_red = L.off_rows + align256((size_t)L.nrows * kNSums * 8);
-  L.off_tiles = L.off_red + align256(reduce_scratch_bytes());
+  L.off_stats = L.off_red + align256(reduce_scratch_bytes());
+  L.off_tiles = L.off_stats + 256;
   L.off_sw = L.off_tiles + align256(tile_scratch_bytes(d));
   const size_t sw = sweep_scratch_bytes(d), sh = shift_scratch_bytes(d);
   L.total = L.off_sw + align256(sw > sh ? sw : sh);
@@ -269,12 +270,14 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
     const int ax = (step_index % 2 == 0) ? s : 2 - s;
     SweepScratch sc = carve_sweep_scratch(ax, d, ws + L.off_sw, sums_to_partials(rows + r * kNSums, kNSums));
     sc.tiles = tm;
+    sc.stats = reinterpret_cast<int*>(ws + L.off_stats) + 2 * ax;
     err = launch_sweep(ax, d, c, e, c, e, uf[ax], state, th, nullptr, sc, st);
     if (err != cudaSuccess) return cuda_status(err);
     r += (size_t)L.nb_sw[ax];
   }
   ShiftScratch shs = carve_shift_scratch(d, ws + L.off_sw);
   shs.tiles = tm;
+  shs.stats = reinterpret_cast<int*>(ws + L.off_stats) + 6;
   const SumOut none = sums_to_partials(nullptr, kNSums);
   err = launch_shift(d, c, e, c, e, dd, dd_uniform, nullptr, shs, none, sums_to_partials(rows + r * kNSums, kNSums),
                      st);
@@ -288,6 +291,16 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
     if (err != cudaSuccess) return cuda_status(err);
   }
   return VOF_OK;
+}
+
+vof_status vof_step_work_counts(const vof_grid* g, const void* workspace, int* counts, void* stream) {
+  if (!grid_ok(g) || !workspace || !counts) return VOF_EINVAL;
+  const StepLayout L = step_layout(g);
+  const char* ws = static_cast<const char*>(workspace);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t err = cudaMemcpyAsync(counts, ws + L.off_stats, VOF_NCOUNTS * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  return cuda_status(err);
 }
 
 vof_status vof_get_device_status(void) {

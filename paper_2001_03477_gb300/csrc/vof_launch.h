@@ -62,6 +62,7 @@ struct SweepScratch {
   int* count;
   SumOut sums;       // per-CTA sums of kernel U: Delta c, Delta e, clipped volume
   TileMap tiles;     // quiet tiles (in-place steps only)
+  int* stats;        // nullable: kernel U copies counters[0..1] here
   uint32_t* mlist;   // per-warp staging lists of mixed cells
   uint32_t* rlist;   // per-warp staging lists of run ends
   int* counters;     // [0] mixed cells, [1] face items (zeroed before kernel A)
@@ -103,6 +104,7 @@ struct ShiftScratch {
   double* cnew;   // [N] shifted volume of a moving mixed cell
   uint32_t* own;  // [N]
   TileMap tiles;  // quiet tiles (in-place steps only)
+  int* stats;     // nullable: the sums kernel copies counters[0..2] here
 };
 
 // The shift's kernels: stream (lists; out of place also copies; sums c, e

@@ -360,6 +360,11 @@ k_shift_sums(GridDev g, const double* c_in, const double* e_in, double* c_out, d
   v[kSumShDc] = acc[0];
   v[kSumUnpl] = acc[1];
   v[kSumShDe] = acc[2];
+  if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
+    sc.stats[0] = sc.counters[0];
+    sc.stats[1] = sc.counters[1];
+    sc.stats[2] = sc.counters[2];
+  }
   block_sums(v, sums, blockIdx.x);
 }
 
@@ -461,6 +466,7 @@ ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   s.cnew = reinterpret_cast<double*>(b);     b += al256(N * 8);
   s.own = reinterpret_cast<uint32_t*>(b);
   s.tiles = TileMap{nullptr, {0, 0, 0}};
+  s.stats = nullptr;
   return s;
 }
 

@@ -575,6 +575,11 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
       v[kSumE] += de;
     }
   }
+  // work counts of this sweep (kernel A's counters are final by now)
+  if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
+    sc.stats[0] = sc.counters[0];
+    sc.stats[1] = sc.counters[1];
+  }
   block_sums(v, sc.sums, blockIdx.x);
 }
 
@@ -743,6 +748,7 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, SumOut su
   s.count = reinterpret_cast<int*>(b);          b += al256((size_t)p.nsub * 4);
   s.sums = sums;
   s.tiles = TileMap{nullptr, {0, 0, 0}};
+  s.stats = nullptr;
   s.mlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
   s.rlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
   s.counters = reinterpret_cast<int*>(b);       b += 256;
