@@ -116,7 +116,8 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
                                               uint8_t* __restrict__ state, double* __restrict__ theta, double& dc,
                                               double& de) {
   const bool dirty = stv & 1;
-  const double ccv = dirty ? (double)((stv >> 1) & 1) : (dgthalf(c) ? 1.0 : 0.0);
+  const bool ccb = dirty ? ((stv >> 1) & 1) != 0 : dgthalf(c);
+  const double ccv = ccb ? 1.0 : 0.0;
   const double lf = Fl - ccv * al, rf = Fr - ccv * ar;
   const double cn = (c + lf) - rf;
   double cc2 = cn, clip = 0.0;
@@ -126,13 +127,14 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
   dc = cc2 - c;
   de = 0.0;
   if (ENERGY) {
-    const double th = dirty ? theta[id] : heat_cap(g.Cp_l, g.Cp_g, ccv) * T;
+    // C_p(cc) with cc in {0, 1} is C_pl or C_pg exactly
+    const double th = dirty ? theta[id] : (ccb ? g.Cp_l : g.Cp_g) * T;
     const double le = Gl - th * al, re = Gr - th * ar;
     const double en = (e + le) - re;
     e_out[id] = en;
     de = en - e;
     if (state && !dirty && (!deq(cc2, c) || !deq(en, e))) {
-      state[id] = (uint8_t)(1 | (ccv > 0.5 ? 2 : 0));
+      state[id] = (uint8_t)(1 | (ccb ? 2 : 0));
       theta[id] = th;
     }
   }
