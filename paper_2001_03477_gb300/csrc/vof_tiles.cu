@@ -24,6 +24,16 @@ constexpr unsigned kFullT = 0xffffffffu;
 
 __device__ __forceinline__ bool same_bits_t(double a, double b) { return dbits(a) == dbits(b); }
 
+__device__ __noinline__ void add_tile_cells(const double (&cv)[kTile], const double (&ev)[kTile], bool on,
+                                           double (&v)[kNSums]) {
+  if (!on) return;
+#pragma unroll
+  for (int zi = 0; zi < kTile; ++zi) {
+    v[kSumC] += cv[zi];
+    v[kSumE] += ev[zi];
+  }
+}
+
 // CTA: 32 x 8 threads covering four tiles along x (32 cells), one along y
 // and one along z (the threads walk its 8 planes).
 __global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e,
@@ -80,17 +90,17 @@ __global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restri
         ts.vc[t] = cr;
         ts.ve[t] = er;
       }
-    } else {
-      if (ty == 0 && (tx & 7) == 0) ts.uni[((size_t)blockIdx.z * nty + blockIdx.y) * ntx + xt] = 0;
-      if (xy_ok) {
-#pragma unroll
-        for (int zi = 0; zi < kTile; ++zi) {
-          v[kSumC] += cv[zi];
-          v[kSumE] += ev[zi];
-        }
-      }
+    } else if (ty == 0 && (tx & 7) == 0) {
+      ts.uni[((size_t)blockIdx.z * nty + blockIdx.y) * ntx + xt] = 0;
     }
   }
+  // cell by cell only in the tiles that are not uniform; the branch is
+  // taken per warp so that the adds are not executed (predicated) for the
+  // uniform majority -- an FP64 add costs ~80 cycles of the SM partition's
+  // FP64 unit per warp on this part
+  const bool add_cells = tile_ok && !tile_uni && xy_ok;
+  if (__any_sync(kFullT, add_cells)) add_tile_cells(cv, ev, add_cells, v);
+
   block_sums(v, sums, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
