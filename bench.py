@@ -41,6 +41,23 @@ SWEEP_BYTES_PER_CELL = 8 + 8 + 8 + 1 + 8 + 8
 STEP_BYTES_PER_CELL = 3 * SWEEP_BYTES_PER_CELL + 1 + 32
 
 
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' values of x (every rank gets it)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells, steps, world, seconds):
+    """Whole-job Gcell/s: every rank advances its own replica (weak scaling),
+    timed by the slowest rank."""
+    return cells * steps * world / seconds / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -204,13 +221,10 @@ def run_gpu(args):
     barrier()
     clocks = sampler.stop() if sampler else None
     ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, world, dev)
     sums = st.sums.cpu().numpy()
     cells = wl.cells
-    value = cells * args.steps * world / (ms * 1e-3) / 1e9
+    value = job_throughput(cells, args.steps, world, ms * 1e-3)
 
     # ---- per-launch durations of the same step ----------------------------
     # the library records a CUDA event on the launching stream after each of
@@ -261,11 +275,8 @@ def run_gpu(args):
         _ = float(sums_h[0])
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
-    e2e_value = cells * e2e_steps * world / e2e_s / 1e9
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e_value = job_throughput(cells, e2e_steps, world, e2e_s)
     h2d = (wl.u.nbytes + wl.v.nbytes + wl.w.nbytes)
 
     if rank == 0:
