@@ -65,9 +65,11 @@ struct SweepScratch {
   int* stats;        // nullable: kernel U copies counters[0..1] here
   uint32_t* mlist;   // per-warp staging lists of mixed cells
   uint32_t* rlist;   // per-warp staging lists of run ends
-  int* counters;     // [0] mixed cells, [1] face items (zeroed before kernel A)
+  int* counters;     // [0] mixed cells, [1] face items at the front, [2] at the
+                     // back (faces next to a mixed cell); zeroed before kernel A
   uint32_t* gmix;    // grid-wide list of mixed cells, in no fixed order
   uint32_t* gface;   // grid-wide face items (cell << 1 | side), no fixed order
+  uint32_t gface_cap;  // entries of gface (2 N)
   double* plane;     // [N][4]: m0, m1, m2, alpha of the listed mixed cells
   double* F;         // face arrays of the axis (face layout of the velocities)
   double* G;

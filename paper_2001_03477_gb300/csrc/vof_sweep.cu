@@ -152,26 +152,59 @@ constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
 constexpr int kPlaneThreads = 128;  // kernel M: CTA size; grid kPlaneCTAs
 constexpr int kPlaneCTAs = 152 * 8;
 
+// Staged face entries carry this flag when a cell next to the face is mixed
+// (its donor may need the PLIC geometry); kernel A's per-warp cell list
+// keeps it too (kernel U masks it off).
+constexpr uint32_t kMixedAdj = 0x80000000u;
+
+// Copies n staged entries to the grid-wide face list, flagged ones to the
+// back and the others to the front, as face items (cell << 1 | side).
+__device__ __forceinline__ void copy_faces(const SweepScratch& sc, const uint32_t* src, int n, uint32_t side, int bf,
+                                           int bb, int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  for (int j0 = 0; j0 < n; j0 += 32) {  // n is warp-uniform
+    const int j = j0 + lane;
+    const uint32_t v = j < n ? src[j] : 0u;
+    const bool ok = j < n, fl = ok && (v & kMixedAdj);
+    const unsigned mf = __ballot_sync(kFull, fl), mo = __ballot_sync(kFull, ok && !fl);
+    const uint32_t item = ((v & ~kMixedAdj) << 1) | side;
+    if (fl) sc.gface[sc.gface_cap - 1 - (uint32_t)(bb + __popc(mf & lt))] = item;
+    else if (ok) sc.gface[bf + __popc(mo & lt)] = item;
+    bf += __popc(mo);
+    bb += __popc(mf);
+  }
+}
+
 // Appends a warp's lists (staged in its own slots) to the grid-wide lists:
 // its mixed cells to the list of kernel M, and one face item per listed cell
 // (its left face) and per run end (the right face of a listed cell whose
-// next cell along the axis is not listed) to the list of kernel F.  One
+// next cell along the axis is not listed) to the list of kernel F -- faces
+// next to a mixed cell at its back, so that the warps of kernel F that
+// evaluate PLIC slab volumes are few and the others never diverge.  One
 // atomic per list and warp reserves the slots; the order of the grid-wide
 // lists varies from run to run, and nothing that reads them depends on it.
-__device__ __forceinline__ void append_lists(const SweepScratch& sc, const uint32_t* list, int nlist,
+__device__ __forceinline__ void append_lists(const SweepScratch& sc, const uint32_t* list, int nlist, int nlist_m,
                                              const uint32_t* mlist, int nmixed, const uint32_t* rlist, int nrun,
-                                             int lane) {
-  int bm = 0, bf = 0;
+                                             int nrun_m, int lane) {
+  int bm = 0, bf = 0, bb = 0;
+  const int nfront = (nlist - nlist_m) + (nrun - nrun_m), nback = nlist_m + nrun_m;
   if (lane == 0) {
     if (nmixed) bm = atomicAdd(sc.counters + 0, nmixed);
-    if (nlist + nrun) bf = atomicAdd(sc.counters + 1, nlist + nrun);
+    if (nfront) bf = atomicAdd(sc.counters + 1, nfront);
+    if (nback) bb = atomicAdd(sc.counters + 2, nback);
   }
   bm = __shfl_sync(kFull, bm, 0);
   bf = __shfl_sync(kFull, bf, 0);
+  bb = __shfl_sync(kFull, bb, 0);
   __syncwarp();
   for (int i = lane; i < nmixed; i += 32) sc.gmix[bm + i] = mlist[i];
-  for (int i = lane; i < nlist; i += 32) sc.gface[bf + i] = list[i] << 1;
-  for (int i = lane; i < nrun; i += 32) sc.gface[bf + nlist + i] = (rlist[i] << 1) | 1u;
+  copy_faces(sc, list, nlist, 0u, bf, bb, lane);
+  copy_faces(sc, rlist, nrun, 1u, bf + (nlist - nlist_m), bb + nlist_m, lane);
+}
+
+// i-th face item of the grid-wide list (front part, then the back part)
+__device__ __forceinline__ uint32_t face_item(const SweepScratch& sc, int i, int nfront) {
+  return i < nfront ? sc.gface[i] : sc.gface[sc.gface_cap - 1 - (uint32_t)(i - nfront)];
 }
 
 template <int AX, bool ENERGY>
@@ -212,8 +245,9 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
       return;
     }
   }
-  int nlist = 0, nmixed = 0, nrun = 0;
+  int nlist = 0, nmixed = 0, nrun = 0, nlist_m = 0, nrun_m = 0;
   bool prev_listed = false;  // cell k-1 of this segment listed
+  double cm1 = 0.0;          // c of cell s0 - 1
   // window: cells k .. k+3 (c, e) and run = equal cells ending at k+3;
   // cells k+4 .. k+7 are in flight (prefetch queue pc/pe)
   double wc[4], we[4], qc[4], qe[4];
@@ -227,8 +261,10 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     const bool same = i > -4 && same_bits(cv, pc) && (!ENERGY || same_bits(ev, pe));
     run = same ? run + 1 : 1;
     if (i >= 0) { wc[i] = cv; we[i] = ev; }
+    if (i == -1) cm1 = cv;
     pc = cv; pe = ev;
   }
+  bool prev_mixed = act && is_mixed_b(cm1, g);  // cell k-1 mixed
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const size_t id = cbase + stride * map_idx(s0 + 4 + i, n_ax, bca);
@@ -254,18 +290,22 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
       if (ENERGY) e_out[id] = we[0];
     }
     const bool listed = act && !noop;
-    const unsigned m = __ballot_sync(kFull, listed);
-    if (listed) list[nlist + __popc(m & lt)] = (uint32_t)id;
-    nlist += __popc(m);
     const bool mixed = act && is_mixed_b(wc[0], g);
+    const uint32_t madj = (mixed || prev_mixed) ? kMixedAdj : 0u;  // face k
+    const unsigned m = __ballot_sync(kFull, listed);
+    if (listed) list[nlist + __popc(m & lt)] = (uint32_t)id | madj;
+    nlist += __popc(m);
+    nlist_m += __popc(__ballot_sync(kFull, listed && madj));
     const unsigned mm = __ballot_sync(kFull, mixed);
     if (mixed) mlist[nmixed + __popc(mm & lt)] = (uint32_t)id;
     nmixed += __popc(mm);
-    const bool rend = prev_listed && !listed;  // cell k-1 ends a run
+    const bool rend = prev_listed && !listed;  // cell k-1 ends a run (face k)
     const unsigned mr = __ballot_sync(kFull, rend);
-    if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(id - stride);
+    if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(id - stride) | madj;
     nrun += __popc(mr);
+    nrun_m += __popc(__ballot_sync(kFull, rend && madj));
     prev_listed = listed;
+    prev_mixed = mixed;
     // shift the window
     const bool same = same_bits(cn, wc[3]) && (!ENERGY || same_bits(en, we[3]));
 #pragma unroll
@@ -283,11 +323,13 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     next_listed = act && !(!force_all && run >= 7 && is01(wc[0]) && !(stn & 1));
   }
   const bool rend = prev_listed && !next_listed;
+  const uint32_t madj = (prev_mixed || (act && is_mixed_b(wc[0], g))) ? kMixedAdj : 0u;  // face s1
   const unsigned mr = __ballot_sync(kFull, rend);
-  if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(cbase + stride * (s1 - 1));
+  if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(cbase + stride * (s1 - 1)) | madj;
   nrun += __popc(mr);
+  nrun_m += __popc(__ballot_sync(kFull, rend && madj));
   if (lane == 0) sc.count[sub] = nlist;
-  append_lists(sc, list, nlist, mlist, nmixed, rlist, nrun, lane);
+  append_lists(sc, list, nlist, nlist_m, mlist, nmixed, rlist, nrun, nrun_m, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -330,7 +372,7 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
       return;
     }
   }
-  int nlist = 0, nmixed = 0, nrun = 0;
+  int nlist = 0, nmixed = 0, nrun = 0, nlist_m = 0, nrun_m = 0;
   auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
   auto lde = [&](int X) { return ENERGY ? __ldg(e_in + rbase + map_idx(X, nx, bcx)) : 0.0; };
   auto eqmask = [&](double cprev, double eprev, double cc, double ee) -> unsigned {
@@ -347,6 +389,7 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
   unsigned eqP = eqmask(cPP, ePP, cP, eP);
   unsigned eqC = eqmask(__shfl_sync(kFull, cP, 31), __shfl_sync(kFull, eP, 31), cC, eC);
   unsigned eqN = eqmask(__shfl_sync(kFull, cC, 31), __shfl_sync(kFull, eC, 31), cN, eN);
+  bool mixed_carry = is_mixed_b(__shfl_sync(kFull, cP, 31), g);  // cell base - 1 mixed
   for (; base < x1; base += 32) {
     const double cNN = ldc(base + 64 + lane), eNN = lde(base + 64 + lane);
     const int X = base + lane;
@@ -365,10 +408,16 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
       }
     }
     const bool listed = cell_ok && !noop;
+    const bool mx_raw = is_mixed_b(cC, g);
+    const bool mx_up = __shfl_up_sync(kFull, mx_raw, 1);
+    const bool mx_prev = lane == 0 ? mixed_carry : mx_up;  // cell X - 1 mixed
+    mixed_carry = __shfl_sync(kFull, mx_raw, 31);
+    const uint32_t madj = (mx_raw || mx_prev) ? kMixedAdj : 0u;  // face X
     const unsigned m = __ballot_sync(kFull, listed);
-    if (listed) list[nlist + __popc(m & lt)] = (uint32_t)(rbase + X);
+    if (listed) list[nlist + __popc(m & lt)] = (uint32_t)(rbase + X) | madj;
     nlist += __popc(m);
-    const bool mixed = cell_ok && is_mixed_b(cC, g);
+    nlist_m += __popc(__ballot_sync(kFull, listed && madj));
+    const bool mixed = cell_ok && mx_raw;
     const unsigned mm = __ballot_sync(kFull, mixed);
     if (mixed) mlist[nmixed + __popc(mm & lt)] = (uint32_t)(rbase + X);
     nmixed += __popc(mm);
@@ -383,9 +432,11 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
     const uint8_t stn = (listed && in_line && state) ? state[rbase + map_idx(Xn, nx, bcx)] : (uint8_t)0;
     const bool next_listed = in_line && !(!force_all && uni_n && is01(c_next) && !(stn & 1));
     const bool rend = listed && !next_listed;
+    const uint32_t madj_r = (mx_raw || is_mixed_b(c_next, g)) ? kMixedAdj : 0u;  // face X + 1
     const unsigned mr = __ballot_sync(kFull, rend);
-    if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(rbase + X);
+    if (rend) rlist[nrun + __popc(mr & lt)] = (uint32_t)(rbase + X) | madj_r;
     nrun += __popc(mr);
+    nrun_m += __popc(__ballot_sync(kFull, rend && madj_r));
     const double c31 = __shfl_sync(kFull, cN, 31), e31 = __shfl_sync(kFull, eN, 31);
     const unsigned eqNN = eqmask(c31, e31, cNN, eNN);
     cP = cC; eP = eC;
@@ -394,7 +445,7 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
     eqP = eqC; eqC = eqN; eqN = eqNN;
   }
   if (lane == 0) sc.count[sub] = nlist;
-  append_lists(sc, list, nlist, mlist, nmixed, rlist, nrun, lane);
+  append_lists(sc, list, nlist, nlist_m, mlist, nmixed, rlist, nrun, nrun_m, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,11 +462,11 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
 __global__ void __launch_bounds__(kPlaneThreads)
 k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int nm = sc.counters[0];
-  const int cnt = nm + (e_in ? sc.counters[1] : 0);
+  const int nm = sc.counters[0], nf = sc.counters[1];
+  const int cnt = nm + (e_in ? nf + sc.counters[2] : 0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
     if (i >= nm) {
-      const uint32_t item = sc.gface[i - nm];
+      const uint32_t item = face_item(sc, i - nm, nf);
       if (item & 1u) continue;  // right-face item: its cell has a left item too
       const size_t id = item >> 1;
       sc.T[id] = __ldg(e_in + id) / heat_cap(g.Cp_l, g.Cp_g, __ldg(c_in + id));
@@ -472,10 +523,11 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  const int cnt = sc.counters[1];
+  const int nf = sc.counters[1];
+  const int cnt = nf + sc.counters[2];
   const size_t stride = AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-    const uint32_t item = sc.gface[i];
+    const uint32_t item = face_item(sc, i, nf);
     const size_t id = item >> 1;
     const int side = (int)(item & 1u);
     int x, y, z;
@@ -556,7 +608,7 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
     const int cnt = sc.count[sub];
     const uint32_t* list = sc.list + (size_t)sub * cap;
     for (int i = lane; i < cnt; i += 32) {
-      const size_t id = list[i];
+      const size_t id = list[i] & ~kMixedAdj;
       int x, y, z;
       cell_xyz(g, id, x, y, z);
       const int k = AX == 0 ? x : (AX == 1 ? y : z);
@@ -580,7 +632,7 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
   // work counts of this sweep (kernel A's counters are final by now)
   if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
     sc.stats[0] = sc.counters[0];
-    sc.stats[1] = sc.counters[1];
+    sc.stats[1] = sc.counters[1] + sc.counters[2];
   }
   block_sums(v, sc.sums, blockIdx.x);
 }
@@ -756,6 +808,7 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, SumOut su
   s.counters = reinterpret_cast<int*>(b);       b += 256;
   s.gmix = reinterpret_cast<uint32_t*>(b);      b += al256(N * 4);
   s.gface = reinterpret_cast<uint32_t*>(b);     b += al256(2 * N * 4);
+  s.gface_cap = (uint32_t)(2 * N);
   s.plane = reinterpret_cast<double*>(b);       b += al256(N * 32);
   s.F = reinterpret_cast<double*>(b);           b += al256(max_faces(g) * 8);
   s.G = reinterpret_cast<double*>(b);
@@ -789,7 +842,7 @@ cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const d
                          SweepScratch sc, cudaStream_t st) {
   int* status = device_status_ptr();
   const SweepPlan p = sweep_plan(axis, g);
-  const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 2 * sizeof(int), st);
+  const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
   if (err != cudaSuccess) return err;
   prof_mark("sweep.memset", st);
   if (e_in) {
