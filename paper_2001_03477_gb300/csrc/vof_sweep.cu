@@ -588,9 +588,9 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 }
 
 // ---------------------------------------------------------------------------
-// Kernel U: one warp per kernel-A list (fixed order, so the clipped-volume
-// sums are reproducible), one listed cell per lane: the WY update from the
-// two face fluxes.  It reads no cell but its own, so it may update in place
+// Kernel U: one CTA per 8 kernel-A lists (fixed order, so the sums are
+// reproducible), one listed cell per thread: the WY update from the two face
+// fluxes.  It reads no cell but its own, so it may update in place
 // (c_out == c_in, e_out == e_in); kernel A then copies nothing.
 // ---------------------------------------------------------------------------
 template <int AX, bool ENERGY>
@@ -601,14 +601,27 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  const int lane = threadIdx.x & 31;
-  const int sub = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  // the CTA takes the 8 lists sub0 .. sub0+7 as one sequence (fixed order):
+  // short lists then still fill whole warps
+  __shared__ int pre[9];
+  const int sub0 = blockIdx.x * 8;
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; ++w) {
+      pre[w] = t;
+      t += (sub0 + w < nsub) ? sc.count[sub0 + w] : 0;
+    }
+    pre[8] = t;
+  }
+  __syncthreads();
+  const int total = pre[8];
   double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (sub < nsub) {
-    const int cnt = sc.count[sub];
-    const uint32_t* list = sc.list + (size_t)sub * cap;
-    for (int i = lane; i < cnt; i += 32) {
-      const size_t id = list[i] & ~kMixedAdj;
+  {
+    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+      int w = 0;
+#pragma unroll
+      for (int q = 1; q < 8; ++q) w += (j >= pre[q]) ? 1 : 0;
+      const size_t id = sc.list[(size_t)(sub0 + w) * cap + (j - pre[w])] & ~kMixedAdj;
       int x, y, z;
       cell_xyz(g, id, x, y, z);
       const int k = AX == 0 ? x : (AX == 1 ? y : z);
