@@ -412,6 +412,58 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
   return am * r.l1 - r.sh;
 }
 
+// The volume function with every compare on the integer pipe: the normal is
+// mirrored to |m_i| (a -0 component becomes +0, which changes no volume), so
+// all compared values are non-negative and order like their bit patterns.
+// Not bit-for-bit the plain routine's steps at a zero component's sign, so
+// the oracle-identical bisection keeps the plain one.
+__device__ __forceinline__ double vol_low_nn(double m1, double m2, double m3, double a) {
+  const double m12 = m1 + m2;
+  if (nn_lt(a, m1)) return a * a * a / (6.0 * m1 * m2 * m3);
+  const double v2 = a * (a - m1) / (2.0 * m2 * m3) + m1 * m1 / (6.0 * m2 * m3);
+  if (nn_lt(a, m2)) return v2;
+  const double t2 = a - m2;
+  const double v3 = v2 - t2 * t2 * t2 / (6.0 * m1 * m2 * m3);
+  const double top = nn_lt(m12, m3) ? m12 : m3;
+  if (nn_lt(a, top)) return v3;
+  if (!nn_lt(m3, m12)) return (2.0 * a - m12) / (2.0 * m3);
+  const double t3 = a - m3;
+  return v3 - t3 * t3 * t3 / (6.0 * m1 * m2 * m3);
+}
+
+__device__ __forceinline__ double volume_nn(double m0, double m1, double m2, double alpha) {
+  double sh = 0.0;
+  if (dlt0(m0)) sh -= m0;
+  if (dlt0(m1)) sh -= m1;
+  if (dlt0(m2)) sh -= m2;
+  double a0 = fabs(m0), a1 = fabs(m1), a2 = fabs(m2);
+  const double l1 = a0 + a1 + a2;
+  if (!dnz(l1)) return dlt0(alpha) ? 0.0 : 1.0;
+  a0 /= l1; a1 /= l1; a2 /= l1;
+  const double a = (alpha + sh) / l1;
+  if (!dgt0(a)) return 0.0;
+  if (!nn_lt(a, 1.0)) return 1.0;
+  // sort the three non-negative components
+  double t;
+  if (nn_lt(a1, a0)) { t = a0; a0 = a1; a1 = t; }
+  if (nn_lt(a2, a1)) { t = a1; a1 = a2; a2 = t; }
+  if (nn_lt(a1, a0)) { t = a0; a0 = a1; a1 = t; }
+  if (!nn_lt(0.5, a)) return vol_low_nn(a0, a1, a2, a);
+  return 1.0 - vol_low_nn(a0, a1, a2, 1.0 - a);
+}
+
+// liquid volume (cell units) in the slab x_axis in [x0, x0+delta], any m,
+// with the integer-pipe volume function
+__device__ __forceinline__ double slab_volume_nn(const double m[3], double alpha, int axis, double x0, double delta) {
+  if (!dgt0(delta)) return 0.0;
+  double mm0 = m[0], mm1 = m[1], mm2 = m[2];
+  const double ma = m[axis];
+  if (axis == 0) mm0 = ma * delta;
+  else if (axis == 1) mm1 = ma * delta;
+  else mm2 = ma * delta;
+  return delta * volume_nn(mm0, mm1, mm2, alpha - ma * x0);
+}
+
 // liquid volume (cell units) in the slab x_axis in [x0, x0+delta]
 __device__ __forceinline__ double slab_volume(const double m[3], double alpha, int axis, double x0, double delta) {
   if (delta <= 0.0) return 0.0;

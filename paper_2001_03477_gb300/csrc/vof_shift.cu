@@ -210,7 +210,7 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
       double ast = al + sft;
       if (ast < lo) ast = lo;
       if (ast > hi) ast = hi;
-      sc.cnew[id] = volume(m[0], m[1], m[2], ast);  // applied by the sums kernel
+      sc.cnew[id] = volume_nn(m[0], m[1], m[2], ast);  // applied by the sums kernel
       // receivers this cell settles
       const bool full = dlt0(ddv);  // the kind of pure cell this shift reaches
       for (int oz = -1; oz <= 1; ++oz)
@@ -288,14 +288,14 @@ k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __re
           const double a_old = al + shiftv;
           const double a_new = (al + sft) + shiftv;
           double lo = 0.0, hi = 0.0;
-          if (m0 < 0.0) lo += m0; else hi += m0;
-          if (m1 < 0.0) lo += m1; else hi += m1;
-          if (m2 < 0.0) lo += m2; else hi += m2;
+          if (dlt0(m0)) lo += m0; else hi += m0;
+          if (dlt0(m1)) lo += m1; else hi += m1;
+          if (dlt0(m2)) lo += m2; else hi += m2;
           // the extended plane stays outside the receiver: both volumes are
           // exactly 1 (or 0); the margin clears the rounding of that test
           if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
-          const double sw = volume(m0, m1, m2, a_new) - volume(m0, m1, m2, a_old);
-          if (fabs(sw) > fabs(best)) best = sw;
+          const double sw = volume_nn(m0, m1, m2, a_new) - volume_nn(m0, m1, m2, a_old);
+          if (nn_lt(fabs(best), fabs(sw))) best = sw;
         }
     sc.sweep[pid] = best;  // applied by the sums kernel
   }

@@ -561,7 +561,7 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
         const double mv[3] = {pl.x, pl.y, pl.z};
         const double da = fabs(a);
         if (da > 1.0 && status) atomicOr(status, DEV_CFL);
-        const double vol = slab_volume(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
+        const double vol = slab_volume_nn(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
         Fv = pos ? vol : -vol;
       } else {
         Fv = cd * a;
