@@ -397,11 +397,37 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
     if (!nn_lt(0.5, a)) return vlow(a);
     return 1.0 - vlow(1.0 - a);
   };
+  // The same volume with the divisions replaced by products with the
+  // rounded reciprocals: within a few ulps of it (relative below the middle
+  // of the cell, of 1 above).  A midpoint whose fast volume is farther from
+  // c than a margin ~500 times that is decided from it -- the exact volume
+  // is on the same side of c -- and only midpoints near the root pay for the
+  // exact volume's divisions (slow on this part).  The decisions, and so the
+  // result, are those of the plain bisection.
+  const double r6 = 1.0 / d6, r2 = 1.0 / d2, r2m3 = 1.0 / d2m3;
+  auto vlow_fast = [&](double a) -> double {
+    if (nn_lt(a, s0)) return a * a * a * r6;
+    const double v2 = a * (a - s0) * r2 + v2c;
+    if (nn_lt(a, s1)) return v2;
+    const double t2 = a - s1;
+    const double v3 = v2 - t2 * t2 * t2 * r6;
+    if (nn_lt(a, top)) return v3;
+    if (lin) return (2.0 * a - m12) * r2m3;
+    const double t3 = a - s2;
+    return v3 - t3 * t3 * t3 * r6;
+  };
+  const double margin_low = 1e-12 * c;
+  const double margin_high = nn_lt(1e-14, 1e-12 * (1.0 - c)) ? 1e-12 * (1.0 - c) : 1e-14;
   double lo = 0.0, hi = 1.0;
   for (int it = 0; it < 200; ++it) {
     double mid = lo + 0.5 * (hi - lo);
     if (!(nn_lt(lo, mid) && nn_lt(mid, hi))) break;
-    if (nn_lt(vpos(mid), c)) lo = mid;
+    const bool low = !nn_lt(0.5, mid);
+    const double d = (low ? vlow_fast(mid) : 1.0 - vlow_fast(1.0 - mid)) - c;
+    bool below;
+    if (nn_lt(low ? margin_low : margin_high, fabs(d))) below = dlt0(d);
+    else below = nn_lt(vpos(mid), c);
+    if (below) lo = mid;
     else hi = mid;
   }
   // lo and hi are 0 or 1 only at a bracket end never left (vpos's end cases)
