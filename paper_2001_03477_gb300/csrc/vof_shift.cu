@@ -69,12 +69,29 @@ __device__ __forceinline__ bool neighbour(const GridDev& g, int x, int y, int z,
   return true;
 }
 
-// moving mixed cell whose shift has the sign that reaches a receiver of this kind
-__device__ __forceinline__ bool reaches(const GridDev& g, const double* __restrict__ c_in,
-                                        const double* __restrict__ dd, double dd_uniform, size_t q, bool full) {
-  if (!is_mixed_b(__ldg(c_in + q), g)) return false;
-  const double ddv = dd ? __ldg(dd + q) : dd_uniform;
-  return dnz(ddv) && (dlt0(ddv) == full);
+// Bit b (offset index, scan order) set when the neighbour at that offset
+// is a moving mixed cell whose shift reaches pure cells of the kind `want`
+// (1: full cells, shift < 0; 2: empty cells, shift > 0), from the per-cell
+// reach bytes the stream kernel wrote.  The 26 byte loads are independent.
+__device__ __forceinline__ unsigned reach_mask(const GridDev& g, const uint8_t* __restrict__ reach, int x, int y,
+                                               int z, unsigned want) {
+  unsigned mask = 0u;
+#pragma unroll
+  for (int b = 0; b < 27; ++b) {
+    if (b == 13) continue;
+    const int ox = b % 3 - 1, oy = (b / 3) % 3 - 1, oz = b / 9 - 1;
+    int px = x + ox, py = y + oy, pz = z + oz;
+    bool ok = true;
+    if (g.bc[0] != 0 && (px < 0 || px >= g.n[0])) ok = false;
+    if (g.bc[1] != 0 && (py < 0 || py >= g.n[1])) ok = false;
+    if (g.bc[2] != 0 && (pz < 0 || pz >= g.n[2])) ok = false;
+    px = map_idx(px, g.n[0], g.bc[0]);
+    py = map_idx(py, g.n[1], g.bc[1]);
+    pz = map_idx(pz, g.n[2], g.bc[2]);
+    const unsigned r = __ldg(reach + ((size_t)pz * g.n[1] + py) * g.n[0] + px);
+    if (ok && (r & want)) mask |= 1u << b;
+  }
+  return mask;
 }
 
 // offsets as bit indices: ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1), 0..26
@@ -128,7 +145,12 @@ k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restr
         }
       }
       bool moving = ok && is_mixed_b(c, g);
-      if (moving) moving = dd ? dnz(__ldg(dd + id)) : uni_moving;
+      double ddv = dd_uniform;
+      if (moving) {
+        if (dd) ddv = __ldg(dd + id);
+        moving = dd ? dnz(ddv) : uni_moving;
+      }
+      if (moving) sc.reach[id] = dlt0(ddv) ? 1 : 2;  // the other cells stay 0
       const unsigned m = __ballot_sync(kFullMask, moving);
       if (moving) list[n + __popc(m & lt)] = (uint32_t)id;
       n += __popc(m);
@@ -223,6 +245,9 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
             if (is_mixed_b(cp, g) || is_full_b(cp, g) != full) continue;
             int px, py, pz;
             decode(g, pid, px, py, pz);
+            // first reaching neighbour of P in the scan order (early exit:
+            // this cell is one of them)
+            const unsigned want = full ? 1u : 2u;
             int first = -1;
             for (int rz = -1; rz <= 1 && first < 0; ++rz)
               for (int ry = -1; ry <= 1 && first < 0; ++ry)
@@ -230,7 +255,7 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
                   if (!rx && !ry && !rz) continue;
                   size_t sid;
                   if (!neighbour(g, px, py, pz, rx, ry, rz, sid)) continue;
-                  if (reaches(g, c_in, dd, dd_uniform, sid, full)) first = offset_bit(rx, ry, rz);
+                  if (__ldg(sc.reach + sid) & want) first = offset_bit(rx, ry, rz);
                 }
             // on periodic axes of 1 or 2 cells several offsets lead to the
             // same cell; only the offset back to this cell settles it
@@ -272,31 +297,31 @@ k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __re
     int px, py, pz;
     decode(g, pid, px, py, pz);
     double best = 0.0;
-    for (int rz = -1; rz <= 1; ++rz)
-      for (int ry = -1; ry <= 1; ++ry)
-        for (int rx = -1; rx <= 1; ++rx) {
-          if (!rx && !ry && !rz) continue;
-          size_t sid;
-          if (!neighbour(g, px, py, pz, rx, ry, rz, sid)) continue;
-          if (!reaches(g, c_in, dd, dd_uniform, sid, full)) continue;
-          const double sft = sc.shift[sid];
-          if (!dnz(sft)) continue;  // a zero normal does not move
-          const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
-          const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
-          // the receiver sits at offset -(rx, ry, rz) from the source
-          const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
-          const double a_old = al + shiftv;
-          const double a_new = (al + sft) + shiftv;
-          double lo = 0.0, hi = 0.0;
-          if (dlt0(m0)) lo += m0; else hi += m0;
-          if (dlt0(m1)) lo += m1; else hi += m1;
-          if (dlt0(m2)) lo += m2; else hi += m2;
-          // the extended plane stays outside the receiver: both volumes are
-          // exactly 1 (or 0); the margin clears the rounding of that test
-          if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
-          const double sw = volume_nn(m0, m1, m2, a_new) - volume_nn(m0, m1, m2, a_old);
-          if (nn_lt(fabs(best), fabs(sw))) best = sw;
-        }
+    unsigned rm = reach_mask(g, sc.reach, px, py, pz, full ? 1u : 2u);
+    while (rm) {  // reaching neighbours in scan order
+      const int b = __ffs(rm) - 1;
+      rm &= rm - 1u;
+      const int rx = b % 3 - 1, ry = (b / 3) % 3 - 1, rz = b / 9 - 1;
+      size_t sid;
+      neighbour(g, px, py, pz, rx, ry, rz, sid);
+      const double sft = sc.shift[sid];
+      if (!dnz(sft)) continue;  // a zero normal does not move
+      const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
+      const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
+      // the receiver sits at offset -(rx, ry, rz) from the source
+      const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
+      const double a_old = al + shiftv;
+      const double a_new = (al + sft) + shiftv;
+      double lo = 0.0, hi = 0.0;
+      if (dlt0(m0)) lo += m0; else hi += m0;
+      if (dlt0(m1)) lo += m1; else hi += m1;
+      if (dlt0(m2)) lo += m2; else hi += m2;
+      // the extended plane stays outside the receiver: both volumes are
+      // exactly 1 (or 0); the margin clears the rounding of that test
+      if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
+      const double sw = volume_nn(m0, m1, m2, a_new) - volume_nn(m0, m1, m2, a_old);
+      if (nn_lt(fabs(best), fabs(sw))) best = sw;
+    }
     sc.sweep[pid] = best;  // applied by the sums kernel
   }
 }
@@ -446,7 +471,8 @@ size_t shift_scratch_bytes(const GridDev& g) {
          + al256(N * 8)       // shifts
          + al256(N * 8)       // sweeps
          + al256(N * 8)       // new c of moving cells
-         + al256(N * 4);      // settled-receiver masks
+         + al256(N * 4)       // settled-receiver masks
+         + al256(N);          // reach bytes
 }
 
 ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
@@ -464,7 +490,8 @@ ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   s.shift = reinterpret_cast<double*>(b);    b += al256(N * 8);
   s.sweep = reinterpret_cast<double*>(b);    b += al256(N * 8);
   s.cnew = reinterpret_cast<double*>(b);     b += al256(N * 8);
-  s.own = reinterpret_cast<uint32_t*>(b);
+  s.own = reinterpret_cast<uint32_t*>(b);    b += al256(N * 4);
+  s.reach = reinterpret_cast<uint8_t*>(b);
   s.tiles = TileMap{nullptr, {0, 0, 0}};
   s.stats = nullptr;
   return s;
@@ -475,6 +502,7 @@ cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_i
                          SumOut sums, cudaStream_t st) {
   const long long nw = shift_warps(g);
   cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
+  if (err == cudaSuccess) err = cudaMemsetAsync(sc.reach, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
   if (err != cudaSuccess) return err;
   prof_mark("shift.memset", st);
   k_shift_stream<<<shift_stream_grid(g), dim3(32, 8), 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc,
