@@ -106,6 +106,7 @@ struct ShiftScratch {
   double* cnew;   // [N] shifted volume of a moving mixed cell
   uint32_t* own;  // [N]
   uint8_t* reach; // [N] 1: moving mixed cell with shift < 0, 2: > 0, else 0
+  uint32_t* claim;  // [N] receivers: bit 31 - b set by the reaching neighbour at offset index b
   TileMap tiles;  // quiet tiles (in-place steps only)
   int* stats;     // nullable: the sums kernel copies counters[0..2] here
 };

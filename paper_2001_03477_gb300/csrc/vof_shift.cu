@@ -189,12 +189,10 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
   const int nn = sc.counters[0], ne = sc.counters[1];
   const int lane = threadIdx.x & 31;
   const int total = nn + ne;
-  // whole warps iterate together (the receiver append below is warp-wide)
   const int stride = gridDim.x * blockDim.x;
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
     const int i = i0 + lane;
     const bool v = i < total;
-    unsigned own = 0u;
     int x = 0, y = 0, z = 0;
     if (v) {
       const size_t id = i < nn ? sc.gmix[i] : sc.gmix[N - 1 - (size_t)(i - nn)];
@@ -233,7 +231,11 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
       if (ast < lo) ast = lo;
       if (ast > hi) ast = hi;
       sc.cnew[id] = volume_nn(m[0], m[1], m[2], ast);  // applied by the sums kernel
-      // receivers this cell settles
+      // claim the receivers this shift reaches: bit 31 - b of a pure
+      // neighbour's claim word, b = this cell's offset index seen from it
+      // (scan order); the first reaching neighbour in the scan order -- the
+      // one that settles the receiver -- holds the highest set bit whatever
+      // the order of the atomics
       const bool full = dlt0(ddv);  // the kind of pure cell this shift reaches
       for (int oz = -1; oz <= 1; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
@@ -243,24 +245,47 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
             if (!neighbour(g, x, y, z, ox, oy, oz, pid)) continue;
             const double cp = __ldg(c_in + pid);
             if (is_mixed_b(cp, g) || is_full_b(cp, g) != full) continue;
-            int px, py, pz;
-            decode(g, pid, px, py, pz);
-            // first reaching neighbour of P in the scan order (early exit:
-            // this cell is one of them)
-            const unsigned want = full ? 1u : 2u;
-            int first = -1;
-            for (int rz = -1; rz <= 1 && first < 0; ++rz)
-              for (int ry = -1; ry <= 1 && first < 0; ++ry)
-                for (int rx = -1; rx <= 1 && first < 0; ++rx) {
-                  if (!rx && !ry && !rz) continue;
-                  size_t sid;
-                  if (!neighbour(g, px, py, pz, rx, ry, rz, sid)) continue;
-                  if (__ldg(sc.reach + sid) & want) first = offset_bit(rx, ry, rz);
-                }
-            // on periodic axes of 1 or 2 cells several offsets lead to the
-            // same cell; only the offset back to this cell settles it
-            if (first == offset_bit(-ox, -oy, -oz)) own |= 1u << offset_bit(ox, oy, oz);
+            atomicOr(sc.claim + pid, 0x80000000u >> offset_bit(-ox, -oy, -oz));
           }
+    }
+  }
+}
+
+// Per moving mixed cell (same list, after all claims are in): the receivers
+// it settles are the pure neighbours whose highest claim bit is its own
+// (on periodic axes of 1 or 2 cells several offsets lead to the same cell;
+// only the first of them in the scan order settles it); they are appended to
+// the receiver list, one atomic per warp.
+__global__ void __launch_bounds__(kListThreads)
+k_shift_own(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
+            ShiftScratch sc) {
+  const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const int nn = sc.counters[0], ne = sc.counters[1];
+  const int lane = threadIdx.x & 31;
+  const int total = nn + ne;
+  // whole warps iterate together (the receiver append below is warp-wide)
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
+    const int i = i0 + lane;
+    const bool v = i < total;
+    unsigned own = 0u;
+    int x = 0, y = 0, z = 0;
+    if (v) {
+      const size_t id = i < nn ? sc.gmix[i] : sc.gmix[N - 1 - (size_t)(i - nn)];
+      decode(g, id, x, y, z);
+      const double ddv = dd ? __ldg(dd + id) : dd_uniform;
+      const bool full = dlt0(ddv);
+#pragma unroll
+      for (int b = 0; b < 27; ++b) {
+        if (b == 13) continue;
+        const int ox = b % 3 - 1, oy = (b / 3) % 3 - 1, oz = b / 9 - 1;
+        size_t pid;
+        if (!neighbour(g, x, y, z, ox, oy, oz, pid)) continue;
+        const double cp = __ldg(c_in + pid);
+        const unsigned cl = __ldg(sc.claim + pid);
+        if (is_mixed_b(cp, g) || is_full_b(cp, g) != full) continue;
+        if (__clz(cl) == offset_bit(-ox, -oy, -oz)) own |= 1u << b;
+      }
       sc.own[id] = own;
     }
     // append the settled receivers: one atomic per warp
@@ -472,7 +497,8 @@ size_t shift_scratch_bytes(const GridDev& g) {
          + al256(N * 8)       // sweeps
          + al256(N * 8)       // new c of moving cells
          + al256(N * 4)       // settled-receiver masks
-         + al256(N);          // reach bytes
+         + al256(N)           // reach bytes
+         + al256(N * 4);      // receiver claims
 }
 
 ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
@@ -491,7 +517,8 @@ ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   s.sweep = reinterpret_cast<double*>(b);    b += al256(N * 8);
   s.cnew = reinterpret_cast<double*>(b);     b += al256(N * 8);
   s.own = reinterpret_cast<uint32_t*>(b);    b += al256(N * 4);
-  s.reach = reinterpret_cast<uint8_t*>(b);
+  s.reach = reinterpret_cast<uint8_t*>(b);   b += al256(N);
+  s.claim = reinterpret_cast<uint32_t*>(b);
   s.tiles = TileMap{nullptr, {0, 0, 0}};
   s.stats = nullptr;
   return s;
@@ -503,6 +530,7 @@ cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_i
   const long long nw = shift_warps(g);
   cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
   if (err == cudaSuccess) err = cudaMemsetAsync(sc.reach, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
+  if (err == cudaSuccess) err = cudaMemsetAsync(sc.claim, 0, (size_t)g.n[0] * g.n[1] * g.n[2] * 4, st);
   if (err != cudaSuccess) return err;
   prof_mark("shift.memset", st);
   k_shift_stream<<<shift_stream_grid(g), dim3(32, 8), 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc,
@@ -510,6 +538,8 @@ cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_i
   prof_mark("shift.stream", st);
   k_shift_planes<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
   prof_mark("shift.planes", st);
+  k_shift_own<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
+  prof_mark("shift.own", st);
   k_shift_receivers<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
   prof_mark("shift.receivers", st);
   k_shift_sums<<<shift_sum_blocks(g), 256, 0, st>>>(g, c_in, e_in, c_out, e_out, sc, nw, sums);
