@@ -65,47 +65,12 @@ __device__ __forceinline__ size_t cell_at(const GridDev& g, int x, int y, int z)
   return ((size_t)z * g.n[1] + y) * g.n[0] + x;
 }
 
-// Face VOF flux of a mixed donor (rare path): MYC on the donor's 27-cell
-// stencil (read through the read-only cache), plane constant, slab volume.
-__device__ __noinline__ double mixed_donor_flux(GridDev g, const double* __restrict__ c_in, int ax, int dx, int dy,
-                                                int dz, double cd, double a, int* status) {
-  double s[27];
-#pragma unroll
-  for (int oz = 0; oz < 3; ++oz) {
-    int zz = map_idx(dz + oz - 1, g.n[2], g.bc[2]);
-#pragma unroll
-    for (int oy = 0; oy < 3; ++oy) {
-      int yy = map_idx(dy + oy - 1, g.n[1], g.bc[1]);
-#pragma unroll
-      for (int ox = 0; ox < 3; ++ox) {
-        int xx = map_idx(dx + ox - 1, g.n[0], g.bc[0]);
-        s[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_at(g, xx, yy, zz));
-      }
-    }
-  }
-  double m[3];
-  myc_normal(s, m);
-  double al = plane_alpha(m[0], m[1], m[2], cd);
-  double da = fabs(a);
-  if (da > 1.0 && status) atomicOr(status, DEV_CFL);
-  double xs = dgt0(a) ? 1.0 - da : 0.0;
-  double vol = slab_volume(m, al, ax, xs, da);
-  return dgt0(a) ? vol : -vol;
-}
-
 // energy flux G = T_f (C_pl F + C_pg (a - F)) with T_f = WENO5 of the
-// upwind-ordered stencil (out of line: only faces next to non-no-op cells)
-__device__ __noinline__ double face_energy_flux(double Cp_l, double Cp_g, double Fv, double a, double t0, double t1,
+// upwind-ordered stencil
+__device__ __forceinline__ double face_energy_flux(double Cp_l, double Cp_g, double Fv, double a, double t0, double t1,
                                                 double t2, double t3, double t4) {
   const double Tf = weno5(t0, t1, t2, t3, t4);
   return (Tf * Cp_l) * Fv + (Tf * Cp_g) * (a - Fv);
-}
-
-// energy flux of a face from its upwind-ordered temperature stencil
-__device__ __forceinline__ double energy_flux(const GridDev& g, double Fv, double a, double t0, double t1, double t2,
-                                              double t3, double t4) {
-  double Tf = weno5(t0, t1, t2, t3, t4);
-  return (Tf * g.Cp_l) * Fv + (Tf * g.Cp_g) * (a - Fv);
 }
 
 // WY update of one cell from its two faces; returns the clipped volume
