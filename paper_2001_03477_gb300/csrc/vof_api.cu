@@ -35,6 +35,7 @@ static bool grid_ok(const vof_grid* g) {
     if (g->bc[d] != 0 && g->bc[d] != 1) return false;
   if (!(g->h > 0.0) || !(g->Cp_l > 0.0) || !(g->Cp_g > 0.0)) return false;
   if (!(g->eps_mixed >= 0.0 && g->eps_mixed < 0.5)) return false;
+  if (g->precision != VOF_F64 && g->precision != VOF_F32_FLUX) return false;
   return true;
 }
 
@@ -47,6 +48,7 @@ static GridDev to_dev(const vof_grid* g, double dt) {
   double ome = 1.0 - g->eps_mixed;
   std::memcpy(&d.eps_bits, &g->eps_mixed, 8);
   std::memcpy(&d.one_m_eps, &ome, 8);
+  d.f32 = g->precision == VOF_F32_FLUX ? 1 : 0;
   return d;
 }
 

@@ -25,6 +25,7 @@ struct GridDev {
   double Cp_l, Cp_g, T_sat, eps;
   long long eps_bits;     // bit pattern of eps
   long long one_m_eps;    // bit pattern of 1 - eps
+  int f32;                // precision form: FP32 reconstruction and flux weights in the sweeps
 };
 
 // ---------------------------------------------------------------------------
@@ -680,6 +681,173 @@ __device__ __forceinline__ double weno5(double vm2, double vm1, double v0, doubl
   const double r0 = fma(5.0, D1, -2.0 * D0), r1 = fma(2.0, D2, D1), r2 = fma(4.0, D2, -D3);
   const double num = fma(w0, r0, fma(w1, r1, w2 * r2));
   return v0 + num / (6.0 * (w0 + w1 + w2));
+}
+
+// ---------------------------------------------------------------------------
+// Precision form (vof_grid.precision = VOF_F32_FLUX): the sweeps'
+// reconstruction and flux weights in FP32, on the FP32 unit (~64x the FP64
+// rate on this part).  The plane constant is still inverted in FP64 from the
+// FP32 normal, stencil differences and cell updates stay FP64, so the fluxes
+// still telescope and volume and energy stay conserved to FP64 round-off.
+// ---------------------------------------------------------------------------
+// MYC normal in FP32.  The three decisions of the method (which
+// centred-columns candidate dominates, its own-axis sign, candidate or
+// Youngs) are taken in FP32 only where FP32 round-off cannot change them; a
+// cell within the error bounds below of any decision takes the FP64 normal,
+// so the precision form makes every decision the FP64 form makes.  Bounds,
+// with stencil values in [0, 1] rounded to FP32 (unit round-off u = 2^-24):
+// a column sum is off by <= 9u, a slope by <= 11u, l1 = |a1| + |a2| + 1 <= 4
+// by <= 30u, so dom = 1/l1 by <= 31u relative; the lower and upper sums of
+// 9 values by <= 60u each; a Youngs component (weights 1, 2, 4, magnitude
+// <= 16) by <= 190u and l1y by <= 670u, so ymax = max|y| / l1y by
+// <= 860u / l1y + u.  The margins below are about twice these.
+__device__ __forceinline__ void myc_normal_f(const double* sd, double m[3]) {
+  float s[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) s[i] = (float)sd[i];
+  auto at = [&](int d, int r, int p, int q) -> float {
+    int o0, o1, o2;
+    if (d == 0) { o0 = r; o1 = p; o2 = q; }
+    else if (d == 1) { o1 = r; o0 = p; o2 = q; }
+    else { o2 = r; o0 = p; o1 = q; }
+    return s[((o2 + 1) * 3 + (o1 + 1)) * 3 + (o0 + 1)];
+  };
+  float best[3] = {0.f, 0.f, 0.f}, dom[3];
+  float bdom = -1.f, bsep = 0.f;
+  int bd = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float h[3][3], lower = 0.f, upper = 0.f;
+#pragma unroll
+    for (int q = -1; q <= 1; ++q)
+#pragma unroll
+      for (int p = -1; p <= 1; ++p) {
+        h[p + 1][q + 1] = (at(d, -1, p, q) + at(d, 0, p, q)) + at(d, 1, p, q);
+        lower += at(d, -1, p, q);
+        upper += at(d, 1, p, q);
+      }
+    const float sg = lower >= upper ? 1.f : -1.f;
+    const float a1 = -(h[2][1] - h[0][1]) * 0.5f, a2 = -(h[1][2] - h[1][0]) * 0.5f;
+    const float l1 = fabsf(a1) + fabsf(a2) + 1.f;
+    dom[d] = 1.f / l1;
+    if (dom[d] > bdom) {
+      bdom = dom[d];
+      bd = d;
+      bsep = fabsf(lower - upper);
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      best[t1] = a1 * dom[d];
+      best[t2] = a2 * dom[d];
+      best[d] = sg * dom[d];
+    }
+  }
+  const float w[3] = {1.f, 2.f, 1.f};
+  float y[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float gsum = 0.f;
+#pragma unroll
+    for (int q = -1; q <= 1; ++q)
+#pragma unroll
+      for (int p = -1; p <= 1; ++p) gsum += (w[p + 1] * w[q + 1]) * (at(d, 1, p, q) - at(d, -1, p, q));
+    y[d] = -gsum;
+  }
+  const float l1y = fabsf(y[0]) + fabsf(y[1]) + fabsf(y[2]);
+  const float amax = fmaxf(fabsf(y[0]), fmaxf(fabsf(y[1]), fabsf(y[2])));
+  const float ymax = l1y > 0.f ? amax / l1y : 1.f;
+  bool near = bsep <= 2e-5f;                                    // own-axis sign
+  near |= fabsf(bdom - ymax) * l1y <= 5e-6f * l1y + 1e-4f;      // candidate or Youngs
+#pragma unroll
+  for (int d = 0; d < 3; ++d) near |= d != bd && bdom - dom[d] <= 8e-6f * bdom;  // dominance
+  if (near) {
+    myc_normal(sd, m);
+    return;
+  }
+  if (bdom <= ymax) {
+    m[0] = best[0]; m[1] = best[1]; m[2] = best[2];
+  } else {
+    m[0] = y[0] / l1y; m[1] = y[1] / l1y; m[2] = y[2] / l1y;
+  }
+}
+
+__device__ __forceinline__ float vol_low_f(float m1, float m2, float m3, float a) {
+  const float m12 = m1 + m2;
+  if (a < m1) return a * a * a / (6.f * m1 * m2 * m3);
+  const float v2 = a * (a - m1) / (2.f * m2 * m3) + m1 * m1 / (6.f * m2 * m3);
+  if (a < m2) return v2;
+  const float t2 = a - m2;
+  const float v3 = v2 - t2 * t2 * t2 / (6.f * m1 * m2 * m3);
+  const float top = m12 < m3 ? m12 : m3;
+  if (a < top) return v3;
+  if (m12 <= m3) return (2.f * a - m12) / (2.f * m3);
+  const float t3 = a - m3;
+  return v3 - t3 * t3 * t3 / (6.f * m1 * m2 * m3);
+}
+
+// donor-slab volume with the cut geometry in FP32.  The plane's offset from
+// the slab's lowest corner (alpha - m_axis x0 + shift) and its complement
+// l1 - offset are formed in FP64, so whichever of the two is small keeps its
+// relative accuracy when rounded to FP32, the slab is empty or full exactly
+// when the FP64 form finds it so, and a slab that is nearly full returns
+// 1 - (FP32 deficit) in FP64: cells next to a full or empty slab are not left
+// with FP32 round-off of size 1e-8, which would exceed the mixed threshold
+// and make them mixed cells that the FP64 form keeps pure.  The result is
+// held to what the slab can hold of the donor's liquid c and gas 1 - c,
+// [c - (1 - delta), c] (exact bounds that FP32 round-off would otherwise
+// cross): a donor emptied of either phase is emptied exactly, as in FP64,
+// and not left a few 1e-9 beyond it for the update to clip (clipping c
+// without e moves T by C_pl / C_pg times the clipped volume).
+__device__ __forceinline__ double slab_volume_f(const double m[3], double alpha, int axis, double x0, double delta,
+                                                double c) {
+  if (!dgt0(delta)) return 0.0;
+  float mm0 = (float)m[0], mm1 = (float)m[1], mm2 = (float)m[2];
+  const double ma = m[axis];
+  const float md = (float)(ma * delta);
+  if (axis == 0) mm0 = md;
+  else if (axis == 1) mm1 = md;
+  else mm2 = md;
+  float sh = 0.f;
+  if (mm0 < 0.f) sh -= mm0;
+  if (mm1 < 0.f) sh -= mm1;
+  if (mm2 < 0.f) sh -= mm2;
+  float a0 = fabsf(mm0), a1 = fabsf(mm1), a2 = fabsf(mm2);
+  const float l1 = (a0 + a1) + a2;
+  const double num = fma(-ma, x0, alpha) + (double)sh;  // offset, cell units
+  const double numc = (double)l1 - num;                // complement
+  if (!dgt0(num)) return 0.0;
+  if (!dgt0(numc)) return delta;
+  const float r = 1.f / l1;
+  a0 *= r; a1 *= r; a2 *= r;
+  float t;
+  if (a1 < a0) { t = a0; a0 = a1; a1 = t; }
+  if (a2 < a1) { t = a1; a1 = a2; a2 = t; }
+  if (a1 < a0) { t = a0; a0 = a1; a1 = t; }
+  const float alo = (float)num * r, ahi = (float)numc * r;
+  double v = alo <= ahi ? delta * (double)vol_low_f(a0, a1, a2, alo)
+                        : delta * (1.0 - (double)vol_low_f(a0, a1, a2, ahi));
+  if (nn_lt(c, v)) v = c;  // both >= 0
+  const double lo = c - (1.0 - delta);
+  if (dgt0(lo) && nn_lt(v, lo)) v = lo;
+  return v;
+}
+
+// WENO5 with the neighbour differences in FP64 and the nonlinear weights and
+// the correction to v0 in FP32: T_f = v0 + correction
+__device__ __forceinline__ double weno5_f(double vm2, double vm1, double v0, double vp1, double vp2) {
+  if (deq(vm2, v0) && deq(vm1, v0) && deq(vp1, v0) && deq(vp2, v0)) return v0;
+  const float D0 = (float)(vm1 - vm2), D1 = (float)(v0 - vm1), D2 = (float)(vp1 - v0), D3 = (float)(vp2 - vp1);
+  const float epsw = 1e-6f;
+  const float d0 = D1 - D0, d1 = D2 - D1, d2 = D3 - D2;
+  const float e0 = 3.f * D1 - D0, e1 = D1 + D2, e2 = D3 - 3.f * D2;
+  const float b0 = (13.f / 12.f) * d0 * d0 + 0.25f * e0 * e0;
+  const float b1 = (13.f / 12.f) * d1 * d1 + 0.25f * e1 * e1;
+  const float b2 = (13.f / 12.f) * d2 * d2 + 0.25f * e2 * e2;
+  // alpha_k = d_k / (eps + beta_k)^2 (bounded by d_k / eps^2: no float
+  // overflow for any stencil), omega = alpha / sum alpha
+  const float i0 = 1.f / (epsw + b0), i1 = 1.f / (epsw + b1), i2 = 1.f / (epsw + b2);
+  const float w0 = 0.1f * i0 * i0, w1 = 0.6f * i1 * i1, w2 = 0.3f * i2 * i2;
+  const float r0 = 5.f * D1 - 2.f * D0, r1 = 2.f * D2 + D1, r2 = 4.f * D2 - D3;
+  const float corr = (w0 * r0 + w1 * r1 + w2 * r2) / (6.f * (w0 + w1 + w2));
+  return v0 + (double)corr;
 }
 
 }  // namespace vofgb

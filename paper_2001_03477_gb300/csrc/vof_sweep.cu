@@ -68,8 +68,8 @@ __device__ __forceinline__ size_t cell_at(const GridDev& g, int x, int y, int z)
 // energy flux G = T_f (C_pl F + C_pg (a - F)) with T_f = WENO5 of the
 // upwind-ordered stencil
 __device__ __forceinline__ double face_energy_flux(double Cp_l, double Cp_g, double Fv, double a, double t0, double t1,
-                                                double t2, double t3, double t4) {
-  const double Tf = weno5(t0, t1, t2, t3, t4);
+                                                double t2, double t3, double t4, bool f32) {
+  const double Tf = f32 ? weno5_f(t0, t1, t2, t3, t4) : weno5(t0, t1, t2, t3, t4);
   return (Tf * Cp_l) * Fv + (Tf * Cp_g) * (a - Fv);
 }
 
@@ -424,6 +424,9 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
 // the only T values kernel F reads back -- and for every listed cell, which
 // kernel U reads.
 // ---------------------------------------------------------------------------
+// F32: the precision form's FP32 MYC normal (its own instance, so that the
+// FP64 form keeps its register budget)
+template <bool F32>
 __global__ void __launch_bounds__(kPlaneThreads)
 k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -455,7 +458,8 @@ k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_
       }
     }
     double m[3];
-    myc_normal(s, m);
+    if (F32) myc_normal_f(s, m);
+    else myc_normal(s, m);
     const double al = plane_alpha(m[0], m[1], m[2], s[13]);
     double4 pl;
     pl.x = m[0]; pl.y = m[1]; pl.z = m[2]; pl.w = al;
@@ -526,7 +530,8 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
         const double mv[3] = {pl.x, pl.y, pl.z};
         const double da = fabs(a);
         if (da > 1.0 && status) atomicOr(status, DEV_CFL);
-        const double vol = slab_volume_nn(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
+        const double vol = g.f32 ? slab_volume_f(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da, cd)
+                                 : slab_volume_nn(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
         Fv = pos ? vol : -vol;
       } else {
         Fv = cd * a;
@@ -538,7 +543,7 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
         const double t2 = pos ? Tw[3] : Tw[4];
         const double t3 = pos ? Tw[4] : Tw[3];
         const double t4 = pos ? Tw[5] : Tw[2];
-        Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, t0, t1, t2, t3, t4);
+        Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, t0, t1, t2, t3, t4, g.f32 != 0);
       }
     }
     sc.F[fid] = Fv;
@@ -672,7 +677,7 @@ k_energy(GridDev g, const double* __restrict__ c_before, const double* __restric
           int px = tx + (AX == 0 ? rr : 0), py = ty + (AX == 1 ? rr : 0), pz = tz + (AX == 2 ? rr : 0);
           v[r + 2] = sT[(pz * TY + py) * TX + px];
         }
-        double Tf = weno5(v[0], v[1], v[2], v[3], v[4]);
+        double Tf = g.f32 ? weno5_f(v[0], v[1], v[2], v[3], v[4]) : weno5(v[0], v[1], v[2], v[3], v[4]);
         Gv = (Tf * g.Cp_l) * Fv + (Tf * g.Cp_g) * (a - Fv);
       }
     }
@@ -806,7 +811,8 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
                                                                           flux_out != nullptr, p.cap, c_out != c_in);
   prof_mark(AX == 0 ? "sweep_x.stream" : (AX == 1 ? "sweep_y.stream" : "sweep_z.stream"), st);
-  k_prep<<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc);
+  if (g.f32) k_prep<true><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc);
+  else k_prep<false><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc);
   prof_mark(AX == 0 ? "sweep_x.prep" : (AX == 1 ? "sweep_y.prep" : "sweep_z.prep"), st);
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);

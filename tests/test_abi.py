@@ -62,10 +62,15 @@ def test_host_validation_without_gpu(lib):
         assert lib.vof_advect_sweep_z(ctypes.byref(cg), fake, nul, ok_out, nul, ctypes.c_void_p(1 << 41), 0.1, nul,
                                       nul, nul, nul, w_, nb, nul) == P.VOF_EINVAL
     # bad grid
+    big_step = lib.vof_step_workspace_bytes(ctypes.byref(cg))
     bad = P.Grid(0, 8, 8).c_struct()
     assert lib.vof_step_workspace_bytes(ctypes.byref(bad)) == 0
     bad2 = P.Grid(8, 8, 8, (0, 2, 0)).c_struct()
     assert lib.vof_reconstruct(ctypes.byref(bad2), fake, fake, fake, fake, nul) == P.VOF_EINVAL
+    bad3 = P.Grid(8, 8, 8, precision=2).c_struct()  # neither VOF_F64 nor VOF_F32_FLUX
+    assert lib.vof_step_workspace_bytes(ctypes.byref(bad3)) == 0
+    assert lib.vof_reconstruct(ctypes.byref(bad3), fake, fake, fake, fake, nul) == P.VOF_EINVAL
+    assert lib.vof_step_workspace_bytes(ctypes.byref(P.Grid(8, 8, 8, precision=P.VOF_F32_FLUX).c_struct())) == big_step
     # negative dt, misaligned workspace
     assert lib.vof_step(ctypes.byref(cg), fake, ctypes.c_void_p(2 << 40), fake, fake, fake, -1.0, 0, nul, 0.0, nul,
                         ctypes.c_void_p(3 << 40), 1 << 30, nul) == P.VOF_EINVAL
