@@ -60,18 +60,25 @@ def ellipsoid_fractions(shape, h, centre, axes, rot=None, inside=1.0, nsub=32, c
     zc = (np.arange(nz) + 0.5) * hz
     yc = (np.arange(ny) + 0.5) * hy
     xc = (np.arange(nx) + 0.5) * hx
-    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
-    # classify by distance of the cell centre (conservative bounds)
+    # classify by distance of the cell centre (conservative bounds), one
+    # z-plane at a time (large grids would not fit the temporaries)
     half_diag = 0.5 * math.sqrt(hx * hx + hy * hy + hz * hz)
-    d = np.stack([X - c[0], Y - c[1], Z - c[2]], axis=-1)
-    qv = np.einsum("...i,ij,...j->...", d, Q, d)
-    dist = np.sqrt(np.einsum("...i,...i->...", d, d))
-    frac = np.where(qv <= 1.0, 1.0, 0.0)
-    # cells that can intersect the surface: inside the outer shell, outside
-    # the inner one
-    cand = (dist <= rmax + half_diag) & ~(dist < rmin - half_diag)
+    Y, X = np.meshgrid(yc, xc, indexing="ij")
+    frac = np.empty((nz, ny, nx))
+    idx = []
+    for k in range(nz):
+        d = np.stack([X - c[0], Y - c[1], np.full_like(X, zc[k] - c[2])], axis=-1)
+        qv = np.einsum("...i,ij,...j->...", d, Q, d)
+        dist = np.sqrt(np.einsum("...i,...i->...", d, d))
+        frac[k] = qv <= 1.0
+        # cells that can intersect the surface: inside the outer shell,
+        # outside the inner one
+        cand = (dist <= rmax + half_diag) & ~(dist < rmin - half_diag)
+        jj, ii = np.nonzero(cand)
+        if len(jj):
+            idx.append(np.stack([np.full_like(jj, k), jj, ii], axis=1))
     # exact classification of candidates by sub-integration
-    idx = np.argwhere(cand)
+    idx = np.concatenate(idx) if idx else np.zeros((0, 3), dtype=np.int64)
     t = (np.arange(nsub) + 0.5) / nsub
     qxx, qxy, qxz, qyy, qyz, qzz = Q[0, 0], Q[0, 1], Q[0, 2], Q[1, 1], Q[1, 2], Q[2, 2]
 
@@ -96,10 +103,9 @@ def ellipsoid_fractions(shape, h, centre, axes, rot=None, inside=1.0, nsub=32, c
         ys = (j[:, None, None] + t[None, :, None]) * hy - c[1]
         zs = (k[:, None, None] + t[None, None, :]) * hz - c[2]
         ys, zs = np.broadcast_arrays(ys, zs)
-        frac[k, j, i] = _chord_fraction(lo_x, hi_x, ys, zs, chord)
-    frac = np.clip(frac, 0.0, 1.0)
+        frac[k, j, i] = np.clip(_chord_fraction(lo_x, hi_x, ys, zs, chord), 0.0, 1.0)
     if inside == 0.0:
-        frac = 1.0 - frac
+        np.subtract(1.0, frac, out=frac)
     return frac
 
 
@@ -265,4 +271,54 @@ def bubble_growth(n=256, nsteps=500, R0=0.1, delta=0.02, Ja=0.5, cells_per_step=
     u, v, w = radial_faces(shape, h, centre, A, 0.5 * R0)
     dd = -(RHO_G / RHO_L) * Rdot * dt / h
     return Workload("bubble-growth-%d^3" % n, shape, (1, 1, 1), h, Cp_l, Cp_g, T_SAT_WATER, dt, nsteps, dd,
+                    c, e, u, v, w)
+
+
+def fourier_field(shape, h, nmodes=8, amp=0.1, kmax=3, seed=0):
+    """1 + sum of `nmodes` seeded modes amp_m sin(2 pi k_m . x + phi_m) with
+    integer wave vectors |k_i| <= kmax (smooth, periodic on the unit box),
+    evaluated as one matrix product of separable complex exponentials."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    ks = rng.integers(-kmax, kmax + 1, size=(nmodes, 3))
+    ks[np.all(ks == 0, axis=1), 0] = 1
+    amps = amp * rng.uniform(0.5, 1.0, nmodes) / nmodes
+    phis = rng.uniform(0.0, 2 * np.pi, nmodes)
+    xs = (np.arange(nx) + 0.5) * h
+    ys = (np.arange(ny) + 0.5) * h
+    zs = (np.arange(nz) + 0.5) * h
+    exs = [np.exp(2j * np.pi * k[0] * xs) for k in ks]
+    # T[z] = 1 + sum_m sin(t_m(z)) Re(E_m) + cos(t_m(z)) Im(E_m) with
+    # E_m = a_m exp(2 pi i (k_y y + k_x x)), t_m(z) = 2 pi k_z z + phi_m:
+    # one (nz x 2M) by (2M x ny nx) product
+    B = np.empty((2 * nmodes, ny * nx))
+    A = np.empty((nz, 2 * nmodes))
+    for m, k in enumerate(ks):
+        E = amps[m] * np.outer(np.exp(2j * np.pi * k[1] * ys), exs[m])
+        B[2 * m] = E.real.ravel()
+        B[2 * m + 1] = E.imag.ravel()
+        t = 2 * np.pi * k[2] * zs + phis[m]
+        A[:, 2 * m] = np.sin(t)
+        A[:, 2 * m + 1] = np.cos(t)
+    T = (A @ B).reshape(shape)
+    T += 1.0
+    return T
+
+
+def deformation_sphere(n=512, nsteps=50, cfl=0.5, nsub=8, seed=3):
+    """Sphere R = 0.15 at (0.35, 0.35, 0.35) in the LeVeque deformation field
+    (period 3, the field at t = 0, exact face averages), zero-gradient faces,
+    dt for face CFL `cfl` (max |u| = 2), water/steam heat capacities of Table
+    atm_water, a seeded smooth T of 8 Fourier modes (T = 1 +- 0.1), no
+    phase change."""
+    h = 1.0 / n
+    shape = (n, n, n)
+    c = sphere_fractions(shape, h, (0.35, 0.35, 0.35), 0.15, nsub=nsub)
+    Cp_l = RHO_L * CP_L_SPEC
+    Cp_g = RHO_G * CP_G_SPEC
+    T = fourier_field(shape, h, seed=seed)
+    e = (Cp_l * c + Cp_g * (1.0 - c)) * T
+    u, v, w = deformation_faces(shape, h, 0.0)
+    dt = cfl * h / 2.0
+    return Workload("deformation-sphere-%d^3" % n, shape, (1, 1, 1), h, Cp_l, Cp_g, 1.0, dt, nsteps, 0.0,
                     c, e, u, v, w)
