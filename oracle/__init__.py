@@ -11,6 +11,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   orc_volume, orc_alpha, orc_slab_volume, orc_plane_area  -- pinned
   orc_youngs, orc_cc_candidate, orc_myc                     -- pinned (planes)
   orc_weno5                                                 -- pinned
+  orc_mass_transfer                                         -- pinned (plane
+      distances exact, Sec. 4.1; linear and curved temperature fields with
+      closed-form gradients and weights; droplet distance convergence)
   orc_sweep, orc_energy_consistent, orc_phase_shift, orc_step -- pinned by
       invariants (conservation, uniform-T preservation, translation return,
       plane translation, exact motion of a shifted plane, kinematic Stefan
@@ -84,6 +87,8 @@ def lib():
             L.orc_energy_consistent.argtypes = [_I, _I, _D, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double, _D]
             L.orc_phase_shift.restype = None
             L.orc_phase_shift.argtypes = [_I, _I, _D, _D, _D, _D, ctypes.c_double, _D]
+            L.orc_mass_transfer.restype = None
+            L.orc_mass_transfer.argtypes = [_I, _I, _D, _D, _D, _D, _D, _D, _D]
             L.orc_sum.restype = ctypes.c_double
             L.orc_sum.argtypes = [_D, ctypes.c_long]
             L.orc_step.restype = None
@@ -222,6 +227,18 @@ def phase_shift(g: Grid, c, e, dd=None, dd_uniform=0.0):
     diag = np.zeros(3)
     lib().orc_phase_shift(*g._args(), _dp(c), _dp(e), _dp(ddp), float(dd_uniform), _dp(diag))
     return c, e, diag
+
+
+def mass_transfer(g: Grid, c, e, k_l, k_g, h_fg):
+    """Mass transfer rate from PLIC interface distances (Sec. 3.2).
+    Returns (mdot, d_gamma, grad_n): mdot at mixed cells (0 elsewhere);
+    |d_Gamma| h of every pure cell with a mixed neighbour (-1 elsewhere);
+    that cell's normal temperature gradient (0 elsewhere)."""
+    c = _c64(c); e = _c64(e)
+    mdot = np.zeros(c.shape); dg = np.zeros(c.shape); gn = np.zeros(c.shape)
+    mpar = np.array([k_l, k_g, h_fg], dtype=np.float64)
+    lib().orc_mass_transfer(*g._args(), _dp(c), _dp(e), _dp(mpar), _dp(mdot), _dp(dg), _dp(gn))
+    return mdot, dg, gn
 
 
 def total(x):
