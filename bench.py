@@ -251,6 +251,9 @@ def run_gpu(args):
     fp64_achieved = FACE_FLOP * faces_per_step / (faces_ms * 1e-3) / 1e12 if faces_ms > 0 else 0.0
     traffic = faces_traffic_from_profile()
 
+    # ---- the mass transfer rate (Sec. 3.2) on the same workload -------------
+    mt = mass_transfer_measure(P, g, wl, c0, e0, stream, barrier)
+
     # ---- end to end through the public API with host buffers ---------------
     # each step the face velocities of the liquid (produced by the flow
     # solver on the host) are copied in from pinned memory, the step runs,
@@ -313,11 +316,60 @@ def run_gpu(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "precision_form": pform,
+            "mass_transfer": mt,
             "final_sums": [float(x) for x in sums],
         }
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# conductivities of water and steam at 1 atm (W/m/K) and the latent heat of
+# the bubble workload: the scale of mdot only
+K_L_WATER, K_G_STEAM = 0.68, 0.025
+
+
+def mass_transfer_measure(P, g, wl, c, e, stream, barrier, reps=20):
+    """vof_mass_transfer on the initial state of the step's workload: the
+    mean time of one call over `reps` calls (CUDA events on the launching
+    stream), its kernels' shares, and its work counts.  Writes mdot and the
+    Step-2 shift dd = -mdot dt / (rho_l h)."""
+    import torch
+    from paper_2001_03477_gb300 import workloads as W
+    ws = torch.empty(P.vof_mass_transfer_workspace_bytes(g), dtype=torch.uint8, device=c.device)
+    mdot = torch.empty_like(c)
+    dd = torch.empty_like(c)
+    dd_per_mdot = -wl.dt / (W.RHO_L * wl.h)
+    for _ in range(3):
+        P.vof_mass_transfer(g, c, e, K_L_WATER, K_G_STEAM, W.H_FG_WATER, mdot, None, None, dd_per_mdot, dd,
+                            workspace=ws, stream=stream)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        P.vof_mass_transfer(g, c, e, K_L_WATER, K_G_STEAM, W.H_FG_WATER, mdot, None, None, dd_per_mdot, dd,
+                            workspace=ws, stream=stream)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / reps
+    P.vof_profile_begin(stream)
+    for _ in range(reps):
+        P.vof_mass_transfer(g, c, e, K_L_WATER, K_G_STEAM, W.H_FG_WATER, mdot, None, None, dd_per_mdot, dd,
+                            workspace=ws, stream=stream)
+    launches = P.vof_profile_end()
+    kms = {}
+    for name, t in launches:
+        kms[name] = kms.get(name, 0.0) + t / reps
+    counts = P.vof_mass_transfer_work_counts(g, ws, stream)
+    mixed = (c > g.eps_mixed) & (c < 1 - g.eps_mixed)
+    md = mdot[mixed]
+    cells = c.numel()
+    return {"workload": "the step's workload, initial state (water k_l = 0.68, steam k_g = 0.025 W/m/K)",
+            "value": round(cells / (ms * 1e-3) / 1e9, 4), "unit": UNIT, "ms_per_call": round(ms, 5),
+            "work_counts": counts, "kernel_ms": {k: round(v_, 5) for k, v_ in kms.items()},
+            "launches_per_call": len(launches) // reps,
+            "mdot_range": [float(md.min()), float(md.max())] if md.numel() else None,
+            "dd_range": [float(dd[mixed].min()), float(dd[mixed].max())] if md.numel() else None}
 
 
 def precision_form(dev, steps=20, n=512):

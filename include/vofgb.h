@@ -200,6 +200,53 @@ VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const doubl
                     void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Mass transfer rate from PLIC interface distances (Sec. 3.2, "Calculating
+ * the mass transfer rate": Eqs. mdot_calc, grad_n_T, plane_m, cell_d,
+ * dint_trans, the collinearity xi, normTgrad and the weights chi, gamma).
+ * For each mixed cell (eps < c < 1 - eps): the MYC normal and plane constant
+ * as in vof_reconstruct, in Hessian form n = m/|m|, d = alpha/|m| (n points
+ * from liquid into gas).  Each pure cell within two cells of a mixed cell
+ * (Chebyshev distance 1 or 2) takes the plane of its mixed neighbour of
+ * largest collinearity xi = |n . dx| (dx from that neighbour's low corner
+ * to the cell's centre; on ties the first in the order z, y, x of the
+ * offsets, each increasing), the normal distance |d_Gamma| = |d - n . dx| h
+ * and the temperature gradient along n, (T_Gamma - T)/|d_Gamma| in the
+ * liquid (c > 1/2), (T - T_Gamma)/|d_Gamma| in the gas, with T = e / C_p(c)
+ * and T_Gamma = g->T_sat; a cell on the plane (d_Gamma = 0) has none.  Each
+ * mixed cell averages its pure neighbours' gradients per phase with weights
+ * gamma = |n . dx| / |dx|^2 (dx the offset of the centres; a phase without
+ * one contributes 0) and
+ *     mdot = (k_g grad_g - k_l grad_l) / h_fg    (> 0: liquid turns to gas).
+ * Offsets leaving the grid on a zero-gradient axis are not cells; periodic
+ * axes wrap.
+ *   c, e         device double[N] (cell layout), read only
+ *   k_l, k_g     thermal conductivities (>= 0), h_fg latent heat (> 0)
+ *   mdot         device double[N]: mdot at mixed cells, 0 elsewhere
+ *   d_gamma      device double[N] or NULL: |d_Gamma| of each pure cell
+ *                within two cells of a mixed cell, -1 elsewhere
+ *   grad_n       device double[N] or NULL: that cell's gradient, 0 elsewhere
+ *                (and where it has none)
+ *   dd           device double[N] or NULL: dd_per_mdot * mdot at mixed cells,
+ *                0 elsewhere -- with dd_per_mdot = -dt / (rho_l h), the shift
+ *                Delta d of Step 2 (Eq. Delta d) for vof_phase_change_shift
+ *   workspace    device buffer of vof_mass_transfer_workspace_bytes(g) bytes,
+ *                256-byte aligned, caller-owned, not shared with concurrent
+ *                calls
+ * Outputs must not overlap each other, the inputs or the workspace.
+ * VOF_EINVAL for a bad grid, null or overlapping arrays, a small or
+ * misaligned workspace, h_fg <= 0 or a negative conductivity.
+ */
+VOF_API size_t vof_mass_transfer_workspace_bytes(const vof_grid* g);
+VOF_API vof_status vof_mass_transfer(const vof_grid* g, const double* c, const double* e, double k_l, double k_g,
+                                     double h_fg, double* mdot, double* d_gamma, double* grad_n, double dd_per_mdot,
+                                     double* dd, void* workspace, size_t workspace_bytes, void* stream);
+/* {mixed cells, pure cells with a mixed neighbour} of the last
+ * vof_mass_transfer() run with this workspace (instrumentation), copied to
+ * host memory after the work queued on `stream` completes. */
+VOF_API vof_status vof_mass_transfer_work_counts(const vof_grid* g, const void* workspace, int* counts,
+                                                 void* stream);
+
+/*
  * A time step that allocates nothing (the paper has no counterpart; this is
  * for callers that cannot allocate device memory when they step -- code in a
  * host callback or an error path where the allocator must not be entered,

@@ -99,6 +99,7 @@ def lib():
             "energy_advect_consistent": [G, I, P, P, P, P, P, P, D, P, P, P],
             "vof_phase_change_shift": [G, P, P, P, P, P, D, P, P, P, S, P],
             "vof_step": [G, P, P, P, P, P, D, L_, P, D, P, P, S, P],
+            "vof_mass_transfer": [G, P, P, D, D, D, P, P, P, D, P, P, S, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -116,6 +117,10 @@ def lib():
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
         L.vof_step_work_counts.restype = ctypes.c_int
+        L.vof_mass_transfer_workspace_bytes.argtypes = [G]
+        L.vof_mass_transfer_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_mass_transfer_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
+        L.vof_mass_transfer_work_counts.restype = ctypes.c_int
         L.vof_profile_begin.argtypes = [P]
         L.vof_profile_begin.restype = ctypes.c_int
         L.vof_profile_end.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
@@ -294,6 +299,38 @@ def vof_step_noalloc(g, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, 
 
 
 VOF_NOALLOC_MAX_CELLS = 262144
+
+
+def vof_mass_transfer_workspace_bytes(g: Grid) -> int:
+    cg = g.c_struct()
+    return int(lib().vof_mass_transfer_workspace_bytes(ctypes.byref(cg)))
+
+
+def vof_mass_transfer(g, c, e, k_l, k_g, h_fg, mdot, d_gamma=None, grad_n=None, dd_per_mdot=0.0, dd=None,
+                      workspace=None, stream=None):
+    """Mass transfer rate from PLIC interface distances (Sec. 3.2) into
+    `mdot` (and the optional per-cell distances, gradients and shift)."""
+    cg = g.c_struct()
+    if workspace is None:
+        workspace = _cached_workspace(vof_mass_transfer_workspace_bytes(g), c.device)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("vof_mass_transfer",
+           lib().vof_mass_transfer(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(e, _f64(), "e"), float(k_l),
+                                   float(k_g), float(h_fg), _ptr(mdot, _f64(), "mdot"),
+                                   _ptr(d_gamma, _f64(), "d_gamma"), _ptr(grad_n, _f64(), "grad_n"),
+                                   float(dd_per_mdot), _ptr(dd, _f64(), "dd"), _ptr(workspace, None, "workspace"),
+                                   ctypes.c_size_t(nbytes), _stream(stream)))
+
+
+def vof_mass_transfer_work_counts(g, workspace, stream=None):
+    """{mixed, band} cell counts of the last vof_mass_transfer run with
+    `workspace`."""
+    cg = g.c_struct()
+    out = (ctypes.c_int * 2)()
+    _check("vof_mass_transfer_work_counts",
+           lib().vof_mass_transfer_work_counts(ctypes.byref(cg), _ptr(workspace, None, "workspace"), out,
+                                               _stream(stream)))
+    return {"mixed": out[0], "band": out[1]}
 
 
 def vof_get_device_status() -> int:

@@ -305,6 +305,42 @@ vof_status vof_step_work_counts(const vof_grid* g, const void* workspace, int* c
   return cuda_status(err);
 }
 
+size_t vof_mass_transfer_workspace_bytes(const vof_grid* g) {
+  if (!grid_ok(g)) return 0;
+  return mdot_scratch_bytes(cells(g));
+}
+
+vof_status vof_mass_transfer(const vof_grid* g, const double* c, const double* e, double k_l, double k_g,
+                             double h_fg, double* mdot, double* d_gamma, double* grad_n, double dd_per_mdot,
+                             double* dd, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!grid_ok(g) || !c || !e || !mdot || !workspace) return VOF_EINVAL;
+  if (!(h_fg > 0.0) || !(k_l >= 0.0) || !(k_g >= 0.0) || !(dd_per_mdot == dd_per_mdot)) return VOF_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
+  const size_t N = cells(g), B = N * 8;
+  const size_t need = mdot_scratch_bytes(N);
+  if (workspace_bytes < need) return VOF_EINVAL;
+  const void* outs[4] = {mdot, d_gamma, grad_n, dd};
+  for (int a = 0; a < 4; ++a) {
+    if (!outs[a]) continue;
+    if (overlap(outs[a], B, c, B) || overlap(outs[a], B, e, B) || overlap(outs[a], B, workspace, need))
+      return VOF_EINVAL;
+    for (int b = a + 1; b < 4; ++b)
+      if (overlap(outs[a], B, outs[b], B)) return VOF_EINVAL;
+  }
+  if (overlap(workspace, need, c, B) || overlap(workspace, need, e, B)) return VOF_EINVAL;
+  return cuda_status(launch_mass_transfer(to_dev(g, 0.0), g->h, c, e, k_l, k_g, h_fg, dd_per_mdot, mdot, d_gamma,
+                                          grad_n, dd, workspace, (cudaStream_t)stream));
+}
+
+vof_status vof_mass_transfer_work_counts(const vof_grid* g, const void* workspace, int* counts, void* stream) {
+  if (!grid_ok(g) || !workspace || !counts) return VOF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t err = cudaMemcpyAsync(counts, mdot_counters(to_dev(g, 0.0), const_cast<void*>(workspace)),
+                                    2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  return cuda_status(err);
+}
+
 vof_status vof_get_device_status(void) {
   int* p = device_status_ptr();
   if (!p) return VOF_ECUDA;

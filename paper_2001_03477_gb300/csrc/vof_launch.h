@@ -172,4 +172,12 @@ void prof_mark(const char* name, cudaStream_t st);
 enum : int { DEV_CFL = 1 };
 int* device_status_ptr();
 
+// Mass transfer rate (vof_mdot.cu): workspace size, the launch of its four
+// kernels, and its counters ([0] mixed cells, [1] band cells) in a workspace.
+size_t mdot_scratch_bytes(size_t N);
+cudaError_t launch_mass_transfer(const GridDev& g, double h, const double* c, const double* e, double k_l, double k_g,
+                                 double h_fg, double dd_per_mdot, double* mdot, double* d_gamma, double* grad_n,
+                                 double* dd, void* workspace, cudaStream_t st);
+int* mdot_counters(const GridDev& g, void* workspace);
+
 }  // namespace vofgb

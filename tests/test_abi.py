@@ -88,6 +88,36 @@ def test_host_validation_without_gpu(lib):
     assert lib.vof_status_string(P.VOF_ECFL).decode() == "face CFL number above 1"
 
 
+def test_mass_transfer_validation_without_gpu(lib):
+    import paper_2001_03477_gb300 as P
+    g = P.Grid(8, 8, 8, (0, 0, 0), 1.0, 2.0, 1.0, 0.0)
+    cg = g.c_struct()
+    nul = ctypes.c_void_p(0)
+    c, e, md = ctypes.c_void_p(1 << 40), ctypes.c_void_p(2 << 40), ctypes.c_void_p(3 << 40)
+    ws = ctypes.c_void_p(5 << 40)
+    nb = lib.vof_mass_transfer_workspace_bytes(ctypes.byref(cg))
+    assert nb > 512 * 40
+
+    def call(c_=c, e_=e, md_=md, dgam=nul, gn=nul, dd=nul, ws_=ws, nb_=nb, hfg=1.0, kl=1.0):
+        return lib.vof_mass_transfer(ctypes.byref(cg), c_, e_, ctypes.c_double(kl), ctypes.c_double(0.1),
+                                     ctypes.c_double(hfg), md_, dgam, gn, ctypes.c_double(-0.5), dd, ws_,
+                                     ctypes.c_size_t(nb_), nul)
+    assert call(c_=nul) == P.VOF_EINVAL
+    assert call(md_=nul) == P.VOF_EINVAL
+    assert call(ws_=nul) == P.VOF_EINVAL
+    assert call(hfg=0.0) == P.VOF_EINVAL
+    assert call(kl=-1.0) == P.VOF_EINVAL
+    assert call(nb_=nb - 8) == P.VOF_EINVAL
+    assert call(ws_=ctypes.c_void_p((5 << 40) + 64)) == P.VOF_EINVAL
+    assert call(md_=ctypes.c_void_p((1 << 40) + 8)) == P.VOF_EINVAL          # mdot over c
+    assert call(dd=ctypes.c_void_p((3 << 40) + 16)) == P.VOF_EINVAL          # dd over mdot
+    assert call(gn=ctypes.c_void_p((5 << 40) + 256)) == P.VOF_EINVAL         # grad_n in the workspace
+    bad = P.Grid(0, 8, 8).c_struct()
+    assert lib.vof_mass_transfer_workspace_bytes(ctypes.byref(bad)) == 0
+    big = P.Grid(16, 16, 16).c_struct()
+    assert lib.vof_mass_transfer_workspace_bytes(ctypes.byref(big)) > 7 * nb
+
+
 def test_workspace_size_scales(lib):
     import paper_2001_03477_gb300 as P
     a = P.vof_step_workspace_bytes(P.Grid(32, 32, 32))
