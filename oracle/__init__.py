@@ -11,6 +11,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   orc_volume, orc_alpha, orc_slab_volume, orc_plane_area  -- pinned
   orc_youngs, orc_cc_candidate, orc_myc                     -- pinned (planes)
   orc_weno5                                                 -- pinned
+  orc_sweep_le, orc_step_scheme                             -- pinned (equal
+      to the Weymouth-Yue sweep for uniform velocity; a plane moved exactly
+      by a linear velocity; uniform T stays uniform; the volume identity)
   orc_mass_transfer                                         -- pinned (plane
       distances exact, Sec. 4.1; linear and curved temperature fields with
       closed-form gradients and weights; droplet distance convergence)
@@ -87,6 +90,11 @@ def lib():
             L.orc_energy_consistent.argtypes = [_I, _I, _D, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double, _D]
             L.orc_phase_shift.restype = None
             L.orc_phase_shift.argtypes = [_I, _I, _D, _D, _D, _D, ctypes.c_double, _D]
+            L.orc_sweep_le.restype = None
+            L.orc_sweep_le.argtypes = [_I, _I, _D, ctypes.c_int, _D, _D, _D, ctypes.c_double, _D, _D, _D]
+            L.orc_step_scheme.restype = None
+            L.orc_step_scheme.argtypes = [_I, _I, _D, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_long, _D,
+                                          ctypes.c_double, _D, ctypes.c_int]
             L.orc_mass_transfer.restype = None
             L.orc_mass_transfer.argtypes = [_I, _I, _D, _D, _D, _D, _D, _D, _D]
             L.orc_sum.restype = ctypes.c_double
@@ -213,6 +221,19 @@ def sweep(g: Grid, axis, c, e, uf, dt, cc, theta, want_flux=False):
     return c, e, float(diag[0])
 
 
+def sweep_le(g: Grid, axis, c, e, uf, dt, want_flux=False):
+    """Li's Lagrangian-explicit sweep (the paper's alternative Step 1).
+    Returns (c_new, e_new, clipped[, F, G])."""
+    c = _c64(c).copy(); e = _c64(e).copy(); uf = _c64(uf)
+    F = np.zeros(g.face_shape(axis)) if want_flux else None
+    G = np.zeros(g.face_shape(axis)) if want_flux else None
+    diag = np.zeros(1)
+    lib().orc_sweep_le(*g._args(), int(axis), _dp(c), _dp(e), _dp(uf), float(dt), _dp(F), _dp(G), _dp(diag))
+    if want_flux:
+        return c, e, float(diag[0]), F, G
+    return c, e, float(diag[0])
+
+
 def energy_consistent(g: Grid, axis, c_before, e, F, uf, dt, theta):
     c_before = _c64(c_before); e = _c64(e).copy(); F = _c64(F); uf = _c64(uf); theta = _c64(theta)
     lib().orc_energy_consistent(*g._args(), int(axis), _dp(c_before), _dp(e), _dp(F), _dp(uf), float(dt),
@@ -246,14 +267,15 @@ def total(x):
     return lib().orc_sum(_dp(x), x.size)
 
 
-def step(g: Grid, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0):
-    """One time step in place on copies; returns (c, e, sums[6])."""
+def step(g: Grid, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, scheme=0):
+    """One time step in place on copies; returns (c, e, sums[6]).
+    scheme 0: Weymouth-Yue sweeps; 1: Lagrangian-explicit sweeps."""
     c = _c64(c).copy(); e = _c64(e).copy()
     u = _c64(u); v = _c64(v); w = _c64(w)
     ddp = _c64(dd) if dd is not None else None
     sums = np.zeros(6)
-    lib().orc_step(*g._args(), _dp(c), _dp(e), _dp(u), _dp(v), _dp(w), float(dt), int(step_index), _dp(ddp),
-                   float(dd_uniform), _dp(sums))
+    lib().orc_step_scheme(*g._args(), _dp(c), _dp(e), _dp(u), _dp(v), _dp(w), float(dt), int(step_index),
+                          _dp(ddp), float(dd_uniform), _dp(sums), int(scheme))
     return c, e, sums
 
 

@@ -509,6 +509,124 @@ ORC_API void orc_sweep(const int dims[3], const int bc[3], const double par[5], 
     free(T); free(cn); free(en);
 }
 
+/* ------------------------------------------------------------------ */
+/* The alternative Step 1 the paper names (Sec. 3.3.1): Li's split      */
+/* scheme (CIAM, "Lagrangian explicit").  Within a sweep the velocity   */
+/* varies linearly across a cell between its face values, so a point    */
+/* at local coordinate x moves to x (1 + a_r - a_l) + a_l (cell units,   */
+/* a = u dt / h).  The part of the donor that crosses a face is the      */
+/* preimage of the region beyond it: width |a| / J next to that face,   */
+/* J = 1 + a_r - a_l the donor's stretch; the liquid in it, stretched by */
+/* J, is the face's liquid flux F.  The cell keeps the stretched rest of */
+/* its own content, which in flux form reads                            */
+/*   c <- c + (F_l - c a_l) - (F_r - c a_r)                             */
+/* (the dilatation term uses the cell's own c, not the step-start cc of  */
+/* the Weymouth-Yue scheme).  Readings: a pure donor (c <= eps or        */
+/* >= 1 - eps) fluxes c a, the same volume without rounding the stretch; */
+/* the piece width is capped at 1 (J <= |a|, outside the scheme's CFL    */
+/* range).  The energy is fluxed in tandem with the same F (Eq.          */
+/* disc_et_adv) and the dilatation term carries Theta = (T C_pl) c +     */
+/* (T C_pg)(1 - c) with T = e / C_p(c) of the cell before the sweep:    */
+/* a uniform T stays uniform, as in Sec. 3.4.1.                          */
+/* ------------------------------------------------------------------ */
+
+static double le_stretch(const int dims[3], const int bc[3], int axis, const double *uf, double lam,
+                         const int don[3]) {
+    int hi[3] = {don[0], don[1], don[2]};
+    hi[axis] += 1;
+    double al = uf[face_id(dims, bc, axis, don[0], don[1], don[2])] * lam;
+    double ar = uf[face_id(dims, bc, axis, hi[0], hi[1], hi[2])] * lam;
+    return 1.0 + (ar - al);  /* exactly 1 where the velocity is uniform */
+}
+
+static void face_flux_le(const int dims[3], const int bc[3], const double par[5], int axis, const double *c,
+                         const double *T, const double *uf, double lam, double a, const int pos[3], double *F,
+                         double *G) {
+    if (a == 0.0) { *F = 0.0; *G = 0.0; return; }
+    int don[3] = {pos[0], pos[1], pos[2]};
+    if (a > 0.0) don[axis] -= 1;
+    /* the donor's own faces, with its coordinates mapped into the grid */
+    int dm[3] = {map_index(don[0], dims[0], bc[0]), map_index(don[1], dims[1], bc[1]),
+                 map_index(don[2], dims[2], bc[2])};
+    long did = cell_id(dims, bc, don[0], don[1], don[2]);
+    double cd = c[did];
+    double Fv;
+    if (is_mixed(cd, par[4])) {
+        double s[27], m[3];
+        gather_stencil(dims, bc, c, don[0], don[1], don[2], s);
+        orc_myc(s, m);
+        double al = orc_alpha(m, cd);
+        double J = le_stretch(dims, bc, axis, uf, lam, dm);
+        double da = fabs(a);
+        double w = (J > da) ? da / J : 1.0;
+        double x0 = a > 0.0 ? 1.0 - w : 0.0;
+        double vol = J * orc_slab_volume(m, al, axis, x0, w);
+        Fv = a > 0.0 ? vol : -vol;
+    } else {
+        Fv = cd * a;
+    }
+    double v[5];
+    for (int r = -2; r <= 2; ++r) {
+        int q[3] = {don[0], don[1], don[2]};
+        q[axis] += (a > 0.0) ? r : -r;
+        v[r + 2] = T[cell_id(dims, bc, q[0], q[1], q[2])];
+    }
+    double Tf = orc_weno5(v, ORC_EPSW);
+    *F = Fv;
+    *G = (Tf * par[1]) * Fv + (Tf * par[2]) * (a - Fv);
+}
+
+ORC_API void orc_sweep_le(const int dims[3], const int bc[3], const double par[5], int axis, double *c, double *e,
+                          const double *uf, double dt, double *Fout, double *Gout, double *diag) {
+    long N = (long)dims[0] * dims[1] * dims[2];
+    double lam = dt / par[0];
+    double *T = (double *)malloc(sizeof(double) * N);
+    double *cn = (double *)malloc(sizeof(double) * N);
+    double *en = (double *)malloc(sizeof(double) * N);
+    for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c[id]);
+    double clip = 0.0;
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                long id = ((long)k * dims[1] + j) * dims[0] + i;
+                int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                hi[axis] += 1;
+                double al = uf[face_id(dims, bc, axis, lo[0], lo[1], lo[2])] * lam;
+                double ar = uf[face_id(dims, bc, axis, hi[0], hi[1], hi[2])] * lam;
+                double Fl, Gl, Fr, Gr;
+                face_flux_le(dims, bc, par, axis, c, T, uf, lam, al, lo, &Fl, &Gl);
+                face_flux_le(dims, bc, par, axis, c, T, uf, lam, ar, hi, &Fr, &Gr);
+                double cv = c[id];
+                double th = (T[id] * par[1]) * cv + (T[id] * par[2]) * (1.0 - cv);
+                double cnew = (cv + (Fl - cv * al)) - (Fr - cv * ar);
+                double enew = (e[id] + (Gl - th * al)) - (Gr - th * ar);
+                double cc2 = cnew;
+                if (cc2 < 0.0) cc2 = 0.0;
+                if (cc2 > 1.0) cc2 = 1.0;
+                clip += cnew - cc2;
+                cn[id] = cc2;
+                en[id] = enew;
+                if (Fout || Gout) {
+                    long fl = face_id(dims, bc, axis, lo[0], lo[1], lo[2]);
+                    if (Fout) Fout[fl] = Fl;
+                    if (Gout) Gout[fl] = Gl;
+                    if (hi[axis] == dims[axis]) {
+                        int nx = dims[0], ny = dims[1];
+                        long fh;
+                        if (axis == 0) fh = ((long)hi[2] * ny + hi[1]) * (nx + 1) + hi[0];
+                        else if (axis == 1) fh = ((long)hi[2] * (ny + 1) + hi[1]) * nx + hi[0];
+                        else fh = ((long)hi[2] * ny + hi[1]) * nx + hi[0];
+                        if (Fout) Fout[fh] = Fr;
+                        if (Gout) Gout[fh] = Gr;
+                    }
+                }
+            }
+    memcpy(c, cn, sizeof(double) * N);
+    memcpy(e, en, sizeof(double) * N);
+    if (diag) diag[0] += clip;
+    free(T); free(cn); free(en);
+}
+
 /* Energy sweep from given VOF face fluxes F (the unfused form of the same
    update): e is advanced with G = T_f (C_pl F + C_pg (a - F)), T from the
    pre-sweep (c_before, e). */
@@ -847,6 +965,34 @@ ORC_API void orc_step(const int dims[3], const int bc[3], const double par[5], d
         sums[5] = sh[2];
     }
     free(cc); free(theta);
+}
+
+/* The same step with the Lagrangian-explicit sweeps of orc_sweep_le
+   (scheme 1); scheme 0 is orc_step. */
+ORC_API void orc_step_scheme(const int dims[3], const int bc[3], const double par[5], double *c, double *e,
+                             const double *u, const double *v, const double *w, double dt, long step_index,
+                             const double *dd, double dd_uniform, double *sums, int scheme) {
+    if (scheme == 0) {
+        orc_step(dims, bc, par, c, e, u, v, w, dt, step_index, dd, dd_uniform, sums);
+        return;
+    }
+    long N = (long)dims[0] * dims[1] * dims[2];
+    const double *uf[3] = {u, v, w};
+    double clip = 0.0;
+    for (int s = 0; s < 3; ++s) {
+        int axis = (step_index % 2 == 0) ? s : 2 - s;
+        orc_sweep_le(dims, bc, par, axis, c, e, uf[axis], dt, NULL, NULL, &clip);
+    }
+    double sh[3] = {0, 0, 0};
+    orc_phase_shift(dims, bc, par, c, e, dd, dd_uniform, sh);
+    if (sums) {
+        sums[0] = orc_sum(c, N);
+        sums[1] = orc_sum(e, N);
+        sums[2] = clip;
+        sums[3] = sh[0];
+        sums[4] = sh[1];
+        sums[5] = sh[2];
+    }
 }
 
 ORC_API void orc_run(const int dims[3], const int bc[3], const double par[5], double *c, double *e,
