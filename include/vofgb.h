@@ -73,10 +73,24 @@ typedef struct {
                          agrees with VOF_F64 to ~4e-7 in c per cell; fluxes
                          telescope, so volume and energy are conserved to
                          FP64 round-off.  Any other value: VOF_EINVAL. */
+  int scheme;         /* Step 1 sweeps (Sec. 3.3.1 names both):
+                         VOF_SCHEME_WY (0): Weymouth-Yue, Eulerian donor slabs
+                         and the dilatation term cc (a_r - a_l) with cc =
+                         [c^n > 1/2] frozen at the step start (the default);
+                         VOF_SCHEME_LE (1): Li's Lagrangian-explicit scheme
+                         (CIAM): the velocity linear across a cell, the piece
+                         of the donor that crosses a face is the preimage of
+                         width |a| / J, J = 1 + (a_r - a_l) of the donor,
+                         its liquid stretched by J is F, and the dilatation
+                         term uses the cell's own c and Theta = (T C_pl) c +
+                         (T C_pg)(1 - c) (no frozen state).  Any other value:
+                         VOF_EINVAL. */
 } vof_grid;
 
 #define VOF_F64 0
 #define VOF_F32_FLUX 1
+#define VOF_SCHEME_WY 0
+#define VOF_SCHEME_LE 1
 
 /* Number of doubles vof_step() writes to `sums`. */
 #define VOF_NSUMS 6

@@ -38,7 +38,8 @@ class VofError(RuntimeError):
 class _CGrid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3),
                 ("h", ctypes.c_double), ("Cp_l", ctypes.c_double), ("Cp_g", ctypes.c_double),
-                ("T_sat", ctypes.c_double), ("eps_mixed", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("T_sat", ctypes.c_double), ("eps_mixed", ctypes.c_double), ("precision", ctypes.c_int),
+                ("scheme", ctypes.c_int)]
 
 
 @dataclass
@@ -54,6 +55,7 @@ class Grid:
     T_sat: float = 0.0
     eps_mixed: float = 1e-12
     precision: int = 0  # VOF_F64; VOF_F32_FLUX = 1: the precision form
+    scheme: int = 0     # VOF_SCHEME_WY; VOF_SCHEME_LE = 1: Lagrangian-explicit sweeps
     _c: _CGrid = field(default=None, repr=False, compare=False)
 
     def c_struct(self):
@@ -64,6 +66,7 @@ class Grid:
         g.h, g.Cp_l, g.Cp_g = float(self.h), float(self.Cp_l), float(self.Cp_g)
         g.T_sat, g.eps_mixed = float(self.T_sat), float(self.eps_mixed)
         g.precision = int(self.precision)
+        g.scheme = int(self.scheme)
         return g
 
     @property
@@ -339,6 +342,7 @@ def vof_get_device_status() -> int:
 
 VOF_NCOUNTS = 9
 VOF_F64, VOF_F32_FLUX = 0, 1  # vof_grid.precision
+VOF_SCHEME_WY, VOF_SCHEME_LE = 0, 1  # vof_grid.scheme
 
 
 def vof_step_work_counts(g, workspace, stream=None):

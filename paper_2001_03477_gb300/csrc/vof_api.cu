@@ -36,6 +36,7 @@ static bool grid_ok(const vof_grid* g) {
   if (!(g->h > 0.0) || !(g->Cp_l > 0.0) || !(g->Cp_g > 0.0)) return false;
   if (!(g->eps_mixed >= 0.0 && g->eps_mixed < 0.5)) return false;
   if (g->precision != VOF_F64 && g->precision != VOF_F32_FLUX) return false;
+  if (g->scheme != VOF_SCHEME_WY && g->scheme != VOF_SCHEME_LE) return false;
   return true;
 }
 
@@ -49,6 +50,7 @@ static GridDev to_dev(const vof_grid* g, double dt) {
   std::memcpy(&d.eps_bits, &g->eps_mixed, 8);
   std::memcpy(&d.one_m_eps, &ome, 8);
   d.f32 = g->precision == VOF_F32_FLUX ? 1 : 0;
+  d.le = g->scheme == VOF_SCHEME_LE ? 1 : 0;
   return d;
 }
 

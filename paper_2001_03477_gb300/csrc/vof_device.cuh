@@ -26,6 +26,7 @@ struct GridDev {
   long long eps_bits;     // bit pattern of eps
   long long one_m_eps;    // bit pattern of 1 - eps
   int f32;                // precision form: FP32 reconstruction and flux weights in the sweeps
+  int le;                 // Lagrangian-explicit sweeps (Li's scheme) instead of Weymouth-Yue
 };
 
 // ---------------------------------------------------------------------------

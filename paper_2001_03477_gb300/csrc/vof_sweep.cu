@@ -8,7 +8,12 @@
 //   e <- e + (G_l - Theta a_l) - (G_r - Theta a_r),
 //   G = (T_f C_pl) F + (T_f C_pg) (a - F),  T_f = WENO5 of T = e / C_p(c),
 // with cc = [c^n > 1/2] and Theta = C_p(cc) T^n frozen at the start of the
-// step (see the `state` convention in include/vofgb.h).
+// step (see the `state` convention in include/vofgb.h).  With Li's
+// Lagrangian-explicit scheme (vof_grid.scheme = VOF_SCHEME_LE, the other
+// Step 1 Sec. 3.3.1 names) cc and Theta are the cell's own c and
+// (T C_pl) c + (T C_pg)(1 - c) before the sweep, and a mixed donor fluxes
+// J times the liquid in the preimage of width |a| / J next to the face,
+// J = 1 + (a_r - a_l) its stretch.
 //
 // Four kernels per sweep:
 //   A (stream): walks the grid lines (skipping quiet tiles in an in-place
@@ -80,9 +85,12 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
                                               double* __restrict__ c_out, double* __restrict__ e_out,
                                               uint8_t* __restrict__ state, double* __restrict__ theta, double& dc,
                                               double& de) {
-  const bool dirty = stv & 1;
+  // Lagrangian-explicit sweeps: the dilatation terms use the cell's own
+  // c and Theta; no frozen state
+  const bool lag = g.le != 0;
+  const bool dirty = !lag && (stv & 1);
   const bool ccb = dirty ? ((stv >> 1) & 1) != 0 : dgthalf(c);
-  const double ccv = ccb ? 1.0 : 0.0;
+  const double ccv = lag ? c : (ccb ? 1.0 : 0.0);
   const double lf = Fl - ccv * al, rf = Fr - ccv * ar;
   const double cn = (c + lf) - rf;
   double cc2 = cn, clip = 0.0;
@@ -93,12 +101,13 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
   de = 0.0;
   if (ENERGY) {
     // C_p(cc) with cc in {0, 1} is C_pl or C_pg exactly
-    const double th = dirty ? theta[id] : (ccb ? g.Cp_l : g.Cp_g) * T;
+    const double th = lag ? (T * g.Cp_l) * c + (T * g.Cp_g) * (1.0 - c)
+                         : (dirty ? theta[id] : (ccb ? g.Cp_l : g.Cp_g) * T);
     const double le = Gl - th * al, re = Gr - th * ar;
     const double en = (e + le) - re;
     e_out[id] = en;
     de = en - e;
-    if (state && !dirty && (!deq(cc2, c) || !deq(en, e))) {
+    if (!lag && state && !dirty && (!deq(cc2, c) || !deq(en, e))) {
       state[id] = (uint8_t)(1 | (ccb ? 2 : 0));
       theta[id] = th;
     }
@@ -530,8 +539,26 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
         const double mv[3] = {pl.x, pl.y, pl.z};
         const double da = fabs(a);
         if (da > 1.0 && status) atomicOr(status, DEV_CFL);
-        const double vol = g.f32 ? slab_volume_f(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da, cd)
-                                 : slab_volume_nn(mv, pl.w, AX, pos ? 1.0 - da : 0.0, da);
+        // Weymouth-Yue: the donor slab of width |a|; Lagrangian explicit:
+        // the preimage of width |a| / J, J = 1 + (a_r - a_l) of the donor,
+        // its liquid stretched by J (the width capped at 1)
+        double w = da, J = 1.0;
+        if (g.le) {
+          const int dk = map_idx(pos ? f - 1 : f, n_ax, bca);
+          const int dk1 = (bca == 0 && dk + 1 == n_ax) ? 0 : dk + 1;
+          const double adl = __ldg(uf + face_of<AX>(g, dk, x, y, z)) * g.lam;
+          const double adr = __ldg(uf + face_of<AX>(g, dk1, x, y, z)) * g.lam;
+          J = 1.0 + (adr - adl);
+          if (J > da) {
+            w = da / J;
+          } else {
+            w = 1.0;
+            if (status) atomicOr(status, DEV_CFL);
+          }
+        }
+        double vol = g.f32 ? slab_volume_f(mv, pl.w, AX, pos ? 1.0 - w : 0.0, w, cd)
+                           : slab_volume_nn(mv, pl.w, AX, pos ? 1.0 - w : 0.0, w);
+        if (g.le) vol = J * vol;
         Fv = pos ? vol : -vol;
       } else {
         Fv = cd * a;
@@ -694,13 +721,16 @@ k_energy(GridDev g, const double* __restrict__ c_before, const double* __restric
     const int qb = qa + (AX == 0 ? 1 : (AX == 1 ? FX : FX * FY));
     const double c = sC[qt], e = sE[qt];
     const uint8_t stv = state ? state[id] : (uint8_t)0;
-    const bool dirty = stv & 1;
+    const bool lag = g.le != 0;  // Lagrangian explicit: the cell's own Theta, no frozen state
+    const bool dirty = !lag && (stv & 1);
     const double ccv = dirty ? (double)((stv >> 1) & 1) : (c > 0.5 ? 1.0 : 0.0);
-    const double th = dirty ? theta[id] : heat_cap(g.Cp_l, g.Cp_g, ccv) * sT[qt];
+    const double Tc = sT[qt];
+    const double th = lag ? (Tc * g.Cp_l) * c + (Tc * g.Cp_g) * (1.0 - c)
+                          : (dirty ? theta[id] : heat_cap(g.Cp_l, g.Cp_g, ccv) * Tc);
     const double le = sG[qa] - th * sA[qa], re = sG[qb] - th * sA[qb];
     const double en = (e + le) - re;
     e_out[id] = en;
-    if (state && !dirty && (c_after[id] != c || en != e)) {
+    if (!lag && state && !dirty && (c_after[id] != c || en != e)) {
       state[id] = (uint8_t)(1 | (ccv > 0.5 ? 2 : 0));
       theta[id] = th;
     }
