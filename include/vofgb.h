@@ -160,7 +160,8 @@ VOF_API vof_status vof_advect_sweep_z(const vof_grid* g, const double* c_in, con
  * the same e_out, state and theta bit for bit as the fused sweep.
  *   axis 0/1/2; c_before, c_after [N] VOF field before/after the sweep;
  *   e_in, e_out [N]; flux_F, u_face: face arrays of the axis;
- *   state/theta as for the sweep (updated for cells whose c or e changed).
+ *   state/theta as for the sweep (updated for cells whose c or e changed;
+ *   with VOF_SCHEME_LE the cell's own Theta is used and they are untouched).
  */
 VOF_API vof_status energy_advect_consistent(const vof_grid* g, int axis, const double* c_before, const double* c_after,
                                     const double* e_in, double* e_out, const double* flux_F, const double* u_face,
@@ -194,6 +195,7 @@ VOF_API vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in,
 
 /*
  * One full time step on the caller's stream: zero the frozen state, three
+ * (g->scheme: Weymouth-Yue or Lagrangian-explicit)
  * sweeps in Strang-alternated order (x,y,z on even step_index, z,y,x on odd),
  * then the shift; c and e are updated in place (ping-pong through the
  * workspace, so the result lands back in c and e).

@@ -166,3 +166,25 @@ def test_fp64_form_is_the_default(P):
         outs.append((host(cd).copy(), host(ed).copy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert not np.array_equal(outs[0][0], outs[2][0])
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sweep_le_precision_form_close_to_fp64(P, name, axis):
+    """The precision form with the Lagrangian-explicit sweeps: the same
+    per-sweep bounds against the oracle's orc_sweep_le (the FP32 slab volume
+    of the preimage, clamped to the donor, then stretched by J in FP64)."""
+    import torch
+    g, c, e, vel, dt, _ = case(name)
+    og = ogrid(g)
+    co, eo, clip, Fo, Go = O.sweep_le(og, axis, c, e, vel[axis], dt, want_flux=True)
+    gf = P.Grid(g.nx, g.ny, g.nz, g.bc, g.h, g.Cp_l, g.Cp_g, g.T_sat, g.eps_mixed, precision=P.VOF_F32_FLUX,
+                scheme=P.VOF_SCHEME_LE)
+    cd, ed, uf = dev(c), dev(e), dev(vel[axis])
+    c2 = torch.empty_like(cd); e2 = torch.empty_like(ed)
+    flux = torch.zeros(g.face_shape(axis), dtype=torch.float64, device="cuda")
+    P.SWEEPS[axis](gf, cd, ed, c2, e2, uf, dt, None, None, flux, None)
+    cg, eg, Fg = host(c2), host(e2), host(flux)
+    assert np.abs(Fg - Fo).max() <= C_TOL_SWEEP / 2
+    assert np.abs(cg - co).max() <= C_TOL_SWEEP
+    assert np.abs(eg - eo).max() <= C_TOL_SWEEP * energy_scale(g, c, e)
