@@ -428,8 +428,13 @@ static void face_flux(const int dims[3], const int bc[3], const double par[5], i
     double cd = c[did];
     double Fv;
     if (is_mixed(cd, par[4])) {
+        /* the donor's plane is that of the cell it maps to: behind a
+           zero-gradient boundary the ghost donor is the boundary cell
+           itself (same c, same plane) */
+        int dm[3] = {map_index(don[0], dims[0], bc[0]), map_index(don[1], dims[1], bc[1]),
+                     map_index(don[2], dims[2], bc[2])};
         double s[27], m[3];
-        gather_stencil(dims, bc, c, don[0], don[1], don[2], s);
+        gather_stencil(dims, bc, c, dm[0], dm[1], dm[2], s);
         orc_myc(s, m);
         double al = orc_alpha(m, cd);
         double da = fabs(a);
@@ -545,7 +550,8 @@ static void face_flux_le(const int dims[3], const int bc[3], const double par[5]
     if (a == 0.0) { *F = 0.0; *G = 0.0; return; }
     int don[3] = {pos[0], pos[1], pos[2]};
     if (a > 0.0) don[axis] -= 1;
-    /* the donor's own faces, with its coordinates mapped into the grid */
+    /* the donor's plane and faces are those of the cell it maps to (behind a
+       zero-gradient boundary: the boundary cell itself) */
     int dm[3] = {map_index(don[0], dims[0], bc[0]), map_index(don[1], dims[1], bc[1]),
                  map_index(don[2], dims[2], bc[2])};
     long did = cell_id(dims, bc, don[0], don[1], don[2]);
@@ -553,7 +559,7 @@ static void face_flux_le(const int dims[3], const int bc[3], const double par[5]
     double Fv;
     if (is_mixed(cd, par[4])) {
         double s[27], m[3];
-        gather_stencil(dims, bc, c, don[0], don[1], don[2], s);
+        gather_stencil(dims, bc, c, dm[0], dm[1], dm[2], s);
         orc_myc(s, m);
         double al = orc_alpha(m, cd);
         double J = le_stretch(dims, bc, axis, uf, lam, dm);

@@ -121,10 +121,28 @@ def case(name):
         T[r < 0.16] = 1.4
         e = (2500.0 * c + 1.5 * (1 - c)) * T
         return g, c, e, (u, v, w), 0.4 * h, -0.02
+    if name == "inflow_walls":
+        # zero-gradient walls on every axis with inflow through three of
+        # them (u > 0 at x = 0, v < 0 at y = ny, w > 0 at z = 0) and an
+        # interface that meets the walls: the ghost donors behind them are
+        # mixed boundary cells
+        nx, ny, nz = 20, 18, 16
+        h = 1.0 / 16
+        g = P.Grid(nx, ny, nz, (1, 1, 1), h, 900.0, 1.3, 1.0)
+        c = W.ellipsoid_fractions((nz, ny, nx), h, (0.2, 0.9, 0.15), (0.55, 0.4, 0.35),
+                                  rot=np.linalg.qr(rng.normal(size=(3, 3)))[0], nsub=10)
+        u, v, w = W.uniform_faces((nz, ny, nx), (0.8, -0.5, 0.6))
+        zc = (np.arange(nz) + 0.5) * h
+        yc = (np.arange(ny) + 0.5) * h
+        xc = (np.arange(nx) + 0.5) * h
+        Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+        T = 1.0 + 0.2 * np.sin(3 * X + 1.0) * np.cos(2 * Y) + 0.1 * Z
+        e = (900.0 * c + 1.3 * (1 - c)) * T
+        return g, c, e, (u, v, w), 0.4 * h / 0.8, -0.02
     raise KeyError(name)
 
 
-CASES = ["sphere32", "deform_ragged", "tiny_periodic", "multi_segment", "tiles_periodic"]
+CASES = ["sphere32", "deform_ragged", "tiny_periodic", "multi_segment", "tiles_periodic", "inflow_walls"]
 
 
 def temperature(g, c, e):
