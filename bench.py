@@ -252,9 +252,10 @@ def run_gpu(args):
     traffic = faces_traffic_from_profile()
 
     # ---- the mass transfer rate (Sec. 3.2) on the same workload -------------
-    mt = mass_transfer_measure(P, g, wl, c0, e0, stream, barrier)
+    mt = None if args.step_only else mass_transfer_measure(P, g, wl, c0, e0, stream, barrier)
     # ---- the step with Li's Lagrangian-explicit sweeps (the other Step 1) ----
-    le = scheme_le_measure(P, wl, c0, e0, u, v, w, stream, barrier, steps=min(args.steps, 100))
+    le = None if args.step_only else scheme_le_measure(P, wl, c0, e0, u, v, w, stream, barrier,
+                                                       steps=min(args.steps, 100))
 
     # ---- end to end through the public API with host buffers ---------------
     # each step the face velocities of the liquid (produced by the flow
@@ -317,7 +318,8 @@ def run_gpu(args):
         cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
         del c, e, c0, e0, u, v, w, st
         torch.cuda.empty_cache()
-        pform = precision_form(dev) if world == 1 and not args.no_precision_form else None
+        pform = (precision_form(dev) if world == 1 and not (args.no_precision_form or args.step_only)
+                 else None)
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -593,6 +595,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the precision-form comparison on the 512^3 deformation workload")
+    ap.add_argument("--step-only", action="store_true",
+                    help="time the step alone: no precision-form, mass-transfer or Lagrangian-explicit lines "
+                         "(the launch list of the step)")
     ap.add_argument("--kernels-once", action="store_true",
                     help="launch each hot-path kernel once on the workload (profiling target)")
     args = ap.parse_args()
