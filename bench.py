@@ -395,6 +395,22 @@ def mass_transfer_measure(P, g, wl, c, e, stream, barrier, reps=20):
     for name, t in launches:
         kms[name] = kms.get(name, 0.0) + t / reps
     counts = P.vof_mass_transfer_work_counts(g, ws, stream)
+    # the velocity extension driven by this mdot (Sec. 3.3.1; its CG loop
+    # reads the residual on the host, so it is timed on the host clock)
+    nz, ny, nx = c.shape
+    xw = torch.empty(P.vof_velocity_extension_workspace_bytes(g), dtype=torch.uint8, device=c.device)
+    ut = torch.empty((nz, ny, nx + 1), dtype=torch.float64, device=c.device)
+    vt = torch.empty((nz, ny + 1, nx), dtype=torch.float64, device=c.device)
+    wt = torch.empty((nz + 1, ny, nx), dtype=torch.float64, device=c.device)
+    P.vof_velocity_extension(g, c, mdot, W.RHO_L, W.RHO_G, wl.dt, ut=ut, vt=vt, wt=wt, workspace=xw, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    ext_reps = 5
+    for _ in range(ext_reps):
+        ext_it, ext_res = P.vof_velocity_extension(g, c, mdot, W.RHO_L, W.RHO_G, wl.dt, ut=ut, vt=vt, wt=wt,
+                                                   workspace=xw, stream=stream)
+    barrier()
+    ext_ms = (time.perf_counter() - t0) * 1e3 / ext_reps
     mixed = (c > g.eps_mixed) & (c < 1 - g.eps_mixed)
     md = mdot[mixed]
     cells = c.numel()
@@ -403,7 +419,9 @@ def mass_transfer_measure(P, g, wl, c, e, stream, barrier, reps=20):
             "work_counts": counts, "kernel_ms": {k: round(v_, 5) for k, v_ in kms.items()},
             "launches_per_call": len(launches) // reps,
             "mdot_range": [float(md.min()), float(md.max())] if md.numel() else None,
-            "dd_range": [float(dd[mixed].min()), float(dd[mixed].max())] if md.numel() else None}
+            "dd_range": [float(dd[mixed].min()), float(dd[mixed].max())] if md.numel() else None,
+            "velocity_extension": {"ms_per_call": round(ext_ms, 4), "cg_iterations": ext_it,
+                                   "residual": ext_res, "max_abs_correction": float(wt.abs().max())}}
 
 
 def scheme_le_measure(P, wl, c0, e0, u, v, w, stream, barrier, steps=100):

@@ -52,7 +52,9 @@ typedef enum {
   VOF_OK = 0,
   VOF_EINVAL = 1,  /* bad argument (null pointer, size, aliasing) */
   VOF_ECUDA = 2,   /* a CUDA call failed; see vof_last_cuda_error() */
-  VOF_ECFL = 3     /* device status: |u| dt / h > 1 on some face */
+  VOF_ECFL = 3,    /* device status: |u| dt / h > 1 on some face */
+  VOF_ESOLVE = 4   /* vof_velocity_extension: no free-flow face, or no
+                      convergence within max_iter */
 } vof_status;
 
 typedef struct {
@@ -261,6 +263,43 @@ VOF_API vof_status vof_mass_transfer(const vof_grid* g, const double* c, const d
  * host memory after the work queued on `stream` completes. */
 VOF_API vof_status vof_mass_transfer_work_counts(const vof_grid* g, const void* workspace, int* counts,
                                                  void* stream);
+
+/*
+ * Velocity extension across the interface (Sec. 3.3.1: Eq. press_inv, the
+ * correction u~ = -(dt/rho) grad p~ and u_l = u^{n+1} + u~).  Sub-domain:
+ * the mixed cells and the pure gas cells (c <= eps) of the first two layers
+ * around them, layers counted across cell faces.  Faces to pure liquid
+ * cells (c >= 1 - eps) and zero-gradient walls are no-slip; faces to gas
+ * cells beyond the second layer are free flow (p~ = 0 there); periodic axes
+ * wrap.  In every sub-domain cell
+ *   sum_faces beta_f (p~_Q - p~_P) = mdot (1/rho_g - 1/rho_l) A / h,
+ *   beta_f = (dt / rho_f) / h^2, rho_f = rho_l c_f + rho_g (1 - c_f),
+ *   c_f the mean of the two cells' c, A the PLIC plane area of a mixed
+ *   cell in cell units (as in vof_reconstruct; gas cells: no source);
+ * solved by preconditioned conjugate gradients until the residual falls to
+ * tol times that of p~ = 0 (or max_iter iterations).  Then on every face
+ * with a sub-domain cell on one side and no liquid cell or wall
+ * u~ = -(dt / rho_f) (p~_R - p~_L) / h (p~ = 0 outside), 0 elsewhere.
+ *   c, mdot      device double[N] (mdot read at mixed cells, e.g. from
+ *                vof_mass_transfer)
+ *   rho_l, rho_g densities (> 0); dt >= 0; tol > 0; max_iter >= 1
+ *   u, v, w      device face arrays or all NULL: u~ is added (u_l = u + u~)
+ *   ut, vt, wt   device face arrays or all NULL: u~ is written
+ *   iterations, residual   host int / double or NULL: CG iterations and the
+ *                final residual norm
+ *   workspace    device buffer of vof_velocity_extension_workspace_bytes(g)
+ *                bytes, 256-byte aligned, caller-owned
+ * The call synchronises `stream` (the convergence test reads the residual).
+ * VOF_EINVAL for bad arguments (also when neither u,v,w nor ut,vt,wt is
+ * given); VOF_ESOLVE when the sub-domain has no free-flow face (nothing
+ * fixes p~; outputs untouched) or CG did not converge (outputs written from
+ * the last iterate).
+ */
+VOF_API size_t vof_velocity_extension_workspace_bytes(const vof_grid* g);
+VOF_API vof_status vof_velocity_extension(const vof_grid* g, const double* c, const double* mdot, double rho_l,
+                                          double rho_g, double dt, double tol, int max_iter, double* u, double* v,
+                                          double* w, double* ut, double* vt, double* wt, int* iterations,
+                                          double* residual, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * A time step that allocates nothing (the paper has no counterpart; this is

@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvofgb.so")
 
-VOF_OK, VOF_EINVAL, VOF_ECUDA, VOF_ECFL = 0, 1, 2, 3
+VOF_OK, VOF_EINVAL, VOF_ECUDA, VOF_ECFL, VOF_ESOLVE = 0, 1, 2, 3, 4
 VOF_NSUMS = 6
 
 
@@ -103,6 +103,8 @@ def lib():
             "vof_phase_change_shift": [G, P, P, P, P, P, D, P, P, P, S, P],
             "vof_step": [G, P, P, P, P, P, D, L_, P, D, P, P, S, P],
             "vof_mass_transfer": [G, P, P, D, D, D, P, P, P, D, P, P, S, P],
+            "vof_velocity_extension": [G, P, P, D, D, D, D, I, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double), P, S, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -120,6 +122,8 @@ def lib():
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
         L.vof_step_work_counts.restype = ctypes.c_int
+        L.vof_velocity_extension_workspace_bytes.argtypes = [G]
+        L.vof_velocity_extension_workspace_bytes.restype = ctypes.c_size_t
         L.vof_mass_transfer_workspace_bytes.argtypes = [G]
         L.vof_mass_transfer_workspace_bytes.restype = ctypes.c_size_t
         L.vof_mass_transfer_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
@@ -323,6 +327,32 @@ def vof_mass_transfer(g, c, e, k_l, k_g, h_fg, mdot, d_gamma=None, grad_n=None, 
                                    _ptr(d_gamma, _f64(), "d_gamma"), _ptr(grad_n, _f64(), "grad_n"),
                                    float(dd_per_mdot), _ptr(dd, _f64(), "dd"), _ptr(workspace, None, "workspace"),
                                    ctypes.c_size_t(nbytes), _stream(stream)))
+
+
+def vof_velocity_extension_workspace_bytes(g: Grid) -> int:
+    cg = g.c_struct()
+    return int(lib().vof_velocity_extension_workspace_bytes(ctypes.byref(cg)))
+
+
+def vof_velocity_extension(g, c, mdot, rho_l, rho_g, dt, tol=1e-13, max_iter=2000, u=None, v=None, w=None,
+                           ut=None, vt=None, wt=None, workspace=None, stream=None):
+    """Velocity extension across the interface (Sec. 3.3.1): adds u~ to
+    (u, v, w) and/or writes it to (ut, vt, wt).  Returns (CG iterations,
+    final residual norm)."""
+    cg = g.c_struct()
+    if workspace is None:
+        workspace = _cached_workspace(vof_velocity_extension_workspace_bytes(g), c.device)
+    nbytes = workspace.numel() * workspace.element_size()
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check("vof_velocity_extension",
+           lib().vof_velocity_extension(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(mdot, _f64(), "mdot"),
+                                        float(rho_l), float(rho_g), float(dt), float(tol), int(max_iter),
+                                        _ptr(u, _f64(), "u"), _ptr(v, _f64(), "v"), _ptr(w, _f64(), "w"),
+                                        _ptr(ut, _f64(), "ut"), _ptr(vt, _f64(), "vt"), _ptr(wt, _f64(), "wt"),
+                                        ctypes.byref(it), ctypes.byref(res), _ptr(workspace, None, "workspace"),
+                                        ctypes.c_size_t(nbytes), _stream(stream)))
+    return it.value, res.value
 
 
 def vof_mass_transfer_work_counts(g, workspace, stream=None):

@@ -343,6 +343,43 @@ vof_status vof_mass_transfer_work_counts(const vof_grid* g, const void* workspac
   return cuda_status(err);
 }
 
+size_t vof_velocity_extension_workspace_bytes(const vof_grid* g) {
+  if (!grid_ok(g)) return 0;
+  return ext_scratch_bytes(cells(g));
+}
+
+vof_status vof_velocity_extension(const vof_grid* g, const double* c, const double* mdot, double rho_l,
+                                  double rho_g, double dt, double tol, int max_iter, double* u, double* v,
+                                  double* w, double* ut, double* vt, double* wt, int* iterations,
+                                  double* residual, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!grid_ok(g) || !c || !mdot || !workspace) return VOF_EINVAL;
+  if (!(rho_l > 0.0) || !(rho_g > 0.0) || !(dt >= 0.0) || !(tol > 0.0) || max_iter < 1) return VOF_EINVAL;
+  const bool add = u || v || w, put = ut || vt || wt;
+  if ((add && !(u && v && w)) || (put && !(ut && vt && wt)) || (!add && !put)) return VOF_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
+  const size_t N = cells(g), B = N * 8;
+  const size_t need = ext_scratch_bytes(N);
+  if (workspace_bytes < need) return VOF_EINVAL;
+  const void* outs[6] = {u, v, w, ut, vt, wt};
+  for (int a = 0; a < 6; ++a) {
+    if (!outs[a]) continue;
+    const size_t fa = face_count(g, a % 3) * 8;
+    if (overlap(outs[a], fa, c, B) || overlap(outs[a], fa, mdot, B) || overlap(outs[a], fa, workspace, need))
+      return VOF_EINVAL;
+    for (int b = a + 1; b < 6; ++b)
+      if (outs[b] && overlap(outs[a], fa, outs[b], face_count(g, b % 3) * 8)) return VOF_EINVAL;
+  }
+  if (overlap(workspace, need, c, B) || overlap(workspace, need, mdot, B)) return VOF_EINVAL;
+  int it = 0, st = 0;
+  double res = 0.0;
+  cudaError_t err = launch_velocity_extension(to_dev(g, 0.0), g->h, c, mdot, rho_l, rho_g, dt, tol, max_iter, u, v,
+                                              w, ut, vt, wt, workspace, (cudaStream_t)stream, &it, &res, &st);
+  if (err != cudaSuccess) return cuda_status(err);
+  if (iterations) *iterations = it;
+  if (residual) *residual = res;
+  return st ? VOF_ESOLVE : VOF_OK;
+}
+
 vof_status vof_get_device_status(void) {
   int* p = device_status_ptr();
   if (!p) return VOF_ECUDA;
@@ -361,6 +398,7 @@ const char* vof_status_string(int status) {
     case VOF_EINVAL: return "invalid argument";
     case VOF_ECUDA: return "CUDA error";
     case VOF_ECFL: return "face CFL number above 1";
+    case VOF_ESOLVE: return "velocity extension: no free-flow face, or no convergence";
     default: return "unknown status";
   }
 }

@@ -180,4 +180,12 @@ cudaError_t launch_mass_transfer(const GridDev& g, double h, const double* c, co
                                  double* dd, void* workspace, cudaStream_t st);
 int* mdot_counters(const GridDev& g, void* workspace);
 
+// Velocity extension (vof_ext.cu): workspace size and the whole solve;
+// *status: 0 ok, 1 no free-flow face (nothing written), 2 not converged.
+size_t ext_scratch_bytes(size_t N);
+cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* c, const double* mdot, double rho_l,
+                                      double rho_g, double dt, double tol, int max_iter, double* u, double* v,
+                                      double* w, double* ut, double* vt, double* wt, void* workspace,
+                                      cudaStream_t st, int* iters_out, double* res_out, int* status);
+
 }  // namespace vofgb

@@ -118,6 +118,35 @@ def test_mass_transfer_validation_without_gpu(lib):
     assert lib.vof_mass_transfer_workspace_bytes(ctypes.byref(big)) > 7 * nb
 
 
+def test_velocity_extension_validation_without_gpu(lib):
+    import paper_2001_03477_gb300 as P
+    g = P.Grid(8, 8, 8, (1, 1, 1), 0.1, 2.0, 1.0, 0.0)
+    cg = g.c_struct()
+    nul = ctypes.c_void_p(0)
+    c, md = ctypes.c_void_p(1 << 40), ctypes.c_void_p(2 << 40)
+    u, v, w = (ctypes.c_void_p(k << 40) for k in (3, 4, 5))
+    ws = ctypes.c_void_p(7 << 40)
+    nb = lib.vof_velocity_extension_workspace_bytes(ctypes.byref(cg))
+    assert nb > 512 * 100
+    it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+
+    def call(c_=c, md_=md, uu=(u, v, w), tt=(nul, nul, nul), rl=958.0, rg=0.6, tol=1e-12, mi=100, ws_=ws, nb_=nb):
+        return lib.vof_velocity_extension(ctypes.byref(cg), c_, md_, rl, rg, 1e-3, tol, mi, *uu, *tt,
+                                          ctypes.byref(it), ctypes.byref(res), ws_, ctypes.c_size_t(nb_), nul)
+    assert call(c_=nul) == P.VOF_EINVAL
+    assert call(md_=nul) == P.VOF_EINVAL
+    assert call(uu=(nul, nul, nul)) == P.VOF_EINVAL            # nothing to write
+    assert call(uu=(u, nul, w)) == P.VOF_EINVAL                # partial set
+    assert call(rg=0.0) == P.VOF_EINVAL
+    assert call(tol=0.0) == P.VOF_EINVAL
+    assert call(mi=0) == P.VOF_EINVAL
+    assert call(nb_=nb - 8) == P.VOF_EINVAL
+    assert call(ws_=ctypes.c_void_p((7 << 40) + 128)) == P.VOF_EINVAL
+    assert call(uu=(ctypes.c_void_p((1 << 40) + 8), v, w)) == P.VOF_EINVAL   # u over c
+    assert call(uu=(u, ctypes.c_void_p((3 << 40) + 64), w)) == P.VOF_EINVAL  # v over u
+    assert lib.vof_status_string(P.VOF_ESOLVE).startswith(b"velocity extension")
+
+
 def test_workspace_size_scales(lib):
     import paper_2001_03477_gb300 as P
     a = P.vof_step_workspace_bytes(P.Grid(32, 32, 32))
