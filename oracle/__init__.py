@@ -14,6 +14,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   orc_sweep_le, orc_step_scheme                             -- pinned (equal
       to the Weymouth-Yue sweep for uniform velocity; a plane moved exactly
       by a linear velocity; uniform T stays uniform; the volume identity)
+  diffusion.diffuse, diffusion_operator (numpy + scipy)     -- pinned (linear
+      profiles about a plane are steady, T_Gamma is a fixed point, the
+      slab decay converges, heights and plane distances agree for planes)
   extension.velocity_extension (numpy + scipy)              -- pinned (plane
       interface closed form, divergence cancels the source, mirror
       symmetry, zero flux, rejection without a free-flow face)

@@ -1,0 +1,133 @@
+"""Pins of the oracle's interface-Dirichlet heat diffusion (Sec. 3.4.2,
+Eqs. T_diff_disc and mod_branchesT) against what the mathematics fixes
+(CPU only).
+
+* A temperature linear in the distance to a plane interface on each side,
+  T_Gamma on the plane: every one-sided gradient of the irregular stencil is
+  the exact gradient (heights and plane distances are exact for planes), so
+  the operator vanishes at every node whose stencil stays inside the domain.
+* T = T_Gamma everywhere is a fixed point of the implicit step.
+* A liquid slab between a no-flux wall and the interface, T - T_Gamma =
+  cos(pi x / 2 L) initially: the discrete decay converges to exp(-k/C_p
+  (pi / 2 L)^2 t) as h and dt shrink together, at about first order in dt
+  (backward Euler) with the interface off the grid nodes (theta < h).
+* The height function and its fallback agree for planes along every axis.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.diffusion import diffuse, diffusion_operator, interface_distance
+from test_oracle_mass_transfer import plane_fractions
+
+
+def tilted(seed):
+    rng = np.random.default_rng(seed)
+    n = np.array([rng.uniform(-0.25, 0.25), rng.uniform(-0.25, 0.25), 1.0])
+    if seed % 2:
+        n = -n
+    n /= np.linalg.norm(n)
+    D = float(n @ np.array([6.0, 6.0, 6.0 + rng.uniform(-0.4, 0.4)]))
+    return n, D
+
+
+def nodes(shape):
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    return X, Y, Z
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_linear_profile_is_steady(seed):
+    shape = (12, 12, 12)
+    n, D = tilted(seed)
+    X, Y, Z = nodes(shape)
+    # keep every node more than the cap (1e-3 cells) from the plane, where
+    # theta would be eps h instead of the distance
+    while np.abs(D - (n[0] * X + n[1] * Y + n[2] * Z)).min() < 2e-2:
+        D += 0.031
+    c = plane_fractions(shape, n, D)
+    h, Tg = 0.1, 2.0
+    s = (D - (n[0] * X + n[1] * Y + n[2] * Z))  # cells, > 0 in the liquid
+    T = np.where(s > 0, Tg + 3.0 * s * h, Tg - 1.5 * s * h)
+    g = O.Grid(12, 12, 12, (1, 1, 1), h, 4.0, 1.0, Tg)
+    L = diffusion_operator(g, c, T, 0.7, 0.03).reshape(shape)
+    inner = np.zeros(shape, bool)
+    inner[1:-1, 4:-4, 4:-4] = True  # stencils clear of the walls and of the walls' MYC columns
+    assert np.abs(L[inner]).max() <= 1e-9 * 3.0 / h
+
+
+def test_saturation_temperature_is_a_fixed_point():
+    shape = (10, 10, 10)
+    n, D = tilted(1)
+    c = plane_fractions(shape, n, D)
+    g = O.Grid(10, 10, 10, (1, 0, 1), 0.1, 4.0, 1.0, 3.0)
+    e = (4.0 * c + (1 - c)) * 3.0
+    e1 = diffuse(g, c, e, 0.7, 0.03, 1e-3)
+    T1 = e1 / (4.0 * c + (1 - c))
+    assert np.abs(T1 - 3.0).max() < 1e-12
+
+
+def slab_decay(N, steps_per_unit):
+    """Liquid in x < x0 = 0.75 (the interface inside a cell), a no-flux wall
+    at x = 0; T - T_G = cos(pi x / (2 x0)); returns the decay at the wall
+    node after time 0.05 against the exact exp(-kappa lambda t)."""
+    L = 1.0
+    h = L / N
+    x0 = 0.75 + 0.37 * h
+    xf = np.arange(N) * h
+    frac = np.clip((x0 - xf) / h, 0.0, 1.0)
+    c = np.broadcast_to(frac[None, None, :], (1, 1, N)).copy()
+    Cp_l, k_l, Tg = 2.0, 0.5, 1.0
+    g = O.Grid(N, 1, 1, (1, 0, 0), h, Cp_l, 1.0, Tg)
+    xc = (np.arange(N) + 0.5) * h
+    T0 = np.where(xc < x0, Tg + np.cos(math.pi * xc / (2 * x0)), Tg)
+    e = (Cp_l * c + (1 - c)) * T0
+    t_end = 0.05
+    nsteps = int(round(t_end * steps_per_unit))
+    dt = t_end / nsteps
+    for _ in range(nsteps):
+        e = diffuse(g, c, e, k_l, 0.01, dt)
+    T = e / (Cp_l * c + (1 - c))
+    kappa, lam = k_l / Cp_l, (math.pi / (2 * x0)) ** 2
+    got = (T[0, 0, 0] - Tg) / (T0[0] - Tg)
+    return abs(got - math.exp(-kappa * lam * t_end))
+
+
+def test_slab_decay_converges():
+    e1 = slab_decay(20, 400)
+    e2 = slab_decay(40, 800)
+    e3 = slab_decay(80, 1600)
+    assert e2 < e1 / 1.7 and e3 < e2 / 1.7
+    assert e3 < 2e-3
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_height_and_plane_distances_agree_for_planes(seed):
+    shape = (12, 12, 12)
+    n, D = tilted(seed + 10)
+    c = plane_fractions(shape, n, D)
+    g = O.Grid(12, 12, 12, (1, 1, 1), 1.0, 1.0, 1.0, 1.0)
+    m, al, _ = O.reconstruct(g, c)
+    checked = 0
+    for P in itertools.product(range(4, 8), range(4, 8), range(4, 8)):
+        liq = c[P] >= 0.5
+        for axis in range(3):
+            for s in (-1, 1):
+                Q = list(P)
+                Q[2 - axis] += s
+                Q = tuple(Q)
+                if (c[Q] >= 0.5) == liq:
+                    continue
+                th = interface_distance(g, c, m, al, P, axis, s)
+                zP, yP, xP = P
+                x = np.array([xP + 0.5, yP + 0.5, zP + 0.5])
+                e_ax = np.zeros(3)
+                e_ax[axis] = s
+                exact = (D - n @ x) / (n @ e_ax)  # along the axis to the plane
+                assert abs(th - min(max(exact, 1e-3), 1.0)) < 1e-12
+                checked += 1
+    assert checked > 10
