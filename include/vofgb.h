@@ -53,8 +53,9 @@ typedef enum {
   VOF_EINVAL = 1,  /* bad argument (null pointer, size, aliasing) */
   VOF_ECUDA = 2,   /* a CUDA call failed; see vof_last_cuda_error() */
   VOF_ECFL = 3,    /* device status: |u| dt / h > 1 on some face */
-  VOF_ESOLVE = 4   /* vof_velocity_extension: no free-flow face, or no
-                      convergence within max_iter */
+  VOF_ESOLVE = 4   /* an iterative solve (vof_velocity_extension,
+                      vof_heat_diffusion) did not converge within max_iter,
+                      or the extension's sub-domain has no free-flow face */
 } vof_status;
 
 typedef struct {
@@ -300,6 +301,40 @@ VOF_API vof_status vof_velocity_extension(const vof_grid* g, const double* c, co
                                           double rho_g, double dt, double tol, int max_iter, double* u, double* v,
                                           double* w, double* ut, double* vt, double* wt, int* iterations,
                                           double* residual, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Implicit heat diffusion with the interface as a Dirichlet boundary
+ * (Sec. 3.4.2: Eqs. T_diff_disc and mod_branchesT).  A node is liquid when
+ * c >= 1/2, else gas; each phase diffuses with its own conductivity, and
+ * T = T_Gamma = g->T_sat on the interface.  Along each axis the gradient
+ * towards a same-phase neighbour is (T_nb - T)/h, towards the other phase
+ * (T_Gamma - T)/theta, and the axis' second difference is divided by
+ * (d_- + d_+)/2 (d = h or theta).  theta: the height function of the 7 cells
+ * centred on the node along the axis when the column ends in pure cells of
+ * the node's phase behind and the other phase beyond (H - 3.5 cells ahead of
+ * a liquid node, 3.5 - H of a gas node), else the distance along the axis
+ * to the PLIC plane of the pair's mixed cell (the node's own if mixed, else
+ * the neighbour's), half a cell when both are pure or the plane is parallel
+ * to the axis; capped to [1e-3 h, h].  Zero-gradient walls carry no flux.
+ * Backward Euler, C_p(c) (T' - T)/dt = k_p sum L(T'), solved by Jacobi
+ * sweeps (the system is strictly diagonally dominant) until no T changes by
+ * more than tol in a sweep (or max_iter sweeps); e' = C_p(c) T'.
+ *   c            device double[N], read only
+ *   e            device double[N], read and overwritten with e'
+ *   k_l, k_g     conductivities (>= 0); dt > 0; tol > 0 (absolute, in T);
+ *                max_iter >= 1
+ *   iterations, change   host int / double or NULL: sweeps made and the
+ *                last sweep's largest change
+ *   workspace    device buffer of vof_heat_diffusion_workspace_bytes(g)
+ *                bytes, 256-byte aligned, caller-owned
+ * The call synchronises `stream`.  VOF_EINVAL for bad arguments or
+ * overlaps; VOF_ESOLVE when max_iter sweeps did not converge (e is written
+ * from the last sweep).
+ */
+VOF_API size_t vof_heat_diffusion_workspace_bytes(const vof_grid* g);
+VOF_API vof_status vof_heat_diffusion(const vof_grid* g, const double* c, double* e, double k_l, double k_g,
+                                      double dt, double tol, int max_iter, int* iterations, double* change,
+                                      void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * A time step that allocates nothing (the paper has no counterpart; this is

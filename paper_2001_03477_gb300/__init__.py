@@ -105,6 +105,8 @@ def lib():
             "vof_mass_transfer": [G, P, P, D, D, D, P, P, P, D, P, P, S, P],
             "vof_velocity_extension": [G, P, P, D, D, D, D, I, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double), P, S, P],
+            "vof_heat_diffusion": [G, P, P, D, D, D, D, I, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_double), P, S, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -122,6 +124,8 @@ def lib():
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
         L.vof_step_work_counts.restype = ctypes.c_int
+        L.vof_heat_diffusion_workspace_bytes.argtypes = [G]
+        L.vof_heat_diffusion_workspace_bytes.restype = ctypes.c_size_t
         L.vof_velocity_extension_workspace_bytes.argtypes = [G]
         L.vof_velocity_extension_workspace_bytes.restype = ctypes.c_size_t
         L.vof_mass_transfer_workspace_bytes.argtypes = [G]
@@ -353,6 +357,28 @@ def vof_velocity_extension(g, c, mdot, rho_l, rho_g, dt, tol=1e-13, max_iter=200
                                         ctypes.byref(it), ctypes.byref(res), _ptr(workspace, None, "workspace"),
                                         ctypes.c_size_t(nbytes), _stream(stream)))
     return it.value, res.value
+
+
+def vof_heat_diffusion_workspace_bytes(g: Grid) -> int:
+    cg = g.c_struct()
+    return int(lib().vof_heat_diffusion_workspace_bytes(ctypes.byref(cg)))
+
+
+def vof_heat_diffusion(g, c, e, k_l, k_g, dt, tol=1e-10, max_iter=10000, workspace=None, stream=None):
+    """Implicit interface-Dirichlet heat diffusion (Sec. 3.4.2) of e in
+    place.  Returns (Jacobi sweeps, last sweep's largest change of T)."""
+    cg = g.c_struct()
+    if workspace is None:
+        workspace = _cached_workspace(vof_heat_diffusion_workspace_bytes(g), c.device)
+    nbytes = workspace.numel() * workspace.element_size()
+    it = ctypes.c_int(0)
+    ch = ctypes.c_double(0.0)
+    _check("vof_heat_diffusion",
+           lib().vof_heat_diffusion(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(e, _f64(), "e"), float(k_l),
+                                    float(k_g), float(dt), float(tol), int(max_iter), ctypes.byref(it),
+                                    ctypes.byref(ch), _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes),
+                                    _stream(stream)))
+    return it.value, ch.value
 
 
 def vof_mass_transfer_work_counts(g, workspace, stream=None):

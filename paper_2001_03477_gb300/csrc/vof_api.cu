@@ -380,6 +380,31 @@ vof_status vof_velocity_extension(const vof_grid* g, const double* c, const doub
   return st ? VOF_ESOLVE : VOF_OK;
 }
 
+size_t vof_heat_diffusion_workspace_bytes(const vof_grid* g) {
+  if (!grid_ok(g)) return 0;
+  return dif_scratch_bytes(cells(g));
+}
+
+vof_status vof_heat_diffusion(const vof_grid* g, const double* c, double* e, double k_l, double k_g, double dt,
+                              double tol, int max_iter, int* iterations, double* change, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+  if (!grid_ok(g) || !c || !e || !workspace) return VOF_EINVAL;
+  if (!(k_l >= 0.0) || !(k_g >= 0.0) || !(dt > 0.0) || !(tol > 0.0) || max_iter < 1) return VOF_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
+  const size_t N = cells(g), B = N * 8;
+  const size_t need = dif_scratch_bytes(N);
+  if (workspace_bytes < need) return VOF_EINVAL;
+  if (overlap(c, B, e, B) || overlap(workspace, need, c, B) || overlap(workspace, need, e, B)) return VOF_EINVAL;
+  int it = 0, st = 0;
+  double ch = 0.0;
+  cudaError_t err = launch_heat_diffusion(to_dev(g, 0.0), g->h, c, e, k_l, k_g, dt, tol, max_iter, workspace,
+                                          (cudaStream_t)stream, &it, &ch, &st);
+  if (err != cudaSuccess) return cuda_status(err);
+  if (iterations) *iterations = it;
+  if (change) *change = ch;
+  return st ? VOF_ESOLVE : VOF_OK;
+}
+
 vof_status vof_get_device_status(void) {
   int* p = device_status_ptr();
   if (!p) return VOF_ECUDA;
@@ -398,7 +423,7 @@ const char* vof_status_string(int status) {
     case VOF_EINVAL: return "invalid argument";
     case VOF_ECUDA: return "CUDA error";
     case VOF_ECFL: return "face CFL number above 1";
-    case VOF_ESOLVE: return "velocity extension: no free-flow face, or no convergence";
+    case VOF_ESOLVE: return "iterative solve not converged (or no free-flow face for the velocity extension)";
     default: return "unknown status";
   }
 }

@@ -188,4 +188,11 @@ cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* 
                                       double* w, double* ut, double* vt, double* wt, void* workspace,
                                       cudaStream_t st, int* iters_out, double* res_out, int* status);
 
+// Heat diffusion (vof_diffuse.cu): workspace size and the whole solve;
+// *status: 0 converged, 2 not converged within max_iter.
+size_t dif_scratch_bytes(size_t N);
+cudaError_t launch_heat_diffusion(const GridDev& g, double h, const double* c, double* e, double k_l, double k_g,
+                                  double dt, double tol, int max_iter, void* workspace, cudaStream_t st,
+                                  int* iters_out, double* change_out, int* status);
+
 }  // namespace vofgb

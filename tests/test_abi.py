@@ -144,7 +144,31 @@ def test_velocity_extension_validation_without_gpu(lib):
     assert call(ws_=ctypes.c_void_p((7 << 40) + 128)) == P.VOF_EINVAL
     assert call(uu=(ctypes.c_void_p((1 << 40) + 8), v, w)) == P.VOF_EINVAL   # u over c
     assert call(uu=(u, ctypes.c_void_p((3 << 40) + 64), w)) == P.VOF_EINVAL  # v over u
-    assert lib.vof_status_string(P.VOF_ESOLVE).startswith(b"velocity extension")
+    assert lib.vof_status_string(P.VOF_ESOLVE).startswith(b"iterative solve")
+
+
+def test_heat_diffusion_validation_without_gpu(lib):
+    import paper_2001_03477_gb300 as P
+    g = P.Grid(8, 8, 8, (1, 1, 1), 0.1, 2.0, 1.0, 0.0)
+    cg = g.c_struct()
+    nul = ctypes.c_void_p(0)
+    c, e, ws = ctypes.c_void_p(1 << 40), ctypes.c_void_p(2 << 40), ctypes.c_void_p(7 << 40)
+    nb = lib.vof_heat_diffusion_workspace_bytes(ctypes.byref(cg))
+    assert nb > 512 * 80
+    it, ch = ctypes.c_int(0), ctypes.c_double(0.0)
+
+    def call(c_=c, e_=e, kl=0.5, dt=1e-3, tol=1e-12, mi=10, ws_=ws, nb_=nb):
+        return lib.vof_heat_diffusion(ctypes.byref(cg), c_, e_, kl, 0.1, dt, tol, mi, ctypes.byref(it),
+                                      ctypes.byref(ch), ws_, ctypes.c_size_t(nb_), nul)
+    assert call(c_=nul) == P.VOF_EINVAL
+    assert call(e_=nul) == P.VOF_EINVAL
+    assert call(kl=-1.0) == P.VOF_EINVAL
+    assert call(dt=0.0) == P.VOF_EINVAL
+    assert call(tol=0.0) == P.VOF_EINVAL
+    assert call(mi=0) == P.VOF_EINVAL
+    assert call(nb_=nb - 8) == P.VOF_EINVAL
+    assert call(e_=ctypes.c_void_p((1 << 40) + 8)) == P.VOF_EINVAL   # e over c
+    assert call(ws_=ctypes.c_void_p((2 << 40) - 256)) == P.VOF_EINVAL  # workspace over e
 
 
 def test_workspace_size_scales(lib):
