@@ -411,6 +411,28 @@ def mass_transfer_measure(P, g, wl, c, e, stream, barrier, reps=20):
                                                    workspace=xw, stream=stream)
     barrier()
     ext_ms = (time.perf_counter() - t0) * 1e3 / ext_reps
+    # the implicit interface-Dirichlet heat diffusion of the same state
+    # (Sec. 3.4.2), host-timed (its Jacobi loop reads the largest change on
+    # the host); a failure here is reported in the line, not raised
+    try:
+        dw = torch.empty(P.vof_heat_diffusion_workspace_bytes(g), dtype=torch.uint8, device=c.device)
+        e_d = e.clone()
+        P.vof_heat_diffusion(g, c, e_d, K_L_WATER, K_G_STEAM, wl.dt, tol=1e-9, max_iter=1000, workspace=dw,
+                             stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        dif_reps = 3
+        for _ in range(dif_reps):
+            e_d.copy_(e)
+            dif_it, dif_ch = P.vof_heat_diffusion(g, c, e_d, K_L_WATER, K_G_STEAM, wl.dt, tol=1e-9,
+                                                  max_iter=1000, workspace=dw, stream=stream)
+        barrier()
+        dif = {"ms_per_call": round((time.perf_counter() - t0) * 1e3 / dif_reps, 4), "jacobi_sweeps": dif_it,
+               "last_change_K": dif_ch,
+               "max_abs_dT_K": float(((e_d - e) / (g.Cp_l * c + g.Cp_g * (1 - c))).abs().max())}
+        del dw, e_d
+    except Exception as exc:  # noqa: BLE001 -- reported, the step's figures stand
+        dif = {"error": str(exc)[:200]}
     mixed = (c > g.eps_mixed) & (c < 1 - g.eps_mixed)
     md = mdot[mixed]
     cells = c.numel()
@@ -421,7 +443,8 @@ def mass_transfer_measure(P, g, wl, c, e, stream, barrier, reps=20):
             "mdot_range": [float(md.min()), float(md.max())] if md.numel() else None,
             "dd_range": [float(dd[mixed].min()), float(dd[mixed].max())] if md.numel() else None,
             "velocity_extension": {"ms_per_call": round(ext_ms, 4), "cg_iterations": ext_it,
-                                   "residual": ext_res, "max_abs_correction": float(wt.abs().max())}}
+                                   "residual": ext_res, "max_abs_correction": float(wt.abs().max())},
+            "heat_diffusion": dif}
 
 
 def scheme_le_measure(P, wl, c0, e0, u, v, w, stream, barrier, steps=100):
