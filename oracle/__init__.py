@@ -14,6 +14,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   orc_sweep_le, orc_step_scheme                             -- pinned (equal
       to the Weymouth-Yue sweep for uniform velocity; a plane moved exactly
       by a linear velocity; uniform T stays uniform; the volume identity)
+  mlp (numpy): learned-normal data, network, gradients,
+      BF16 rounding, MYC fallback                           -- pinned (finite
+      differences, GELU identities, a library BF16 conversion, ellipsoid
+      nearest points, label orientation, plane residual, training)
   diffusion.diffuse, diffusion_operator (numpy + scipy)     -- pinned (linear
       profiles about a plane are steady, T_Gamma is a fixed point, the
       slab decay converges, heights and plane distances agree for planes)
