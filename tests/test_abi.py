@@ -190,3 +190,19 @@ def test_binding_refuses_cpu_tensors(lib):
     c = torch.zeros(4, 4, 4, dtype=torch.float64)
     with pytest.raises(ValueError):
         P.vof_reconstruct(g, c, c, c, c)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every call raises."""
+    import torch
+    import paper_2001_03477_gb300 as P
+    monkeypatch.setattr(P, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(P, "_lib", None)
+    with pytest.raises(RuntimeError):
+        P.lib()
+    g = P.Grid(4, 4, 4)
+    c = torch.zeros(4, 4, 4, dtype=torch.float64)
+    with pytest.raises(RuntimeError):
+        P.vof_mass_transfer(g, c, c, 1.0, 1.0, 1.0, c)
+    with pytest.raises(RuntimeError):
+        P.vof_step_workspace_bytes(g)
