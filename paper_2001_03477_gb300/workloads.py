@@ -152,22 +152,25 @@ def radial_faces(shape, h, centre, strength, r_cut):
     sym = (nx == ny == nz) and np.allclose(c, c[0]) and abs(c[0] - 0.5 * nx * h) < 1e-15
     for axis in range(1 if sym else 3):
         fs = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][axis]
-        kk, jj, ii = np.meshgrid(np.arange(fs[0]), np.arange(fs[1]), np.arange(fs[2]), indexing="ij")
-        # low corner of the face in physical coordinates
-        base = np.stack([ii * h, jj * h, kk * h], axis=-1) - c
         e1 = np.zeros(3); e2 = np.zeros(3)
         t1, t2 = [(1, 2), (2, 0), (0, 1)][axis]  # right-handed: t1 x t2 = +axis
         e1[t1] = h; e2[t2] = h
-        p0 = base
-        p1 = base + e1
-        p2 = base + e1 + e2
-        p3 = base + e2
-        om = _solid_angle_tri(p0, p1, p2) + _solid_angle_tri(p0, p2, p3)
-        fc = base + 0.5 * (e1 + e2)
-        rc = np.linalg.norm(fc, axis=-1)
-        vel = strength * om / (h * h)
-        vel = np.where(rc < r_cut, 0.0, vel)
-        out.append(np.ascontiguousarray(vel))
+        vel = np.empty(fs)
+        for k0 in range(0, fs[0], 8):  # a few z-planes at a time (bounded temporaries)
+            k1 = min(k0 + 8, fs[0])
+            kk, jj, ii = np.meshgrid(np.arange(k0, k1), np.arange(fs[1]), np.arange(fs[2]), indexing="ij")
+            # low corner of the face in physical coordinates
+            base = np.stack([ii * h, jj * h, kk * h], axis=-1) - c
+            p0 = base
+            p1 = base + e1
+            p2 = base + e1 + e2
+            p3 = base + e2
+            om = _solid_angle_tri(p0, p1, p2) + _solid_angle_tri(p0, p2, p3)
+            fc = base + 0.5 * (e1 + e2)
+            rc = np.linalg.norm(fc, axis=-1)
+            v_ = strength * om / (h * h)
+            vel[k0:k1] = np.where(rc < r_cut, 0.0, v_)
+        out.append(vel)
     if sym:
         u = out[0]
         out.append(np.ascontiguousarray(np.swapaxes(u, 1, 2)))   # v[k][f][i] = u[k][i][f]
