@@ -325,3 +325,38 @@ def deformation_sphere(n=512, nsteps=50, cfl=0.5, nsub=8, seed=3):
     dt = cfl * h / 2.0
     return Workload("deformation-sphere-%d^3" % n, shape, (1, 1, 1), h, Cp_l, Cp_g, 1.0, dt, nsteps, 0.0,
                     c, e, u, v, w)
+
+
+def droplet_subdomain(index, seed=4, n_lo=24, n_hi=96, nsub=6):
+    """Subdomain `index` of the batched droplet workload (many independent
+    periodic boxes): edge N ~ U{n_lo..n_hi}; one sphere or ellipsoid (equal
+    odds), radius / semi-axes ~ U(0.15, 0.35) of the box, random rotation,
+    centre 0.5 +- U(-0.1, 0.1); T = 1 in the liquid, 0 in the gas, heat
+    capacity ratio 1000:1; a uniform velocity with |u| ~ U(0, 1) in a
+    uniform random direction, dt for a face CFL number of 0.25; a uniform
+    shift dd ~ U(-0.02, 0.02).  Each index draws from its own seeded stream,
+    so any subdomain is generated alone, in any order."""
+    rng = np.random.default_rng([seed, index])
+    n = int(rng.integers(n_lo, n_hi + 1))
+    h = 1.0 / n
+    shape = (n, n, n)
+    centre = tuple(0.5 + rng.uniform(-0.1, 0.1, 3))
+    rot, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if rng.random() < 0.5:
+        r = rng.uniform(0.15, 0.35)
+        axes = (r, r, r)
+    else:
+        axes = tuple(rng.uniform(0.15, 0.35, 3))
+    c = ellipsoid_fractions(shape, h, centre, axes, rot=rot, nsub=nsub)
+    Cp_l, Cp_g = 1000.0, 1.0
+    e = Cp_l * c
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    speed = rng.uniform(0.0, 1.0)
+    vel = speed * d
+    u, v, w = uniform_faces(shape, tuple(vel))
+    amax = float(np.abs(vel).max())
+    dt = 0.25 * h / amax if amax > 0 else 0.25 * h
+    dd = float(rng.uniform(-0.02, 0.02))
+    return Workload("droplet-%d-%d^3" % (index, n), shape, (0, 0, 0), h, Cp_l, Cp_g, 1.0, dt, 1, dd,
+                    c, e, u, v, w)
