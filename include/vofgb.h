@@ -337,6 +337,23 @@ VOF_API vof_status vof_heat_diffusion(const vof_grid* g, const double* c, double
                                       void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Checkpoint and resume (host code; the paper has no counterpart): the
+ * grid, the step index, the time and the fields c and e in one
+ * little-endian file -- magic "VOFGBCK1", a fixed header, c[N], e[N], an
+ * FNV-1a 64-bit checksum.  Save writes `path`.tmp and renames it into place.
+ * Info reads the header into *g (and *step, *t when not NULL); load checks
+ * magic, version, sizes (cells must equal the file's N) and checksum, then
+ * copies c and e into the caller's host buffers.
+ *   c, e           host double[N] (cell layout)
+ * VOF_EINVAL for null arguments, an unreadable, truncated, foreign or
+ * corrupted file, or a size mismatch.
+ */
+VOF_API vof_status vof_checkpoint_save(const char* path, const vof_grid* g, const double* c, const double* e,
+                                       long step, double t);
+VOF_API vof_status vof_checkpoint_info(const char* path, vof_grid* g, long* step, double* t);
+VOF_API vof_status vof_checkpoint_load(const char* path, size_t cells, double* c, double* e);
+
+/*
  * A time step that allocates nothing (the paper has no counterpart; this is
  * for callers that cannot allocate device memory when they step -- code in a
  * host callback or an error path where the allocator must not be entered,

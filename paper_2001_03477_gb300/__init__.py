@@ -124,6 +124,13 @@ def lib():
         L.vof_step_workspace_bytes.restype = ctypes.c_size_t
         L.vof_step_work_counts.argtypes = [G, P, ctypes.POINTER(ctypes.c_int), P]
         L.vof_step_work_counts.restype = ctypes.c_int
+        L.vof_checkpoint_save.argtypes = [ctypes.c_char_p, G, P, P, L_, D]
+        L.vof_checkpoint_save.restype = ctypes.c_int
+        L.vof_checkpoint_info.argtypes = [ctypes.c_char_p, G, ctypes.POINTER(ctypes.c_long),
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.vof_checkpoint_info.restype = ctypes.c_int
+        L.vof_checkpoint_load.argtypes = [ctypes.c_char_p, S, P, P]
+        L.vof_checkpoint_load.restype = ctypes.c_int
         L.vof_heat_diffusion_workspace_bytes.argtypes = [G]
         L.vof_heat_diffusion_workspace_bytes.restype = ctypes.c_size_t
         L.vof_velocity_extension_workspace_bytes.argtypes = [G]
@@ -379,6 +386,46 @@ def vof_heat_diffusion(g, c, e, k_l, k_g, dt, tol=1e-10, max_iter=10000, workspa
                                     ctypes.byref(ch), _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes),
                                     _stream(stream)))
     return it.value, ch.value
+
+
+def _host_f64(a, name):
+    """A C-contiguous float64 numpy array of a numpy array or a torch tensor
+    (device tensors are copied to the host)."""
+    import numpy as np
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def vof_checkpoint_save(path, g: Grid, c, e, step=0, t=0.0):
+    """Write (g, step, t, c, e) to `path` (c, e: numpy arrays or torch
+    tensors, device tensors copied to the host)."""
+    cg = g.c_struct()
+    ch, eh = _host_f64(c, "c"), _host_f64(e, "e")
+    if ch.size != g.cells or eh.size != g.cells:
+        raise ValueError("vof_checkpoint_save: c and e must hold one value per cell")
+    _check("vof_checkpoint_save",
+           lib().vof_checkpoint_save(str(path).encode(), ctypes.byref(cg), ch.ctypes.data, eh.ctypes.data,
+                                     int(step), float(t)))
+
+
+def vof_checkpoint_load(path):
+    """(Grid, step, t, c, e) from a checkpoint; c, e as numpy arrays of the
+    grid's (nz, ny, nx) shape."""
+    import numpy as np
+    cg = _CGrid()
+    step = ctypes.c_long(0)
+    t = ctypes.c_double(0.0)
+    _check("vof_checkpoint_info", lib().vof_checkpoint_info(str(path).encode(), ctypes.byref(cg),
+                                                            ctypes.byref(step), ctypes.byref(t)))
+    g = Grid(cg.nx, cg.ny, cg.nz, tuple(cg.bc), cg.h, cg.Cp_l, cg.Cp_g, cg.T_sat, cg.eps_mixed,
+             precision=cg.precision, scheme=cg.scheme)
+    c = np.empty(g.shape)
+    e = np.empty(g.shape)
+    _check("vof_checkpoint_load", lib().vof_checkpoint_load(str(path).encode(), ctypes.c_size_t(g.cells),
+                                                            c.ctypes.data, e.ctypes.data))
+    return g, step.value, t.value, c, e
 
 
 def vof_mass_transfer_work_counts(g, workspace, stream=None):
