@@ -485,6 +485,27 @@ class Stepper:
         self.workspace = torch.empty(nb, dtype=torch.uint8, device=device)
         self.sums = torch.zeros(VOF_NSUMS, dtype=torch.float64, device=device)
 
-    def step(self, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, stream=None):
+    def step(self, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, stream=None, log=None, t=None):
+        """One vof_step; with `log` (a writable text file) also appends the
+        step's JSON-lines record (reads the sums and work counts back, which
+        waits for the step)."""
         vof_step(self.g, c, e, u, v, w, dt, step_index, dd, dd_uniform, self.sums, self.workspace, stream)
+        if log is not None:
+            counts = vof_step_work_counts(self.g, self.workspace, stream)
+            sums = [float(x) for x in self.sums.cpu()]
+            log.write(step_record(step_index, t, sums, counts) + "\n")
         return self.sums
+
+
+def step_record(step_index, t, sums, counts):
+    """One JSON line per step: the six sums of vof_step and its work counts
+    (the run's volume and energy history; the paper reports volume against
+    time)."""
+    import json
+    names = ("sum_c", "sum_e", "clipped", "shift_dc", "shift_unplaced", "shift_de")
+    rec = {"step": int(step_index)}
+    if t is not None:
+        rec["t"] = float(t)
+    rec.update({k: float(v) for k, v in zip(names, sums)})
+    rec.update(counts)
+    return json.dumps(rec, sort_keys=False)

@@ -66,3 +66,14 @@ def test_wrong_field_size_is_refused(P, tmp_path):
     g, c, e = state(P)
     with pytest.raises(ValueError):
         P.vof_checkpoint_save(tmp_path / "x.ckpt", g, c[:2], e)
+
+
+def test_step_record_is_one_json_line(P):
+    import json
+    line = P.step_record(12, 0.5, [1.0, 2.0, -1e-17, -0.25, 0.0, -300.0],
+                         {"mixed": [1, 2, 3], "faces": [4, 5, 6], "shift_analytic": 7, "shift_bisection": 8,
+                          "receivers": 9})
+    assert "\n" not in line
+    rec = json.loads(line)
+    assert rec["step"] == 12 and rec["t"] == 0.5 and rec["sum_e"] == 2.0 and rec["shift_de"] == -300.0
+    assert rec["mixed"] == [1, 2, 3] and rec["receivers"] == 9
