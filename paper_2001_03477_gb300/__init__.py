@@ -2,7 +2,10 @@
 "A Geometric VOF Method for Interface Resolved Phase Change and Conservative
 Thermal Energy Advection" (arXiv:2001.03477): PLIC reconstruction, the
 direction-split geometric VOF sweeps with the thermal energy fluxed in tandem
-(Sec. 3.3.1, 3.4.1) and the phase-change interface shift (Sec. 3.3.2).
+(Sec. 3.3.1, 3.4.1; Weymouth-Yue or Li's Lagrangian-explicit scheme) and the
+phase-change interface shift (Sec. 3.3.2); around it the mass transfer rate
+from PLIC distances (Sec. 3.2), the velocity extension (Sec. 3.3.1), the
+interface-Dirichlet heat diffusion (Sec. 3.4.2), and checkpoint / resume.
 
 This module is a thin ctypes binding over the C ABI in include/vofgb.h
 (libvofgb.so, built in-tree by `build.py`).  It only marshals arguments:
