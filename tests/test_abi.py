@@ -206,3 +206,18 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         P.vof_mass_transfer(g, c, c, 1.0, 1.0, 1.0, c)
     with pytest.raises(RuntimeError):
         P.vof_step_workspace_bytes(g)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_alone(tmp_path, lang, std):
+    """include/vofgb.h is self-contained plain C (usable from C and C++)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("t.c" if lang == "c" else "t.cpp")
+    src.write_text('#include "vofgb.h"\nint main(void) { vof_grid g; (void)g; return (int)VOF_OK; }\n')
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
