@@ -120,3 +120,15 @@ def test_plane_linear_profile_stays_on_gpu(P):
     inner = np.zeros(c.shape, bool)
     inner[3:-3, 4:-4, 4:-4] = True
     assert np.abs(Tg - T)[inner].max() < 1e-9
+
+
+def test_iteration_cap_reports_esolve(P):
+    """A sweep budget too small for the tolerance ends with VOF_ESOLVE (the
+    host reads it; nothing waits without a bound)."""
+    c, T, bc, h, Cpl, Cpg, Ts, kl, kg, dt = case("droplet")
+    nz, ny, nx = c.shape
+    g = P.Grid(nx, ny, nz, bc, h, Cpl, Cpg, Ts)
+    ed = dev((Cpl * c + Cpg * (1 - c)) * T)
+    with pytest.raises(P.VofError) as err:
+        P.vof_heat_diffusion(g, dev(c), ed, kl, kg, dt, tol=1e-300, max_iter=1)
+    assert err.value.status == P.VOF_ESOLVE

@@ -150,3 +150,16 @@ def test_no_free_flow_face_on_gpu(P):
     with pytest.raises(P.VofError):
         P.vof_velocity_extension(g, dev(c), dev(np.where(c == 0.5, 0.01, 0.0)), RHO_L, RHO_G, 1e-3, ut=ut, vt=vt,
                                  wt=wt)
+
+
+def test_iteration_cap_reports_esolve(P):
+    import torch
+    c, mdot, bc, h = case("drop")
+    n = c.shape[0]
+    g = P.Grid(n, n, n, bc, h, 1.0, 1.0, 1.0)
+    ut, vt, wt = (torch.zeros(s, dtype=torch.float64, device="cuda")
+                  for s in ((n, n, n + 1), (n, n + 1, n), (n + 1, n, n)))
+    with pytest.raises(P.VofError) as err:
+        P.vof_velocity_extension(g, dev(c), dev(mdot), RHO_L, RHO_G, 1e-3, tol=1e-300, max_iter=1, ut=ut, vt=vt,
+                                 wt=wt)
+    assert err.value.status == P.VOF_ESOLVE
