@@ -200,8 +200,9 @@ VOF_API vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in,
  * One full time step on the caller's stream: zero the frozen state, three
  * (g->scheme: Weymouth-Yue or Lagrangian-explicit)
  * sweeps in Strang-alternated order (x,y,z on even step_index, z,y,x on odd),
- * then the shift; c and e are updated in place (ping-pong through the
- * workspace, so the result lands back in c and e).
+ * then the shift; c and e are updated in place (every sweep and the shift
+ * read and write them directly; the workspace holds the frozen state, the
+ * per-sweep lists, planes and face fluxes, and the partial sums).
  *   u, v, w        face velocities
  *   dd, dd_uniform as for vof_phase_change_shift
  *   sums           device double[VOF_NSUMS] (nullable), OVERWRITTEN with
@@ -217,6 +218,63 @@ VOF_API size_t vof_step_workspace_bytes(const vof_grid* g);
 VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, const double* v, const double* w,
                     double dt, long step_index, const double* dd, double dd_uniform, double* sums,
                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Many independent subdomains ("boxes") stepped together (the paper steps one
+ * domain; this serves workloads of thousands of small, uneven domains such as
+ * separate droplets).  Each box is one vof_step() on its own grid, arrays and
+ * time step; the boxes are spread over `lanes` streams that run concurrently
+ * and share nothing but the read-only inputs.
+ *
+ * The plan (host only, nothing launched): boxes in decreasing cell count (ties
+ * by index) go one by one to the lane with the fewest cells so far (ties: the
+ * lowest lane); a lane runs its boxes in that order, one after the other,
+ * reusing one step workspace of the largest size its boxes need.
+ *   lane_of_box    host int[nbox]: the lane of each box (written)
+ *   lane_offset    host size_t[lanes]: byte offset of each lane's workspace
+ *                  in the batch workspace (256-byte aligned; written)
+ *   workspace_bytes  host: bytes the batch workspace needs (written)
+ * vof_batched_workspace_bytes() returns the same total (0 for bad boxes).
+ *
+ * vof_batched_step(): records an event on `stream`, makes each lane stream
+ * wait for it, queues each lane's boxes (vof_step with the box's own dt, dd,
+ * dd_uniform and sums + VOF_NSUMS * box), then makes `stream` wait for every
+ * lane.  Work queued on `stream` before the call is therefore complete before
+ * any box starts, and work queued after it sees every box finished; under
+ * stream capture of `stream` the lanes become parallel branches of the graph.
+ *   boxes          host array of nbox vof_box; their c, e, u, v, w, dd device
+ *                  arrays.  c and e of different boxes must not overlap each
+ *                  other or the workspace; u, v, w, dd are read only and may
+ *                  be shared between boxes of the same shape.
+ *   step_index     the step's index (sweep order as vof_step)
+ *   sums           device double[nbox][VOF_NSUMS] (nullable): each box's
+ *                  vof_step sums
+ *   lanes          >= 1; lane_streams: host array of `lanes` cudaStream_t
+ *                  (NULL allowed when lanes == 1: the boxes run on `stream`)
+ *   workspace      device, 256-byte aligned, >= the plan's workspace_bytes
+ * nbox == 0 returns VOF_OK with nothing launched.  Every box is checked
+ * before anything is launched (VOF_EINVAL for a bad grid, null array, dt < 0,
+ * overlapping c/e arrays, a short or misaligned workspace); a CUDA failure
+ * returns VOF_ECUDA after the lanes have been joined back into `stream`.
+ * Events are created and destroyed inside the call; the lanes' streams must
+ * not be used by other work while the call's work runs.
+ */
+typedef struct {
+  vof_grid grid;
+  double* c;                      /* device [N] */
+  double* e;                      /* device [N] */
+  const double* u, *v, *w;        /* device face arrays of the box */
+  double dt;
+  const double* dd;               /* device [N], nullable */
+  double dd_uniform;
+} vof_box;
+
+VOF_API vof_status vof_batched_plan(const vof_box* boxes, int nbox, int lanes, int* lane_of_box, size_t* lane_offset,
+                                    size_t* workspace_bytes);
+VOF_API size_t vof_batched_workspace_bytes(const vof_box* boxes, int nbox, int lanes);
+VOF_API vof_status vof_batched_step(const vof_box* boxes, int nbox, long step_index, double* sums, int lanes,
+                                    void* const* lane_streams, void* workspace, size_t workspace_bytes,
+                                    void* stream);
 
 /*
  * Mass transfer rate from PLIC interface distances (Sec. 3.2, "Calculating

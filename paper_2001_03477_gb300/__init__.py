@@ -5,7 +5,9 @@ direction-split geometric VOF sweeps with the thermal energy fluxed in tandem
 (Sec. 3.3.1, 3.4.1; Weymouth-Yue or Li's Lagrangian-explicit scheme) and the
 phase-change interface shift (Sec. 3.3.2); around it the mass transfer rate
 from PLIC distances (Sec. 3.2), the velocity extension (Sec. 3.3.1), the
-interface-Dirichlet heat diffusion (Sec. 3.4.2), and checkpoint / resume.
+interface-Dirichlet heat diffusion (Sec. 3.4.2), many independent
+subdomains stepped together on concurrent streams (vof_batched_step,
+BoxBatch), and checkpoint / resume.
 
 This module is a thin ctypes binding over the C ABI in include/vofgb.h
 (libvofgb.so, built in-tree by `build.py`).  It only marshals arguments:
@@ -43,6 +45,12 @@ class _CGrid(ctypes.Structure):
                 ("h", ctypes.c_double), ("Cp_l", ctypes.c_double), ("Cp_g", ctypes.c_double),
                 ("T_sat", ctypes.c_double), ("eps_mixed", ctypes.c_double), ("precision", ctypes.c_int),
                 ("scheme", ctypes.c_int)]
+
+
+class _CBox(ctypes.Structure):
+    _fields_ = [("grid", _CGrid), ("c", ctypes.c_void_p), ("e", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("dt", ctypes.c_double), ("dd", ctypes.c_void_p),
+                ("dd_uniform", ctypes.c_double)]
 
 
 @dataclass
@@ -115,6 +123,14 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        B = ctypes.POINTER(_CBox)
+        L.vof_batched_plan.argtypes = [B, I, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+        L.vof_batched_plan.restype = ctypes.c_int
+        L.vof_batched_workspace_bytes.argtypes = [B, I, I]
+        L.vof_batched_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_batched_step.argtypes = [B, I, L_, P, I, ctypes.POINTER(ctypes.c_void_p), P, S, P]
+        L.vof_batched_step.restype = ctypes.c_int
         L.vof_step_noalloc.argtypes = [G, P, P, P, P, P, D, L_, P, D, P, P]
         L.vof_step_noalloc.restype = ctypes.c_int
         L.vof_noalloc_scratch_bytes.argtypes = []
@@ -498,6 +514,142 @@ class Stepper:
             sums = [float(x) for x in self.sums.cpu()]
             log.write(step_record(step_index, t, sums, counts) + "\n")
         return self.sums
+
+
+@dataclass
+class Box:
+    """One subdomain of a batch (vof_box): its grid, fields c, e (float64,
+    updated in place), face velocities u, v, w, time step and shift."""
+    grid: Grid
+    c: object
+    e: object
+    u: object
+    v: object
+    w: object
+    dt: float
+    dd: object = None
+    dd_uniform: float = 0.0
+
+
+def _box_array(boxes, with_arrays=True):
+    arr = (_CBox * max(len(boxes), 1))()
+    for i, b in enumerate(boxes):
+        g = b.grid if isinstance(b, Box) else b
+        arr[i].grid = g.c_struct()
+        if with_arrays:
+            arr[i].c = _ptr(b.c, _f64(), "c")
+            arr[i].e = _ptr(b.e, _f64(), "e")
+            arr[i].u = _ptr(b.u, _f64(), "u")
+            arr[i].v = _ptr(b.v, _f64(), "v")
+            arr[i].w = _ptr(b.w, _f64(), "w")
+            arr[i].dt = float(b.dt)
+            arr[i].dd = _ptr(b.dd, _f64(), "dd")
+            arr[i].dd_uniform = float(b.dd_uniform)
+    return arr
+
+
+def vof_batched_plan(grids, lanes):
+    """Host-only plan of a batch (nothing launched): (lane of each box,
+    workspace offset of each lane, total workspace bytes).  `grids`: Grid or
+    Box objects."""
+    arr = _box_array(grids, with_arrays=False)
+    lane = (ctypes.c_int * max(len(grids), 1))()
+    off = (ctypes.c_size_t * max(int(lanes), 1))()
+    total = ctypes.c_size_t(0)
+    _check("vof_batched_plan", lib().vof_batched_plan(arr, len(grids), int(lanes), lane, off, ctypes.byref(total)))
+    return list(lane)[:len(grids)], list(off)[:int(lanes)], int(total.value)
+
+
+def vof_batched_workspace_bytes(grids, lanes) -> int:
+    arr = _box_array(grids, with_arrays=False)
+    return int(lib().vof_batched_workspace_bytes(arr, len(grids), int(lanes)))
+
+
+def vof_batched_step(boxes, step_index, sums=None, lanes=1, lane_streams=None, workspace=None, stream=None,
+                     _arr=None):
+    """One vof_step of every box, the boxes spread over `lanes` streams
+    (`lane_streams`: torch.cuda.Stream objects; None with lanes == 1 runs them
+    on `stream`).  sums: float64 [len(boxes), VOF_NSUMS] or None."""
+    arr = _arr if _arr is not None else _box_array(boxes)
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ls = None
+    if lane_streams is not None:
+        if len(lane_streams) != int(lanes):
+            raise ValueError(f"vof_batched_step: {len(lane_streams)} lane streams for {lanes} lanes")
+        ls = (ctypes.c_void_p * len(lane_streams))(*[s.cuda_stream for s in lane_streams])
+    _check("vof_batched_step",
+           lib().vof_batched_step(arr, len(boxes), int(step_index), _ptr(sums, _f64(), "sums"), int(lanes), ls,
+                                  _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes), _stream(stream)))
+
+
+def pick_fastest(measure, candidates):
+    """The autotuner's choice: the candidate with the smallest measure(c)
+    (seconds per step); ties go to the earlier candidate."""
+    best, best_t = None, None
+    for cand in candidates:
+        t = float(measure(cand))
+        if best_t is None or t < best_t:
+            best, best_t = cand, t
+    return best
+
+
+class BoxBatch:
+    """A batch of boxes with its lane streams and workspace (allocated
+    through torch).  `autotune()` picks the number of lanes by timing steps
+    of a copy of (a sample of) the boxes; `step()` runs vof_batched_step."""
+
+    def __init__(self, boxes, lanes=8, device="cuda"):
+        import torch
+        self.boxes = list(boxes)
+        self.device = device
+        self._arr = _box_array(self.boxes)
+        self.sums = torch.zeros((max(len(self.boxes), 1), VOF_NSUMS), dtype=torch.float64, device=device)
+        self.set_lanes(lanes)
+
+    def set_lanes(self, lanes):
+        import torch
+        self.lanes = int(lanes)
+        self.lane_streams = [torch.cuda.Stream(device=self.device) for _ in range(self.lanes)]
+        nb = vof_batched_workspace_bytes(self.boxes, self.lanes)
+        if nb == 0 and self.boxes:
+            raise VofError("vof_batched_workspace_bytes", VOF_EINVAL, lib())
+        self.workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=self.device)
+
+    def step(self, step_index, stream=None):
+        vof_batched_step(self.boxes, step_index, self.sums if self.boxes else None, self.lanes, self.lane_streams,
+                         self.workspace, stream, _arr=self._arr)
+        return self.sums
+
+    def autotune(self, candidates=(1, 2, 4, 8, 16, 32), sample=None, steps=3, warmup=1):
+        """Time `steps` batched steps of a copy of the first `sample` boxes
+        (all by default; fields cloned, velocities shared) for each lane
+        count with CUDA events; keep the fastest."""
+        import torch
+        src = self.boxes if sample is None else self.boxes[:int(sample)]
+        copy = [Box(b.grid, b.c.clone(), b.e.clone(), b.u, b.v, b.w, b.dt, b.dd, b.dd_uniform) for b in src]
+
+        def measure(lanes):
+            trial = BoxBatch(copy, lanes, self.device)
+            for k in range(warmup):
+                trial.step(k)
+            s = torch.cuda.current_stream()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0.record(s)
+            for k in range(steps):
+                trial.step(warmup + k)
+            t1.record(s)
+            torch.cuda.synchronize()
+            return t0.elapsed_time(t1) / 1e3 / steps
+
+        self.timings = {}
+
+        def timed(lanes):
+            self.timings[lanes] = measure(lanes)
+            return self.timings[lanes]
+
+        self.set_lanes(pick_fastest(timed, candidates))
+        return self.lanes
 
 
 def step_record(step_index, t, sums, counts):

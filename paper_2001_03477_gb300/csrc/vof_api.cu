@@ -12,6 +12,8 @@ __device__ int g_vof_status;
 
 static thread_local int t_last_cuda = 0;
 
+void set_last_cuda_error(int err) { t_last_cuda = err; }
+
 int* device_status_ptr() {
   static std::mutex mu;
   static int* ptrs[64] = {nullptr};

@@ -168,6 +168,10 @@ cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cu
 // per-launch timing (vof_profile_begin/end): records an event after a launch
 void prof_mark(const char* name, cudaStream_t st);
 
+// records the cudaError_t that vof_last_cuda_error() reports (for entry
+// points outside vof_api.cu that return VOF_ECUDA)
+void set_last_cuda_error(int err);
+
 // sticky device status word (iteration caps, CFL > 1): bit flags
 enum : int { DEV_CFL = 1 };
 int* device_status_ptr();
