@@ -11,6 +11,10 @@ gradients and the MYC fallback, against what the mathematics fixes (CPU).
 * Plane residual: zero for a plane stencil and its own normal, above the
   1e-3 fallback threshold for a normal 5 degrees off; an untrained network
   therefore falls back to MYC on planes.
+* Fallback bound (1.25 x MYC's residual + 1e-3): a fixed 1e-3 alone rejects
+  the exact normal on nearly every curved stencil; the bound accepts the
+  exact normal on curved stencils, rejects most normals 45 degrees off, and
+  keeps MYC's exact plane wherever MYC fits a plane stencil exactly.
 * Adam on a few hundred stencils lowers the loss several-fold.
 """
 import math
@@ -117,3 +121,50 @@ def test_training_lowers_the_loss():
     l1, _ = M.loss_and_grad(p, X, Y)
     assert l1 < 0.2 * l0
     assert hist[-1] < hist[0]
+
+
+def _tilted(n, deg, rng):
+    axis = np.cross(n, rng.normal(size=3))
+    axis /= np.linalg.norm(axis)
+    a = math.radians(deg)
+    return n * math.cos(a) + np.cross(axis, n) * math.sin(a)
+
+
+def test_fallback_bound_on_curved_stencils():
+    rng = np.random.default_rng(7)
+    X, Y = M.dataset(240, rng, kinds=("sphere", "ellipsoid"))
+    over_fixed = accepted_exact = accepted_far = 0
+    for s, n in zip(X, Y):
+        r_exact = M.plane_residual(s, n)
+        over_fixed += r_exact > 1e-3
+        bound = M.accept_bound(s)
+        accepted_exact += r_exact <= bound
+        accepted_far += M.plane_residual(s, _tilted(n, 45.0, rng)) <= bound
+    N = len(X)
+    assert over_fixed >= 0.95 * N      # a fixed 1e-3 would reject the exact normal
+    assert accepted_exact >= 0.98 * N  # the bound keeps it
+    assert accepted_far <= 0.10 * N    # and rejects most normals 45 degrees off
+
+
+def test_fallback_keeps_myc_where_it_is_exact():
+    rng = np.random.default_rng(8)
+    p = M.init_params(rng)
+    checked = 0
+    for _ in range(60):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        s = M.plane_stencil(n, rng.uniform(-0.3, 0.3) * np.abs(n).sum())
+        if not 1e-6 < s[13] < 1 - 1e-6:
+            continue
+        m_myc = O.myc(s.reshape(3, 3, 3))
+        if M.plane_residual(s, m_myc) > 1e-13:
+            continue  # MYC is exact only where the columns span the plane
+        checked += 1
+        assert M.plane_residual(s, _tilted(n, 0.5, rng)) > M.accept_bound(s)
+        # a network whose output is that slightly tilted normal falls back
+        q = {k: v.copy() for k, v in p.items()}
+        q["W3"][:] = 0.0
+        q["b3"][:] = _tilted(n, 0.5, rng)
+        m, fell = M.learned_normal(q, s, weights=lambda w: w)
+        assert fell and np.array_equal(m, m_myc)
+    assert checked >= 15
