@@ -11,7 +11,11 @@ Cases (Sec. 4 of Malan et al.):
   * translating sphere with T = 1 in the liquid (periodic box),
   * vapour bubble in superheated liquid (Sec. 4.4), radial liquid velocity
     built from exact face solid angles (discretely divergence free),
-  * deformation field (LeVeque) with exact face averages.
+  * deformation field (LeVeque) with exact face averages,
+  * many small periodic droplet boxes (batched form),
+  * training stencils of the learned normal: 3 x 3 x 3 fractions around
+    spheres, ellipsoids and planes with the unit normal at the nearest
+    surface point as label.
 
 Water / steam data are those of Table atm_water (Sec. 4.3).
 """
@@ -360,3 +364,183 @@ def droplet_subdomain(index, seed=4, n_lo=24, n_hi=96, nsub=6):
     dd = float(rng.uniform(-0.02, 0.02))
     return Workload("droplet-%d-%d^3" % (index, n), shape, (0, 0, 0), h, Cp_l, Cp_g, 1.0, dt, 1, dd,
                     c, e, u, v, w)
+
+
+# ---------------------------------------------------------------------------
+# Training stencils for the learned interface normal
+# ---------------------------------------------------------------------------
+
+# offsets of the 27 cells of a stencil, index (dz*3+dy)*3+dx with dx, dy, dz
+# in {0, 1, 2} for offsets -1, 0, 1 (x fastest)
+_STENCIL = np.array([[dx, dy, dz] for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)], dtype=float)
+
+
+def _curved_params(rng, kind):
+    if kind == "sphere":
+        axes = np.full(3, math.exp(rng.uniform(0.0, math.log(50.0))))
+    else:
+        axes = np.exp(rng.uniform(0.0, math.log(50.0), 3))
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    R = q * np.sign(np.linalg.det(q))
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    p_local = u / np.sqrt(np.sum(u * u / axes ** 2))  # a point of the surface
+    centre = -(R @ p_local) + rng.uniform(-0.5, 0.5, 3)
+    inside = 1.0 if rng.random() < 0.5 else 0.0
+    return axes, R, centre, inside
+
+
+def _plane_params(rng):
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    d = rng.uniform(-0.4, 0.4) * np.abs(n).sum()
+    return n, d
+
+
+def nearest_on_ellipsoids(axes, y, iters=200):
+    """Points of the ellipsoids sum x_i^2 / a_i^2 = 1 (principal frames,
+    axes [K, 3]) nearest to the points y [K, 3]: x_i = a_i^2 y_i / (a_i^2 +
+    t) with t the root of sum (a_i y_i / (a_i^2 + t))^2 = 1 on t > -min
+    a_i^2, by bisection (the sum decreases in t there)."""
+    a2 = np.asarray(axes, dtype=float) ** 2
+    y = np.asarray(y, dtype=float)
+    f = lambda t: np.sum(a2 * y * y / (a2 + t[:, None]) ** 2, axis=1) - 1.0
+    lo = -a2.min(axis=1) + 1e-12 * a2.min(axis=1)
+    hi = np.sqrt(a2).max(axis=1) * np.abs(y).max(axis=1) * 2.0 + a2.max(axis=1)
+    for _ in range(64):
+        grow = f(hi) > 0
+        if not grow.any():
+            break
+        hi = np.where(grow, hi * 2.0, hi)
+    degenerate = f(lo) < 0  # y at the centre along the shortest axis: take lo
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        pos = f(mid) > 0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+    t = np.where(degenerate, lo, 0.5 * (lo + hi))
+    return a2 * y / (a2 + t[:, None])
+
+
+def _curved_fractions(axes, R, centre, inside, nsub, chunk=96):
+    """[K, 27] volume fractions of the stencils' cells (unit cells centred
+    on the offsets) for ellipsoids {(x - c)^T Q (x - c) <= 1}, Q = R
+    diag(1/a^2) R^T, by chord integration along x on an nsub x nsub
+    midpoint rule (a few stencils at a time: small temporaries)."""
+    if len(axes) > chunk:
+        return np.concatenate([_curved_fractions(axes[s:s + chunk], R[s:s + chunk], centre[s:s + chunk],
+                                                 inside[s:s + chunk], nsub, chunk)
+                               for s in range(0, len(axes), chunk)])
+    Q = np.einsum("kij,kj,klj->kil", R, 1.0 / axes ** 2, R)
+    t = (np.arange(nsub) + 0.5) / nsub - 0.5
+    o = _STENCIL[None, :, :]
+    c = centre[:, None, :]
+    ys = (o[..., 1] - c[..., 1])[..., None, None] + t[None, None, :, None]
+    zs = (o[..., 2] - c[..., 2])[..., None, None] + t[None, None, None, :]
+    ys, zs = np.broadcast_arrays(ys, zs)
+    q = lambda a, b: Q[:, a, b][:, None, None, None]
+    b = q(0, 1) * ys + q(0, 2) * zs
+    cc = q(1, 1) * ys * ys + 2.0 * q(1, 2) * ys * zs + q(2, 2) * zs * zs - 1.0
+    disc = b * b - q(0, 0) * cc
+    sq = np.sqrt(np.clip(disc, 0.0, None))
+    x0 = (-b - sq) / q(0, 0)
+    x1 = (-b + sq) / q(0, 0)
+    empty = disc < 0.0
+    x0 = np.where(empty, 1.0, x0) + c[..., 0][..., None, None]
+    x1 = np.where(empty, 0.0, x1) + c[..., 0][..., None, None]
+    lo = (o[..., 0] - 0.5)[..., None, None]
+    ln = np.clip(np.minimum(x1, lo + 1.0) - np.maximum(x0, lo), 0.0, None)
+    frac = np.clip(ln.mean(axis=(-1, -2)), 0.0, 1.0)
+    return np.where(inside[:, None] == 1.0, frac, 1.0 - frac)
+
+
+def _plane_fractions(n, d, nsub, chunk=96):
+    """[K, 27] volume fractions of {x : n . x <= d} by chord integration
+    along each plane's dominant axis (where the chord is linear in the other
+    two coordinates) on an nsub x nsub midpoint rule."""
+    if len(n) > chunk:
+        return np.concatenate([_plane_fractions(n[s:s + chunk], d[s:s + chunk], nsub, chunk)
+                               for s in range(0, len(n), chunk)])
+    K = n.shape[0]
+    a = np.argmax(np.abs(n), axis=1)
+    others = np.array([[1, 2], [0, 2], [0, 1]])[a]
+    ar = np.arange(K)
+    na = n[ar, a][:, None, None, None]
+    nb = n[ar, others[:, 0]][:, None, None, None]
+    nc = n[ar, others[:, 1]][:, None, None, None]
+    oa = _STENCIL[:, a].T[:, :, None, None]
+    ob = _STENCIL[:, others[:, 0]].T[:, :, None, None]
+    oc = _STENCIL[:, others[:, 1]].T[:, :, None, None]
+    t = (np.arange(nsub) + 0.5) / nsub - 0.5
+    xb = ob + t[None, None, :, None]
+    xc = oc + t[None, None, None, :]
+    bound = (d[:, None, None, None] - nb * xb - nc * xc) / na  # n_a x_a <= ... on the dominant axis
+    lo = oa - 0.5
+    below = np.clip(bound - lo, 0.0, 1.0)  # length of {x_a <= bound} in the cell
+    ln = np.where(na > 0, below, 1.0 - below)
+    return np.clip(ln.mean(axis=(-1, -2)), 0.0, 1.0)
+
+
+def _training_batch(kinds_i, rngs, nsub):
+    K = len(kinds_i)
+    X = np.zeros((K, 27))
+    Y = np.zeros((K, 3))
+    curved = [k for k in range(K) if kinds_i[k] != "plane"]
+    planes = [k for k in range(K) if kinds_i[k] == "plane"]
+    if curved:
+        ps = [_curved_params(rngs[k], kinds_i[k]) for k in curved]
+        axes = np.array([p[0] for p in ps])
+        R = np.array([p[1] for p in ps])
+        centre = np.array([p[2] for p in ps])
+        inside = np.array([p[3] for p in ps])
+        X[curved] = _curved_fractions(axes, R, centre, inside, nsub)
+        yp = np.einsum("kji,kj->ki", R, -centre)  # the stencil centre in each principal frame
+        xn = nearest_on_ellipsoids(axes, yp)
+        g = np.einsum("kij,kj->ki", R, xn / axes ** 2)  # outward normal direction
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        Y[curved] = np.where(inside[:, None] == 1.0, g, -g)
+    if planes:
+        ps = [_plane_params(rngs[k]) for k in planes]
+        n = np.array([p[0] for p in ps])
+        d = np.array([p[1] for p in ps])
+        X[planes] = _plane_fractions(n, d, nsub)
+        Y[planes] = n
+    return X, Y
+
+
+def training_stencils(count, seed=50, start=0, kinds=("sphere", "ellipsoid", "plane"), nsub=12, batch=2048):
+    """Training stencils of the learned interface normal: (X [count, 27]
+    volume fractions of the 3 x 3 x 3 block around a mixed cell, Y [count,
+    3] unit normals, liquid -> gas, at the surface point nearest the
+    central cell's centre).  Sample i (global index start + i) has kind
+    kinds[i % len(kinds)] and draws from its own stream, so any range is
+    generated alone, in any order:
+      * sphere: radius log-uniform in [1, 50] cells; ellipsoid: semi-axes
+        log-uniform in [1, 50]; random rotation; the surface passes within
+        half a cell (per axis) of the central cell's centre; liquid inside
+        or outside with equal odds;
+      * plane: uniform normal, offset U(-0.4, 0.4) |n|_1 from the central
+        cell's centre;
+    redrawn until the central cell is mixed (1e-6 < c < 1 - 1e-6).  Volume
+    fractions by chord integration on an nsub x nsub midpoint rule (curved
+    shapes along x, planes along their dominant axis)."""
+    X = np.zeros((count, 27))
+    Y = np.zeros((count, 3))
+    for s in range(0, count, batch):
+        idx = list(range(s, min(s + batch, count)))
+        rngs = [np.random.default_rng([seed, start + i]) for i in idx]
+        kinds_i = [kinds[(start + i) % len(kinds)] for i in idx]
+        todo = list(range(len(idx)))
+        for _ in range(1000):
+            if not todo:
+                break
+            xb, yb = _training_batch([kinds_i[k] for k in todo], [rngs[k] for k in todo], nsub)
+            ok = (xb[:, 13] > 1e-6) & (xb[:, 13] < 1 - 1e-6)
+            for j, k in enumerate(todo):
+                if ok[j]:
+                    X[idx[k]] = xb[j]
+                    Y[idx[k]] = yb[j]
+            todo = [k for j, k in enumerate(todo) if not ok[j]]
+        if todo:
+            raise RuntimeError("no stencil with a mixed central cell")
+    return X, Y
