@@ -74,11 +74,16 @@ struct Span {
   const char* hi;
 };
 
-// true when two of the spans overlap
+// true when two of the spans overlap: in order of their starts, a span
+// overlaps an earlier one exactly when it starts before the furthest end
+// seen so far
 bool any_overlap(std::vector<Span>& s) {
   std::sort(s.begin(), s.end(), [](const Span& a, const Span& b) { return a.lo < b.lo; });
-  for (size_t i = 1; i < s.size(); ++i)
-    if (s[i].lo < s[i - 1].hi) return true;
+  const char* reach = nullptr;
+  for (size_t i = 0; i < s.size(); ++i) {
+    if (i > 0 && s[i].lo < reach) return true;
+    if (i == 0 || s[i].hi > reach) reach = s[i].hi;
+  }
   return false;
 }
 

@@ -119,6 +119,16 @@ def test_step_checks_before_launch(lib):
     bad, _ = _boxes(grids)
     bad[2].c = bad[0].e + 64
     assert call(a=bad) == P.VOF_EINVAL
+    # one box's c covering several other arrays
+    bad, _ = _boxes(grids)
+    bad[2].c = bad[0].c  # 16^3 doubles from box 0's c cover box 0's e and box 1's c
+    assert call(a=bad) == P.VOF_EINVAL
+    big = P.Grid(40, 40, 40)
+    arr3, _ = _boxes([grids[0], grids[1], big])
+    arr3[2].c = arr3[0].c - 4096 * 8  # starts before every other array and ends past box 1's e
+    arr3[2].e = arr3[1].e + (1 << 30)
+    assert lib.vof_batched_step(arr3, 3, 0, nul, 2, streams, ws, S(P.vof_batched_workspace_bytes(
+        [grids[0], grids[1], big], 2)), nul) == P.VOF_EINVAL
     bad, _ = _boxes(grids)
     bad[1].u = None
     assert call(a=bad) == P.VOF_EINVAL
