@@ -238,12 +238,16 @@ def _cached_workspace(nb, device):
 
 
 def sweep_workspace(g: Grid, device=None):
-    """A cached scratch buffer (torch allocation) for the stand-alone sweeps."""
+    """A cached scratch buffer (torch allocation) for the stand-alone sweeps.
+    It is the one buffer of its size on the device, shared by every sweep or
+    shift call that omits `workspace`: calls that may overlap on the GPU
+    (different streams) must pass workspaces of their own."""
     return _cached_workspace(vof_sweep_workspace_bytes(g), device)
 
 
 def shift_workspace(g: Grid, device=None):
-    """A cached scratch buffer (torch allocation) for the stand-alone shift."""
+    """A cached scratch buffer (torch allocation) for the stand-alone shift,
+    shared like sweep_workspace()."""
     return _cached_workspace(vof_shift_workspace_bytes(g), device)
 
 
