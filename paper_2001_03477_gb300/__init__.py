@@ -187,6 +187,22 @@ def _ptr(t, dtype=None, name="tensor"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _faces(g, axis):
+    a, b, c = g.face_shape(axis)
+    return a * b * c
+
+
+def _sizes(*needs):
+    """Refuse, before anything reaches the library, a tensor with fewer
+    elements than the call reads or writes through it: needs are (tensor or
+    None, elements, argument name).  The C ABI takes bare device pointers and
+    cannot see array sizes, so a short array would be accessed out of range
+    on the GPU."""
+    for t, n, name in needs:
+        if t is not None and hasattr(t, "numel") and t.numel() < n:
+            raise ValueError(f"{name}: {t.numel()} elements, the call needs {n}")
+
+
 def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -209,6 +225,8 @@ def _u8():
 
 
 def vof_reconstruct(g: Grid, c, m, alpha, mixed, stream=None):
+    N = g.cells
+    _sizes((c, N, "c"), (m, 3 * N, "m"), (alpha, N, "alpha"), (mixed, N, "mixed"))
     cg = g.c_struct()
     _check("vof_reconstruct", lib().vof_reconstruct(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(m, _f64(), "m"),
                                                     _ptr(alpha, _f64(), "alpha"), _ptr(mixed, _u8(), "mixed"),
@@ -252,6 +270,9 @@ def shift_workspace(g: Grid, device=None):
 
 
 def _sweep(name, g, c_in, e_in, c_out, e_out, uf, dt, state, theta, flux_out, diag, workspace, stream):
+    N, Fa = g.cells, _faces(g, "xyz".index(name[-1]))
+    _sizes((c_in, N, "c_in"), (e_in, N, "e_in"), (c_out, N, "c_out"), (e_out, N, "e_out"), (uf, Fa, "face"),
+           (state, N, "state"), (theta, N, "theta"), (flux_out, Fa, "flux_out"), (diag, 1, "diag"))
     cg = g.c_struct()
     fn = getattr(lib(), name)
     if workspace is None:
@@ -287,6 +308,11 @@ SWEEPS = (vof_advect_sweep_x, vof_advect_sweep_y, vof_advect_sweep_z)
 
 def energy_advect_consistent(g, axis, c_before, c_after, e_in, e_out, flux_F, u_face, dt, state=None, theta=None,
                              stream=None):
+    N = g.cells
+    if int(axis) in (0, 1, 2):
+        Fa = _faces(g, int(axis))
+        _sizes((c_before, N, "c_before"), (c_after, N, "c_after"), (e_in, N, "e_in"), (e_out, N, "e_out"),
+               (flux_F, Fa, "flux_F"), (u_face, Fa, "u_face"), (state, N, "state"), (theta, N, "theta"))
     cg = g.c_struct()
     _check("energy_advect_consistent",
            lib().energy_advect_consistent(ctypes.byref(cg), int(axis), _ptr(c_before, _f64(), "c_before"),
@@ -298,6 +324,9 @@ def energy_advect_consistent(g, axis, c_before, c_after, e_in, e_out, flux_F, u_
 
 def vof_phase_change_shift(g, c_in, e_in, c_out, e_out, dd=None, dd_uniform=0.0, state=None, diag=None,
                            workspace=None, stream=None):
+    N = g.cells
+    _sizes((c_in, N, "c_in"), (e_in, N, "e_in"), (c_out, N, "c_out"), (e_out, N, "e_out"), (dd, N, "dd"),
+           (state, N, "state"), (diag, 5, "diag"))
     cg = g.c_struct()
     if workspace is None:
         workspace = shift_workspace(g, c_in.device)
@@ -315,7 +344,14 @@ def vof_step_workspace_bytes(g: Grid) -> int:
     return int(lib().vof_step_workspace_bytes(ctypes.byref(cg)))
 
 
+def _step_sizes(g, c, e, u, v, w, dd, sums):
+    N = g.cells
+    _sizes((c, N, "c"), (e, N, "e"), (u, _faces(g, 0), "u"), (v, _faces(g, 1), "v"), (w, _faces(g, 2), "w"),
+           (dd, N, "dd"), (sums, VOF_NSUMS, "sums"))
+
+
 def vof_step(g, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, sums=None, workspace=None, stream=None):
+    _step_sizes(g, c, e, u, v, w, dd, sums)
     cg = g.c_struct()
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("vof_step",
@@ -331,6 +367,7 @@ def vof_step_noalloc(g, c, e, u, v, w, dt, step_index, dd=None, dd_uniform=0.0, 
     (grids up to VOF_NOALLOC_MAX_CELLS = 64^3 cells).  Calls that overlap on
     the GPU share that array and race; the first call on a device must come
     before any stream capture on it."""
+    _step_sizes(g, c, e, u, v, w, dd, sums)
     cg = g.c_struct()
     _check("vof_step_noalloc",
            lib().vof_step_noalloc(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(e, _f64(), "e"),
@@ -351,6 +388,9 @@ def vof_mass_transfer(g, c, e, k_l, k_g, h_fg, mdot, d_gamma=None, grad_n=None, 
                       workspace=None, stream=None):
     """Mass transfer rate from PLIC interface distances (Sec. 3.2) into
     `mdot` (and the optional per-cell distances, gradients and shift)."""
+    N = g.cells
+    _sizes((c, N, "c"), (e, N, "e"), (mdot, N, "mdot"), (d_gamma, N, "d_gamma"), (grad_n, N, "grad_n"),
+           (dd, N, "dd"))
     cg = g.c_struct()
     if workspace is None:
         workspace = _cached_workspace(vof_mass_transfer_workspace_bytes(g), c.device)
@@ -373,6 +413,9 @@ def vof_velocity_extension(g, c, mdot, rho_l, rho_g, dt, tol=1e-13, max_iter=200
     """Velocity extension across the interface (Sec. 3.3.1): adds u~ to
     (u, v, w) and/or writes it to (ut, vt, wt).  Returns (CG iterations,
     final residual norm)."""
+    F = [_faces(g, a) for a in range(3)]
+    _sizes((c, g.cells, "c"), (mdot, g.cells, "mdot"), (u, F[0], "u"), (v, F[1], "v"), (w, F[2], "w"),
+           (ut, F[0], "ut"), (vt, F[1], "vt"), (wt, F[2], "wt"))
     cg = g.c_struct()
     if workspace is None:
         workspace = _cached_workspace(vof_velocity_extension_workspace_bytes(g), c.device)
@@ -397,6 +440,7 @@ def vof_heat_diffusion_workspace_bytes(g: Grid) -> int:
 def vof_heat_diffusion(g, c, e, k_l, k_g, dt, tol=1e-10, max_iter=10000, workspace=None, stream=None):
     """Implicit interface-Dirichlet heat diffusion (Sec. 3.4.2) of e in
     place.  Returns (Jacobi sweeps, last sweep's largest change of T)."""
+    _sizes((c, g.cells, "c"), (e, g.cells, "e"))
     cg = g.c_struct()
     if workspace is None:
         workspace = _cached_workspace(vof_heat_diffusion_workspace_bytes(g), c.device)
@@ -541,6 +585,7 @@ def _box_array(boxes, with_arrays=True):
         g = b.grid if isinstance(b, Box) else b
         arr[i].grid = g.c_struct()
         if with_arrays:
+            _step_sizes(g, b.c, b.e, b.u, b.v, b.w, b.dd, None)
             arr[i].c = _ptr(b.c, _f64(), "c")
             arr[i].e = _ptr(b.e, _f64(), "e")
             arr[i].u = _ptr(b.u, _f64(), "u")
@@ -575,6 +620,7 @@ def vof_batched_step(boxes, step_index, sums=None, lanes=1, lane_streams=None, w
     (`lane_streams`: torch.cuda.Stream objects; None with lanes == 1 runs them
     on `stream`).  sums: float64 [len(boxes), VOF_NSUMS] or None."""
     arr = _arr if _arr is not None else _box_array(boxes)
+    _sizes((sums, len(boxes) * VOF_NSUMS, "sums"))
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     ls = None
     if lane_streams is not None:
