@@ -30,7 +30,22 @@ What it computes (readings of the paper's 2D description, in 3D):
   * zero-gradient walls carry no heat flux (a ghost node at the same T);
     periodic axes wrap;
   * backward Euler: C_p(c) (T^{n+1} - T^n) / dt = k_p sum_axes L_axis(T^{n+1})
-    with T^n = e / C_p(c), and e^{n+1} = C_p(c) T^{n+1}.
+    with T^n = e / C_p(c), and e^{n+1} = C_p(c) T^{n+1}
+    (heat_capacity="mixture", the reading the GPU kernel follows);
+  * heat_capacity="phase": the other reading of the phase-by-phase solve
+    with constant properties in each phase: every node diffuses with the
+    constant C_p of its phase, C_p,node (T^{n+1} - T^n) / dt = k_p sum L,
+    and the cell's energy changes by the heat conducted into it,
+    e^{n+1} = e^n + C_p,node (T^{n+1} - T^n).  Pure cells are unchanged by
+    the choice; in a mixed cell the node's temperature follows its phase
+    instead of being held by the mixture's heat capacity (a gas node in a
+    half-liquid cell has ~1600 times the gas heat capacity under
+    "mixture").  With it the coupled Stefan loop reproduces the paper's
+    Table stefan_errors (tests/test_oracle_stefan.py);
+  * wall_T (optional): {(axis, side): T_w} makes the low (side -1) or high
+    (side +1) boundary of a zero-gradient axis a wall at fixed temperature,
+    the node half a cell from it: gradient (T_w - T) / (h / 2), d = h / 2
+    (the heated wall of the Stefan problem, Sec. 4.3).
 """
 from __future__ import annotations
 
@@ -112,13 +127,13 @@ def interface_distance(g: Grid, c, m, al, P, axis, s):
     return min(max(theta, THETA_EPS), 1.0)
 
 
-def diffusion_operator(g: Grid, c, T, k_l, k_g):
+def diffusion_operator(g: Grid, c, T, k_l, k_g, wall_T=None):
     """k_p sum_axes L_axis(T) per cell (the explicit form of the operator)."""
-    A, b = _system(g, c, k_l, k_g)
+    A, b = _system(g, c, k_l, k_g, wall_T)
     return A @ T.ravel() + b
 
 
-def _system(g: Grid, c, k_l, k_g):
+def _system(g: Grid, c, k_l, k_g, wall_T=None):
     """(A, b) with k_p sum L(T) = A T + b (b: the T_Gamma terms)."""
     from scipy.sparse import lil_matrix
     h = float(g.par[0])
@@ -140,7 +155,11 @@ def _system(g: Grid, c, k_l, k_g):
             dists = {}
             for s in (-1, 1):
                 Q = _cell(P, axis, s, shape, bc)
-                if Q is None:
+                if Q is None and wall_T and (axis, s) in wall_T:
+                    Tw = float(wall_T[(axis, s)])  # wall at fixed T, half a cell away
+                    terms[s] = (2.0 / h, None, 0.0, Tw * 2.0 / h)
+                    dists[s] = 0.5 * h
+                elif Q is None:
                     terms[s] = (0.0, None, 0.0, 0.0)  # wall: no flux
                     dists[s] = h
                 elif (c[Q] >= 0.5) == liquid_p:
@@ -162,7 +181,7 @@ def _system(g: Grid, c, k_l, k_g):
     return A.tocsr(), b
 
 
-def diffuse(g: Grid, c, e, k_l, k_g, dt):
+def diffuse(g: Grid, c, e, k_l, k_g, dt, wall_T=None, heat_capacity="mixture"):
     """One backward-Euler diffusion step; returns e^{n+1}."""
     from scipy.sparse import diags
     from scipy.sparse.linalg import spsolve
@@ -170,8 +189,16 @@ def diffuse(g: Grid, c, e, k_l, k_g, dt):
     e = np.ascontiguousarray(e, dtype=np.float64)
     Cp = float(g.par[1]) * c + float(g.par[2]) * (1.0 - c)
     T0 = e / Cp
-    A, b = _system(g, c, k_l, k_g)
-    M = diags((Cp / dt).ravel()) - A
-    rhs = (Cp / dt * T0).ravel() + b
+    if heat_capacity == "mixture":
+        Cd = Cp
+    elif heat_capacity == "phase":
+        Cd = np.where(c >= 0.5, float(g.par[1]), float(g.par[2]))
+    else:
+        raise ValueError(heat_capacity)
+    A, b = _system(g, c, k_l, k_g, wall_T)
+    M = diags((Cd / dt).ravel()) - A
+    rhs = (Cd / dt * T0).ravel() + b
     T1 = spsolve(M.tocsr(), rhs).reshape(c.shape)
+    if heat_capacity == "phase":
+        return e + Cd * (T1 - T0)
     return Cp * T1

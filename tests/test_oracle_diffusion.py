@@ -12,6 +12,12 @@ Eqs. T_diff_disc and mod_branchesT) against what the mathematics fixes
   (pi / 2 L)^2 t) as h and dt shrink together, at about first order in dt
   (backward Euler) with the interface off the grid nodes (theta < h).
 * The height function and its fallback agree for planes along every axis.
+* A wall at fixed temperature (wall_T) half a cell from the first node:
+  between it and a plane interface the steady gas profile is the straight
+  line from T_w to T_Gamma, node by node.
+* heat_capacity="phase" is the "mixture" step wherever no cell is mixed; in
+  a mixed cell the node changes temperature at its phase's heat capacity,
+  and the cell's energy changes by exactly the heat conducted into it.
 """
 import itertools
 import math
@@ -131,3 +137,53 @@ def test_height_and_plane_distances_agree_for_planes(seed):
                 assert abs(th - min(max(exact, 1e-3), 1.0)) < 1e-12
                 checked += 1
     assert checked > 10
+
+
+def test_wall_temperature_gives_the_straight_steady_profile():
+    N, x_if = 16, 10.3  # interface 10.3 cells from the heated wall; liquid beyond
+    c = np.clip(np.arange(N) + 1.0 - x_if, 0.0, 1.0).reshape(1, 1, N)
+    Tsat, Tw = 2.0, 7.0
+    g = O.Grid(N, 1, 1, (1, 0, 0), 1.0, 50.0, 1.0, Tsat)
+    x = np.arange(N) + 0.5
+    T0 = np.where(c.ravel() >= 0.5, Tsat, Tsat + 1.0)
+    e = ((50.0 * c + (1.0 - c)).ravel() * T0).reshape(1, 1, N)
+    for hc in ("mixture", "phase"):
+        e1 = diffuse(g, c, e, 3.0, 0.5, 1e12, wall_T={(0, -1): Tw}, heat_capacity=hc)
+        T1 = (e1 / (50.0 * c + (1.0 - c))).ravel()
+        gas = c.ravel() < 0.5
+        want = Tw + (Tsat - Tw) * x[gas] / x_if
+        assert np.abs(T1[gas] - want).max() <= 1e-9 * (Tw - Tsat)
+        assert np.abs(T1[~gas] - Tsat).max() <= 1e-9 * (Tw - Tsat)
+
+
+def test_phase_heat_capacity():
+    rng = np.random.default_rng(12)
+    g = O.Grid(6, 5, 4, (0, 1, 1), 1.0, 40.0, 1.5, 1.0)
+    c = (rng.random((4, 5, 6)) < 0.5).astype(float)  # pure cells only
+    T = 1.0 + rng.random(c.shape)
+    e = (40.0 * c + 1.5 * (1.0 - c)) * T
+    a = diffuse(g, c, e, 2.0, 0.3, 0.7, heat_capacity="mixture")
+    b = diffuse(g, c, e, 2.0, 0.3, 0.7, heat_capacity="phase")
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+    # one mixed cell, a gas node (c = 0.3) in a hot gas column next to liquid
+    N = 8
+    c1 = np.array([0, 0, 0, 0.3, 1, 1, 1, 1], dtype=float).reshape(1, 1, N)
+    g1 = O.Grid(N, 1, 1, (1, 0, 0), 1.0, 40.0, 1.5, 1.0)
+    T1 = np.array([3, 3, 3, 1.0, 1, 1, 1, 1], dtype=float).reshape(1, 1, N)
+    Cp = 40.0 * c1 + 1.5 * (1.0 - c1)
+    e1 = Cp * T1
+    dt = 0.05
+    mix = diffuse(g1, c1, e1, 2.0, 0.3, dt, heat_capacity="mixture")
+    ph = diffuse(g1, c1, e1, 2.0, 0.3, dt, heat_capacity="phase")
+    # the gas node of the mixed cell warms far more at its phase's heat
+    # capacity than at the mixture's (C_p(0.3) = 13.05 against 1.5)
+    dT_phase = (ph[0, 0, 3] - e1[0, 0, 3]) / 1.5
+    dT_mix = mix[0, 0, 3] / Cp[0, 0, 3] - T1[0, 0, 3]
+    assert dT_phase > 5.0 * dT_mix > 0.0
+    # its energy change is the heat conducted into it over dt (backward Euler:
+    # the operator at the new temperatures), at the gas heat capacity
+    # (pure cells: e / C_p; the mixed node: its old T plus its energy change over C_pg)
+    Tnew = (ph / Cp).ravel()
+    Tnew[3] = T1.ravel()[3] + dT_phase
+    L = diffusion_operator(g1, c1, Tnew.reshape(1, 1, N), 2.0, 0.3).ravel()
+    assert abs((ph.ravel()[3] - e1.ravel()[3]) - dt * L[3]) <= 1e-12 * abs(dt * L[3])
