@@ -7,9 +7,10 @@
 // fully reserved up front by their own pool and who cannot hand out an
 // extra buffer, or tools that drive a few steps on a small grid and have no
 // allocator of their own.  For them vof_step_noalloc() runs the same time
-// step as vof_step(), but its scratch space (the ping-pong copy of c and e,
-// the frozen-state flags and Theta, the per-CTA partial sums) lives in one
-// fixed array in device memory that the library reserves when it is loaded.
+// step as vof_step() (in place on the caller's c and e), but its scratch
+// space (the frozen-state flags and Theta, the per-sweep lists, planes and
+// face fluxes, the per-CTA partial sums) lives in one fixed array in device
+// memory that the library reserves when it is loaded.
 //
 // Limits and rules for callers:
 //   * the grid may have at most VOF_NOALLOC_MAX_CELLS cells (64^3), and its
@@ -84,7 +85,10 @@ vof_status vof_step_noalloc(const vof_grid* g, double* c, double* e, const doubl
   if (need == 0 || need > kNoAllocBytes) return VOF_EINVAL;
   int err = 0;
   void* ws = scratch_on_current_device(&err);
-  if (!ws) return VOF_ECUDA;
+  if (!ws) {
+    vofgb::set_last_cuda_error(err);
+    return VOF_ECUDA;
+  }
   return vof_step(g, c, e, u, v, w, dt, step_index, dd, dd_uniform, sums, ws, kNoAllocBytes, stream);
 }
 

@@ -68,6 +68,47 @@ def test_noalloc_matches_vof_step_two_calls(P):
         assert abs(s2[1] - s1[1]) <= SUM_TOL * abs(s1[1])
 
 
+def test_noalloc_after_other_grid(P):
+    """The array still holds what a call on a grid of another shape left in
+    it (other offsets of the frozen state, counters and lists): a step on
+    the 45x38x29 case after two steps on a thin 64x8x8 grid must match
+    vof_step with a fresh workspace."""
+    import torch
+    from paper_2001_03477_gb300 import workloads as W
+    dev = torch.device("cuda")
+    # a thin periodic grid with a tilted slab of liquid and uniform velocity
+    h0 = 1.0 / 64
+    g0 = P.Grid(64, 8, 8, (0, 0, 0), h0, 1000.0, 1.0, 1.0)
+    zz, yy, xx = np.meshgrid(np.arange(8), np.arange(8), np.arange(64), indexing="ij")
+    c0 = np.clip(0.5 + (20.0 - xx - 0.7 * yy - 0.3 * zz) / 3.0, 0.0, 1.0)
+    e0 = (1000.0 * c0 + (1 - c0)) * 1.5
+    f0 = [np.full(s, v) for s, v in (((8, 8, 65), 0.8), ((8, 9, 64), -0.3), ((9, 8, 64), 0.2))]
+    cg0, eg0 = torch.from_numpy(c0).to(dev), torch.from_numpy(e0).to(dev)
+    fd0 = [torch.from_numpy(a).to(dev) for a in f0]
+    for s in range(2):
+        P.vof_step_noalloc(g0, cg0, eg0, *fd0, 0.2 * h0, s, dd_uniform=0.01)
+    torch.cuda.synchronize()
+    assert np.isfinite(cg0.cpu().numpy()).all()
+
+    g, c, e, (u, v, w), dt, dd = _case(P)
+    ud, vd, wd = (torch.from_numpy(a).to(dev) for a in (u, v, w))
+    c1, e1 = torch.from_numpy(c).to(dev), torch.from_numpy(e).to(dev)
+    s1 = P.Stepper(g, device=dev).step(c1, e1, ud, vd, wd, dt, 0, dd_uniform=dd).cpu().numpy()
+    c2, e2 = torch.from_numpy(c).to(dev), torch.from_numpy(e).to(dev)
+    sums2 = torch.zeros(P.VOF_NSUMS, dtype=torch.float64, device=dev)
+    P.vof_step_noalloc(g, c2, e2, ud, vd, wd, dt, 0, dd_uniform=dd, sums=sums2)
+    torch.cuda.synchronize()
+    a1, a2 = c1.cpu().numpy(), c2.cpu().numpy()
+    b1, b2 = e1.cpu().numpy(), e2.cpu().numpy()
+    assert np.abs(a1 - a2).max() <= C_TOL
+    T1 = b1 / (1000.0 * a1 + (1 - a1))
+    T2 = b2 / (1000.0 * a2 + (1 - a2))
+    assert (np.abs(T1 - T2) / np.abs(T1)).max() <= T_TOL
+    s2 = sums2.cpu().numpy()
+    assert abs(s2[0] - s1[0]) <= SUM_TOL * abs(s1[0])
+    assert abs(s2[1] - s1[1]) <= SUM_TOL * abs(s1[1])
+
+
 def test_noalloc_rejects_large_grid(P):
     import torch
     g = P.Grid(65, 64, 64)  # one plane above the limit
