@@ -60,7 +60,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
            "-std=c99", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -107,6 +107,10 @@ def lib():
                                           ctypes.c_double, _D, ctypes.c_int]
             L.orc_mass_transfer.restype = None
             L.orc_mass_transfer.argtypes = [_I, _I, _D, _D, _D, _D, _D, _D, _D]
+            L.orc_set_threads.restype = None
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_get_threads.restype = ctypes.c_int
+            L.orc_get_threads.argtypes = []
             L.orc_sum.restype = ctypes.c_double
             L.orc_sum.argtypes = [_D, ctypes.c_long]
             L.orc_step.restype = None
@@ -122,6 +126,16 @@ def lib():
 # ---------------------------------------------------------------------------
 # numpy-facing helpers
 # ---------------------------------------------------------------------------
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's per-cell loops (results do not depend
+    on the count: every sum is taken in cell order from per-cell values)."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().orc_get_threads())
+
 
 def _dp(a):
     return a.ctypes.data_as(_D) if a is not None else None

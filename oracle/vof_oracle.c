@@ -30,6 +30,16 @@
 
 #define ORC_API __attribute__((visibility("default")))
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* Threads.  The per-cell loops of the sweeps, the shift and the frozen
+   state run on several host threads when the oracle is built with OpenMP:
+   every cell's result is computed by the same arithmetic as in a serial
+   run, and every sum is taken afterwards in cell order from per-cell
+   values, so the results are bit-identical for any thread count. */
+#define ORC_PAR _Pragma("omp parallel for collapse(2) schedule(static)")
+
 /* ------------------------------------------------------------------ */
 /* Indexing                                                            */
 /* ------------------------------------------------------------------ */
@@ -347,6 +357,7 @@ ORC_API void orc_reconstruct(const int dims[3], const int bc[3], const double pa
                              double *m_soa, double *alpha, unsigned char *mixed) {
     long N = (long)dims[0] * dims[1] * dims[2];
     double eps = par[4];
+    ORC_PAR
     for (int k = 0; k < dims[2]; ++k)
         for (int j = 0; j < dims[1]; ++j)
             for (int i = 0; i < dims[0]; ++i) {
@@ -402,6 +413,7 @@ static double heat_cap(const double par[5], double c) { return par[1] * c + par[
 ORC_API void orc_frozen(const int dims[3], const double par[5], const double *c, const double *e,
                         unsigned char *cc, double *theta) {
     long N = (long)dims[0] * dims[1] * dims[2];
+#pragma omp parallel for schedule(static)
     for (long id = 0; id < N; ++id) {
         unsigned char b = c[id] > 0.5 ? 1 : 0;
         double Tn = e[id] / heat_cap(par, c[id]);
@@ -428,13 +440,13 @@ static void face_flux(const int dims[3], const int bc[3], const double par[5], i
     double cd = c[did];
     double Fv;
     if (is_mixed(cd, par[4])) {
-        /* the donor's plane is that of the cell it maps to: behind a
-           zero-gradient boundary the ghost donor is the boundary cell
-           itself (same c, same plane) */
-        int dm[3] = {map_index(don[0], dims[0], bc[0]), map_index(don[1], dims[1], bc[1]),
-                     map_index(don[2], dims[2], bc[2])};
+        /* the donor is reconstructed from its own 3x3x3 stencil of the
+           boundary-filled field (Sec. 3.2).  Behind a zero-gradient
+           boundary the ghost donor's stencil holds copies of the boundary
+           layer (dc/dn = 0), so its plane is perpendicular to the wall
+           wherever MYC picks a transverse candidate or Youngs. */
         double s[27], m[3];
-        gather_stencil(dims, bc, c, dm[0], dm[1], dm[2], s);
+        gather_stencil(dims, bc, c, don[0], don[1], don[2], s);
         orc_myc(s, m);
         double al = orc_alpha(m, cd);
         double da = fabs(a);
@@ -467,8 +479,10 @@ ORC_API void orc_sweep(const int dims[3], const int bc[3], const double par[5], 
     double *T = (double *)malloc(sizeof(double) * N);
     double *cn = (double *)malloc(sizeof(double) * N);
     double *en = (double *)malloc(sizeof(double) * N);
+    double *clipv = (double *)malloc(sizeof(double) * N);
+#pragma omp parallel for schedule(static)
     for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c[id]);
-    double clip = 0.0;
+    ORC_PAR
     for (int k = 0; k < dims[2]; ++k)
         for (int j = 0; j < dims[1]; ++j)
             for (int i = 0; i < dims[0]; ++i) {
@@ -488,7 +502,7 @@ ORC_API void orc_sweep(const int dims[3], const int bc[3], const double par[5], 
                 double cc2 = cnew;
                 if (cc2 < 0.0) cc2 = 0.0;
                 if (cc2 > 1.0) cc2 = 1.0;
-                clip += cnew - cc2;
+                clipv[id] = cnew - cc2;
                 cn[id] = cc2;
                 en[id] = enew;
                 if (Fout || Gout) {
@@ -508,10 +522,12 @@ ORC_API void orc_sweep(const int dims[3], const int bc[3], const double par[5], 
                     }
                 }
             }
+    double clip = 0.0;
+    for (long id = 0; id < N; ++id) clip += clipv[id];
     memcpy(c, cn, sizeof(double) * N);
     memcpy(e, en, sizeof(double) * N);
     if (diag) diag[0] += clip;
-    free(T); free(cn); free(en);
+    free(T); free(cn); free(en); free(clipv);
 }
 
 /* ------------------------------------------------------------------ */
@@ -550,8 +566,9 @@ static void face_flux_le(const int dims[3], const int bc[3], const double par[5]
     if (a == 0.0) { *F = 0.0; *G = 0.0; return; }
     int don[3] = {pos[0], pos[1], pos[2]};
     if (a > 0.0) don[axis] -= 1;
-    /* the donor's plane and faces are those of the cell it maps to (behind a
-       zero-gradient boundary: the boundary cell itself) */
+    /* the donor's faces are those of the cell it maps to (behind a
+       zero-gradient boundary: the boundary cell's); its plane comes from its
+       own stencil of the boundary-filled field, as in face_flux */
     int dm[3] = {map_index(don[0], dims[0], bc[0]), map_index(don[1], dims[1], bc[1]),
                  map_index(don[2], dims[2], bc[2])};
     long did = cell_id(dims, bc, don[0], don[1], don[2]);
@@ -559,7 +576,7 @@ static void face_flux_le(const int dims[3], const int bc[3], const double par[5]
     double Fv;
     if (is_mixed(cd, par[4])) {
         double s[27], m[3];
-        gather_stencil(dims, bc, c, dm[0], dm[1], dm[2], s);
+        gather_stencil(dims, bc, c, don[0], don[1], don[2], s);
         orc_myc(s, m);
         double al = orc_alpha(m, cd);
         double J = le_stretch(dims, bc, axis, uf, lam, dm);
@@ -589,8 +606,10 @@ ORC_API void orc_sweep_le(const int dims[3], const int bc[3], const double par[5
     double *T = (double *)malloc(sizeof(double) * N);
     double *cn = (double *)malloc(sizeof(double) * N);
     double *en = (double *)malloc(sizeof(double) * N);
+    double *clipv = (double *)malloc(sizeof(double) * N);
+#pragma omp parallel for schedule(static)
     for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c[id]);
-    double clip = 0.0;
+    ORC_PAR
     for (int k = 0; k < dims[2]; ++k)
         for (int j = 0; j < dims[1]; ++j)
             for (int i = 0; i < dims[0]; ++i) {
@@ -609,7 +628,7 @@ ORC_API void orc_sweep_le(const int dims[3], const int bc[3], const double par[5
                 double cc2 = cnew;
                 if (cc2 < 0.0) cc2 = 0.0;
                 if (cc2 > 1.0) cc2 = 1.0;
-                clip += cnew - cc2;
+                clipv[id] = cnew - cc2;
                 cn[id] = cc2;
                 en[id] = enew;
                 if (Fout || Gout) {
@@ -627,10 +646,12 @@ ORC_API void orc_sweep_le(const int dims[3], const int bc[3], const double par[5
                     }
                 }
             }
+    double clip = 0.0;
+    for (long id = 0; id < N; ++id) clip += clipv[id];
     memcpy(c, cn, sizeof(double) * N);
     memcpy(e, en, sizeof(double) * N);
     if (diag) diag[0] += clip;
-    free(T); free(cn); free(en);
+    free(T); free(cn); free(en); free(clipv);
 }
 
 /* Energy sweep from given VOF face fluxes F (the unfused form of the same
@@ -643,7 +664,9 @@ ORC_API void orc_energy_consistent(const int dims[3], const int bc[3], const dou
     double lam = dt / par[0];
     double *T = (double *)malloc(sizeof(double) * N);
     double *en = (double *)malloc(sizeof(double) * N);
+#pragma omp parallel for schedule(static)
     for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c_before[id]);
+    ORC_PAR
     for (int k = 0; k < dims[2]; ++k)
         for (int j = 0; j < dims[1]; ++j)
             for (int i = 0; i < dims[0]; ++i) {
@@ -706,6 +729,8 @@ ORC_API void orc_phase_shift(const int dims[3], const int bc[3], const double pa
     double *cn = (double *)malloc(sizeof(double) * N);
     double *pm = (double *)malloc(sizeof(double) * 4 * N); /* m (unmirrored) and alpha of mixed cells */
     double *ps = (double *)malloc(sizeof(double) * N);     /* |m|_2 dd of mixed cells (0: not moving) */
+    double *unv = (double *)malloc(sizeof(double) * N);    /* volume clamped away per receiving cell */
+    ORC_PAR
     for (int k = 0; k < dims[2]; ++k)
         for (int j = 0; j < dims[1]; ++j)
             for (int i = 0; i < dims[0]; ++i) {
@@ -734,12 +759,13 @@ ORC_API void orc_phase_shift(const int dims[3], const int bc[3], const double pa
                 pm[4 * id + 0] = m[0]; pm[4 * id + 1] = m[1]; pm[4 * id + 2] = m[2]; pm[4 * id + 3] = al;
                 ps[id] = sft;
             }
-    double unpl = 0.0;
+    ORC_PAR
     for (int k = 0; k < dims[2]; ++k)
         for (int j = 0; j < dims[1]; ++j)
             for (int i = 0; i < dims[0]; ++i) {
                 long id = ((long)k * dims[1] + j) * dims[0] + i;
                 double ct = c[id];
+                unv[id] = 0.0;
                 if (is_mixed(ct, eps)) continue;
                 int full = ct >= 1.0 - eps;
                 double best = 0.0;
@@ -770,10 +796,12 @@ ORC_API void orc_phase_shift(const int dims[3], const int bc[3], const double pa
                 if (best != 0.0) {
                     double v = ct + best;
                     double vc = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-                    unpl += v - vc;
+                    unv[id] = v - vc;
                     cn[id] = vc;
                 }
             }
+    double unpl = 0.0;
+    for (long id = 0; id < N; ++id) unpl += unv[id];
     double sdc = 0.0, sde = 0.0;
     double dCp = par[1] - par[2];
     for (long id = 0; id < N; ++id) {
@@ -785,7 +813,7 @@ ORC_API void orc_phase_shift(const int dims[3], const int bc[3], const double pa
         e[id] = e[id] + de;
     }
     if (diag) { diag[0] += sdc; diag[1] += unpl; diag[2] += sde; }
-    free(cn); free(pm); free(ps);
+    free(cn); free(pm); free(ps); free(unv);
 }
 
 /* ------------------------------------------------------------------ */
@@ -930,6 +958,23 @@ ORC_API void orc_mass_transfer(const int dims[3], const int bc[3], const double 
                 mdot[id] = (k_g * gg - k_l * gl) / h_fg;
             }
     free(nrm); free(dpl); free(grad); free(mixed); free(has);
+}
+
+/* Host threads of the parallel loops (1 when built without OpenMP). */
+ORC_API void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+ORC_API int orc_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 ORC_API double orc_sum(const double *x, long n) {

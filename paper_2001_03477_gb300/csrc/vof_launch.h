@@ -71,6 +71,9 @@ struct SweepScratch {
   uint32_t* gface;   // grid-wide face items (cell << 1 | side), no fixed order
   uint32_t gface_cap;  // entries of gface (2 N)
   double* plane;     // [N][4]: m0, m1, m2, alpha of the listed mixed cells
+  double* gplane;    // [2][N / n_axis][4]: planes of the ghost donors beyond the
+                     // low / high zero-gradient end of each line (boundary
+                     // cells that are mixed only)
   double* F;         // face arrays of the axis (face layout of the velocities)
   double* G;
 };

@@ -433,15 +433,69 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
 // the only T values kernel F reads back -- and for every listed cell, which
 // kernel U reads.
 // ---------------------------------------------------------------------------
+// PLIC plane (MYC normal, plane constant) of the 3x3x3 stencil centred on
+// position (qx, qy, qz), each index mapped by the boundary conditions.
 // F32: the precision form's FP32 MYC normal (its own instance, so that the
 // FP64 form keeps its register budget)
 template <bool F32>
+__device__ __forceinline__ double4 stencil_plane(const GridDev& g, const double* __restrict__ c_in, int qx, int qy,
+                                                 int qz) {
+  double s[27];
+#pragma unroll
+  for (int oz = 0; oz < 3; ++oz) {
+    const int zz = map_idx(qz + oz - 1, g.n[2], g.bc[2]);
+#pragma unroll
+    for (int oy = 0; oy < 3; ++oy) {
+      const int yy = map_idx(qy + oy - 1, g.n[1], g.bc[1]);
+#pragma unroll
+      for (int ox = 0; ox < 3; ++ox) {
+        const int xx = map_idx(qx + ox - 1, g.n[0], g.bc[0]);
+        s[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_at(g, xx, yy, zz));
+      }
+    }
+  }
+  double m[3];
+  if (F32) myc_normal_f(s, m);
+  else myc_normal(s, m);
+  double4 pl;
+  pl.x = m[0]; pl.y = m[1]; pl.z = m[2];
+  pl.w = plane_alpha(m[0], m[1], m[2], s[13]);
+  return pl;
+}
+
+// Items: the mixed cells (their planes), then with e_in the T items, then,
+// on a zero-gradient sweep axis `ax`, the two ends of every line: where the
+// end cell is mixed, the plane of the ghost donor beyond it (position -1 or
+// n) from the ghost's own 3x3x3 stencil of the boundary-filled field, whose
+// cells beyond the boundary are copies of the boundary layer (dc/dn = 0);
+// stored in sc.gplane[side][line].
+template <bool F32>
 __global__ void __launch_bounds__(kPlaneThreads)
-k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc) {
+k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc, int ax) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int nm = sc.counters[0], nf = sc.counters[1];
   const int cnt = nm + (e_in ? nf + sc.counters[2] : 0);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+  const int n_ax = g.n[ax];
+  const int lines = g.bc[ax] != 0 ? (int)((size_t)nx * ny * nz / (size_t)n_ax) : 0;
+  const int total = cnt + 2 * lines;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    if (i >= cnt) {
+      const int j = i - cnt;
+      const int side = j >= lines ? 1 : 0;
+      const int li = j - side * lines;
+      // the line's two other coordinates (x fastest)
+      int x = 0, y = 0, z = 0;
+      if (ax == 0) { y = li % ny; z = li / ny; }
+      else if (ax == 1) { x = li % nx; z = li / nx; }
+      else { x = li % nx; y = li / nx; }
+      const int kend = side ? n_ax - 1 : 0;
+      const int ex = ax == 0 ? kend : x, ey = ax == 1 ? kend : y, ez = ax == 2 ? kend : z;
+      if (!is_mixed_b(__ldg(c_in + cell_at(g, ex, ey, ez)), g)) continue;
+      const int qk = side ? n_ax : -1;
+      const double4 pl = stencil_plane<F32>(g, c_in, ax == 0 ? qk : x, ax == 1 ? qk : y, ax == 2 ? qk : z);
+      reinterpret_cast<double4*>(sc.gplane)[j] = pl;
+      continue;
+    }
     if (i >= nm) {
       const uint32_t item = face_item(sc, i - nm, nf);
       if (item & 1u) continue;  // right-face item: its cell has a left item too
@@ -452,27 +506,7 @@ k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_
     const size_t id = sc.gmix[i];
     int x, y, z;
     cell_xyz(g, id, x, y, z);
-    double s[27];
-#pragma unroll
-    for (int oz = 0; oz < 3; ++oz) {
-      const int zz = map_idx(z + oz - 1, nz, g.bc[2]);
-#pragma unroll
-      for (int oy = 0; oy < 3; ++oy) {
-        const int yy = map_idx(y + oy - 1, ny, g.bc[1]);
-#pragma unroll
-        for (int ox = 0; ox < 3; ++ox) {
-          const int xx = map_idx(x + ox - 1, nx, g.bc[0]);
-          s[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_at(g, xx, yy, zz));
-        }
-      }
-    }
-    double m[3];
-    if (F32) myc_normal_f(s, m);
-    else myc_normal(s, m);
-    const double al = plane_alpha(m[0], m[1], m[2], s[13]);
-    double4 pl;
-    pl.x = m[0]; pl.y = m[1]; pl.z = m[2]; pl.w = al;
-    reinterpret_cast<double4*>(sc.plane)[id] = pl;
+    reinterpret_cast<double4*>(sc.plane)[id] = stencil_plane<F32>(g, c_in, x, y, z);
   }
 }
 
@@ -534,8 +568,16 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
       const bool pos = dgt0(a);
       const double cd = pos ? cw[3] : cw[4];  // donor f-1 (a > 0) or f (a < 0)
       if (is_mixed_b(cd, g)) {
-        const size_t did = lbase + stride * map_idx(pos ? f - 1 : f, n_ax, bca);
-        const double4 pl = reinterpret_cast<const double4*>(sc.plane)[did];
+        const int dq = pos ? f - 1 : f;  // donor position along the axis
+        double4 pl;
+        if (bca != 0 && (dq < 0 || dq >= n_ax)) {
+          // ghost donor behind a zero-gradient boundary: its own plane (k_prep)
+          const size_t lines = (size_t)nx * ny * g.n[2] / (size_t)n_ax;
+          const size_t li = AX == 0 ? (size_t)z * ny + y : (AX == 1 ? (size_t)z * nx + x : (size_t)y * nx + x);
+          pl = reinterpret_cast<const double4*>(sc.gplane)[(dq < 0 ? 0 : lines) + li];
+        } else {
+          pl = reinterpret_cast<const double4*>(sc.plane)[lbase + stride * dq];
+        }
         const double mv[3] = {pl.x, pl.y, pl.z};
         const double da = fabs(a);
         if (da > 1.0 && status) atomicOr(status, DEV_CFL);
@@ -799,6 +841,7 @@ size_t sweep_scratch_bytes(const GridDev& g) {
     b += al256(N * 4);                          // grid-wide mixed list
     b += al256(2 * N * 4);                      // grid-wide face list
     b += al256(N * 32);                         // planes
+    b += al256(2 * (N / (size_t)g.n[a]) * 32);  // ghost donors' planes
     b += 2 * al256(max_faces(g) * 8);           // face fluxes F, G
     best = b > best ? b : best;
   }
@@ -823,6 +866,7 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, SumOut su
   s.gface = reinterpret_cast<uint32_t*>(b);     b += al256(2 * N * 4);
   s.gface_cap = (uint32_t)(2 * N);
   s.plane = reinterpret_cast<double*>(b);       b += al256(N * 32);
+  s.gplane = reinterpret_cast<double*>(b);      b += al256(2 * (N / (size_t)g.n[axis]) * 32);
   s.F = reinterpret_cast<double*>(b);           b += al256(max_faces(g) * 8);
   s.G = reinterpret_cast<double*>(b);
   return s;
@@ -841,8 +885,8 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
                                                                           flux_out != nullptr, p.cap, c_out != c_in);
   prof_mark(AX == 0 ? "sweep_x.stream" : (AX == 1 ? "sweep_y.stream" : "sweep_z.stream"), st);
-  if (g.f32) k_prep<true><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc);
-  else k_prep<false><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc);
+  if (g.f32) k_prep<true><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+  else k_prep<false><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
   prof_mark(AX == 0 ? "sweep_x.prep" : (AX == 1 ? "sweep_y.prep" : "sweep_z.prep"), st);
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
