@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,11 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "Gcell/s per 3-sweep PLIC+energy advection step; % of HBM roofline"
 UNIT = "Gcell/s"
 N_CELLS = 256
-# algorithmic bytes per cell of one sweep launch: read c, e, face velocity
-# (8 B each) and the 1-byte frozen-state flag; write c, e
-SWEEP_BYTES_PER_CELL = 8 + 8 + 8 + 1 + 8 + 8
-# per step: 3 sweeps + zeroing the state (1 B) + shift (read c, e; write c, e)
-STEP_BYTES_PER_CELL = 3 * SWEEP_BYTES_PER_CELL + 1 + 32
+# Algorithmic bytes per cell of one time step of the FP64 form: each sweep
+# reads c, e, the face velocity of its axis, the frozen Theta (8 B each) and
+# cc (1 B) and writes c, e (49 B); the first sweep also writes Theta and cc
+# (9 B); the shift reads c, e and the per-cell shift dd and writes c, e
+# (40 B): 3 x 49 + 9 + 40 = 196 B.  (The kernels move less: Theta is
+# written only for cells that change, and quiet tiles are skipped.)
+SWEEP_BYTES_PER_CELL = 8 + 8 + 8 + 8 + 1 + 8 + 8
+STEP_BYTES_PER_CELL = 3 * SWEEP_BYTES_PER_CELL + 9 + 40
 
 
 def max_over_ranks(x, world, device):
@@ -196,6 +200,9 @@ def run_gpu(args):
     v = torch.from_numpy(wl.v).to(dev)
     w = torch.from_numpy(wl.w).to(dev)
     c, e = c0.clone(), e0.clone()
+    # the Step-2 shift as a per-cell array (the mass-flux-driven interface
+    # shift of the workload, equal in every cell here)
+    dd = torch.full_like(c0, wl.dd_uniform)
     st = P.Stepper(g, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -206,7 +213,7 @@ def run_gpu(args):
 
     # ---- device-resident timed region --------------------------------------
     for s in range(args.warmup):
-        st.step(c, e, u, v, w, wl.dt, s, dd_uniform=wl.dd_uniform)
+        st.step(c, e, u, v, w, wl.dt, s, dd=dd)
     barrier()
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
@@ -216,7 +223,7 @@ def run_gpu(args):
     barrier()
     ev0.record(stream)
     for s in range(args.steps):
-        st.step(c, e, u, v, w, wl.dt, args.warmup + s, dd_uniform=wl.dd_uniform)
+        st.step(c, e, u, v, w, wl.dt, args.warmup + s, dd=dd)
     ev1.record(stream)
     barrier()
     clocks = sampler.stop() if sampler else None
@@ -234,7 +241,7 @@ def run_gpu(args):
     barrier()
     P.vof_profile_begin(stream)
     for r in range(reps):
-        st.step(c, e, u, v, w, wl.dt, args.warmup + args.steps + r, dd_uniform=wl.dd_uniform)
+        st.step(c, e, u, v, w, wl.dt, args.warmup + args.steps + r, dd=dd)
     launches = P.vof_profile_end()
     barrier()
     kern_ms = {}
@@ -250,6 +257,8 @@ def run_gpu(args):
     step_ms_prof = sum(kern_ms.values())
     fp64_achieved = FACE_FLOP * faces_per_step / (faces_ms * 1e-3) / 1e12 if faces_ms > 0 else 0.0
     traffic = faces_traffic_from_profile()
+    fp64 = fp64_rate(P, dev, stream) if rank == 0 else None
+    fp64_peak = fp64["dfma_tflops"] if fp64 else fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None)
 
     # ---- the mass transfer rate (Sec. 3.2) on the same workload -------------
     mt = None if args.step_only else mass_transfer_measure(P, g, wl, c0, e0, stream, barrier)
@@ -292,7 +301,7 @@ def run_gpu(args):
             if s_ + 1 < nsteps:
                 issue_copy(1 - b)
             stream.wait_event(ready[b])
-            st.step(c, e, *bufs[b], wl.dt, s_, dd_uniform=wl.dd_uniform)
+            st.step(c, e, *bufs[b], wl.dt, s_, dd=dd)
             free[b].record(stream)
             sums_h[b].copy_(st.sums, non_blocking=True)
             got[b].record(stream)
@@ -318,8 +327,10 @@ def run_gpu(args):
         cpu = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
         del c, e, c0, e0, u, v, w, st
         torch.cuda.empty_cache()
-        pform = (precision_form(dev) if world == 1 and not (args.no_precision_form or args.step_only)
-                 else None)
+        pform = (precision_form(dev, fp64_peak=fp64_peak, hbm_peak=peak)
+                 if world == 1 and not (args.no_precision_form or args.step_only) else None)
+        learned = (learned_form(dev, fp64_peak=fp64_peak)
+                   if world == 1 and not (args.no_learned_form or args.step_only) else None)
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -332,11 +343,15 @@ def run_gpu(args):
                        "algorithmic_bytes_per_cell_step": STEP_BYTES_PER_CELL,
                        "hbm_roofline_frac_step": round(value / world * STEP_BYTES_PER_CELL / peak, 4)},
             "roofline": {"bound": "alu", "kernel": "k_faces (sweep x, y, z)", "achieved": round(fp64_achieved, 4),
-                         "peak": round(fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None), 4),
+                         "peak": round(fp64_peak, 4),
                          "unit": "TFLOP/s",
-                         "frac": round(fp64_achieved / fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None), 4),
+                         "frac": round(fp64_achieved / fp64_peak, 4),
                          "traffic": traffic,
-                         "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x max SM clock",
+                         "peak_kind": ("measured: FP64 fused multiply-add chains on every SM (vof_fp64_probe), "
+                                       "2 flop each" if fp64 else
+                                       "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x max SM clock"),
+                         "fp64_probe": fp64,
+                         "peak_derived_tflops": round(fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None), 4),
                          "flop_per_face": FACE_FLOP, "faces_per_launch": round(faces_per_step / 3),
                          "ms_per_launch": round(faces_ms / 3, 5),
                          "share_of_step": round(faces_ms / step_ms_prof, 4) if step_ms_prof > 0 else None,
@@ -349,6 +364,7 @@ def run_gpu(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "precision_form": pform,
+            "learned_form": learned,
             "mass_transfer": mt,
             "scheme_le": le,
             "final_sums": [float(x) for x in sums],
@@ -471,12 +487,63 @@ def scheme_le_measure(P, wl, c0, e0, u, v, w, stream, barrier, steps=100):
             "ms_per_step": round(ms, 5)}
 
 
-def precision_form(dev, steps=20, n=512):
+def fp64_rate(P, dev, stream, iters=20000, blocks=152 * 8):
+    """Measured FP64 rate of the part: the library's FP64 probe (8
+    independent chains of fused multiply-adds, or adds, per thread on every
+    SM), best of 3 launches timed with CUDA events on the launching stream."""
+    import torch
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    res = {}
+    for op, name, flop in ((0, "dfma", 2), (1, "dadd", 1)):
+        P.vof_fp64_probe(op, 1000, blocks, out, stream)
+        best = None
+        for _ in range(3):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            P.vof_fp64_probe(op, iters, blocks, out, stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            best = ms if best is None else min(best, ms)
+        ops = blocks * 256 * 8 * iters
+        res[name + "_tflops"] = round(ops * flop / (best * 1e-3) / 1e12, 4)
+        res[name + "_ginstr_per_s"] = round(ops / (best * 1e-3) / 1e9, 2)
+    return res
+
+
+def dense_roofline(P, st, g, c, e, u, v, w, dt, stream, fp64_peak, hbm_peak, value, reps=3):
+    """The FP64 step's kernels on a workload where T varies everywhere (no
+    quiet tiles): per-launch times of `reps` steps (CUDA events recorded by
+    the library after each launch), faces evaluated, and k_faces' FP64 rate
+    against the measured peak; the step against the HBM ledger."""
+    import torch
+    torch.cuda.synchronize()
+    P.vof_profile_begin(stream)
+    for r in range(reps):
+        st.step(c, e, u, v, w, dt, r)
+    launches = P.vof_profile_end()
+    kms = {}
+    for name, t in launches:
+        kms[name] = kms.get(name, 0.0) + t / reps
+    counts = P.vof_step_work_counts(g, st.workspace, stream)
+    faces_ms = sum(kms.get(f"sweep_{a}.faces", 0.0) for a in "xyz")
+    faces = sum(counts["faces"])
+    ach = FACE_FLOP * faces / (faces_ms * 1e-3) / 1e12 if faces_ms > 0 else 0.0
+    return {"kernel": "k_faces (sweep x, y, z)", "bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 4),
+            "peak": round(fp64_peak, 4), "frac": round(ach / fp64_peak, 4), "flop_per_face": FACE_FLOP,
+            "faces_per_launch": round(faces / 3), "ms_per_launch": round(faces_ms / 3, 5),
+            "share_of_step": round(faces_ms / sum(kms.values()), 4),
+            "hbm_frac_step": round(value * STEP_BYTES_PER_CELL / hbm_peak, 4), "work_counts": counts,
+            "kernel_ms": {k: round(v_, 5) for k, v_ in sorted(kms.items(), key=lambda kv: -kv[1])}}
+
+
+def precision_form(dev, steps=20, n=512, fp64_peak=None, hbm_peak=None):
     """The precision form against the FP64 form on the 512^3 deformation
     workload (sphere R = 0.15 in the LeVeque field, smooth random T, no
     phase change): Gcell/s of each (CUDA events around `steps` in-place
     steps from the same initial state) and the difference of the two final
-    states, with the totals each form conserves."""
+    states, with the totals each form conserves; and the FP64 step's
+    kernels on this dense workload (T varies in every cell)."""
     import torch
     import paper_2001_03477_gb300 as P
     from paper_2001_03477_gb300 import workloads as W
@@ -514,6 +581,11 @@ def precision_form(dev, steps=20, n=512):
         sums = st.sums.cpu().numpy()
         res[name] = {"value": round(n ** 3 * steps / (ms * 1e-3) / 1e9, 4), "ms_per_step": round(ms / steps, 5),
                      "sum_c": float(sums[0]), "sum_e": float(sums[1]), "clipped": float(clip)}
+        if name == "f64" and fp64_peak:
+            cx, ex = c0.clone(), e0.clone()
+            dense = dense_roofline(P, st, g, cx, ex, u, v, w, wl.dt, stream, fp64_peak, hbm_peak,
+                                   res[name]["value"])
+            del cx, ex
         finals[name] = (c, e)
         del st
     sc0 = float(c0.sum())
@@ -542,7 +614,179 @@ def precision_form(dev, steps=20, n=512):
         "energy_drift_rel": {k: (r["sum_e"] - se0) / se0 for k, r in res.items()},
         "input_generation_s": round(gen_s, 1),
     }
+    if fp64_peak:
+        out["roofline_fp64_dense"] = dense
     return out
+
+
+def _training_part(n, seed, start):
+    from paper_2001_03477_gb300 import workloads as W
+    return W.training_stencils(n, seed=seed, start=start)
+
+
+def training_set(count, seed=50):
+    """`count` training stencils of the learned normal (spheres, ellipsoids,
+    planes; workloads.training_stencils) generated on all host cores by a
+    spawn pool (each range of sample indices from its own seeded streams)."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    chunk = max(2048, -(-count // (nproc * 4)))
+    jobs = [(min(chunk, count - s), seed, s) for s in range(0, count, chunk)]
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        parts = pool.starmap(_training_part, jobs)
+    return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]), nproc
+
+
+def _angles_deg(m, y):
+    m = np.asarray(m, dtype=np.float64)
+    cosv = np.sum(m * y, axis=1) / (np.linalg.norm(m, axis=1) * np.linalg.norm(y, axis=1))
+    return np.degrees(np.arccos(np.clip(cosv, -1.0, 1.0)))
+
+
+def shape_error_run(P, g, c0, e0, u0, v0, w0, dt, nsteps, dev, period=3.0):
+    """L1 shape error sum |c(T) - c(0)| h^3 after one full period of the
+    LeVeque field (the velocity of step s is the t = 0 field times
+    cos(pi t / T) at t = (s + 1/2) dt), and the step rate."""
+    import torch
+    st = P.Stepper(g, device=dev)
+    c, e = c0.clone(), e0.clone()
+    u, v, w = torch.empty_like(u0), torch.empty_like(v0), torch.empty_like(w0)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(nsteps):
+        gt = math.cos(math.pi * (s + 0.5) * dt / period)
+        torch.mul(u0, gt, out=u)
+        torch.mul(v0, gt, out=v)
+        torch.mul(w0, gt, out=w)
+        st.step(c, e, u, v, w, dt, s)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    counts = P.vof_step_work_counts(g, st.workspace, stream)
+    err = float((c - c0).abs().sum()) * g.h ** 3
+    return {"l1_shape_error": err, "rel_to_volume": err / (float(c0.sum()) * g.h ** 3),
+            "ms_per_step": round(ev0.elapsed_time(ev1) / nsteps, 5), "last_step_mlp_fallback": counts["mlp_fallback"],
+            "last_step_mixed": counts["mixed"]}
+
+
+def learned_form(dev, fp64_peak=None, n=512, steps=20, ntrain=1_000_000, train_steps=8000, batch=16384,
+                 n_shape=128):
+    """The learned-normal form (the sweeps' MYC normals replaced by the
+    27-64-64-3 network on the tensor cores, MYC as fallback), against the
+    plain FP64 form:
+      * training on the GPU (the library's forward, backward and Adam
+        kernels) on `ntrain` generated stencils, and the trained network's
+        mean angular error on held-out sphere stencils against MYC's;
+      * throughput at n^3 on the deformation sphere with the phase-change
+        shift dd = -0.01 (precision form + learned normals vs FP64 + MYC)
+        and the volume drift over `steps` steps;
+      * the L1 shape error after a full period of the LeVeque field at
+        n_shape^3 for the learned, MYC and Youngs normals."""
+    import torch
+    import paper_2001_03477_gb300 as P
+    from paper_2001_03477_gb300 import workloads as W
+    t0 = time.perf_counter()
+    X, Y, nproc = training_set(ntrain)
+    gen_s = time.perf_counter() - t0
+    Xd, Yd = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
+    del X, Y
+    mlp = P.MLP(P.MLP.init_master(5), device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    hist = []
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(train_steps):
+        lr = 3e-3 if s < train_steps // 2 else (1e-3 if s < (4 * train_steps) // 5 else 3e-4)
+        mlp.train_step(Xd, Yd, batch, lr, seed=50, loss=loss)
+        if s % (train_steps // 16) == 0 or s == train_steps - 1:
+            hist.append((s, loss.clone()))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    train_ms = ev0.elapsed_time(ev1)
+    hist = [(s, float(l_.item())) for s, l_ in hist]
+    del Xd, Yd
+    # held-out sphere stencils: learned (with fallback) against MYC alone
+    # (a zero network has no usable normal, so it falls back everywhere)
+    Xt, Yt = W.training_stencils(3000, seed=99, kinds=("sphere",))
+    Xtd = torch.from_numpy(Xt).to(dev)
+    zero = P.MLP(np.zeros(P.VOF_MLP_PARAMS, dtype=np.float32), device=dev)
+    out = {}
+    for name, net in (("learned", mlp), ("myc", zero)):
+        m = torch.zeros((len(Xt), 3), dtype=torch.float64, device=dev)
+        fb = torch.zeros(len(Xt), dtype=torch.uint8, device=dev)
+        P.vof_mlp_normals(net.packed, Xtd, m, fb)
+        ang = _angles_deg(m.cpu().numpy(), Yt)
+        out[name] = {"mean_deg": round(float(ang.mean()), 4), "median_deg": round(float(np.median(ang)), 4),
+                     "p99_deg": round(float(np.percentile(ang, 99)), 4), "fallback_frac": float(fb.float().mean())}
+    training = {"stencils": ntrain, "generation_s": round(gen_s, 1), "generation_procs": nproc,
+                "steps": train_steps, "batch": batch, "samples_per_s": round(train_steps * batch / (train_ms * 1e-3)),
+                "ms_per_step": round(train_ms / train_steps, 4), "loss": hist,
+                "held_out_spheres": out}
+    # ---- throughput on the deformation sphere with the shift -------------
+    wl = W.deformation_sphere(n=n, nsub=8)
+    c0 = torch.from_numpy(wl.c).to(dev)
+    e0 = torch.from_numpy(wl.e).to(dev)
+    u, v, w = (torch.from_numpy(a).to(dev) for a in (wl.u, wl.v, wl.w))
+    del wl.c, wl.e, wl.u, wl.v, wl.w
+    dd = -0.01
+    forms = {"fp64_myc": dict(precision=P.VOF_F64, normal=P.VOF_NORMAL_MYC),
+             "f32_learned": dict(precision=P.VOF_F32_FLUX, normal=P.VOF_NORMAL_MLP, mlp=mlp.packed)}
+    res = {}
+    sc0 = float(c0.sum())
+    for name, kw in forms.items():
+        g = P.Grid(n, n, n, wl.bc, wl.h, wl.Cp_l, wl.Cp_g, wl.T_sat, **kw)
+        st = P.Stepper(g, device=dev)
+        c, e = c0.clone(), e0.clone()
+        for s in range(3):
+            st.step(c, e, u, v, w, wl.dt, s, dd_uniform=dd)
+        c.copy_(c0); e.copy_(e0)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(steps):
+            st.step(c, e, u, v, w, wl.dt, s, dd_uniform=dd)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1)
+        # volume bookkeeping of the same steps: sum c changes only by the
+        # clipped volume and the shift's sum dc (closed box)
+        c.copy_(c0); e.copy_(e0)
+        book = 0.0
+        for s in range(steps):
+            sums = st.step(c, e, u, v, w, wl.dt, s, dd_uniform=dd).cpu().numpy()
+            book += -sums[2] + sums[3]
+        counts = P.vof_step_work_counts(g, st.workspace, stream)
+        res[name] = {"value": round(n ** 3 * steps / (ms * 1e-3) / 1e9, 4), "ms_per_step": round(ms / steps, 5),
+                     "mass_drift_rel": (float(sums[0]) - sc0 - book) / sc0,
+                     "mlp_fallback_last_step": counts["mlp_fallback"], "mixed_last_step": counts["mixed"]}
+        del st, c, e
+    del c0, e0, u, v, w
+    torch.cuda.empty_cache()
+    # ---- shape error after a full period at n_shape^3 ---------------------
+    ws = W.deformation_sphere(n=n_shape, nsub=8)
+    dts = 0.25 * ws.h / 2.0  # face CFL 0.25 (max |u| = 2)
+    nper = int(round(3.0 / dts))
+    cs = torch.from_numpy(ws.c).to(dev)
+    es = torch.from_numpy((ws.Cp_l * ws.c + ws.Cp_g * (1 - ws.c)) * 1.0).to(dev)  # uniform T: c alone matters
+    us, vs, wsf = (torch.from_numpy(a).to(dev) for a in (ws.u, ws.v, ws.w))
+    shape = {}
+    for name, kw in (("learned_f32", dict(precision=P.VOF_F32_FLUX, normal=P.VOF_NORMAL_MLP, mlp=mlp.packed)),
+                     ("myc_f64", dict(precision=P.VOF_F64, normal=P.VOF_NORMAL_MYC)),
+                     ("myc_f32", dict(precision=P.VOF_F32_FLUX, normal=P.VOF_NORMAL_MYC)),
+                     ("youngs_f64", dict(precision=P.VOF_F64, normal=P.VOF_NORMAL_YOUNGS))):
+        g = P.Grid(n_shape, n_shape, n_shape, ws.bc, ws.h, ws.Cp_l, ws.Cp_g, ws.T_sat, **kw)
+        shape[name] = shape_error_run(P, g, cs, es, us, vs, wsf, dts, nper, dev)
+    return {"workload": f"deformation-sphere {n}^3 (R=0.15 at (0.35,0.35,0.35), LeVeque field t=0, CFL 0.5, "
+                        f"water/steam Cp ratio {wl.Cp_l / wl.Cp_g:.1f}, T = 1 + 8 seeded Fourier modes) with the "
+                        f"phase-change shift dd = {dd} in every mixed cell",
+            "steps": steps, "unit": UNIT,
+            "value": res["f32_learned"]["value"], "value_fp64_myc": res["fp64_myc"]["value"],
+            "speedup_vs_fp64": round(res["f32_learned"]["value"] / res["fp64_myc"]["value"], 4),
+            "forms": res, "training": training,
+            "shape_error_full_period": {"grid": f"{n_shape}^3", "steps": nper, "dt": dts, "forms": shape}}
 
 
 def oracle_sample(nz_slab=8):
@@ -562,8 +806,26 @@ def oracle_sample(nz_slab=8):
     return O, g, wl, c, e, u, v, w
 
 
-def cpu_baseline(budget_s=15.0):
-    O, g, wl, c, e, u, v, w = oracle_sample()
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001 -- informative only
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def _oracle_rate(O, g, wl, c, e, u, v, w, budget_s):
     t0 = time.perf_counter()
     steps = 0
     while True:
@@ -572,10 +834,27 @@ def cpu_baseline(budget_s=15.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    return c.size * steps / dt / 1e9, steps, dt
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle (as it stands) on the host cores: all cores (OpenMP over
+    the per-cell loops; bit-identical to one thread) and one thread, on the
+    256 x 256 x 8 z-slab through the bubble centre."""
+    O, g, wl, c, e, u, v, w = oracle_sample()
+    nproc = os.cpu_count() or 1
+    O.set_threads(nproc)
+    v_all, s_all, t_all = _oracle_rate(O, g, wl, c, e, u, v, w, budget_s)
+    O.set_threads(1)
+    v_one, s_one, t_one = _oracle_rate(O, g, wl, c, e, u, v, w, budget_s)
+    O.set_threads(nproc)
     cells = c.size
-    return {"value": round(cells * steps / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps on the 256x256x8 z-slab through the bubble centre "
-                      f"({cells} cells, {dt:.1f} s, single thread)"}
+    return {"value": round(v_all, 6), "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": f"{s_all} oracle steps on the 256x256x8 z-slab through the bubble centre "
+                      f"({cells} cells, {t_all:.1f} s, {nproc} threads)",
+            "cpu_model": cpu_model(), "nproc": nproc,
+            "single_thread": {"value": round(v_one, 6), "unit": UNIT, "cores": 1,
+                              "sample": f"{s_one} steps of the same slab, {t_one:.1f} s"}}
 
 
 def run_reference(args):
@@ -583,6 +862,7 @@ def run_reference(args):
     if rank != 0:
         return
     O, g, wl, c, e, u, v, w = oracle_sample(nz_slab=2)
+    O.set_threads(1)
     for s in range(args.warmup):
         c, e, _ = O.step(g, c, e, u, v, w, wl.dt, s, dd_uniform=wl.dd_uniform)
     t0 = time.perf_counter()
@@ -636,6 +916,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the precision-form comparison on the 512^3 deformation workload")
+    ap.add_argument("--no-learned-form", action="store_true",
+                    help="skip the learned-normal form (GPU training, 512^3 step, full-period shape errors)")
     ap.add_argument("--step-only", action="store_true",
                     help="time the step alone: no precision-form, mass-transfer or Lagrangian-explicit lines "
                          "(the launch list of the step)")

@@ -53,9 +53,11 @@ typedef enum {
   VOF_EINVAL = 1,  /* bad argument (null pointer, size, aliasing) */
   VOF_ECUDA = 2,   /* a CUDA call failed; see vof_last_cuda_error() */
   VOF_ECFL = 3,    /* device status: |u| dt / h > 1 on some face */
-  VOF_ESOLVE = 4   /* an iterative solve (vof_velocity_extension,
+  VOF_ESOLVE = 4,  /* an iterative solve (vof_velocity_extension,
                       vof_heat_diffusion) did not converge within max_iter,
                       or the extension's sub-domain has no free-flow face */
+  VOF_EWAIT = 5    /* device status: a bounded wait of a tensor-core kernel
+                      gave up (its results are not valid) */
 } vof_status;
 
 typedef struct {
@@ -88,12 +90,30 @@ typedef struct {
                          term uses the cell's own c and Theta = (T C_pl) c +
                          (T C_pg)(1 - c) (no frozen state).  Any other value:
                          VOF_EINVAL. */
+  int normal;         /* interface normal of the sweeps' reconstruction:
+                         VOF_NORMAL_MYC (0): MYC (Sec. 3.2, the paper's method);
+                         VOF_NORMAL_MLP (1): the learned normal of vof_mlp_*
+                         (network parameters `mlp`) with MYC as its fallback,
+                         for the mixed cells of each sweep (ghost donors
+                         behind zero-gradient boundaries and the shift keep
+                         MYC);
+                         VOF_NORMAL_YOUNGS (2): Youngs' normal -grad c (the
+                         1-2-1 weighted 3x3x3 gradient, L1-normalised), for the
+                         same cells (a reference for shape-error comparisons).
+                         Any other value: VOF_EINVAL. */
+  const void* mlp;    /* VOF_NORMAL_MLP: device buffer of
+                         vof_mlp_packed_bytes() bytes written by vof_mlp_pack
+                         or vof_mlp_train_step (16-byte aligned); ignored
+                         otherwise */
 } vof_grid;
 
 #define VOF_F64 0
 #define VOF_F32_FLUX 1
 #define VOF_SCHEME_WY 0
 #define VOF_SCHEME_LE 1
+#define VOF_NORMAL_MYC 0
+#define VOF_NORMAL_MLP 1
+#define VOF_NORMAL_YOUNGS 2
 
 /* Number of doubles vof_step() writes to `sums`. */
 #define VOF_NSUMS 6
@@ -442,11 +462,13 @@ VOF_API vof_status vof_step_noalloc(const vof_grid* g, double* c, double* e, con
  * (instrumentation; the paper has no counterpart): counts[VOF_NCOUNTS] =
  *   {mixed cells, faces evaluated} of the x, y and z sweeps (6 ints),
  *   {moving mixed cells by the analytic plane constant, by bisection,
- *    receivers settled} of the shift (3 ints).
+ *    receivers settled} of the shift (3 ints),
+ *   {learned normals replaced by MYC} of the x, y and z sweeps (3 ints; 0
+ *    with VOF_NORMAL_MYC).
  * Copies them to host memory after the work queued on `stream` (the step's
  * stream) completes.  VOF_EINVAL for a bad grid or null pointers.
  */
-#define VOF_NCOUNTS 9
+#define VOF_NCOUNTS 12
 VOF_API vof_status vof_step_work_counts(const vof_grid* g, const void* workspace, int* counts, void* stream);
 
 /*
@@ -463,7 +485,79 @@ VOF_API vof_status vof_step_work_counts(const vof_grid* g, const void* workspace
 VOF_API vof_status vof_profile_begin(void* stream);
 VOF_API int vof_profile_end(float* ms, const char** names, int max_entries);
 
-/* Sticky device status (synchronises the device): VOF_OK or VOF_ECFL; reading clears it. */
+/*
+ * FP64 rate probe (instrumentation; the paper has no counterpart): `blocks`
+ * CTAs of 256 threads, each thread running 8 independent chains of `iters`
+ * dependent FP64 fused multiply-adds (op 0: 2 flops each) or adds (op 1:
+ * 1 flop each); one double per thread is stored to out[blocks * 256]
+ * (device).  The caller times it (CUDA events on `stream`): flops =
+ * blocks * 256 * 8 * iters * (2 or 1).  VOF_EINVAL for a bad op, iters or
+ * blocks < 1, or null out.
+ */
+VOF_API vof_status vof_fp64_probe(int op, long iters, int blocks, double* out, void* stream);
+
+/*
+ * Learned interface normal (the paper reconstructs with MYC, Sec. 3.2,
+ * Eq. plane_m [Aulisa07]; the learned-normal form replaces that step): a
+ * network 27 -> 64 -> 64 -> 3 with GELU (x Phi(x)) maps the 27 volume
+ * fractions of a cell's 3x3x3 stencil (x fastest, inputs 2 c - 1) to the
+ * normal direction y (liquid -> gas), m = y / |y|_1.  BF16 weights, FP32
+ * accumulation on the tensor cores; activations enter the products as the
+ * sum of three BF16 numbers (FP32-accurate).
+ *
+ * Parameters.  master: FP32 device vector of VOF_MLP_PARAMS values in the
+ * order W1[64][27], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] (W[out][in]).
+ * packed: device buffer of vof_mlp_packed_bytes() bytes, 16-byte aligned,
+ * the BF16 weight images the kernels load; vof_mlp_pack() writes it from
+ * master (round to nearest even).
+ *
+ * vof_mlp_forward: y[n][3] (FP32) of the stencils X[n][27] (FP64 volume
+ *   fractions), n >= 0.
+ * vof_mlp_normals: the learned normal with the MYC fallback: the plane
+ *   residual of a normal is the RMS over the 26 neighbours of (volume of the
+ *   plane with that normal through the central cell's plane constant) - c,
+ *   evaluated in FP32; the network's normal is kept when its residual is at
+ *   most 1.25 x that of the MYC normal + 1e-3 (and |y|_1 > 0), else MYC
+ *   (the precision form's MYC, decisions as in FP64).  m[n][3] (FP64,
+ *   L1-normalised) and fallback[n] (nullable; 1 where MYC was taken).
+ * Both: VOF_EINVAL for null pointers, n < 0, misaligned packed.
+ */
+#define VOF_MLP_PARAMS 6147
+VOF_API size_t vof_mlp_packed_bytes(void);
+VOF_API vof_status vof_mlp_pack(const float* master, void* packed, void* stream);
+VOF_API vof_status vof_mlp_forward(const void* packed, const double* X, long n, float* y, void* stream);
+VOF_API vof_status vof_mlp_normals(const void* packed, const double* X, long n, double* m, uint8_t* fallback,
+                                   void* stream);
+
+/*
+ * One training step of the learned normal on the GPU (forward, backward and
+ * Adam in the library's kernels; the loss is the batch mean of the squared
+ * distance between y / |y|_2 and the label).  The batch holds `batch`
+ * samples (a multiple of 128, 128 ... 65536) of the training set X[ntrain][27]
+ * (FP64 fractions), N[ntrain][3] (FP64 unit normals): with idx == NULL
+ * drawn with replacement, sample s of step `step` being
+ * splitmix64(seed ^ splitmix64(step * 0x100000001B3 + s)) mod ntrain; else
+ * idx[batch] (device, int64) gives them.  Gradients are taken with respect to
+ * the BF16-rounded weights in `packed` (the values the forward pass uses)
+ * and summed over 128-sample tiles in a fixed order (deterministic).  With
+ * lr > 0: Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction with
+ * step >= 1) updates master, adam_m, adam_v (FP32, VOF_MLP_PARAMS each,
+ * zero before step 1) and rewrites packed from the new master; with lr == 0
+ * nothing but grad and loss is written.
+ *   grad       device float[VOF_MLP_PARAMS] (nullable): the batch gradient
+ *   loss       device float[1] (nullable): the batch-mean loss
+ *   workspace  device, vof_mlp_train_workspace_bytes(batch) bytes, 256-byte
+ *              aligned (per-tile partial sums)
+ * VOF_EINVAL for a bad batch, ntrain < 1, null arrays, a short workspace.
+ */
+VOF_API size_t vof_mlp_train_workspace_bytes(int batch);
+VOF_API vof_status vof_mlp_train_step(const double* X, const double* N, long ntrain, int batch,
+                                      unsigned long long seed, long step, float lr, float* master, float* adam_m,
+                                      float* adam_v, void* packed, float* grad, float* loss, const int64_t* idx,
+                                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* Sticky device status (synchronises the device): VOF_OK, VOF_ECFL or
+ * VOF_EWAIT; reading clears it. */
 VOF_API vof_status vof_get_device_status(void);
 /* Message for a status code (static string). */
 VOF_API const char* vof_status_string(int status);

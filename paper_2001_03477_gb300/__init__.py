@@ -25,7 +25,7 @@ from dataclasses import dataclass, field
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvofgb.so")
 
-VOF_OK, VOF_EINVAL, VOF_ECUDA, VOF_ECFL, VOF_ESOLVE = 0, 1, 2, 3, 4
+VOF_OK, VOF_EINVAL, VOF_ECUDA, VOF_ECFL, VOF_ESOLVE, VOF_EWAIT = 0, 1, 2, 3, 4, 5
 VOF_NSUMS = 6
 
 
@@ -44,7 +44,7 @@ class _CGrid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3),
                 ("h", ctypes.c_double), ("Cp_l", ctypes.c_double), ("Cp_g", ctypes.c_double),
                 ("T_sat", ctypes.c_double), ("eps_mixed", ctypes.c_double), ("precision", ctypes.c_int),
-                ("scheme", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("normal", ctypes.c_int), ("mlp", ctypes.c_void_p)]
 
 
 class _CBox(ctypes.Structure):
@@ -67,6 +67,8 @@ class Grid:
     eps_mixed: float = 1e-12
     precision: int = 0  # VOF_F64; VOF_F32_FLUX = 1: the precision form
     scheme: int = 0     # VOF_SCHEME_WY; VOF_SCHEME_LE = 1: Lagrangian-explicit sweeps
+    normal: int = 0     # VOF_NORMAL_MYC; VOF_NORMAL_MLP = 1: learned normals (needs mlp); 2: Youngs
+    mlp: object = field(default=None, repr=False, compare=False)  # packed network parameters (uint8 CUDA tensor)
     _c: _CGrid = field(default=None, repr=False, compare=False)
 
     def c_struct(self):
@@ -78,6 +80,13 @@ class Grid:
         g.T_sat, g.eps_mixed = float(self.T_sat), float(self.eps_mixed)
         g.precision = int(self.precision)
         g.scheme = int(self.scheme)
+        g.normal = int(self.normal)
+        if self.mlp is not None:
+            if getattr(self.mlp, "numel", None) and self.mlp.numel() * self.mlp.element_size() < vof_mlp_packed_bytes():
+                raise ValueError("mlp: shorter than vof_mlp_packed_bytes()")
+            g.mlp = _ptr(self.mlp, None, "mlp").value
+        else:
+            g.mlp = None
         return g
 
     @property
@@ -168,6 +177,21 @@ def lib():
         L.vof_status_string.restype = ctypes.c_char_p
         L.vof_last_cuda_error.argtypes = []
         L.vof_last_cuda_error.restype = ctypes.c_int
+        L.vof_fp64_probe.argtypes = [ctypes.c_int, ctypes.c_long, ctypes.c_int, P, P]
+        L.vof_fp64_probe.restype = ctypes.c_int
+        L.vof_mlp_packed_bytes.argtypes = []
+        L.vof_mlp_packed_bytes.restype = ctypes.c_size_t
+        L.vof_mlp_pack.argtypes = [P, P, P]
+        L.vof_mlp_pack.restype = ctypes.c_int
+        L.vof_mlp_forward.argtypes = [P, P, ctypes.c_long, P, P]
+        L.vof_mlp_forward.restype = ctypes.c_int
+        L.vof_mlp_normals.argtypes = [P, P, ctypes.c_long, P, P, P]
+        L.vof_mlp_normals.restype = ctypes.c_int
+        L.vof_mlp_train_workspace_bytes.argtypes = [ctypes.c_int]
+        L.vof_mlp_train_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_mlp_train_step.argtypes = [P, P, ctypes.c_long, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_long,
+                                         ctypes.c_float, P, P, P, P, P, P, P, P, S, P]
+        L.vof_mlp_train_step.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -510,9 +534,10 @@ def vof_get_device_status() -> int:
     return int(lib().vof_get_device_status())
 
 
-VOF_NCOUNTS = 9
+VOF_NCOUNTS = 12
 VOF_F64, VOF_F32_FLUX = 0, 1  # vof_grid.precision
 VOF_SCHEME_WY, VOF_SCHEME_LE = 0, 1  # vof_grid.scheme
+VOF_NORMAL_MYC, VOF_NORMAL_MLP, VOF_NORMAL_YOUNGS = 0, 1, 2  # vof_grid.normal
 
 
 def vof_step_work_counts(g, workspace, stream=None):
@@ -524,7 +549,15 @@ def vof_step_work_counts(g, workspace, stream=None):
                                                               out, _stream(stream)))
     v = list(out)
     return {"mixed": v[0:6:2], "faces": v[1:6:2], "shift_analytic": v[6], "shift_bisection": v[7],
-            "receivers": v[8]}
+            "receivers": v[8], "mlp_fallback": v[9:12]}
+
+
+def vof_fp64_probe(op, iters, blocks, out, stream=None):
+    """Launch the FP64 rate probe (op 0: fused multiply-adds, 1: adds);
+    out: float64 CUDA tensor of blocks * 256 elements."""
+    _sizes((out, blocks * 256, "out"))
+    _check("vof_fp64_probe", lib().vof_fp64_probe(int(op), int(iters), int(blocks), _ptr(out, _f64(), "out"),
+                                                  _stream(stream)))
 
 
 def vof_profile_begin(stream=None):
@@ -539,6 +572,103 @@ def vof_profile_end(max_entries=4096):
     if n < 0:
         raise VofError("vof_profile_end", VOF_ECUDA, lib())
     return [(names[i].decode(), float(ms[i])) for i in range(min(n, max_entries))]
+
+
+# ---------------------------------------------------------------------------
+# learned interface normal (vof_mlp_*)
+# ---------------------------------------------------------------------------
+VOF_MLP_PARAMS = 6147
+MLP_SIZES = (27, 64, 64, 3)
+
+
+def vof_mlp_packed_bytes() -> int:
+    return int(lib().vof_mlp_packed_bytes())
+
+
+def vof_mlp_pack(master, packed, stream=None):
+    """BF16 weight images of the FP32 master parameters (VOF_MLP_PARAMS
+    floats: W1[64][27], b1, W2[64][64], b2, W3[3][64], b3)."""
+    import torch
+    _sizes((master, VOF_MLP_PARAMS, "master"), (packed, vof_mlp_packed_bytes(), "packed"))
+    _check("vof_mlp_pack", lib().vof_mlp_pack(_ptr(master, torch.float32, "master"), _ptr(packed, None, "packed"),
+                                              _stream(stream)))
+
+
+def vof_mlp_forward(packed, X, y, stream=None):
+    """Network output y[n][3] (float32) of the stencils X[n][27] (float64)."""
+    import torch
+    n = X.numel() // 27
+    _sizes((packed, vof_mlp_packed_bytes(), "packed"), (y, 3 * n, "y"))
+    _check("vof_mlp_forward", lib().vof_mlp_forward(_ptr(packed, None, "packed"), _ptr(X, _f64(), "X"), n,
+                                                    _ptr(y, torch.float32, "y"), _stream(stream)))
+
+
+def vof_mlp_normals(packed, X, m, fallback=None, stream=None):
+    """Learned normals with the MYC fallback: m[n][3] (float64) and
+    fallback[n] (uint8, optional) of the stencils X[n][27]."""
+    n = X.numel() // 27
+    _sizes((packed, vof_mlp_packed_bytes(), "packed"), (m, 3 * n, "m"), (fallback, n, "fallback"))
+    _check("vof_mlp_normals", lib().vof_mlp_normals(_ptr(packed, None, "packed"), _ptr(X, _f64(), "X"), n,
+                                                    _ptr(m, _f64(), "m"), _ptr(fallback, _u8(), "fallback"),
+                                                    _stream(stream)))
+
+
+class MLP:
+    """The learned normal's parameters on the GPU: FP32 master vector, Adam
+    moments, the packed BF16 images and the training workspace (device
+    memory through torch; every computation runs in the library)."""
+
+    def __init__(self, master, device=None):
+        import torch
+        dev = device or torch.device("cuda")
+        self.master = torch.as_tensor(master, dtype=torch.float32).to(dev).contiguous()
+        assert self.master.numel() == VOF_MLP_PARAMS
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        nb = (vof_mlp_packed_bytes() + 255) // 256 * 256
+        self.packed = torch.zeros(nb, dtype=torch.uint8, device=dev)
+        self.step_count = 0
+        self._ws = {}
+        vof_mlp_pack(self.master, self.packed)
+
+    @staticmethod
+    def init_master(seed=0):
+        """He-normal weights, zero biases (numpy float32 vector)."""
+        import numpy as np
+        rng = np.random.default_rng(seed)
+        parts = []
+        for a, b in zip(MLP_SIZES[:-1], MLP_SIZES[1:]):
+            parts.append(rng.normal(0.0, (2.0 / a) ** 0.5, size=(b, a)).reshape(-1))
+            parts.append(np.zeros(b))
+        return np.concatenate(parts).astype(np.float32)
+
+    def workspace(self, batch):
+        import torch
+        if batch not in self._ws:
+            nb = int(lib().vof_mlp_train_workspace_bytes(int(batch)))
+            if nb == 0:
+                raise ValueError(f"batch {batch}: a multiple of 128 in 128..65536")
+            self._ws[batch] = torch.empty(nb + 256, dtype=torch.uint8, device=self.master.device)
+        w = self._ws[batch]
+        off = (-w.data_ptr()) % 256
+        return w[off:], w.numel() - off
+
+    def train_step(self, X, N, batch, lr, seed=0, grad=None, loss=None, idx=None, stream=None):
+        """One Adam step (lr > 0) or only the gradient and loss (lr == 0)."""
+        import torch
+        ntrain = X.numel() // 27
+        _sizes((N, 3 * ntrain, "N"), (grad, VOF_MLP_PARAMS, "grad"), (loss, 1, "loss"), (idx, batch, "idx"))
+        ws, nb = self.workspace(batch)
+        if lr > 0:
+            self.step_count += 1
+        _check("vof_mlp_train_step",
+               lib().vof_mlp_train_step(_ptr(X, _f64(), "X"), _ptr(N, _f64(), "N"), ntrain, int(batch),
+                                        int(seed) & 0xFFFFFFFFFFFFFFFF, max(self.step_count, 1), float(lr),
+                                        _ptr(self.master, torch.float32, "master"),
+                                        _ptr(self.m, torch.float32, "adam_m"), _ptr(self.v, torch.float32, "adam_v"),
+                                        _ptr(self.packed, None, "packed"), _ptr(grad, torch.float32, "grad"),
+                                        _ptr(loss, torch.float32, "loss"), _ptr(idx, torch.int64, "idx"),
+                                        _ptr(ws, None, "workspace"), nb, _stream(stream)))
 
 
 class Stepper:

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvofgb.so")
-SOURCES = ["vof_sweep.cu", "vof_shift.cu", "vof_tiles.cu", "vof_api.cu", "vof_noalloc.cu", "vof_prof.cu",
+SOURCES = ["vof_sweep.cu", "vof_shift.cu", "vof_tiles.cu", "vof_api.cu", "vof_noalloc.cu", "vof_prof.cu", "vof_mlp.cu",
            "vof_mdot.cu", "vof_ext.cu", "vof_diffuse.cu", "vof_ckpt.cu", "vof_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

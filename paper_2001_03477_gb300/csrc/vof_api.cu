@@ -39,6 +39,8 @@ static bool grid_ok(const vof_grid* g) {
   if (!(g->eps_mixed >= 0.0 && g->eps_mixed < 0.5)) return false;
   if (g->precision != VOF_F64 && g->precision != VOF_F32_FLUX) return false;
   if (g->scheme != VOF_SCHEME_WY && g->scheme != VOF_SCHEME_LE) return false;
+  if (g->normal != VOF_NORMAL_MYC && g->normal != VOF_NORMAL_MLP && g->normal != VOF_NORMAL_YOUNGS) return false;
+  if (g->normal == VOF_NORMAL_MLP && (!g->mlp || ((uintptr_t)g->mlp & 15) != 0)) return false;
   return true;
 }
 
@@ -53,6 +55,8 @@ static GridDev to_dev(const vof_grid* g, double dt) {
   std::memcpy(&d.one_m_eps, &ome, 8);
   d.f32 = g->precision == VOF_F32_FLUX ? 1 : 0;
   d.le = g->scheme == VOF_SCHEME_LE ? 1 : 0;
+  d.mlp = g->normal == VOF_NORMAL_MLP ? 1 : (g->normal == VOF_NORMAL_YOUNGS ? 2 : 0);
+  d.mlp_params = d.mlp == 1 ? g->mlp : nullptr;
   return d;
 }
 
@@ -277,6 +281,7 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
     SweepScratch sc = carve_sweep_scratch(ax, d, ws + L.off_sw, sums_to_partials(rows + r * kNSums, kNSums));
     sc.tiles = tm;
     sc.stats = reinterpret_cast<int*>(ws + L.off_stats) + 2 * ax;
+    sc.mlp_stat = reinterpret_cast<int*>(ws + L.off_stats) + 9 + ax;
     err = launch_sweep(ax, d, c, e, c, e, uf[ax], state, th, nullptr, sc, st);
     if (err != cudaSuccess) return cuda_status(err);
     r += (size_t)L.nb_sw[ax];
@@ -416,6 +421,7 @@ vof_status vof_get_device_status(void) {
   int z = 0;
   e = cudaMemcpy(p, &z, sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_status(e);
+  if (h & DEV_WAIT) return VOF_EWAIT;
   return (h & DEV_CFL) ? VOF_ECFL : VOF_OK;
 }
 
@@ -426,6 +432,7 @@ const char* vof_status_string(int status) {
     case VOF_ECUDA: return "CUDA error";
     case VOF_ECFL: return "face CFL number above 1";
     case VOF_ESOLVE: return "iterative solve not converged (or no free-flow face for the velocity extension)";
+    case VOF_EWAIT: return "a bounded device wait gave up (tensor-core completion not seen in time)";
     default: return "unknown status";
   }
 }

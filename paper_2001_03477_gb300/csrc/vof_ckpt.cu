@@ -108,6 +108,9 @@ vof_status vof_checkpoint_info(const char* path, vof_grid* g, long* step, double
   g->precision = hd.precision;
   g->scheme = hd.scheme;
   g->h = hd.h; g->Cp_l = hd.Cp_l; g->Cp_g = hd.Cp_g; g->T_sat = hd.T_sat; g->eps_mixed = hd.eps_mixed;
+  // the network parameters of a learned-normal run are not in the file
+  g->normal = VOF_NORMAL_MYC;
+  g->mlp = nullptr;
   if (step) *step = (long)hd.step;
   if (t) *t = hd.t;
   return VOF_OK;

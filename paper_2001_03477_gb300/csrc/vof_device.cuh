@@ -27,6 +27,9 @@ struct GridDev {
   long long one_m_eps;    // bit pattern of 1 - eps
   int f32;                // precision form: FP32 reconstruction and flux weights in the sweeps
   int le;                 // Lagrangian-explicit sweeps (Li's scheme) instead of Weymouth-Yue
+  int mlp;                // normal of the sweeps' reconstruction: 0 MYC, 1 learned
+                          // (with MYC fallback), 2 Youngs
+  const void* mlp_params; // packed network parameters (device)
 };
 
 // ---------------------------------------------------------------------------

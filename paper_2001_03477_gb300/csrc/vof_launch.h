@@ -66,7 +66,8 @@ struct SweepScratch {
   uint32_t* mlist;   // per-warp staging lists of mixed cells
   uint32_t* rlist;   // per-warp staging lists of run ends
   int* counters;     // [0] mixed cells, [1] face items at the front, [2] at the
-                     // back (faces next to a mixed cell); zeroed before kernel A
+                     // back (faces next to a mixed cell), [3] learned normals
+                     // replaced by MYC; zeroed before kernel A
   uint32_t* gmix;    // grid-wide list of mixed cells, in no fixed order
   uint32_t* gface;   // grid-wide face items (cell << 1 | side), no fixed order
   uint32_t gface_cap;  // entries of gface (2 N)
@@ -74,6 +75,8 @@ struct SweepScratch {
   double* gplane;    // [2][N / n_axis][4]: planes of the ghost donors beyond the
                      // low / high zero-gradient end of each line (boundary
                      // cells that are mixed only)
+  int* mlp_stat;     // nullable: kernel U copies counters[3] (learned normals
+                     // replaced by MYC in this sweep) here
   double* F;         // face arrays of the axis (face layout of the velocities)
   double* G;
 };
@@ -176,7 +179,7 @@ void prof_mark(const char* name, cudaStream_t st);
 void set_last_cuda_error(int err);
 
 // sticky device status word (iteration caps, CFL > 1): bit flags
-enum : int { DEV_CFL = 1 };
+enum : int { DEV_CFL = 1, DEV_WAIT = 2 };
 int* device_status_ptr();
 
 // Mass transfer rate (vof_mdot.cu): workspace size, the launch of its four
@@ -194,6 +197,22 @@ cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* 
                                       double rho_g, double dt, double tol, int max_iter, double* u, double* v,
                                       double* w, double* ut, double* vt, double* wt, void* workspace,
                                       cudaStream_t st, int* iters_out, double* res_out, int* status);
+
+// Learned interface normal (vof_mlp.cu): packed parameter size, packing of
+// the FP32 master parameters, forward pass and normals (with MYC fallback)
+// on explicit stencils, the normals of a sweep's mixed cells, and one
+// training step (forward, backward, Adam).
+size_t mlp_packed_bytes();
+int mlp_param_count();
+cudaError_t launch_mlp_pack(const float* master, void* packed, cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* params, const double* X, long n, float* y, cudaStream_t st);
+cudaError_t launch_mlp_normals(const void* params, const double* X, long n, double* m, uint8_t* flag,
+                               int* nfallback, cudaStream_t st);
+cudaError_t launch_mlp_sweep_normals(const GridDev& g, const double* c, const SweepScratch& sc, cudaStream_t st);
+cudaError_t launch_mlp_train_step(const double* X, const double* N, long ntrain, int batch, unsigned long long seed,
+                                  long step, float* master, float* mom, float* vel, void* packed, float* partial,
+                                  float* loss_part, const long* idx_fixed, float lr, float beta1, float beta2,
+                                  float eps, float* grad_out, float* loss_out, cudaStream_t st);
 
 // Heat diffusion (vof_diffuse.cu): workspace size and the whole solve;
 // *status: 0 converged, 2 not converged within max_iter.

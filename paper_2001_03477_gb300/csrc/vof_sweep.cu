@@ -436,8 +436,8 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
 // PLIC plane (MYC normal, plane constant) of the 3x3x3 stencil centred on
 // position (qx, qy, qz), each index mapped by the boundary conditions.
 // F32: the precision form's FP32 MYC normal (its own instance, so that the
-// FP64 form keeps its register budget)
-template <bool F32>
+// FP64 form keeps its register budget); YOUNGS: Youngs' normal instead
+template <bool F32, bool YOUNGS = false>
 __device__ __forceinline__ double4 stencil_plane(const GridDev& g, const double* __restrict__ c_in, int qx, int qy,
                                                  int qz) {
   double s[27];
@@ -455,7 +455,8 @@ __device__ __forceinline__ double4 stencil_plane(const GridDev& g, const double*
     }
   }
   double m[3];
-  if (F32) myc_normal_f(s, m);
+  if (YOUNGS) youngs_normal(s, m);
+  else if (F32) myc_normal_f(s, m);
   else myc_normal(s, m);
   double4 pl;
   pl.x = m[0]; pl.y = m[1]; pl.z = m[2];
@@ -469,7 +470,10 @@ __device__ __forceinline__ double4 stencil_plane(const GridDev& g, const double*
 // n) from the ghost's own 3x3x3 stencil of the boundary-filled field, whose
 // cells beyond the boundary are copies of the boundary layer (dc/dn = 0);
 // stored in sc.gplane[side][line].
-template <bool F32>
+// NRM 1: the mixed cells' normals are already in sc.plane (the learned
+// normal with its MYC fallback, vof_mlp.cu); only their plane constants are
+// formed here.  NRM 2: Youngs' normal.  Ghost donors keep MYC.
+template <bool F32, int NRM>
 __global__ void __launch_bounds__(kPlaneThreads)
 k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc, int ax) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -504,9 +508,15 @@ k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_
       continue;
     }
     const size_t id = sc.gmix[i];
+    if (NRM == 1) {
+      double4* pl = reinterpret_cast<double4*>(sc.plane) + id;
+      const double4 m = *pl;
+      pl->w = plane_alpha(m.x, m.y, m.z, __ldg(c_in + id));
+      continue;
+    }
     int x, y, z;
     cell_xyz(g, id, x, y, z);
-    reinterpret_cast<double4*>(sc.plane)[id] = stencil_plane<F32>(g, c_in, x, y, z);
+    reinterpret_cast<double4*>(sc.plane)[id] = stencil_plane<F32, NRM == 2>(g, c_in, x, y, z);
   }
 }
 
@@ -576,7 +586,7 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
           const size_t li = AX == 0 ? (size_t)z * ny + y : (AX == 1 ? (size_t)z * nx + x : (size_t)y * nx + x);
           pl = reinterpret_cast<const double4*>(sc.gplane)[(dq < 0 ? 0 : lines) + li];
         } else {
-          pl = reinterpret_cast<const double4*>(sc.plane)[lbase + stride * dq];
+          pl = reinterpret_cast<const double4*>(sc.plane)[lbase + stride * map_idx(dq, n_ax, bca)];
         }
         const double mv[3] = {pl.x, pl.y, pl.z};
         const double da = fabs(a);
@@ -685,6 +695,9 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
   if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
     sc.stats[0] = sc.counters[0];
     sc.stats[1] = sc.counters[1] + sc.counters[2];
+  }
+  if (sc.mlp_stat && blockIdx.x == 0 && threadIdx.x == 0) {
+    sc.mlp_stat[0] = sc.counters[3];
   }
   block_sums(v, sc.sums, blockIdx.x);
 }
@@ -859,6 +872,7 @@ SweepScratch carve_sweep_scratch(int axis, const GridDev& g, void* ws, SumOut su
   s.sums = sums;
   s.tiles = TileMap{nullptr, {0, 0, 0}};
   s.stats = nullptr;
+  s.mlp_stat = nullptr;
   s.mlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
   s.rlist = reinterpret_cast<uint32_t*>(b);     b += al256((size_t)p.nsub * p.cap * 4);
   s.counters = reinterpret_cast<int*>(b);       b += 256;
@@ -885,8 +899,18 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
     k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
                                                                           flux_out != nullptr, p.cap, c_out != c_in);
   prof_mark(AX == 0 ? "sweep_x.stream" : (AX == 1 ? "sweep_y.stream" : "sweep_z.stream"), st);
-  if (g.f32) k_prep<true><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
-  else k_prep<false><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+  if (g.mlp == 1) {
+    // learned normals of the mixed cells (tensor cores), then their planes
+    launch_mlp_sweep_normals(g, c_in, sc, st);
+    if (g.f32) k_prep<true, 1><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+    else k_prep<false, 1><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+  } else if (g.mlp == 2) {
+    k_prep<false, 2><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+  } else if (g.f32) {
+    k_prep<true, 0><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+  } else {
+    k_prep<false, 0><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+  }
   prof_mark(AX == 0 ? "sweep_x.prep" : (AX == 1 ? "sweep_y.prep" : "sweep_z.prep"), st);
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
@@ -900,7 +924,7 @@ cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const d
                          SweepScratch sc, cudaStream_t st) {
   int* status = device_status_ptr();
   const SweepPlan p = sweep_plan(axis, g);
-  const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
+  const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(int), st);
   if (err != cudaSuccess) return err;
   prof_mark("sweep.memset", st);
   if (e_in) {
