@@ -903,8 +903,19 @@ def kernels_once():
     # and one evaluation of the mass transfer rate of the state reached
     mdot = torch.empty_like(c)
     P.vof_mass_transfer(g, c, e, K_L_WATER, K_G_STEAM, W.H_FG_WATER, mdot)
+    # the learned normal: one forward pass over 131072 stencils, their
+    # normals with the MYC fallback, and one training step of 16384 samples
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.random((131072, 27))).to(dev)
+    N = torch.nn.functional.normalize(torch.from_numpy(rng.normal(size=(131072, 3))), dim=1).to(dev)
+    mlp = P.MLP(P.MLP.init_master(5), device=dev)
+    y = torch.empty((131072, 3), dtype=torch.float32, device=dev)
+    P.vof_mlp_forward(mlp.packed, X, y)
+    m = torch.empty((131072, 3), dtype=torch.float64, device=dev)
+    P.vof_mlp_normals(mlp.packed, X, m)
+    mlp.train_step(X, N, 16384, 1e-3, seed=1)
     torch.cuda.synchronize()
-    print("kernels-once ok", [float(x) for x in st.sums.cpu()], float(mdot.sum()))
+    print("kernels-once ok", [float(x) for x in st.sums.cpu()], float(mdot.sum()), float(y.abs().sum()))
 
 
 def main():
