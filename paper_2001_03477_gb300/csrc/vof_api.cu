@@ -50,6 +50,8 @@ static GridDev to_dev(const vof_grid* g, double dt) {
   d.bc[0] = g->bc[0]; d.bc[1] = g->bc[1]; d.bc[2] = g->bc[2];
   d.lam = dt / g->h;
   d.Cp_l = g->Cp_l; d.Cp_g = g->Cp_g; d.T_sat = g->T_sat; d.eps = g->eps_mixed;
+  d.rCp_l = 1.0 / g->Cp_l;
+  d.rCp_g = 1.0 / g->Cp_g;
   double ome = 1.0 - g->eps_mixed;
   std::memcpy(&d.eps_bits, &g->eps_mixed, 8);
   std::memcpy(&d.one_m_eps, &ome, 8);

@@ -13,6 +13,8 @@
 #pragma once
 #include <cstdint>
 
+#include "vof_df.cuh"
+
 namespace vofgb {
 
 // ---------------------------------------------------------------------------
@@ -27,6 +29,7 @@ struct GridDev {
   long long one_m_eps;    // bit pattern of 1 - eps
   int f32;                // precision form: FP32 reconstruction and flux weights in the sweeps
   int le;                 // Lagrangian-explicit sweeps (Li's scheme) instead of Weymouth-Yue
+  double rCp_l, rCp_g;    // 1 / Cp_l, 1 / Cp_g (T of pure cells by a multiply)
   int mlp;                // normal of the sweeps' reconstruction: 0 MYC, 1 learned
                           // (with MYC fallback), 2 Youngs
   const void* mlp_params; // packed network parameters (device)
@@ -71,6 +74,18 @@ __device__ __forceinline__ int map_idx(int i, int n, int bc) {
 
 __device__ __forceinline__ double heat_cap(double Cp_l, double Cp_g, double c) {
   return Cp_l * c + Cp_g * (1.0 - c);
+}
+
+// T = e / C_p(c).  A pure cell (c exactly 0 or 1) multiplies by the
+// phase's reciprocal heat capacity, within 2 ulps of the quotient, instead
+// of dividing (an FP64 division costs ~10 FP64 instructions on this part);
+// every kernel that needs T of a cell calls this one function, so equal
+// (c, e) always give equal T.
+__device__ __forceinline__ double temp_of(const GridDev& g, double e, double c) {
+  const long long b = __double_as_longlong(c);
+  if (b == 0x3FF0000000000000LL) return e * g.rCp_l;
+  if (b == 0) return e * g.rCp_g;
+  return e / heat_cap(g.Cp_l, g.Cp_g, c);
 }
 
 __device__ __forceinline__ bool is_mixed(double c, double eps) { return c > eps && c < 1.0 - eps; }
@@ -660,32 +675,11 @@ __device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
 }
 
 // ---------------------------------------------------------------------------
-// WENO5 face value (Jiang-Shu weights, eps 1e-6), upwind-ordered stencil
+// WENO5 face value (Jiang-Shu weights, eps 1e-6), upwind-ordered stencil:
+// weno5_df (vof_df.cuh), the weights and the correction to the donor value
+// in double-float pairs (FP64-accurate, a fraction of the FP64 instructions).
+// Five equal values return the donor value exactly.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double weno5(double vm2, double vm1, double v0, double vp1, double vp2) {
-  if (deq(vm2, v0) && deq(vm1, v0) && deq(vp1, v0) && deq(vp2, v0)) return v0;
-  // Jiang-Shu weights alpha_k = d_k / (eps + beta_k)^2 written over a common
-  // denominator, T_f = v0 + sum d_k r_k prod_{j!=k} s_j / (6 sum d_k
-  // prod_{j!=k} s_j) with s_j = (eps + beta_j)^2, everything in the four
-  // neighbour differences D: the candidate values are 6 v0 + r_k, the
-  // smoothness indicators' second and first differences are differences of
-  // D.  One division and ~45 FP64 operations (the FP64 unit is the scarce
-  // resource on this part); the same value as the textbook form up to
-  // rounding.
-  const double epsw = 1e-6;
-  const double D0 = vm1 - vm2, D1 = v0 - vm1, D2 = vp1 - v0, D3 = vp2 - vp1;
-  const double d0 = D1 - D0, d1 = D2 - D1, d2 = D3 - D2;
-  const double e0 = fma(3.0, D1, -D0), e1 = D1 + D2, e2 = fma(-3.0, D2, D3);
-  const double b0 = fma(13.0 / 12.0 * d0, d0, 0.25 * e0 * e0);
-  const double b1 = fma(13.0 / 12.0 * d1, d1, 0.25 * e1 * e1);
-  const double b2 = fma(13.0 / 12.0 * d2, d2, 0.25 * e2 * e2);
-  const double t0 = epsw + b0, t1 = epsw + b1, t2 = epsw + b2;
-  const double s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
-  const double w0 = 0.1 * (s1 * s2), w1 = 0.6 * (s0 * s2), w2 = 0.3 * (s0 * s1);
-  const double r0 = fma(5.0, D1, -2.0 * D0), r1 = fma(2.0, D2, D1), r2 = fma(4.0, D2, -D3);
-  const double num = fma(w0, r0, fma(w1, r1, w2 * r2));
-  return v0 + num / (6.0 * (w0 + w1 + w2));
-}
 
 // ---------------------------------------------------------------------------
 // Precision form (vof_grid.precision = VOF_F32_FLUX): the sweeps'

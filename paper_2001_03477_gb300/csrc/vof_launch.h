@@ -85,7 +85,8 @@ struct SweepPlan {
   dim3 gridA, blockA;
   int cap;          // list capacity per warp of kernel A
   long long nsub;   // number of lists (warps of kernel A)
-  unsigned gridB;   // CTAs of kernel U (8 lists each)
+  unsigned gridB;   // CTAs of kernel U (lpc lists each)
+  int lpc;          // kernel-A lists per CTA of kernel U
 };
 
 SweepPlan sweep_plan(int axis, const GridDev& g);

@@ -74,8 +74,10 @@ __device__ __forceinline__ size_t cell_at(const GridDev& g, int x, int y, int z)
 // upwind-ordered stencil
 __device__ __forceinline__ double face_energy_flux(double Cp_l, double Cp_g, double Fv, double a, double t0, double t1,
                                                 double t2, double t3, double t4, bool f32) {
-  const double Tf = f32 ? weno5_f(t0, t1, t2, t3, t4) : weno5(t0, t1, t2, t3, t4);
-  return (Tf * Cp_l) * Fv + (Tf * Cp_g) * (a - Fv);
+  const double Tf = f32 ? weno5_f(t0, t1, t2, t3, t4) : weno5_df(t0, t1, t2, t3, t4);
+  // one rounding of (T_f C_pl) F, as in the separate product: a pure cell
+  // (F = a or 0) still gives (T_f C_pl) a or (T_f C_pg) a exactly
+  return fma(Tf * Cp_l, Fv, (Tf * Cp_g) * (a - Fv));
 }
 
 // WY update of one cell from its two faces; returns the clipped volume
@@ -90,8 +92,10 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
   const bool lag = g.le != 0;
   const bool dirty = !lag && (stv & 1);
   const bool ccb = dirty ? ((stv >> 1) & 1) != 0 : dgthalf(c);
-  const double ccv = lag ? c : (ccb ? 1.0 : 0.0);
-  const double lf = Fl - ccv * al, rf = Fr - ccv * ar;
+  // Weymouth-Yue: cc is 0 or 1, so cc a is a or 0 exactly (no multiply);
+  // Lagrangian explicit: the cell's own c
+  const double lf = lag ? Fl - c * al : (ccb ? Fl - al : Fl);
+  const double rf = lag ? Fr - c * ar : (ccb ? Fr - ar : Fr);
   const double cn = (c + lf) - rf;
   double cc2 = cn, clip = 0.0;
   if (dlt0(cn)) { cc2 = 0.0; clip = cn; }
@@ -123,6 +127,7 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
 constexpr int kSegA = 32;     // cells per lane along y / z
 constexpr int kWarpsA = 8;    // warps per CTA of kernel A
 constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
+constexpr int kMaxLPC = 256;  // kernel-A lists per CTA of kernel U, at most
 constexpr int kPlaneThreads = 128;  // kernel M: CTA size; grid kPlaneCTAs
 constexpr int kPlaneCTAs = 152 * 8;
 
@@ -504,7 +509,7 @@ k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_
       const uint32_t item = face_item(sc, i - nm, nf);
       if (item & 1u) continue;  // right-face item: its cell has a left item too
       const size_t id = item >> 1;
-      sc.T[id] = __ldg(e_in + id) / heat_cap(g.Cp_l, g.Cp_g, __ldg(c_in + id));
+      sc.T[id] = temp_of(g, __ldg(e_in + id), __ldg(c_in + id));
       continue;
     }
     const size_t id = sc.gmix[i];
@@ -567,7 +572,7 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
       ew[j] = ENERGY ? __ldg(e_in + jd) : 0.0;
       if (ENERGY && j >= 1) {
         const bool dif = !(same_bits(cw[j], cw[j - 1]) && same_bits(ew[j], ew[j - 1]));
-        Tw[j] = dif ? sc.T[jd] : (j == 1 ? ew[j] / heat_cap(g.Cp_l, g.Cp_g, cw[j]) : Tw[j - 1]);
+        Tw[j] = dif ? sc.T[jd] : (j == 1 ? temp_of(g, ew[j], cw[j]) : Tw[j - 1]);
       }
     }
     const int fr = (bca == 0 && f == n_ax) ? 0 : f;
@@ -637,39 +642,53 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 }
 
 // ---------------------------------------------------------------------------
-// Kernel U: one CTA per 8 kernel-A lists (fixed order, so the sums are
-// reproducible), one listed cell per thread: the WY update from the two face
-// fluxes.  It reads no cell but its own, so it may update in place
-// (c_out == c_in, e_out == e_in); kernel A then copies nothing.
+// Kernel U: one CTA per `lpc` consecutive kernel-A lists (fixed order, so
+// the sums are reproducible), one listed cell per thread: the WY update from
+// the two face fluxes.  It reads no cell but its own, so it may update in
+// place (c_out == c_in, e_out == e_in); kernel A then copies nothing.
 // ---------------------------------------------------------------------------
 template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(256)
 k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out,
          const double* __restrict__ uf, uint8_t* __restrict__ state,
-         double* __restrict__ theta, SweepScratch sc, int nsub, int cap) {
+         double* __restrict__ theta, SweepScratch sc, int nsub, int cap, int lpc) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  // the CTA takes the 8 lists sub0 .. sub0+7 as one sequence (fixed order):
-  // short lists then still fill whole warps
-  __shared__ int pre[9];
-  const int sub0 = blockIdx.x * 8;
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < 8; ++w) {
-      pre[w] = t;
-      t += (sub0 + w < nsub) ? sc.count[sub0 + w] : 0;
+  // the CTA takes the lists sub0 .. sub0 + lpc - 1 as one sequence (fixed
+  // order): short lists then still fill whole warps.  pre[w] = cells of
+  // the lists before list w (an exclusive scan by the first warp)
+  __shared__ int pre[kMaxLPC + 1];
+  const int sub0 = blockIdx.x * lpc;
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int w0 = 0; w0 < lpc; w0 += 32) {
+      const int w = w0 + (int)threadIdx.x;
+      const int cnt = (w < lpc && sub0 + w < nsub) ? sc.count[sub0 + w] : 0;
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)threadIdx.x >= o) incl += y;
+      }
+      if (w < lpc) pre[w] = carry + incl - cnt;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    pre[8] = t;
+    if (threadIdx.x == 0) pre[lpc] = carry;
   }
   __syncthreads();
-  const int total = pre[8];
+  const int total = pre[lpc];
   double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   {
     for (int j = threadIdx.x; j < total; j += blockDim.x) {
-      int w = 0;
-#pragma unroll
-      for (int q = 1; q < 8; ++q) w += (j >= pre[q]) ? 1 : 0;
+      // the list holding entry j: the last w with pre[w] <= j
+      int lo = 0, hi = lpc - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= j) lo = mid;
+        else hi = mid - 1;
+      }
+      const int w = lo;
       const size_t id = sc.list[(size_t)(sub0 + w) * cap + (j - pre[w])] & ~kMixedAdj;
       int x, y, z;
       cell_xyz(g, id, x, y, z);
@@ -730,7 +749,7 @@ k_energy(GridDev g, const double* __restrict__ c_before, const double* __restric
     double ev = e_in[id], cv = c_before[id];
     sE[q] = ev;
     sC[q] = cv;
-    sT[q] = ev / heat_cap(g.Cp_l, g.Cp_g, cv);
+    sT[q] = temp_of(g, ev, cv);
   }
   __syncthreads();
   const int nax = g.n[AX];
@@ -759,8 +778,8 @@ k_energy(GridDev g, const double* __restrict__ c_before, const double* __restric
           int px = tx + (AX == 0 ? rr : 0), py = ty + (AX == 1 ? rr : 0), pz = tz + (AX == 2 ? rr : 0);
           v[r + 2] = sT[(pz * TY + py) * TX + px];
         }
-        double Tf = g.f32 ? weno5_f(v[0], v[1], v[2], v[3], v[4]) : weno5(v[0], v[1], v[2], v[3], v[4]);
-        Gv = (Tf * g.Cp_l) * Fv + (Tf * g.Cp_g) * (a - Fv);
+        // the fused sweep's face energy flux, bit for bit
+        Gv = face_energy_flux(g.Cp_l, g.Cp_g, Fv, a, v[0], v[1], v[2], v[3], v[4], g.f32 != 0);
       }
     }
     sG[q] = Gv;
@@ -822,7 +841,14 @@ SweepPlan sweep_plan(int axis, const GridDev& g) {
     p.cap = (g.n[0] < 32 ? g.n[0] : 32) * (g.n[axis] < kSegA ? g.n[axis] : kSegA);
     p.nsub = (long long)p.gridA.x * p.gridA.y * p.gridA.z * kWarpsA;
   }
-  p.gridB = (unsigned)((p.nsub + 7) / 8);
+  // kernel U: consecutive lists per CTA, enough that the CTAs (and their
+  // FP64 sum trees) number at most ~16 per SM whatever the list count (a
+  // few waves of resident CTAs: fewer, larger CTAs leave a tail of idle
+  // SMs in the last wave); a power of two from 8 to kMaxLPC
+  int lpc = 8;
+  while (lpc < kMaxLPC && p.nsub / lpc > 152 * 16) lpc *= 2;
+  p.lpc = lpc;
+  p.gridB = (unsigned)((p.nsub + lpc - 1) / lpc);
   return p;
 }
 
@@ -915,7 +941,7 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
   k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,
-                                                 p.cap);
+                                                 p.cap, p.lpc);
   prof_mark(AX == 0 ? "sweep_x.update" : (AX == 1 ? "sweep_y.update" : "sweep_z.update"), st);
 }
 

@@ -198,8 +198,11 @@ def test_sweep(P, name, axis):
     changed = (cg != c) | (eg != e)
     assert np.array_equal(st & 1, changed.astype(np.uint8))
     assert np.array_equal(((st >> 1) & 1) == 1, (cc == 1) & changed)
+    # Theta = C_p(cc) T^n (reading A6) is an FP64 value of the update, not a
+    # decision: T of a pure cell is formed as e x (1 / C_p) on the GPU
+    # (within 2 ulps of the oracle's quotient), so Theta agrees to 8 ulps
     thg = host(theta)
-    assert np.array_equal(thg[changed], th[changed])
+    assert (np.abs(thg[changed] - th[changed]) <= 8 * np.finfo(float).eps * np.abs(th[changed])).all()
 
     # unfused: VOF-only sweep + consistent energy update == fused, bitwise
     c3 = torch.empty_like(cd); e3 = torch.empty_like(ed)
