@@ -393,14 +393,24 @@ VOF_API vof_status vof_velocity_extension(const vof_grid* g, const double* c, co
  * a liquid node, 3.5 - H of a gas node), else the distance along the axis
  * to the PLIC plane of the pair's mixed cell (the node's own if mixed, else
  * the neighbour's), half a cell when both are pure or the plane is parallel
- * to the axis; capped to [1e-3 h, h].  Zero-gradient walls carry no flux.
- * Backward Euler, C_p(c) (T' - T)/dt = k_p sum L(T'), solved by Jacobi
- * sweeps (the system is strictly diagonally dominant) until no T changes by
- * more than tol in a sweep (or max_iter sweeps); e' = C_p(c) T'.
+ * to the axis; capped to [1e-3 h, h].  Zero-gradient walls carry no flux,
+ * unless wall_T gives the face a fixed temperature T_w: the node then sees
+ * the wall half a cell away, gradient (T_w - T)/(h/2), d = h/2 (the heated
+ * wall of the Stefan problem, Sec. 4.3).  Backward Euler with T = e/C_p(c),
+ * solved by Jacobi sweeps (the system is strictly diagonally dominant)
+ * until no T changes by more than tol in a sweep (or max_iter sweeps):
+ *   VOF_CP_PHASE (the paper's phase-by-phase solve with constant properties
+ *     in each phase): C_p,node (T' - T)/dt = k_p sum L(T'), C_p,node the
+ *     heat capacity of the node's phase, and e' = e + C_p,node (T' - T);
+ *   VOF_CP_MIXTURE: C_p(c) (T' - T)/dt = k_p sum L(T'), e' = C_p(c) T'.
  *   c            device double[N], read only
  *   e            device double[N], read and overwritten with e'
  *   k_l, k_g     conductivities (>= 0); dt > 0; tol > 0 (absolute, in T);
  *                max_iter >= 1
+ *   heat_capacity  VOF_CP_PHASE or VOF_CP_MIXTURE
+ *   wall_T       host double[6] or NULL: fixed temperatures of the faces
+ *                x-, x+, y-, y+, z-, z+ (NaN: none); only on zero-gradient
+ *                axes
  *   iterations, change   host int / double or NULL: sweeps made and the
  *                last sweep's largest change
  *   workspace    device buffer of vof_heat_diffusion_workspace_bytes(g)
@@ -410,9 +420,12 @@ VOF_API vof_status vof_velocity_extension(const vof_grid* g, const double* c, co
  * from the last sweep).
  */
 VOF_API size_t vof_heat_diffusion_workspace_bytes(const vof_grid* g);
+#define VOF_CP_PHASE 0
+#define VOF_CP_MIXTURE 1
 VOF_API vof_status vof_heat_diffusion(const vof_grid* g, const double* c, double* e, double k_l, double k_g,
-                                      double dt, double tol, int max_iter, int* iterations, double* change,
-                                      void* workspace, size_t workspace_bytes, void* stream);
+                                      double dt, double tol, int max_iter, int heat_capacity, const double* wall_T,
+                                      int* iterations, double* change, void* workspace, size_t workspace_bytes,
+                                      void* stream);
 
 /*
  * Checkpoint and resume (host code; the paper has no counterpart): the

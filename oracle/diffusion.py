@@ -31,9 +31,9 @@ What it computes (readings of the paper's 2D description, in 3D):
     periodic axes wrap;
   * backward Euler: C_p(c) (T^{n+1} - T^n) / dt = k_p sum_axes L_axis(T^{n+1})
     with T^n = e / C_p(c), and e^{n+1} = C_p(c) T^{n+1}
-    (heat_capacity="mixture", the reading the GPU kernel follows);
-  * heat_capacity="phase": the other reading of the phase-by-phase solve
-    with constant properties in each phase: every node diffuses with the
+    (heat_capacity="mixture", reading A22);
+  * heat_capacity="phase" (the default, reading A24): the phase-by-phase
+    solve with constant properties in each phase: every node diffuses with the
     constant C_p of its phase, C_p,node (T^{n+1} - T^n) / dt = k_p sum L,
     and the cell's energy changes by the heat conducted into it,
     e^{n+1} = e^n + C_p,node (T^{n+1} - T^n).  Pure cells are unchanged by
@@ -181,7 +181,7 @@ def _system(g: Grid, c, k_l, k_g, wall_T=None):
     return A.tocsr(), b
 
 
-def diffuse(g: Grid, c, e, k_l, k_g, dt, wall_T=None, heat_capacity="mixture"):
+def diffuse(g: Grid, c, e, k_l, k_g, dt, wall_T=None, heat_capacity="phase"):
     """One backward-Euler diffusion step; returns e^{n+1}."""
     from scipy.sparse import diags
     from scipy.sparse.linalg import spsolve

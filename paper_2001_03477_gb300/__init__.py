@@ -125,7 +125,7 @@ def lib():
             "vof_mass_transfer": [G, P, P, D, D, D, P, P, P, D, P, P, S, P],
             "vof_velocity_extension": [G, P, P, D, D, D, D, I, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double), P, S, P],
-            "vof_heat_diffusion": [G, P, P, D, D, D, D, I, ctypes.POINTER(ctypes.c_int),
+            "vof_heat_diffusion": [G, P, P, D, D, D, D, I, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_double), P, S, P],
         }
         for name, args in sig.items():
@@ -461,9 +461,16 @@ def vof_heat_diffusion_workspace_bytes(g: Grid) -> int:
     return int(lib().vof_heat_diffusion_workspace_bytes(ctypes.byref(cg)))
 
 
-def vof_heat_diffusion(g, c, e, k_l, k_g, dt, tol=1e-10, max_iter=10000, workspace=None, stream=None):
+VOF_CP_PHASE, VOF_CP_MIXTURE = 0, 1  # heat capacity of vof_heat_diffusion
+
+
+def vof_heat_diffusion(g, c, e, k_l, k_g, dt, tol=1e-10, max_iter=10000, heat_capacity=VOF_CP_PHASE, wall_T=None,
+                       workspace=None, stream=None):
     """Implicit interface-Dirichlet heat diffusion (Sec. 3.4.2) of e in
-    place.  Returns (Jacobi sweeps, last sweep's largest change of T)."""
+    place, each node with its phase's heat capacity (VOF_CP_PHASE) or the
+    cell's mixture (VOF_CP_MIXTURE); wall_T: {(axis, side): T_w} fixed wall
+    temperatures (side -1 low, +1 high).  Returns (Jacobi sweeps, last
+    sweep's largest change of T)."""
     _sizes((c, g.cells, "c"), (e, g.cells, "e"))
     cg = g.c_struct()
     if workspace is None:
@@ -471,9 +478,15 @@ def vof_heat_diffusion(g, c, e, k_l, k_g, dt, tol=1e-10, max_iter=10000, workspa
     nbytes = workspace.numel() * workspace.element_size()
     it = ctypes.c_int(0)
     ch = ctypes.c_double(0.0)
+    walls = None
+    if wall_T:
+        walls = (ctypes.c_double * 6)(*([float("nan")] * 6))
+        for (axis, side), Tw in wall_T.items():
+            walls[2 * int(axis) + (0 if side < 0 else 1)] = float(Tw)
     _check("vof_heat_diffusion",
            lib().vof_heat_diffusion(ctypes.byref(cg), _ptr(c, _f64(), "c"), _ptr(e, _f64(), "e"), float(k_l),
-                                    float(k_g), float(dt), float(tol), int(max_iter), ctypes.byref(it),
+                                    float(k_g), float(dt), float(tol), int(max_iter), int(heat_capacity), walls,
+                                    ctypes.byref(it),
                                     ctypes.byref(ch), _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes),
                                     _stream(stream)))
     return it.value, ch.value

@@ -395,10 +395,18 @@ size_t vof_heat_diffusion_workspace_bytes(const vof_grid* g) {
 }
 
 vof_status vof_heat_diffusion(const vof_grid* g, const double* c, double* e, double k_l, double k_g, double dt,
-                              double tol, int max_iter, int* iterations, double* change, void* workspace,
-                              size_t workspace_bytes, void* stream) {
+                              double tol, int max_iter, int heat_capacity, const double* wall_T, int* iterations,
+                              double* change, void* workspace, size_t workspace_bytes, void* stream) {
   if (!grid_ok(g) || !c || !e || !workspace) return VOF_EINVAL;
   if (!(k_l >= 0.0) || !(k_g >= 0.0) || !(dt > 0.0) || !(tol > 0.0) || max_iter < 1) return VOF_EINVAL;
+  if (heat_capacity != VOF_CP_PHASE && heat_capacity != VOF_CP_MIXTURE) return VOF_EINVAL;
+  if (wall_T) {
+    for (int f = 0; f < 6; ++f) {
+      const double Tw = wall_T[f];
+      if (Tw != Tw) continue;                                   // NaN: no wall temperature on this face
+      if (g->bc[f / 2] != 1 || !(Tw > -1e300 && Tw < 1e300)) return VOF_EINVAL;  // finite, zero-gradient axis
+    }
+  }
   if (((uintptr_t)workspace & 255) != 0) return VOF_EINVAL;
   const size_t N = cells(g), B = N * 8;
   const size_t need = dif_scratch_bytes(N);
@@ -406,7 +414,8 @@ vof_status vof_heat_diffusion(const vof_grid* g, const double* c, double* e, dou
   if (overlap(c, B, e, B) || overlap(workspace, need, c, B) || overlap(workspace, need, e, B)) return VOF_EINVAL;
   int it = 0, st = 0;
   double ch = 0.0;
-  cudaError_t err = launch_heat_diffusion(to_dev(g, 0.0), g->h, c, e, k_l, k_g, dt, tol, max_iter, workspace,
+  cudaError_t err = launch_heat_diffusion(to_dev(g, 0.0), g->h, c, e, k_l, k_g, dt, tol, max_iter,
+                                          heat_capacity == VOF_CP_PHASE ? 1 : 0, wall_T, workspace,
                                           (cudaStream_t)stream, &it, &ch, &st);
   if (err != cudaSuccess) return cuda_status(err);
   if (iterations) *iterations = it;

@@ -14,8 +14,17 @@
 // of a gas node), else the distance along the axis to the PLIC plane of the
 // pair's mixed cell (the node's own if mixed, else the neighbour's), half a
 // cell when both are pure or the plane is parallel to the axis; capped to
-// [1e-3 h, h].  Zero-gradient walls carry no flux; periodic axes wrap.
-// Backward Euler: C_p(c) (T' - T) / dt = k_p sum L(T'), e' = C_p(c) T'.
+// [1e-3 h, h].  Zero-gradient walls carry no flux unless the caller fixes
+// their temperature T_w: the node then sees the wall half a cell away,
+// gradient (T_w - T) / (h / 2), d = h / 2 (the heated wall of Sec. 4.3).
+// Periodic axes wrap.  Backward Euler with the heat capacity of the
+// reading chosen:
+//   phase (the default): every node diffuses with the constant C_p of its
+//     phase, C_p,node (T' - T) / dt = k_p sum L(T'), and the cell's energy
+//     changes by the heat conducted into it, e' = e + C_p,node (T' - T)
+//     (Sec. 3.4.2 solves phase by phase with constant properties);
+//   mixture: C_p(c) (T' - T) / dt = k_p sum L(T'), e' = C_p(c) T'.
+// T = e / C_p(c) in both.
 //
 // Kernels: k_dif_planes (MYC normal and plane constant of the mixed cells),
 // k_dif_assemble (per cell: the six couplings, the diagonal and the right
@@ -128,6 +137,12 @@ __device__ double interface_theta(const GridDev& g, const double* __restrict__ c
   return fmin(fmax(theta, kThetaEps), 1.0);
 }
 
+// walls at fixed temperature, per face x-, x+, y-, y+, z-, z+
+struct DifWalls {
+  double T[6];
+  int on[6];
+};
+
 struct DifVec {
   double* off;    // [6 N]: coupling to the neighbour (face order -x, +x, -y, +y, -z, +z)
   double* diag;   // [N]
@@ -139,7 +154,8 @@ struct DifVec {
 
 __global__ void __launch_bounds__(kDifThreads)
 k_dif_assemble(GridDev g, double h, double dt, double k_l, double k_g, const double* __restrict__ c,
-               const double* __restrict__ e, const double4* __restrict__ plane, DifVec v, size_t N) {
+               const double* __restrict__ e, const double4* __restrict__ plane, DifVec v, size_t N,
+               DifWalls walls, int phase_cp) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(g, i, x, y, z);
@@ -148,7 +164,8 @@ k_dif_assemble(GridDev g, double h, double dt, double k_l, double k_g, const dou
     const double kp = liq ? k_l : k_g;
     const double Cp = g.Cp_l * cv + g.Cp_g * (1.0 - cv);
     const double T0 = __ldg(e + i) / Cp;
-    double diag = Cp / dt, rhs = Cp / dt * T0;
+    const double Cd = phase_cp ? (liq ? g.Cp_l : g.Cp_g) : Cp;
+    double diag = Cd / dt, rhs = Cd / dt * T0;
     const int pc[3] = {x, y, z};
     for (int axis = 0; axis < 3; ++axis) {
       double cs[2], cq[2], cst[2], d[2];
@@ -156,7 +173,10 @@ k_dif_assemble(GridDev g, double h, double dt, double k_l, double k_g, const dou
         const int s = side ? 1 : -1;
         int q[3] = {x, y, z};
         q[axis] = step_coord(pc[axis], s, g.n[axis], g.bc[axis]);
-        if (q[axis] < 0) {  // a wall: no flux
+        if (q[axis] < 0 && walls.on[2 * axis + side]) {  // a wall at fixed T, half a cell away
+          const double Tw = walls.T[2 * axis + side];
+          cs[side] = 2.0 / h; cq[side] = 0.0; cst[side] = Tw * 2.0 / h; d[side] = 0.5 * h;
+        } else if (q[axis] < 0) {  // a wall: no flux
           cs[side] = 0.0; cq[side] = 0.0; cst[side] = 0.0; d[side] = h;
         } else if ((__ldg(c + dcid(g, q[0], q[1], q[2])) >= 0.5) == liq) {
           cs[side] = 1.0 / h; cq[side] = 1.0 / h; cst[side] = 0.0; d[side] = h;
@@ -211,10 +231,18 @@ k_dif_jacobi(GridDev g, DifVec v, const double* __restrict__ Tin, double* __rest
 }
 
 __global__ void k_dif_store(GridDev g, const double* __restrict__ c, const double* __restrict__ T,
-                            double* __restrict__ e, size_t N) {
+                            double* __restrict__ e, size_t N, int phase_cp) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     const double cv = __ldg(c + i);
-    e[i] = (g.Cp_l * cv + g.Cp_g * (1.0 - cv)) * T[i];
+    const double Cp = g.Cp_l * cv + g.Cp_g * (1.0 - cv);
+    if (phase_cp) {
+      // e' = e + C_p,node (T' - T), T = e / C_p(c)
+      const double ev = e[i];
+      const double Cd = cv >= 0.5 ? g.Cp_l : g.Cp_g;
+      e[i] = ev + Cd * (T[i] - ev / Cp);
+    } else {
+      e[i] = Cp * T[i];
+    }
   }
 }
 
@@ -242,8 +270,9 @@ DifLayout dif_layout(size_t N) {
 size_t dif_scratch_bytes(size_t N) { return dif_layout(N).total; }
 
 cudaError_t launch_heat_diffusion(const GridDev& g, double h, const double* c, double* e, double k_l, double k_g,
-                                  double dt, double tol, int max_iter, void* workspace, cudaStream_t st,
-                                  int* iters_out, double* change_out, int* status) {
+                                  double dt, double tol, int max_iter, int phase_cp, const double* wall_T,
+                                  void* workspace, cudaStream_t st, int* iters_out, double* change_out,
+                                  int* status) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const DifLayout L = dif_layout(N);
   char* ws = static_cast<char*>(workspace);
@@ -258,7 +287,12 @@ cudaError_t launch_heat_diffusion(const GridDev& g, double h, const double* c, d
   *status = 0;
   const int grid = (int)std::min<size_t>((N + kDifThreads - 1) / kDifThreads, (size_t)kDifCTAs);
   k_dif_planes<<<grid, kDifThreads, 0, st>>>(g, c, plane, N);
-  k_dif_assemble<<<grid, kDifThreads, 0, st>>>(g, h, dt, k_l, k_g, c, e, plane, v, N);
+  DifWalls walls;
+  for (int f = 0; f < 6; ++f) {
+    walls.on[f] = wall_T && wall_T[f] == wall_T[f] ? 1 : 0;  // NaN: no wall temperature
+    walls.T[f] = walls.on[f] ? wall_T[f] : 0.0;
+  }
+  k_dif_assemble<<<grid, kDifThreads, 0, st>>>(g, h, dt, k_l, k_g, c, e, plane, v, N, walls, phase_cp);
   prof_mark("diffuse.assemble", st);
   std::vector<double> part(grid);
   double* Tin = v.Ta;
@@ -282,7 +316,7 @@ cudaError_t launch_heat_diffusion(const GridDev& g, double h, const double* c, d
   }
   prof_mark("diffuse.jacobi", st);
   if (!done) *status = 2;
-  k_dif_store<<<grid, kDifThreads, 0, st>>>(g, c, Tin, e, N);
+  k_dif_store<<<grid, kDifThreads, 0, st>>>(g, c, Tin, e, N, phase_cp);
   prof_mark("diffuse.store", st);
   if (iters_out) *iters_out = it;
   if (change_out) *change_out = change;

@@ -86,7 +86,7 @@ struct SweepPlan {
   int cap;          // list capacity per warp of kernel A
   long long nsub;   // number of lists (warps of kernel A)
   unsigned gridB;   // CTAs of kernel U (lpc lists each)
-  int lpc;          // kernel-A lists per CTA of kernel U
+  int lpc;          // kernel-A lists per CTA of kernel U (groups of 8)
 };
 
 SweepPlan sweep_plan(int axis, const GridDev& g);
@@ -219,7 +219,8 @@ cudaError_t launch_mlp_train_step(const double* X, const double* N, long ntrain,
 // *status: 0 converged, 2 not converged within max_iter.
 size_t dif_scratch_bytes(size_t N);
 cudaError_t launch_heat_diffusion(const GridDev& g, double h, const double* c, double* e, double k_l, double k_g,
-                                  double dt, double tol, int max_iter, void* workspace, cudaStream_t st,
-                                  int* iters_out, double* change_out, int* status);
+                                  double dt, double tol, int max_iter, int phase_cp, const double* wall_T,
+                                  void* workspace, cudaStream_t st, int* iters_out, double* change_out,
+                                  int* status);
 
 }  // namespace vofgb

@@ -157,9 +157,14 @@ def test_heat_diffusion_validation_without_gpu(lib):
     assert nb > 512 * 80
     it, ch = ctypes.c_int(0), ctypes.c_double(0.0)
 
-    def call(c_=c, e_=e, kl=0.5, dt=1e-3, tol=1e-12, mi=10, ws_=ws, nb_=nb):
-        return lib.vof_heat_diffusion(ctypes.byref(cg), c_, e_, kl, 0.1, dt, tol, mi, ctypes.byref(it),
+    def call(c_=c, e_=e, kl=0.5, dt=1e-3, tol=1e-12, mi=10, ws_=ws, nb_=nb, hc=0, walls=None, grid=cg):
+        return lib.vof_heat_diffusion(ctypes.byref(grid), c_, e_, kl, 0.1, dt, tol, mi, hc, walls, ctypes.byref(it),
                                       ctypes.byref(ch), ws_, ctypes.c_size_t(nb_), nul)
+    assert call(hc=2) == P.VOF_EINVAL
+    nan = float("nan")
+    assert call(walls=(ctypes.c_double * 6)(nan, nan, nan, nan, float("inf"), nan)) == P.VOF_EINVAL
+    gp = P.Grid(8, 8, 8, (0, 1, 1), 0.1, 2.0, 1.0, 0.0).c_struct()  # x periodic: no wall temperature there
+    assert call(walls=(ctypes.c_double * 6)(300.0, nan, nan, nan, nan, nan), grid=gp) == P.VOF_EINVAL
     assert call(c_=nul) == P.VOF_EINVAL
     assert call(e_=nul) == P.VOF_EINVAL
     assert call(kl=-1.0) == P.VOF_EINVAL

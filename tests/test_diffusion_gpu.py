@@ -86,17 +86,22 @@ CASES = ["plane", "droplet", "ragged_periodic", "slab"]
 
 
 @pytest.mark.parametrize("name", CASES)
-def test_heat_diffusion_parity(P, name):
+@pytest.mark.parametrize("hc", ["phase", "mixture"])
+def test_heat_diffusion_parity(P, name, hc):
     c, T, bc, h, Cpl, Cpg, Ts, kl, kg, dt = case(name)
     nz, ny, nx = c.shape
     Cp = Cpl * c + Cpg * (1 - c)
     e = Cp * T
     og = O.Grid(nx, ny, nz, bc, h, Cpl, Cpg, Ts)
-    eo = diffuse(og, c, e, kl, kg, dt)
+    # the slab case with its low x wall heated (the Stefan problem's wall)
+    walls = {(0, -1): 1.7} if name == "slab" else None
+    eo = diffuse(og, c, e, kl, kg, dt, wall_T=walls, heat_capacity=hc)
     g = P.Grid(nx, ny, nz, bc, h, Cpl, Cpg, Ts)
     ed = dev(e)
     tscale = np.abs(T).max()
-    it, ch = P.vof_heat_diffusion(g, dev(c), ed, kl, kg, dt, tol=1e-13 * tscale, max_iter=200000)
+    it, ch = P.vof_heat_diffusion(g, dev(c), ed, kl, kg, dt, tol=1e-13 * tscale, max_iter=200000,
+                                  heat_capacity=P.VOF_CP_PHASE if hc == "phase" else P.VOF_CP_MIXTURE,
+                                  wall_T=walls)
     assert it >= 1 and ch <= 1e-13 * tscale
     Tg, To = host(ed) / Cp, eo / Cp
     assert np.abs(Tg - To).max() <= 1e-10 * tscale
