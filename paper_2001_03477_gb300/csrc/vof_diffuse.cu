@@ -145,7 +145,7 @@ struct DifWalls {
 
 struct DifVec {
   double* off;    // [6 N]: coupling to the neighbour (face order -x, +x, -y, +y, -z, +z)
-  double* diag;   // [N]
+  double* diag;   // [N] reciprocal of the diagonal
   double* rhs;    // [N]
   double* Ta;     // [N] the two Jacobi iterates
   double* Tb;
@@ -153,9 +153,9 @@ struct DifVec {
 };
 
 __global__ void __launch_bounds__(kDifThreads)
-k_dif_assemble(GridDev g, double h, double dt, double k_l, double k_g, const double* __restrict__ c,
-               const double* __restrict__ e, const double4* __restrict__ plane, DifVec v, size_t N,
-               DifWalls walls, int phase_cp) {
+k_dif_assemble(GridDev g, double h, double inv_h, double inv_dt, double k_l, double k_g,
+               const double* __restrict__ c, const double* __restrict__ e, const double4* __restrict__ plane,
+               DifVec v, size_t N, DifWalls walls, int phase_cp) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(g, i, x, y, z);
@@ -163,36 +163,52 @@ k_dif_assemble(GridDev g, double h, double dt, double k_l, double k_g, const dou
     const bool liq = cv >= 0.5;
     const double kp = liq ? k_l : k_g;
     const double Cp = g.Cp_l * cv + g.Cp_g * (1.0 - cv);
-    const double T0 = __ldg(e + i) / Cp;
+    const double T0 = temp_of(g, __ldg(e + i), cv);
     const double Cd = phase_cp ? (liq ? g.Cp_l : g.Cp_g) : Cp;
-    double diag = Cd / dt, rhs = Cd / dt * T0;
+    // a same-phase neighbour couples by k_p / h^2 (no division); only the
+    // interface and heated-wall sides need their own distances
+    const double kq = kp * (inv_h * inv_h);
+    double diag = Cd * inv_dt, rhs = Cd * inv_dt * T0;
     const int pc[3] = {x, y, z};
     for (int axis = 0; axis < 3; ++axis) {
       double cs[2], cq[2], cst[2], d[2];
+      bool reg[2];  // the side's distance is h (same phase or a wall without flux)
       for (int side = 0; side < 2; ++side) {
+        reg[side] = true;
         const int s = side ? 1 : -1;
         int q[3] = {x, y, z};
         q[axis] = step_coord(pc[axis], s, g.n[axis], g.bc[axis]);
         if (q[axis] < 0 && walls.on[2 * axis + side]) {  // a wall at fixed T, half a cell away
           const double Tw = walls.T[2 * axis + side];
-          cs[side] = 2.0 / h; cq[side] = 0.0; cst[side] = Tw * 2.0 / h; d[side] = 0.5 * h;
+          cs[side] = 2.0 * inv_h; cq[side] = 0.0; cst[side] = Tw * 2.0 * inv_h; d[side] = 0.5 * h;
+          reg[side] = false;
         } else if (q[axis] < 0) {  // a wall: no flux
           cs[side] = 0.0; cq[side] = 0.0; cst[side] = 0.0; d[side] = h;
         } else if ((__ldg(c + dcid(g, q[0], q[1], q[2])) >= 0.5) == liq) {
-          cs[side] = 1.0 / h; cq[side] = 1.0 / h; cst[side] = 0.0; d[side] = h;
+          cs[side] = inv_h; cq[side] = inv_h; cst[side] = 0.0; d[side] = h;
         } else {
           const double th = interface_theta(g, c, plane, x, y, z, axis, s, liq) * h;
           cs[side] = 1.0 / th; cq[side] = 0.0; cst[side] = g.T_sat / th; d[side] = th;
+          reg[side] = false;
         }
       }
-      const double denom = 0.5 * (d[0] + d[1]);
-      for (int side = 0; side < 2; ++side) {
-        diag += kp * cs[side] / denom;
-        v.off[6 * i + 2 * axis + side] = kp * cq[side] / denom;
-        rhs += kp * cst[side] / denom;
+      if (reg[0] && reg[1]) {
+        // both sides h: k_p / h^2 each (walls without flux contribute 0)
+        for (int side = 0; side < 2; ++side) {
+          const double o = dnz(cq[side]) ? kq : 0.0;
+          diag += o;
+          v.off[6 * i + 2 * axis + side] = o;
+        }
+      } else {
+        const double kd = kp / (0.5 * (d[0] + d[1]));
+        for (int side = 0; side < 2; ++side) {
+          diag += kd * cs[side];
+          v.off[6 * i + 2 * axis + side] = kd * cq[side];
+          rhs += kd * cst[side];
+        }
       }
     }
-    v.diag[i] = diag;
+    v.diag[i] = 1.0 / diag;  // stored as its reciprocal: the sweeps multiply
     v.rhs[i] = rhs;
     v.Ta[i] = T0;
   }
@@ -210,14 +226,13 @@ k_dif_jacobi(GridDev g, DifVec v, const double* __restrict__ Tin, double* __rest
     const int pc[3] = {x, y, z};
     double acc = v.rhs[i];
     for (int f = 0; f < 6; ++f) {
-      const double o = v.off[6 * i + f];
-      if (o == 0.0) continue;
       const int axis = f >> 1, s = (f & 1) ? 1 : -1;
       int q[3] = {x, y, z};
       q[axis] = step_coord(pc[axis], s, g.n[axis], g.bc[axis]);
-      acc += o * Tin[dcid(g, q[0], q[1], q[2])];
+      if (q[axis] < 0) continue;  // a wall: its coupling is 0
+      acc = fma(v.off[6 * i + f], Tin[dcid(g, q[0], q[1], q[2])], acc);
     }
-    const double t = acc / v.diag[i];
+    const double t = acc * v.diag[i];
     Tout[i] = t;
     dmax = fmax(dmax, fabs(t - Tin[i]));
   }
@@ -239,7 +254,7 @@ __global__ void k_dif_store(GridDev g, const double* __restrict__ c, const doubl
       // e' = e + C_p,node (T' - T), T = e / C_p(c)
       const double ev = e[i];
       const double Cd = cv >= 0.5 ? g.Cp_l : g.Cp_g;
-      e[i] = ev + Cd * (T[i] - ev / Cp);
+      e[i] = ev + Cd * (T[i] - temp_of(g, ev, cv));  // the T the assembly started from
     } else {
       e[i] = Cp * T[i];
     }
@@ -292,7 +307,8 @@ cudaError_t launch_heat_diffusion(const GridDev& g, double h, const double* c, d
     walls.on[f] = wall_T && wall_T[f] == wall_T[f] ? 1 : 0;  // NaN: no wall temperature
     walls.T[f] = walls.on[f] ? wall_T[f] : 0.0;
   }
-  k_dif_assemble<<<grid, kDifThreads, 0, st>>>(g, h, dt, k_l, k_g, c, e, plane, v, N, walls, phase_cp);
+  k_dif_assemble<<<grid, kDifThreads, 0, st>>>(g, h, 1.0 / h, 1.0 / dt, k_l, k_g, c, e, plane, v, N, walls,
+                                                phase_cp);
   prof_mark("diffuse.assemble", st);
   std::vector<double> part(grid);
   double* Tin = v.Ta;

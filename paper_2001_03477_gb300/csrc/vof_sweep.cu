@@ -127,7 +127,6 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
 constexpr int kSegA = 32;     // cells per lane along y / z
 constexpr int kWarpsA = 8;    // warps per CTA of kernel A
 constexpr int kSegRow = 256;  // cells per warp along x (multiple of 32)
-constexpr int kMaxLPC = 256;  // kernel-A lists per CTA of kernel U, at most
 constexpr int kPlaneThreads = 128;  // kernel M: CTA size; grid kPlaneCTAs
 constexpr int kPlaneCTAs = 152 * 8;
 
@@ -642,53 +641,41 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 }
 
 // ---------------------------------------------------------------------------
-// Kernel U: one CTA per `lpc` consecutive kernel-A lists (fixed order, so
-// the sums are reproducible), one listed cell per thread: the WY update from
-// the two face fluxes.  It reads no cell but its own, so it may update in
-// place (c_out == c_in, e_out == e_in); kernel A then copies nothing.
+// Kernel U: one CTA per `ngrp` groups of 8 consecutive kernel-A lists
+// (fixed order, so the sums are reproducible), one listed cell per thread:
+// the WY update from the two face fluxes.  It reads no cell but its own, so
+// it may update in place (c_out == c_in, e_out == e_in); kernel A then
+// copies nothing.
 // ---------------------------------------------------------------------------
 template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(256)
 k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out,
          const double* __restrict__ uf, uint8_t* __restrict__ state,
-         double* __restrict__ theta, SweepScratch sc, int nsub, int cap, int lpc) {
+         double* __restrict__ theta, SweepScratch sc, int nsub, int cap, int ngrp) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  // the CTA takes the lists sub0 .. sub0 + lpc - 1 as one sequence (fixed
-  // order): short lists then still fill whole warps.  pre[w] = cells of
-  // the lists before list w (an exclusive scan by the first warp)
-  __shared__ int pre[kMaxLPC + 1];
-  const int sub0 = blockIdx.x * lpc;
-  if (threadIdx.x < 32) {
-    int carry = 0;
-    for (int w0 = 0; w0 < lpc; w0 += 32) {
-      const int w = w0 + (int)threadIdx.x;
-      const int cnt = (w < lpc && sub0 + w < nsub) ? sc.count[sub0 + w] : 0;
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((int)threadIdx.x >= o) incl += y;
-      }
-      if (w < lpc) pre[w] = carry + incl - cnt;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (threadIdx.x == 0) pre[lpc] = carry;
-  }
-  __syncthreads();
-  const int total = pre[lpc];
+  __shared__ int pre[9];
   double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  {
-    for (int j = threadIdx.x; j < total; j += blockDim.x) {
-      // the list holding entry j: the last w with pre[w] <= j
-      int lo = 0, hi = lpc - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= j) lo = mid;
-        else hi = mid - 1;
+  for (int grp = 0; grp < ngrp; ++grp) {
+    // the group's 8 lists sub0 .. sub0+7 as one sequence (fixed order):
+    // short lists then still fill whole warps
+    const int sub0 = (blockIdx.x * ngrp + grp) * 8;
+    if (sub0 >= nsub) break;  // uniform over the CTA
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < 8; ++w) {
+        pre[w] = t;
+        t += (sub0 + w < nsub) ? sc.count[sub0 + w] : 0;
       }
-      const int w = lo;
+      pre[8] = t;
+    }
+    __syncthreads();
+    const int total = pre[8];
+    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+      int w = 0;
+#pragma unroll
+      for (int q = 1; q < 8; ++q) w += (j >= pre[q]) ? 1 : 0;
       const size_t id = sc.list[(size_t)(sub0 + w) * cap + (j - pre[w])] & ~kMixedAdj;
       int x, y, z;
       cell_xyz(g, id, x, y, z);
@@ -709,6 +696,7 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
       v[kSumC] += dc;
       v[kSumE] += de;
     }
+    __syncthreads();  // pre[] is rewritten by the next group
   }
   // work counts of this sweep (kernel A's counters are final by now)
   if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -841,14 +829,13 @@ SweepPlan sweep_plan(int axis, const GridDev& g) {
     p.cap = (g.n[0] < 32 ? g.n[0] : 32) * (g.n[axis] < kSegA ? g.n[axis] : kSegA);
     p.nsub = (long long)p.gridA.x * p.gridA.y * p.gridA.z * kWarpsA;
   }
-  // kernel U: consecutive lists per CTA, enough that the CTAs (and their
-  // FP64 sum trees) number at most ~16 per SM whatever the list count (a
-  // few waves of resident CTAs: fewer, larger CTAs leave a tail of idle
-  // SMs in the last wave); a power of two from 8 to kMaxLPC
-  int lpc = 8;
-  while (lpc < kMaxLPC && p.nsub / lpc > 152 * 16) lpc *= 2;
-  p.lpc = lpc;
-  p.gridB = (unsigned)((p.nsub + lpc - 1) / lpc);
+  // kernel U: groups of 8 consecutive lists per CTA, enough groups that the
+  // CTAs (and their FP64 sum trees) number at most ~16 per SM whatever the
+  // list count
+  int ngrp = 1;
+  while (ngrp < 64 && p.nsub / (8 * ngrp) > 152 * 16) ngrp *= 2;
+  p.lpc = 8 * ngrp;
+  p.gridB = (unsigned)((p.nsub + p.lpc - 1) / p.lpc);
   return p;
 }
 
@@ -941,7 +928,7 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
   k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,
-                                                 p.cap, p.lpc);
+                                                 p.cap, p.lpc / 8);
   prof_mark(AX == 0 ? "sweep_x.update" : (AX == 1 ? "sweep_y.update" : "sweep_z.update"), st);
 }
 
