@@ -297,6 +297,42 @@ VOF_API vof_status vof_batched_step(const vof_box* boxes, int nbox, long step_in
                                     void* stream);
 
 /*
+ * The same batch as ONE launch per kernel of the time step (the grouped
+ * form): vof_group_create() carves every box's own step workspace out of
+ * the caller's buffer and writes, once, every kernel's per-box arguments
+ * and the CTA -> box maps of the grouped launches into the same buffer
+ * (synchronising `stream`); vof_group_step() then runs a time step of every
+ * box with ~22 launches on `stream` whatever the number of boxes: each CTA
+ * finds its box and its block within that box's own launch shape, so every
+ * box computes exactly what vof_step() computes on it (the same kernels, sum
+ * rows and reductions: bit-identical results).  No host work per box; the
+ * step can be captured in a CUDA graph.
+ *   boxes         host array, as for vof_batched_step; all boxes share the
+ *                 grid's precision and normal (VOF_NORMAL_MLP is not
+ *                 grouped: VOF_EINVAL)
+ *   sums          device double[nbox][VOF_NSUMS] or NULL: each box's step
+ *                 sums, written by every vof_group_step()
+ *   work_per_cta  cells per CTA of the grid-stride kernels (planes, faces,
+ *                 shift lists; >= 32): the grouped launches' granularity
+ *                 (results do not depend on it; the autotuner picks it)
+ *   workspace     device, 256-byte aligned, vof_group_workspace_bytes()
+ *                 bytes; it holds the boxes' workspaces and the tables while
+ *                 the group lives.  Fields must not overlap it or each other.
+ *   *group        host-side handle (launch sizes and table addresses);
+ *                 vof_group_destroy() frees it (nothing on the device).
+ * The boxes' arrays, dt, dd and sums are captured at creation: a later
+ * change to them needs a new group.  VOF_EINVAL for a bad box, mixed
+ * precision or normal, a small or misaligned workspace; VOF_ECUDA if the
+ * table copy or a launch fails.
+ */
+typedef struct vof_group vof_group;
+VOF_API size_t vof_group_workspace_bytes(const vof_box* boxes, int nbox, int work_per_cta);
+VOF_API vof_status vof_group_create(const vof_box* boxes, int nbox, double* sums, int work_per_cta, void* workspace,
+                                    size_t workspace_bytes, void* stream, vof_group** group);
+VOF_API vof_status vof_group_step(vof_group* group, long step_index, void* stream);
+VOF_API void vof_group_destroy(vof_group* group);
+
+/*
  * Mass transfer rate from PLIC interface distances (Sec. 3.2, "Calculating
  * the mass transfer rate": Eqs. mdot_calc, grad_n_T, plane_m, cell_d,
  * dint_trans, the collinearity xi, normTgrad and the weights chi, gamma).

@@ -140,6 +140,14 @@ def lib():
         L.vof_batched_workspace_bytes.restype = ctypes.c_size_t
         L.vof_batched_step.argtypes = [B, I, L_, P, I, ctypes.POINTER(ctypes.c_void_p), P, S, P]
         L.vof_batched_step.restype = ctypes.c_int
+        L.vof_group_workspace_bytes.argtypes = [B, I, I]
+        L.vof_group_workspace_bytes.restype = ctypes.c_size_t
+        L.vof_group_create.argtypes = [B, I, P, I, P, S, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.vof_group_create.restype = ctypes.c_int
+        L.vof_group_step.argtypes = [P, L_, P]
+        L.vof_group_step.restype = ctypes.c_int
+        L.vof_group_destroy.argtypes = [P]
+        L.vof_group_destroy.restype = None
         L.vof_step_noalloc.argtypes = [G, P, P, P, P, P, D, L_, P, D, P, P]
         L.vof_step_noalloc.restype = ctypes.c_int
         L.vof_noalloc_scratch_bytes.argtypes = []
@@ -773,6 +781,74 @@ def vof_batched_step(boxes, step_index, sums=None, lanes=1, lane_streams=None, w
     _check("vof_batched_step",
            lib().vof_batched_step(arr, len(boxes), int(step_index), _ptr(sums, _f64(), "sums"), int(lanes), ls,
                                   _ptr(workspace, None, "workspace"), ctypes.c_size_t(nbytes), _stream(stream)))
+
+
+class Group:
+    """A batch of boxes stepped with one launch per kernel of the time step
+    (vof_group_*): the boxes' workspaces and the launch tables live in one
+    device buffer (allocated through torch); `step()` runs vof_group_step.
+    `work_per_cta`: cells per CTA of the grid-stride kernels."""
+
+    def __init__(self, boxes, work_per_cta=4096, device="cuda", stream=None):
+        import torch
+        self.boxes = list(boxes)
+        self._arr = _box_array(self.boxes)
+        n = len(self.boxes)
+        self.sums = torch.zeros((max(n, 1), VOF_NSUMS), dtype=torch.float64, device=device)
+        nb = int(lib().vof_group_workspace_bytes(self._arr, n, int(work_per_cta)))
+        if nb == 0:
+            raise VofError("vof_group_workspace_bytes", VOF_EINVAL, lib())
+        self.workspace = torch.empty(nb + 256, dtype=torch.uint8, device=device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws = self.workspace[off:]
+        h = ctypes.c_void_p(0)
+        _check("vof_group_create",
+               lib().vof_group_create(self._arr, n, _ptr(self.sums, _f64(), "sums"), int(work_per_cta),
+                                      ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_size_t(nb), _stream(stream),
+                                      ctypes.byref(h)))
+        self._h = h
+        self.work_per_cta = int(work_per_cta)
+
+    def step(self, step_index, stream=None):
+        _check("vof_group_step", lib().vof_group_step(self._h, int(step_index), _stream(stream)))
+        return self.sums
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().vof_group_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass
+
+    @staticmethod
+    def autotune(boxes, candidates=(1024, 4096, 16384, 65536), steps=2, device="cuda"):
+        """The work_per_cta with the fastest grouped step on a copy of the
+        boxes (fields cloned, velocities shared), by CUDA events."""
+        import torch
+        copy = [Box(b.grid, b.c.clone(), b.e.clone(), b.u, b.v, b.w, b.dt, b.dd, b.dd_uniform) for b in boxes]
+        timings = {}
+
+        def measure(w):
+            g = Group(copy, w, device)
+            g.step(0)
+            s = torch.cuda.current_stream()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0.record(s)
+            for k in range(steps):
+                g.step(1 + k)
+            t1.record(s)
+            torch.cuda.synchronize()
+            g.close()
+            timings[w] = t0.elapsed_time(t1) / 1e3 / steps
+            return timings[w]
+
+        best = pick_fastest(measure, candidates)
+        return best, timings
 
 
 def pick_fastest(measure, candidates):

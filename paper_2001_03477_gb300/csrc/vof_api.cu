@@ -246,6 +246,103 @@ size_t vof_step_workspace_bytes(const vof_grid* g) {
   return step_layout(g).total;
 }
 
+}  // extern "C"
+
+namespace vofgb {
+
+// One box's arguments for the grouped step: the same carving, sum rows and
+// launch shapes as vof_step below (keep the two in step).
+bool step_box(const vof_grid* g, double* c, double* e, const double* u, const double* v, const double* w,
+              double dt, const double* dd, double dd_uniform, double* sums, char* ws, StepBox* out) {
+  if (!grid_ok(g) || !c || !e || !u || !v || !w || !(dt >= 0.0) || !ws) return false;
+  if (g->normal == VOF_NORMAL_MLP) return false;  // the learned normal runs per grid (vof_step)
+  const StepLayout L = step_layout(g);
+  const GridDev d = to_dev(g, dt);
+  const size_t N = cells(g);
+  StepBox& B = *out;
+  B.cells = N;
+  double* th = reinterpret_cast<double*>(ws + L.off_th);
+  uint8_t* state = reinterpret_cast<uint8_t*>(ws + L.off_st);
+  double* rows = reinterpret_cast<double*>(ws + L.off_rows);
+  B.zero_state = ZeroRange{reinterpret_cast<unsigned char*>(state), (unsigned long long)N};
+  // tile pass
+  const TileScratch ts = carve_tile_scratch(d, ws + L.off_tiles);
+  int nt[3];
+  tile_counts(d, nt);
+  B.tiles.g = d;
+  B.tiles.c = c;
+  B.tiles.e = e;
+  B.tiles.ts = ts;
+  B.tiles.nt[0] = nt[0]; B.tiles.nt[1] = nt[1]; B.tiles.nt[2] = nt[2];
+  B.tiles.sums = sums_to_partials(rows, kNSums);
+  B.grid_tiles = dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]);
+  B.grid_quiet = quiet_blocks(d);
+  size_t r = (size_t)L.nb_tiles;
+  TileMap tm{nullptr, {0, 0, 0}};
+  if (tiles_usable(d)) {
+    tm.quiet = ts.quiet;
+    tile_counts(d, tm.nt);
+  }
+  const double* uf[3] = {u, v, w};
+  // sum rows in the order of the axes of an even step (x, y, z): the rows of
+  // a sweep belong to its axis, as in vof_step
+  size_t row_of_axis[3];  // fixed per axis, as in vof_step
+  {
+    size_t rr = r;
+    for (int a = 0; a < 3; ++a) {
+      row_of_axis[a] = rr;
+      rr += (size_t)L.nb_sw[a];
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    SweepScratch sc = carve_sweep_scratch(a, d, ws + L.off_sw, sums_to_partials(rows + row_of_axis[a] * kNSums, kNSums));
+    sc.tiles = tm;
+    sc.stats = reinterpret_cast<int*>(ws + L.off_stats) + 2 * a;
+    sc.mlp_stat = reinterpret_cast<int*>(ws + L.off_stats) + 9 + a;
+    const SweepPlan p = sweep_plan(a, d);
+    SweepArgs& A = B.sweep[a];
+    A.g = d;
+    A.c = c;
+    A.e = e;
+    A.uf = uf[a];
+    A.state = state;
+    A.theta = th;
+    A.sc = sc;
+    A.cap = p.cap;
+    A.nsub = (int)p.nsub;
+    A.ngrp = p.lpc / 8;
+    A.status = device_status_ptr();
+    B.zero_counters[a] = ZeroRange{reinterpret_cast<unsigned char*>(sc.counters), 4 * sizeof(int)};
+    B.grid_stream[a] = p.gridA;
+    B.grid_update[a] = p.gridB;
+    r += (size_t)L.nb_sw[a];
+  }
+  ShiftScratch shs = carve_shift_scratch(d, ws + L.off_sw);
+  shs.tiles = tm;
+  shs.stats = reinterpret_cast<int*>(ws + L.off_stats) + 6;
+  ShiftArgs& S = B.shift;
+  S.g = d;
+  S.c = c;
+  S.e = e;
+  S.dd = dd;
+  S.dd_uniform = dd_uniform;
+  S.sc = shs;
+  S.sums = sums_to_partials(rows + r * kNSums, kNSums);
+  S.nw = shift_warps_of(d);
+  B.zero_shift[0] = ZeroRange{reinterpret_cast<unsigned char*>(shs.counters), 3 * sizeof(int)};
+  B.zero_shift[1] = ZeroRange{reinterpret_cast<unsigned char*>(shs.reach), (unsigned long long)N};
+  B.zero_shift[2] = ZeroRange{reinterpret_cast<unsigned char*>(shs.claim), (unsigned long long)N * 4};
+  B.grid_shift_stream = shift_stream_grid_of(d);
+  B.grid_shift_sums = (unsigned)shift_sum_blocks(d);
+  r += (size_t)L.nb_sh;
+  B.red = ReduceBox{rows, (int)r, sums, reinterpret_cast<double*>(ws + L.off_red)};
+  return true;
+}
+
+}  // namespace vofgb
+
+extern "C" {
+
 vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, const double* v, const double* w,
                     double dt, long step_index, const double* dd, double dd_uniform, double* sums, void* workspace,
                     size_t workspace_bytes, void* stream) {
@@ -278,15 +375,22 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
     tm.quiet = ts.quiet;
     tile_counts(d, tm.nt);
   }
+  // each axis' sum rows have a fixed place (x, y, z after the tile rows),
+  // whatever the order the sweeps run in
+  size_t row_of_axis[3];
+  for (int a = 0; a < 3; ++a) {
+    row_of_axis[a] = r;
+    r += (size_t)L.nb_sw[a];
+  }
   for (int s = 0; s < 3; ++s) {
     const int ax = (step_index % 2 == 0) ? s : 2 - s;
-    SweepScratch sc = carve_sweep_scratch(ax, d, ws + L.off_sw, sums_to_partials(rows + r * kNSums, kNSums));
+    SweepScratch sc =
+        carve_sweep_scratch(ax, d, ws + L.off_sw, sums_to_partials(rows + row_of_axis[ax] * kNSums, kNSums));
     sc.tiles = tm;
     sc.stats = reinterpret_cast<int*>(ws + L.off_stats) + 2 * ax;
     sc.mlp_stat = reinterpret_cast<int*>(ws + L.off_stats) + 9 + ax;
     err = launch_sweep(ax, d, c, e, c, e, uf[ax], state, th, nullptr, sc, st);
     if (err != cudaSuccess) return cuda_status(err);
-    r += (size_t)L.nb_sw[ax];
   }
   ShiftScratch shs = carve_shift_scratch(d, ws + L.off_sw);
   shs.tiles = tm;

@@ -6,9 +6,34 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/vofgb.h"
 #include "vof_device.cuh"
 
 namespace vofgb {
+
+// Virtual block index of a kernel body: the hardware's for a launch over one
+// grid; in a grouped launch over many boxes (vof_batched_step without lanes)
+// the CTA's box and its block within the box's own launch shape, from the
+// group map.  Bodies use vb.b* / vb.g* where a single launch uses blockIdx /
+// gridDim.
+struct VB {
+  unsigned bx, by, bz, gx, gy, gz;
+};
+__device__ __forceinline__ VB vb_self() { return VB{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z}; }
+
+// Grouped launch: cta_box[blockIdx.x] = the box of the CTA, box_first[b] =
+// its first CTA, gdim[b] = the box's own launch shape (x fastest).
+struct GroupMap {
+  const uint32_t* cta_box;
+  const uint32_t* box_first;
+  const uint3* gdim;
+};
+__device__ __forceinline__ VB vb_group(const GroupMap& m, unsigned& b) {
+  b = __ldg(m.cta_box + blockIdx.x);
+  const unsigned l = blockIdx.x - __ldg(m.box_first + b);
+  const uint3 d = m.gdim[b];
+  return VB{l % d.x, (l / d.x) % d.y, l / (d.x * d.y), d.x, d.y, d.z};
+}
 
 // Sums.  Every kernel that sums produces one row of kNSums values per CTA,
 // in one layout:
@@ -27,7 +52,7 @@ struct SumOut {
   double* diag;
   signed char map[kNSums];
 };
-inline SumOut sums_to_partials(double* p, int stride) {
+__host__ __device__ inline SumOut sums_to_partials(double* p, int stride) {
   SumOut s{p, stride, nullptr, {-1, -1, -1, -1, -1, -1}};
   return s;
 }
@@ -171,6 +196,86 @@ struct ReduceJobs {
 };
 size_t reduce_scratch_bytes();
 cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Grouped launches: one launch runs one kernel of the time step for every box
+// of a batch (vof_group_*), each CTA on its box's arguments (from a table in
+// device memory) with its virtual block index in the box's own launch shape.
+// ---------------------------------------------------------------------------
+struct SweepArgs {  // one box's in-place sweep along one axis
+  GridDev g;
+  double* c;
+  double* e;
+  const double* uf;
+  uint8_t* state;
+  double* theta;
+  SweepScratch sc;
+  int cap, nsub, ngrp;
+  int* status;
+};
+struct TileArgs {
+  GridDev g;
+  const double* c;
+  const double* e;
+  TileScratch ts;
+  int nt[3];
+  SumOut sums;
+};
+struct ShiftArgs {
+  GridDev g;
+  double* c;
+  double* e;
+  const double* dd;
+  double dd_uniform;
+  ShiftScratch sc;
+  SumOut sums;
+  long long nw;
+};
+struct ZeroRange {  // bytes to clear (one CTA per 64 KiB chunk)
+  unsigned char* p;
+  unsigned long long bytes;
+};
+struct ReduceBox {  // one box's sum rows and its output
+  const double* rows;
+  int nblocks;
+  double* out;
+  double* scratch;  // kReduceCTAs x kMaxReduceK partials
+};
+constexpr unsigned kZeroChunk = 65536;
+cudaError_t launch_zero_grp(const GroupMap& m, const ZeroRange* r, unsigned ctas, cudaStream_t st);
+cudaError_t launch_tiles_grp(const GroupMap& mt, const GroupMap& mq, const TileArgs* a, unsigned ct, unsigned cq,
+                             cudaStream_t st);
+// maps / ctas: [0] kernel A, [1] prep, [2] faces, [3] update
+cudaError_t launch_sweep_grp(int axis, int f32, int youngs, const GroupMap* maps, const SweepArgs* a,
+                             const unsigned* ctas, cudaStream_t st);
+// maps / ctas: [0] stream, [1] planes, [2] own, [3] receivers, [4] sums
+cudaError_t launch_shift_grp(const GroupMap* maps, const ShiftArgs* a, const unsigned* ctas, cudaStream_t st);
+// m1: (box, part) CTAs of the first level; the second level runs one CTA per box
+cudaError_t launch_reduce_grp(const GroupMap& m1, const ReduceBox* rb, unsigned ctas1, unsigned nbox,
+                              cudaStream_t st);
+// One box's arguments and launch shapes for every kernel of a grouped time
+// step (vof_api.cu builds them exactly as vof_step carves its workspace).
+struct StepBox {
+  size_t cells;
+  TileArgs tiles;
+  SweepArgs sweep[3];
+  ShiftArgs shift;
+  ReduceBox red;
+  ZeroRange zero_state;         // the frozen-state flags, at the step start
+  ZeroRange zero_counters[3];   // a sweep's list counters, before its kernel A
+  ZeroRange zero_shift[3];      // the shift's counters, reach bytes and claims
+  dim3 grid_tiles, grid_stream[3], grid_shift_stream;
+  unsigned grid_quiet, grid_update[3], grid_shift_sums;
+};
+// false for a grid vof_step refuses; ws: the box's step workspace
+// (vof_step_workspace_bytes), sums: device double[VOF_NSUMS] or null
+bool step_box(const vof_grid* g, double* c, double* e, const double* u, const double* v, const double* w,
+              double dt, const double* dd, double dd_uniform, double* sums, char* ws, StepBox* out);
+int shift_list_ctas();
+long long shift_warps_of(const GridDev& g);
+int prep_ctas();
+dim3 shift_stream_grid_of(const GridDev& g);
+unsigned quiet_blocks(const GridDev& g);
 
 // per-launch timing (vof_profile_begin/end): records an event after a launch
 void prof_mark(const char* name, cudaStream_t st);

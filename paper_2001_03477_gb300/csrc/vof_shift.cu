@@ -97,19 +97,16 @@ __device__ __forceinline__ unsigned reach_mask(const GridDev& g, const uint8_t* 
 // offsets as bit indices: ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1), 0..26
 __device__ __forceinline__ int offset_bit(int ox, int oy, int oz) { return ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1); }
 
-__global__ void __launch_bounds__(256)
-k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
-               SumOut sums, int copy) {
+__device__ __forceinline__ void k_shift_stream_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out, double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, const ShiftScratch& sc, const SumOut& sums, int copy, const VB vb) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int nx = g.n[0], ny = g.n[1];
   const int lane = threadIdx.x, warp = threadIdx.y;
   const unsigned lt = (1u << lane) - 1u;
-  const int row = blockIdx.x * 8 + warp;  // row = z * ny + y (grid x: rows, grid y: segments)
+  const int row = vb.bx * 8 + warp;  // row = z * ny + y (grid x: rows, grid y: segments)
   const bool rowok = row < ny * g.n[2];
-  const int x0 = blockIdx.y * kWarpCells, x1 = min(x0 + kWarpCells, nx);
+  const int x0 = vb.by * kWarpCells, x1 = min(x0 + kWarpCells, nx);
   const size_t rbase = (size_t)(rowok ? row : 0) * nx;
-  const size_t w = (size_t)row * gridDim.y + blockIdx.y;  // list of this warp
+  const size_t w = (size_t)row * vb.gy + vb.by;  // list of this warp
   const int cap = nx < kWarpCells ? nx : kWarpCells;
   uint32_t* list = sc.list + w * cap;
   const bool do_sums = sums.partials || sums.diag;
@@ -179,18 +176,23 @@ k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restr
       bn += __popc(mn);
     }
   }
-  block_sums(v, sums, blockIdx.x + gridDim.x * blockIdx.y);
+  block_sums(v, sums, vb.bx + vb.gx * vb.by);
 }
 
-__global__ void __launch_bounds__(kListThreads)
-k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
-               ShiftScratch sc) {
+__global__ void __launch_bounds__(256)
+k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+               double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
+               SumOut sums, int copy) {
+  k_shift_stream_body(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, sums, copy, vb_self());
+}
+
+__device__ __forceinline__ void k_shift_planes_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform, const ShiftScratch& sc, const VB vb) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int nn = sc.counters[0], ne = sc.counters[1];
   const int lane = threadIdx.x & 31;
   const int total = nn + ne;
-  const int stride = gridDim.x * blockDim.x;
-  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
+  const int stride = vb.gx * blockDim.x;
+  for (int i0 = vb.bx * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
     const int i = i0 + lane;
     const bool v = i < total;
     int x = 0, y = 0, z = 0;
@@ -251,21 +253,25 @@ k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restr
   }
 }
 
+__global__ void __launch_bounds__(kListThreads)
+k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
+               ShiftScratch sc) {
+  k_shift_planes_body(g, c_in, dd, dd_uniform, sc, vb_self());
+}
+
 // Per moving mixed cell (same list, after all claims are in): the receivers
 // it settles are the pure neighbours whose highest claim bit is its own
 // (on periodic axes of 1 or 2 cells several offsets lead to the same cell;
 // only the first of them in the scan order settles it); they are appended to
 // the receiver list, one atomic per warp.
-__global__ void __launch_bounds__(kListThreads)
-k_shift_own(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
-            ShiftScratch sc) {
+__device__ __forceinline__ void k_shift_own_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform, const ShiftScratch& sc, const VB vb) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int nn = sc.counters[0], ne = sc.counters[1];
   const int lane = threadIdx.x & 31;
   const int total = nn + ne;
   // whole warps iterate together (the receiver append below is warp-wide)
-  const int stride = gridDim.x * blockDim.x;
-  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
+  const int stride = vb.gx * blockDim.x;
+  for (int i0 = vb.bx * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
     const int i = i0 + lane;
     const bool v = i < total;
     unsigned own = 0u;
@@ -312,10 +318,14 @@ k_shift_own(GridDev g, const double* __restrict__ c_in, const double* __restrict
 }
 
 __global__ void __launch_bounds__(kListThreads)
-k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
-                  ShiftScratch sc) {
+k_shift_own(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
+            ShiftScratch sc) {
+  k_shift_own_body(g, c_in, dd, dd_uniform, sc, vb_self());
+}
+
+__device__ __forceinline__ void k_shift_receivers_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform, const ShiftScratch& sc, const VB vb) {
   const int nr = sc.counters[2];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+  for (int i = vb.bx * blockDim.x + threadIdx.x; i < nr; i += vb.gx * blockDim.x) {
     const size_t pid = sc.recv[i];
     const double cp = __ldg(c_in + pid);
     const bool full = is_full_b(cp, g);
@@ -351,14 +361,18 @@ k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __re
   }
 }
 
+__global__ void __launch_bounds__(kListThreads)
+k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
+                  ShiftScratch sc) {
+  k_shift_receivers_body(g, c_in, dd, dd_uniform, sc, vb_self());
+}
+
 // Applies the new values (moving cells and the receivers they settle) and
 // sums the changes, per warp list in fixed order.  Every cell it writes is
 // read and written by one thread only, so it may work in place.
-__global__ void __launch_bounds__(256)
-k_shift_sums(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out, ShiftScratch sc,
-             long long nwarps, SumOut sums) {
+__device__ __forceinline__ void k_shift_sums_body(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out, const ShiftScratch& sc, long long nwarps, const SumOut& sums, const VB vb) {
   const int lane = threadIdx.x & 31;
-  const size_t w = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const size_t w = (size_t)vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int cap = g.n[0] < kWarpCells ? g.n[0] : kWarpCells;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // dc, clamped, de
   if ((long long)w < nwarps) {
@@ -410,12 +424,18 @@ k_shift_sums(GridDev g, const double* c_in, const double* e_in, double* c_out, d
   v[kSumShDc] = acc[0];
   v[kSumUnpl] = acc[1];
   v[kSumShDe] = acc[2];
-  if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sc.stats && vb.bx == 0 && threadIdx.x == 0) {
     sc.stats[0] = sc.counters[0];
     sc.stats[1] = sc.counters[1];
     sc.stats[2] = sc.counters[2];
   }
-  block_sums(v, sums, blockIdx.x);
+  block_sums(v, sums, vb.bx);
+}
+
+__global__ void __launch_bounds__(256)
+k_shift_sums(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out, ShiftScratch sc,
+             long long nwarps, SumOut sums) {
+  k_shift_sums_body(g, c_in, e_in, c_out, e_out, sc, nwarps, sums, vb_self());
 }
 
 __global__ void __launch_bounds__(kShThreads)
@@ -524,6 +544,56 @@ ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
   return s;
 }
 
+__global__ void __launch_bounds__(256) k_shift_stream_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ShiftArgs& A = args[b];
+  const SumOut none = sums_to_partials(nullptr, kNSums);
+  k_shift_stream_body(A.g, A.c, A.e, A.c, A.e, A.dd, A.dd_uniform, A.sc, none, 0, vb);
+}
+__global__ void __launch_bounds__(kListThreads) k_shift_planes_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ShiftArgs& A = args[b];
+  k_shift_planes_body(A.g, A.c, A.dd, A.dd_uniform, A.sc, vb);
+}
+__global__ void __launch_bounds__(kListThreads) k_shift_own_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ShiftArgs& A = args[b];
+  k_shift_own_body(A.g, A.c, A.dd, A.dd_uniform, A.sc, vb);
+}
+__global__ void __launch_bounds__(kListThreads) k_shift_receivers_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ShiftArgs& A = args[b];
+  k_shift_receivers_body(A.g, A.c, A.dd, A.dd_uniform, A.sc, vb);
+}
+__global__ void __launch_bounds__(256) k_shift_sums_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ShiftArgs& A = args[b];
+  k_shift_sums_body(A.g, A.c, A.e, A.c, A.e, A.sc, A.nw, A.sums, vb);
+}
+
+cudaError_t launch_shift_grp(const GroupMap* m, const ShiftArgs* a, const unsigned* n, cudaStream_t st) {
+  if (n[0]) k_shift_stream_grp<<<n[0], dim3(32, 8), 0, st>>>(m[0], a);
+  prof_mark("group.shift_stream", st);
+  if (n[1]) k_shift_planes_grp<<<n[1], kListThreads, 0, st>>>(m[1], a);
+  prof_mark("group.shift_planes", st);
+  if (n[2]) k_shift_own_grp<<<n[2], kListThreads, 0, st>>>(m[2], a);
+  prof_mark("group.shift_own", st);
+  if (n[3]) k_shift_receivers_grp<<<n[3], kListThreads, 0, st>>>(m[3], a);
+  prof_mark("group.shift_receivers", st);
+  if (n[4]) k_shift_sums_grp<<<n[4], 256, 0, st>>>(m[4], a);
+  prof_mark("group.shift_sums", st);
+  return cudaGetLastError();
+}
+
+int shift_list_ctas() { return kListCTAs; }
+long long shift_warps_of(const GridDev& g) { return shift_warps(g); }
+dim3 shift_stream_grid_of(const GridDev& g) { return shift_stream_grid(g); }
+
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
                          const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut stream_sums,
                          SumOut sums, cudaStream_t st) {
@@ -579,30 +649,65 @@ __device__ __forceinline__ double tree_sum(double x, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(kReduceThreads) k_reduce1(ReduceJobs jobs, double* __restrict__ scratch) {
-  __shared__ double red[kReduceThreads];
-  const ReduceJob J = jobs.job[blockIdx.y];
-  const int chunk = (J.nblocks + gridDim.x - 1) / gridDim.x;
-  const int b0 = blockIdx.x * chunk, b1 = min(b0 + chunk, J.nblocks);
+// part `part` of `nparts` of a job's rows into out[k] (k < nk)
+__device__ __forceinline__ void reduce1_body(const ReduceJob& J, unsigned part, unsigned nparts, double* out,
+                                             double* red) {
+  const int chunk = (J.nblocks + (int)nparts - 1) / (int)nparts;
+  const int b0 = (int)part * chunk, b1 = min(b0 + chunk, J.nblocks);
   for (int k = 0; k < J.nk; ++k) {
     double s = 0.0;
     for (int b = b0 + threadIdx.x; b < b1; b += kReduceThreads) s += J.partials[(size_t)b * J.stride + J.k0 + k];
     const double t = tree_sum(s, red);
-    if (threadIdx.x == 0) scratch[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kMaxReduceK + k] = t;
+    if (threadIdx.x == 0) out[k] = t;
   }
+}
+// a job's nparts partials (kMaxReduceK apart) into J.out
+__device__ __forceinline__ void reduce2_body(const ReduceJob& J, const double* part, int nparts, double* red) {
+  for (int k = 0; k < J.nk; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kReduceThreads) s += part[(size_t)b * kMaxReduceK + k];
+    const double t = tree_sum(s, red);
+    if (threadIdx.x == 0) J.out[k] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_reduce1(ReduceJobs jobs, double* __restrict__ scratch) {
+  __shared__ double red[kReduceThreads];
+  const ReduceJob J = jobs.job[blockIdx.y];
+  reduce1_body(J, blockIdx.x, gridDim.x, scratch + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kMaxReduceK, red);
 }
 
 __global__ void __launch_bounds__(kReduceThreads) k_reduce2(ReduceJobs jobs, const double* __restrict__ scratch,
                                                             int nparts) {
   __shared__ double red[kReduceThreads];
   const ReduceJob J = jobs.job[blockIdx.x];
-  for (int k = 0; k < J.nk; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nparts; b += kReduceThreads)
-      s += scratch[((size_t)blockIdx.x * nparts + b) * kMaxReduceK + k];
-    const double t = tree_sum(s, red);
-    if (threadIdx.x == 0) J.out[k] = t;
-  }
+  reduce2_body(J, scratch + (size_t)blockIdx.x * nparts * kMaxReduceK, nparts, red);
+}
+
+// grouped: the first level over (box, part) CTAs, the second one CTA per box,
+// in the same order as a box's own reduction (job 0, kReduceCTAs parts)
+__global__ void __launch_bounds__(kReduceThreads) k_reduce1_grp(GroupMap m, const ReduceBox* __restrict__ rb) {
+  __shared__ double red[kReduceThreads];
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ReduceBox R = rb[b];
+  const ReduceJob J{R.rows, R.nblocks, kNSums, 0, kNSums, R.out};
+  reduce1_body(J, vb.bx, kReduceCTAs, R.scratch + (size_t)vb.bx * kMaxReduceK, red);
+}
+__global__ void __launch_bounds__(kReduceThreads) k_reduce2_grp(const ReduceBox* __restrict__ rb) {
+  __shared__ double red[kReduceThreads];
+  const ReduceBox R = rb[blockIdx.x];
+  const ReduceJob J{R.rows, R.nblocks, kNSums, 0, kNSums, R.out};
+  reduce2_body(J, R.scratch, kReduceCTAs, red);
+}
+
+cudaError_t launch_reduce_grp(const GroupMap& m1, const ReduceBox* rb, unsigned ctas1, unsigned nbox,
+                              cudaStream_t st) {
+  if (ctas1) k_reduce1_grp<<<ctas1, kReduceThreads, 0, st>>>(m1, rb);
+  prof_mark("group.reduce1", st);
+  if (nbox) k_reduce2_grp<<<nbox, kReduceThreads, 0, st>>>(rb);
+  prof_mark("group.reduce2", st);
+  return cudaGetLastError();
 }
 
 size_t reduce_scratch_bytes() { return (size_t)kMaxReduceJobs * kReduceCTAs * kMaxReduceK * sizeof(double); }

@@ -186,24 +186,21 @@ __device__ __forceinline__ uint32_t face_item(const SweepScratch& sc, int i, int
 }
 
 template <int AX, bool ENERGY>
-__global__ void __launch_bounds__(32 * kWarpsA)
-k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
-             int cap, int copy) {
+__device__ __forceinline__ void k_stream_col_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out, double* __restrict__ e_out, const uint8_t* __restrict__ state, const SweepScratch& sc, int force_all, int cap, int copy, const VB vb) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int n_t = AX == 1 ? g.n[2] : g.n[1];
   const int lane = threadIdx.x, warp = threadIdx.y;
-  const int x = blockIdx.x * 32 + lane;
-  const int t = blockIdx.y * kWarpsA + warp;
-  const int s0 = blockIdx.z * kSegA, s1 = min(s0 + kSegA, n_ax);
+  const int x = vb.bx * 32 + lane;
+  const int t = vb.by * kWarpsA + warp;
+  const int s0 = vb.bz * kSegA, s1 = min(s0 + kSegA, n_ax);
   const bool act = x < nx && t < n_t;
   const int xs = act ? x : 0, ts = act ? t : 0;
   const int bca = g.bc[AX];
   const size_t stride = AX == 1 ? (size_t)nx : (size_t)nx * ny;
   const size_t cbase = AX == 1 ? (size_t)ts * ny * nx + xs : (size_t)ts * nx + xs;
-  const size_t sub = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * kWarpsA * gridDim.x + (size_t)warp * gridDim.x +
-                     blockIdx.x;
+  const size_t sub = ((size_t)vb.bz * vb.gy + vb.by) * kWarpsA * vb.gx + (size_t)warp * vb.gx +
+                     vb.bx;
   uint32_t* list = sc.list + sub * (size_t)cap;
   uint32_t* mlist = sc.mlist + sub * (size_t)cap;
   uint32_t* rlist = sc.rlist + sub * (size_t)cap;
@@ -212,7 +209,7 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
     // in place: a warp whose 32 x 32 cells lie in quiet tiles has no work
     // (lanes 0..15 check its 4 x 4 tiles; t is the same for the warp)
     bool q = true;
-    const int txi = blockIdx.x * 4 + (lane & 3), tai = (s0 >> 3) + (lane >> 2);
+    const int txi = vb.bx * 4 + (lane & 3), tai = (s0 >> 3) + (lane >> 2);
     if (lane < 16 && txi * kTile < nx && tai * kTile < s1 && t < n_t) {
       const int tt = t >> 3;
       const int ty_ = AX == 1 ? tai : tt, tz_ = AX == 1 ? tt : tai;
@@ -310,24 +307,29 @@ k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restric
   append_lists(sc, list, nlist, nlist_m, mlist, nmixed, rlist, nrun, nrun_m, lane);
 }
 
+template <int AX, bool ENERGY>
+__global__ void __launch_bounds__(32 * kWarpsA)
+k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
+             int cap, int copy) {
+  k_stream_col_body<AX, ENERGY>(g, c_in, e_in, c_out, e_out, state, sc, force_all, cap, copy, vb_self());
+}
+
 // ---------------------------------------------------------------------------
 // Kernel A for the sweep along x: a warp owns kSegRow cells of one row and
 // walks them in chunks of 32 (lane = cell); equality with the previous cell
 // is a ballot mask, so "cells l-3..l+3 equal" is a 6-bit window test.
 // ---------------------------------------------------------------------------
 template <bool ENERGY>
-__global__ void __launch_bounds__(256)
-k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
-             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
-             int cap, int copy) {
+__device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out, double* __restrict__ e_out, const uint8_t* __restrict__ state, const SweepScratch& sc, int force_all, int cap, int copy, const VB vb) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int lane = threadIdx.x, warp = threadIdx.y;
-  const int row = blockIdx.x * 8 + warp;  // row = z * ny + y (grid x: rows, grid y: segments)
-  const int x0 = blockIdx.y * kSegRow, x1 = min(x0 + kSegRow, nx);
+  const int row = vb.bx * 8 + warp;  // row = z * ny + y (grid x: rows, grid y: segments)
+  const int x0 = vb.by * kSegRow, x1 = min(x0 + kSegRow, nx);
   const bool rowok = row < ny * nz;
   const size_t rbase = (size_t)(rowok ? row : 0) * nx;
   const int bcx = g.bc[0];
-  const size_t sub = (size_t)row * gridDim.y + blockIdx.y;
+  const size_t sub = (size_t)row * vb.gy + vb.by;
   if (!rowok) {  // whole warp: empty list
     if (lane == 0) sc.count[sub] = 0;
     return;
@@ -426,6 +428,14 @@ k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restric
   append_lists(sc, list, nlist, nlist_m, mlist, nmixed, rlist, nrun, nrun_m, lane);
 }
 
+template <bool ENERGY>
+__global__ void __launch_bounds__(256)
+k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
+             double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
+             int cap, int copy) {
+  k_stream_row_body<ENERGY>(g, c_in, e_in, c_out, e_out, state, sc, force_all, cap, copy, vb_self());
+}
+
 // ---------------------------------------------------------------------------
 // Kernel M: per-cell preparation over the grid-wide lists, one item per
 // thread (every lane busy): first the PLIC plane (MYC normal + plane
@@ -478,15 +488,14 @@ __device__ __forceinline__ double4 stencil_plane(const GridDev& g, const double*
 // normal with its MYC fallback, vof_mlp.cu); only their plane constants are
 // formed here.  NRM 2: Youngs' normal.  Ghost donors keep MYC.
 template <bool F32, int NRM>
-__global__ void __launch_bounds__(kPlaneThreads)
-k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc, int ax) {
+__device__ __forceinline__ void k_prep_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ e_in, const SweepScratch& sc, int ax, const VB vb) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int nm = sc.counters[0], nf = sc.counters[1];
   const int cnt = nm + (e_in ? nf + sc.counters[2] : 0);
   const int n_ax = g.n[ax];
   const int lines = g.bc[ax] != 0 ? (int)((size_t)nx * ny * nz / (size_t)n_ax) : 0;
   const int total = cnt + 2 * lines;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  for (int i = vb.bx * blockDim.x + threadIdx.x; i < total; i += vb.gx * blockDim.x) {
     if (i >= cnt) {
       const int j = i - cnt;
       const int side = j >= lines ? 1 : 0;
@@ -524,6 +533,12 @@ k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_
   }
 }
 
+template <bool F32, int NRM>
+__global__ void __launch_bounds__(kPlaneThreads)
+k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc, int ax) {
+  k_prep_body<F32, NRM>(g, c_in, e_in, sc, ax, vb_self());
+}
+
 // ---------------------------------------------------------------------------
 // Kernel F: one face per thread over the grid-wide face list -- the left face
 // of every listed cell and the right face of every run end, so each face is
@@ -543,16 +558,14 @@ __device__ __forceinline__ size_t face_of(const GridDev& g, int f, int x, int y,
 }
 
 template <int AX, bool ENERGY>
-__global__ void __launch_bounds__(kFaceThreads)
-k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, const double* __restrict__ uf,
-        double* __restrict__ flux_out, SweepScratch sc, int* __restrict__ status) {
+__device__ __forceinline__ void k_faces_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ e_in, const double* __restrict__ uf, double* __restrict__ flux_out, const SweepScratch& sc, int* __restrict__ status, const VB vb) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
   const int nf = sc.counters[1];
   const int cnt = nf + sc.counters[2];
   const size_t stride = AX == 0 ? 1 : (AX == 1 ? (size_t)nx : (size_t)nx * ny);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+  for (int i = vb.bx * blockDim.x + threadIdx.x; i < cnt; i += vb.gx * blockDim.x) {
     const uint32_t item = face_item(sc, i, nf);
     const size_t id = item >> 1;
     const int side = (int)(item & 1u);
@@ -640,6 +653,13 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
   }
 }
 
+template <int AX, bool ENERGY>
+__global__ void __launch_bounds__(kFaceThreads)
+k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, const double* __restrict__ uf,
+        double* __restrict__ flux_out, SweepScratch sc, int* __restrict__ status) {
+  k_faces_body<AX, ENERGY>(g, c_in, e_in, uf, flux_out, sc, status, vb_self());
+}
+
 // ---------------------------------------------------------------------------
 // Kernel U: one CTA per `ngrp` groups of 8 consecutive kernel-A lists
 // (fixed order, so the sums are reproducible), one listed cell per thread:
@@ -648,10 +668,7 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 // copies nothing.
 // ---------------------------------------------------------------------------
 template <int AX, bool ENERGY>
-__global__ void __launch_bounds__(256)
-k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out,
-         const double* __restrict__ uf, uint8_t* __restrict__ state,
-         double* __restrict__ theta, SweepScratch sc, int nsub, int cap, int ngrp) {
+__device__ __forceinline__ void k_update_body(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out, const double* __restrict__ uf, uint8_t* __restrict__ state, double* __restrict__ theta, const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb) {
   const int nx = g.n[0], ny = g.n[1];
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
@@ -660,7 +677,7 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
   for (int grp = 0; grp < ngrp; ++grp) {
     // the group's 8 lists sub0 .. sub0+7 as one sequence (fixed order):
     // short lists then still fill whole warps
-    const int sub0 = (blockIdx.x * ngrp + grp) * 8;
+    const int sub0 = (vb.bx * ngrp + grp) * 8;
     if (sub0 >= nsub) break;  // uniform over the CTA
     if (threadIdx.x == 0) {
       int t = 0;
@@ -699,14 +716,22 @@ k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, doubl
     __syncthreads();  // pre[] is rewritten by the next group
   }
   // work counts of this sweep (kernel A's counters are final by now)
-  if (sc.stats && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sc.stats && vb.bx == 0 && threadIdx.x == 0) {
     sc.stats[0] = sc.counters[0];
     sc.stats[1] = sc.counters[1] + sc.counters[2];
   }
-  if (sc.mlp_stat && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sc.mlp_stat && vb.bx == 0 && threadIdx.x == 0) {
     sc.mlp_stat[0] = sc.counters[3];
   }
-  block_sums(v, sc.sums, blockIdx.x);
+  block_sums(v, sc.sums, vb.bx);
+}
+
+template <int AX, bool ENERGY>
+__global__ void __launch_bounds__(256)
+k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out,
+         const double* __restrict__ uf, uint8_t* __restrict__ state,
+         double* __restrict__ theta, SweepScratch sc, int nsub, int cap, int ngrp) {
+  k_update_body<AX, ENERGY>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb_self());
 }
 
 // Energy update from given face VOF fluxes (the unfused form).
@@ -952,6 +977,69 @@ cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const d
   }
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Grouped sweep kernels: every box of a batch in one launch (in place, with
+// energy, no exported fluxes); each CTA takes its box's arguments.
+// ---------------------------------------------------------------------------
+template <int AX>
+__global__ void __launch_bounds__(256) k_stream_grp(GroupMap m, const SweepArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const SweepArgs& A = args[b];
+  if (AX == 0)
+    k_stream_row_body<true>(A.g, A.c, A.e, A.c, A.e, A.state, A.sc, 0, A.cap, 0, vb);
+  else
+    k_stream_col_body<AX == 0 ? 1 : AX, true>(A.g, A.c, A.e, A.c, A.e, A.state, A.sc, 0, A.cap, 0, vb);
+}
+template <bool F32, int NRM>
+__global__ void __launch_bounds__(kPlaneThreads) k_prep_grp(GroupMap m, const SweepArgs* __restrict__ args, int ax) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const SweepArgs& A = args[b];
+  k_prep_body<F32, NRM>(A.g, A.c, A.e, A.sc, ax, vb);
+}
+template <int AX>
+__global__ void __launch_bounds__(kFaceThreads) k_faces_grp(GroupMap m, const SweepArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const SweepArgs& A = args[b];
+  k_faces_body<AX, true>(A.g, A.c, A.e, A.uf, nullptr, A.sc, A.status, vb);
+}
+template <int AX>
+__global__ void __launch_bounds__(256) k_update_grp(GroupMap m, const SweepArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const SweepArgs& A = args[b];
+  k_update_body<AX, true>(A.g, A.c, A.e, A.c, A.e, A.uf, A.state, A.theta, A.sc, A.nsub, A.cap, A.ngrp, vb);
+}
+
+template <int AX>
+static void launch_sweep_grp_t(int f32, int youngs, const GroupMap* m, const SweepArgs* a, const unsigned* n,
+                               cudaStream_t st) {
+  if (n[0]) k_stream_grp<AX><<<n[0], dim3(32, 8), 0, st>>>(m[0], a);
+  prof_mark("group.stream", st);
+  if (n[1]) {
+    if (youngs) k_prep_grp<false, 2><<<n[1], kPlaneThreads, 0, st>>>(m[1], a, AX);
+    else if (f32) k_prep_grp<true, 0><<<n[1], kPlaneThreads, 0, st>>>(m[1], a, AX);
+    else k_prep_grp<false, 0><<<n[1], kPlaneThreads, 0, st>>>(m[1], a, AX);
+  }
+  prof_mark("group.prep", st);
+  if (n[2]) k_faces_grp<AX><<<n[2], kFaceThreads, 0, st>>>(m[2], a);
+  prof_mark("group.faces", st);
+  if (n[3]) k_update_grp<AX><<<n[3], 256, 0, st>>>(m[3], a);
+  prof_mark("group.update", st);
+}
+
+cudaError_t launch_sweep_grp(int axis, int f32, int youngs, const GroupMap* maps, const SweepArgs* a,
+                             const unsigned* ctas, cudaStream_t st) {
+  if (axis == 0) launch_sweep_grp_t<0>(f32, youngs, maps, a, ctas, st);
+  else if (axis == 1) launch_sweep_grp_t<1>(f32, youngs, maps, a, ctas, st);
+  else launch_sweep_grp_t<2>(f32, youngs, maps, a, ctas, st);
+  return cudaGetLastError();
+}
+
+int prep_ctas() { return kPlaneCTAs; }
 
 cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, const double* c_after,
                           const double* e_in, double* e_out, const double* F, const double* uf, uint8_t* state,

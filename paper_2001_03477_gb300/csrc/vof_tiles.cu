@@ -36,15 +36,14 @@ __device__ __noinline__ void add_tile_cells(const double (&cv)[kTile], const dou
 
 // CTA: 32 x 8 threads covering four tiles along x (32 cells), one along y
 // and one along z (the threads walk its 8 planes).
-__global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e,
-                                               TileScratch ts, int ntx, int nty, SumOut sums) {
+__device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, const SumOut& sums, const VB vb) {
   __shared__ unsigned uni_w[8];
   __shared__ double ref[4][2];
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int j = tx >> 3;  // tile of this thread within the CTA
-  const int x = blockIdx.x * 32 + tx, y = blockIdx.y * kTile + ty, z0 = blockIdx.z * kTile;
-  const int xt = blockIdx.x * 4 + j;
+  const int x = vb.bx * 32 + tx, y = vb.by * kTile + ty, z0 = vb.bz * kTile;
+  const int xt = vb.bx * 4 + j;
   const bool tile_ok = xt * kTile < nx;
   double cv[kTile], ev[kTile];
   const bool xy_ok = x < nx && y < ny;
@@ -80,18 +79,18 @@ __global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restri
     if (tile_uni) {
       // one thread per tile: (cells of the tile) x value
       if (ty == 0 && (tx & 7) == 0) {
-        const int cx = min(kTile, nx - xt * kTile), cy = min(kTile, ny - (int)blockIdx.y * kTile),
+        const int cx = min(kTile, nx - xt * kTile), cy = min(kTile, ny - (int)vb.by * kTile),
                   cz = min(kTile, nz - z0);
         const double n = (double)(cx * cy * cz);
         v[kSumC] = n * cr;
         v[kSumE] = n * er;
-        const size_t t = ((size_t)blockIdx.z * nty + blockIdx.y) * ntx + xt;
+        const size_t t = ((size_t)vb.bz * nty + vb.by) * ntx + xt;
         ts.uni[t] = 1;
         ts.vc[t] = cr;
         ts.ve[t] = er;
       }
     } else if (ty == 0 && (tx & 7) == 0) {
-      ts.uni[((size_t)blockIdx.z * nty + blockIdx.y) * ntx + xt] = 0;
+      ts.uni[((size_t)vb.bz * nty + vb.by) * ntx + xt] = 0;
     }
   }
   // cell by cell only in the tiles that are not uniform; the branch is
@@ -101,12 +100,18 @@ __global__ void __launch_bounds__(256) k_tiles(GridDev g, const double* __restri
   const bool add_cells = tile_ok && !tile_uni && xy_ok;
   if (__any_sync(kFullT, add_cells)) add_tile_cells(cv, ev, add_cells, v);
 
-  block_sums(v, sums, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+  block_sums(v, sums, vb.bx + vb.gx * (vb.by + vb.gy * vb.bz));
 }
 
-__global__ void __launch_bounds__(256) k_quiet(GridDev g, TileScratch ts, int ntx, int nty, int ntz) {
+__global__ void __launch_bounds__(256)
+k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e,
+                                               TileScratch ts, int ntx, int nty, SumOut sums) {
+  k_tiles_body(g, c, e, ts, ntx, nty, sums, vb_self());
+}
+
+__device__ __forceinline__ void k_quiet_body(const GridDev& g, const TileScratch& ts, int ntx, int nty, int ntz, const VB vb) {
   const long long nt = (long long)ntx * nty * ntz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nt; t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = vb.bx * (long long)blockDim.x + threadIdx.x; t < nt; t += (long long)vb.gx * blockDim.x) {
     const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
     bool q = ts.uni[t] != 0;
     double cr = 0.0, er = 0.0;
@@ -135,6 +140,11 @@ __global__ void __launch_bounds__(256) k_quiet(GridDev g, TileScratch ts, int nt
         }
     ts.quiet[t] = q ? 1 : 0;
   }
+}
+
+__global__ void __launch_bounds__(256)
+k_quiet(GridDev g, TileScratch ts, int ntx, int nty, int ntz) {
+  k_quiet_body(g, ts, ntx, nty, ntz, vb_self());
 }
 
 size_t al256t(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -179,6 +189,52 @@ TileScratch carve_tile_scratch(const GridDev& g, void* ws) {
   return s;
 }
 
+__global__ void __launch_bounds__(256) k_tiles_grp(GroupMap m, const TileArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const TileArgs& A = args[b];
+  k_tiles_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.sums, vb);
+}
+__global__ void __launch_bounds__(256) k_quiet_grp(GroupMap m, const TileArgs* __restrict__ args) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const TileArgs& A = args[b];
+  k_quiet_body(A.g, A.ts, A.nt[0], A.nt[1], A.nt[2], vb);
+}
+
+cudaError_t launch_tiles_grp(const GroupMap& mt, const GroupMap& mq, const TileArgs* a, unsigned ct, unsigned cq,
+                             cudaStream_t st) {
+  if (ct) k_tiles_grp<<<ct, dim3(32, 8), 0, st>>>(mt, a);
+  prof_mark("group.tiles", st);
+  if (cq) k_quiet_grp<<<cq, 256, 0, st>>>(mq, a);
+  prof_mark("group.quiet", st);
+  return cudaGetLastError();
+}
+
+unsigned quiet_blocks(const GridDev& g) {
+  int nt[3];
+  tile_counts(g, nt);
+  const long long T = (long long)nt[0] * nt[1] * nt[2];
+  return (unsigned)((T + 255) / 256 < 152 * 8 ? (T + 255) / 256 : 152 * 8);
+}
+
+// clears every range of a batch: one CTA per 64 KiB chunk of a range
+__global__ void __launch_bounds__(256) k_zero_grp(GroupMap m, const ZeroRange* __restrict__ r) {
+  unsigned b;
+  const VB vb = vb_group(m, b);
+  const ZeroRange R = r[b];
+  const unsigned long long lo = (unsigned long long)vb.bx * kZeroChunk;
+  unsigned long long hi = lo + kZeroChunk;
+  if (hi > R.bytes) hi = R.bytes;
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) R.p[i] = 0;
+}
+
+cudaError_t launch_zero_grp(const GroupMap& m, const ZeroRange* r, unsigned ctas, cudaStream_t st) {
+  if (ctas) k_zero_grp<<<ctas, 256, 0, st>>>(m, r);
+  prof_mark("group.zero", st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, TileScratch ts, SumOut sums,
                          cudaStream_t st) {
   int nt[3];
@@ -186,9 +242,7 @@ cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, Til
   k_tiles<<<dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]), dim3(32, 8), 0, st>>>(
       g, c, e, ts, nt[0], nt[1], sums);
   prof_mark("tiles", st);
-  const long long T = (long long)nt[0] * nt[1] * nt[2];
-  const unsigned nb = (unsigned)((T + 255) / 256 < 152 * 8 ? (T + 255) / 256 : 152 * 8);
-  k_quiet<<<nb, 256, 0, st>>>(g, ts, nt[0], nt[1], nt[2]);
+  k_quiet<<<quiet_blocks(g), 256, 0, st>>>(g, ts, nt[0], nt[1], nt[2]);
   prof_mark("tiles.quiet", st);
   return cudaGetLastError();
 }

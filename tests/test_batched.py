@@ -159,3 +159,25 @@ def test_autotuner_keeps_the_fastest():
     assert P.pick_fastest(measure, (1, 2, 4, 8, 16, 32)) == 8  # tie with 16: the earlier one
     assert seen == [1, 2, 4, 8, 16, 32]
     assert P.pick_fastest(lambda x: 1.0, (4,)) == 4
+
+
+def test_group_plan_sizes_without_gpu():
+    import ctypes
+    import paper_2001_03477_gb300 as P
+    boxes = []
+    for n in (9, 17, 24):
+        g = P.Grid(n, n, n, (0, 0, 0), 1.0 / n, 1000.0, 1.0, 1.0)
+        boxes.append(g)
+    arr = P._box_array(boxes, with_arrays=False)
+    for i in range(len(boxes)):
+        addr = (i + 1) << 36
+        arr[i].c, arr[i].e = ctypes.c_void_p(addr), ctypes.c_void_p(addr + (1 << 34))
+        arr[i].u = arr[i].v = arr[i].w = ctypes.c_void_p(addr + (2 << 34))
+        arr[i].dt = 0.01
+    L = P.lib()
+    nb = L.vof_group_workspace_bytes(arr, 3, 4096)
+    assert nb >= sum(P.vof_step_workspace_bytes(g) for g in boxes)
+    assert L.vof_group_workspace_bytes(arr, 3, 16) == 0      # granularity below 32 cells
+    assert L.vof_group_workspace_bytes(arr, 0, 4096) == 0    # empty batch
+    arr[1].grid.precision = 1
+    assert L.vof_group_workspace_bytes(arr, 3, 4096) == 0    # mixed precision
