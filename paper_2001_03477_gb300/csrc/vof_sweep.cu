@@ -986,7 +986,7 @@ template <int AX>
 __global__ void __launch_bounds__(256) k_stream_grp(GroupMap m, const SweepArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs& A = args[b];
+  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
   if (AX == 0)
     k_stream_row_body<true>(A.g, A.c, A.e, A.c, A.e, A.state, A.sc, 0, A.cap, 0, vb);
   else
@@ -996,21 +996,21 @@ template <bool F32, int NRM>
 __global__ void __launch_bounds__(kPlaneThreads) k_prep_grp(GroupMap m, const SweepArgs* __restrict__ args, int ax) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs& A = args[b];
+  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
   k_prep_body<F32, NRM>(A.g, A.c, A.e, A.sc, ax, vb);
 }
 template <int AX>
 __global__ void __launch_bounds__(kFaceThreads) k_faces_grp(GroupMap m, const SweepArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs& A = args[b];
+  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
   k_faces_body<AX, true>(A.g, A.c, A.e, A.uf, nullptr, A.sc, A.status, vb);
 }
 template <int AX>
 __global__ void __launch_bounds__(256) k_update_grp(GroupMap m, const SweepArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs& A = args[b];
+  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
   k_update_body<AX, true>(A.g, A.c, A.e, A.c, A.e, A.uf, A.state, A.theta, A.sc, A.nsub, A.cap, A.ngrp, vb);
 }
 

@@ -192,13 +192,13 @@ TileScratch carve_tile_scratch(const GridDev& g, void* ws) {
 __global__ void __launch_bounds__(256) k_tiles_grp(GroupMap m, const TileArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const TileArgs& A = args[b];
+  const TileArgs A = args[b];
   k_tiles_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.sums, vb);
 }
 __global__ void __launch_bounds__(256) k_quiet_grp(GroupMap m, const TileArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const TileArgs& A = args[b];
+  const TileArgs A = args[b];
   k_quiet_body(A.g, A.ts, A.nt[0], A.nt[1], A.nt[2], vb);
 }
 
