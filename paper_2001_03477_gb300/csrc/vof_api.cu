@@ -135,7 +135,7 @@ static vof_status sweep_common(int axis, const vof_grid* g, const double* c_in, 
   // stand-alone sweep: diag[0] += clipped volume
   static const signed char kMap[kNSums] = {-1, -1, 0, -1, -1, -1};
   SweepScratch sc = carve_sweep_scratch(axis, d, workspace, sums_to_diag(diag, kMap));
-  return cuda_status(launch_sweep(axis, d, c_in, e_in, c_out, e_in ? e_out : nullptr, uf, state, theta, flux_out, sc,
+  return cuda_status(launch_sweep(axis, d, c_in, e_in, c_out, e_in ? e_out : nullptr, uf, state, theta, flux_out, sc, true,
                                   (cudaStream_t)stream));
 }
 
@@ -202,12 +202,13 @@ vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in, const d
   static const signed char kMap[kNSums] = {3, 4, -1, 0, 1, 2};
   const SumOut so = sums_to_diag(diag, kMap);
   return cuda_status(launch_shift(d, c_in, e_in, c_out, e_out, dd, dd_uniform, state, carve_shift_scratch(d, workspace),
-                                  so, so, (cudaStream_t)stream));
+                                  so, so, true, (cudaStream_t)stream));
 }
 
 // workspace layout: theta | state | sum rows (tile pass, the three sweeps'
 // update kernels, the shift's sums kernel; kNSums doubles per CTA) |
-// reduction scratch | work counts | tiles |
+// reduction scratch | work counts (12 ints) and, 128 bytes in, the passes'
+// list counters (kStepCounters ints, cleared by the tile pass) | tiles |
 // scratch (reused by the three sweeps, then the shift).  The sweeps and the
 // shift all run in place on c and e; the tile pass sums c and e at the start
 // and every later kernel adds the changes it makes, so one fixed-order
@@ -241,6 +242,11 @@ static StepLayout step_layout(const vof_grid* g) {
   return L;
 }
 
+// the passes' list counters: 128 bytes into the work-count block
+static int* step_counters(char* ws, const StepLayout& L) {
+  return reinterpret_cast<int*>(ws + L.off_stats + 128);
+}
+
 size_t vof_step_workspace_bytes(const vof_grid* g) {
   if (!grid_ok(g)) return 0;
   return step_layout(g).total;
@@ -264,7 +270,7 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
   double* th = reinterpret_cast<double*>(ws + L.off_th);
   uint8_t* state = reinterpret_cast<uint8_t*>(ws + L.off_st);
   double* rows = reinterpret_cast<double*>(ws + L.off_rows);
-  B.zero_state = ZeroRange{reinterpret_cast<unsigned char*>(state), (unsigned long long)N};
+  int* cnt = step_counters(ws, L);
   // tile pass
   const TileScratch ts = carve_tile_scratch(d, ws + L.off_tiles);
   int nt[3];
@@ -275,6 +281,8 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
   B.tiles.ts = ts;
   B.tiles.nt[0] = nt[0]; B.tiles.nt[1] = nt[1]; B.tiles.nt[2] = nt[2];
   B.tiles.sums = sums_to_partials(rows, kNSums);
+  B.tiles.state = state;
+  B.tiles.counters = cnt;
   B.grid_tiles = dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]);
   B.grid_quiet = quiet_blocks(d);
   size_t r = (size_t)L.nb_tiles;
@@ -299,6 +307,7 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
     sc.tiles = tm;
     sc.stats = reinterpret_cast<int*>(ws + L.off_stats) + 2 * a;
     sc.mlp_stat = reinterpret_cast<int*>(ws + L.off_stats) + 9 + a;
+    sc.counters = cnt + 4 * a;
     const SweepPlan p = sweep_plan(a, d);
     SweepArgs& A = B.sweep[a];
     A.g = d;
@@ -312,7 +321,6 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
     A.nsub = (int)p.nsub;
     A.ngrp = p.lpc / 8;
     A.status = device_status_ptr();
-    B.zero_counters[a] = ZeroRange{reinterpret_cast<unsigned char*>(sc.counters), 4 * sizeof(int)};
     B.grid_stream[a] = p.gridA;
     B.grid_update[a] = p.gridB;
     r += (size_t)L.nb_sw[a];
@@ -320,6 +328,7 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
   ShiftScratch shs = carve_shift_scratch(d, ws + L.off_sw);
   shs.tiles = tm;
   shs.stats = reinterpret_cast<int*>(ws + L.off_stats) + 6;
+  shs.counters = cnt + 12;
   ShiftArgs& S = B.shift;
   S.g = d;
   S.c = c;
@@ -329,9 +338,6 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
   S.sc = shs;
   S.sums = sums_to_partials(rows + r * kNSums, kNSums);
   S.nw = shift_warps_of(d);
-  B.zero_shift[0] = ZeroRange{reinterpret_cast<unsigned char*>(shs.counters), 3 * sizeof(int)};
-  B.zero_shift[1] = ZeroRange{reinterpret_cast<unsigned char*>(shs.reach), (unsigned long long)N};
-  B.zero_shift[2] = ZeroRange{reinterpret_cast<unsigned char*>(shs.claim), (unsigned long long)N * 4};
   B.grid_shift_stream = shift_stream_grid_of(d);
   B.grid_shift_sums = (unsigned)shift_sum_blocks(d);
   r += (size_t)L.nb_sh;
@@ -361,13 +367,12 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
   double* rows = reinterpret_cast<double*>(ws + L.off_rows);
   GridDev d = to_dev(g, dt);
   const double* uf[3] = {u, v, w};
-  cudaError_t err = cudaMemsetAsync(state, 0, N, st);
-  if (err != cudaSuccess) return cuda_status(err);
-  prof_mark("step.memset_state", st);
-  // tile pass: quiet tiles and the sums of c, e at the start of the step
+  int* cnt = step_counters(ws, L);
+  // tile pass: quiet tiles and the sums of c, e at the start of the step;
+  // it also clears the frozen-state flags and the passes' list counters
   const TileScratch ts = carve_tile_scratch(d, ws + L.off_tiles);
   size_t r = 0;
-  err = launch_tiles(d, c, e, ts, sums_to_partials(rows, kNSums), st);
+  cudaError_t err = launch_tiles(d, c, e, ts, sums_to_partials(rows, kNSums), state, cnt, st);
   if (err != cudaSuccess) return cuda_status(err);
   r += (size_t)L.nb_tiles;
   TileMap tm{nullptr, {0, 0, 0}};
@@ -389,15 +394,17 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
     sc.tiles = tm;
     sc.stats = reinterpret_cast<int*>(ws + L.off_stats) + 2 * ax;
     sc.mlp_stat = reinterpret_cast<int*>(ws + L.off_stats) + 9 + ax;
-    err = launch_sweep(ax, d, c, e, c, e, uf[ax], state, th, nullptr, sc, st);
+    sc.counters = cnt + 4 * ax;
+    err = launch_sweep(ax, d, c, e, c, e, uf[ax], state, th, nullptr, sc, false, st);
     if (err != cudaSuccess) return cuda_status(err);
   }
   ShiftScratch shs = carve_shift_scratch(d, ws + L.off_sw);
   shs.tiles = tm;
   shs.stats = reinterpret_cast<int*>(ws + L.off_stats) + 6;
+  shs.counters = cnt + 12;
   const SumOut none = sums_to_partials(nullptr, kNSums);
   err = launch_shift(d, c, e, c, e, dd, dd_uniform, nullptr, shs, none, sums_to_partials(rows + r * kNSums, kNSums),
-                     st);
+                     false, st);
   if (err != cudaSuccess) return cuda_status(err);
   r += (size_t)L.nb_sh;
   if (sums) {

@@ -228,11 +228,7 @@ struct vof_group {
   const SweepArgs* sweep[3] = {nullptr, nullptr, nullptr};
   const ShiftArgs* shift = nullptr;
   const ReduceBox* red = nullptr;
-  const ZeroRange* zstate = nullptr;
-  const ZeroRange* zcnt[3] = {nullptr, nullptr, nullptr};
-  const ZeroRange* zshift = nullptr;
-  Launch l_zstate, l_tiles, l_quiet, l_zcnt[3], l_stream[3], l_prep[3], l_faces[3], l_update[3], l_zshift, l_sh[5],
-      l_red1;
+  Launch l_tiles, l_quiet, l_stream[3], l_prep[3], l_faces[3], l_update[3], l_sh[5], l_red1;
   bool sums = false;
 };
 
@@ -271,10 +267,7 @@ static vof_status group_plan(const vof_box* boxes, int nbox, double* sums, int w
   const size_t tables = off;
   std::vector<StepBox> sb(nbox);
   // launch plans
-  LaunchPlan p_zstate, p_tiles, p_quiet, p_zcnt[3], p_stream[3], p_prep[3], p_faces[3], p_update[3], p_zshift,
-      p_sh[5], p_red1;
-  std::vector<ZeroRange> zshift;
-  zshift.reserve(3 * (size_t)nbox);
+  LaunchPlan p_tiles, p_quiet, p_stream[3], p_prep[3], p_faces[3], p_update[3], p_sh[5], p_red1;
   size_t base = 0;
   for (int b = 0; b < nbox; ++b) {
     const vof_box& x = boxes[b];
@@ -285,19 +278,13 @@ static vof_status group_plan(const vof_box* boxes, int nbox, double* sums, int w
       return VOF_EINVAL;
     base += align256(ws[b]);
     const StepBox& B = sb[b];
-    p_zstate.add(div_up(B.zero_state.bytes, kZeroChunk), 1, 1);
     p_tiles.add(B.grid_tiles.x, B.grid_tiles.y, B.grid_tiles.z);
     p_quiet.add(B.grid_quiet, 1, 1);
     for (int a = 0; a < 3; ++a) {
-      p_zcnt[a].add(1, 1, 1);
       p_stream[a].add(B.grid_stream[a].x, B.grid_stream[a].y, B.grid_stream[a].z);
       p_prep[a].add(gs_ctas(B.cells, work, prep_ctas()), 1, 1);
       p_faces[a].add(gs_ctas(B.cells, work, prep_ctas()), 1, 1);
       p_update[a].add(B.grid_update[a], 1, 1);
-    }
-    for (int k = 0; k < 3; ++k) {
-      zshift.push_back(B.zero_shift[k]);
-      p_zshift.add(div_up(B.zero_shift[k].bytes, kZeroChunk), 1, 1);
     }
     p_sh[0].add(B.grid_shift_stream.x, B.grid_shift_stream.y, 1);
     for (int k = 1; k < 4; ++k) p_sh[k].add(gs_ctas(B.cells, work, shift_list_ctas()), 1, 1);
@@ -305,10 +292,10 @@ static vof_status group_plan(const vof_box* boxes, int nbox, double* sums, int w
     p_red1.add(kReduceCTAs, 1, 1);
   }
   // table region after the boxes' workspaces
-  LaunchPlan* plans[] = {&p_zstate, &p_tiles, &p_quiet, &p_zcnt[0], &p_zcnt[1], &p_zcnt[2], &p_stream[0],
-                         &p_stream[1], &p_stream[2], &p_prep[0], &p_prep[1], &p_prep[2], &p_faces[0], &p_faces[1],
-                         &p_faces[2], &p_update[0], &p_update[1], &p_update[2], &p_zshift, &p_sh[0], &p_sh[1],
-                         &p_sh[2], &p_sh[3], &p_sh[4], &p_red1};
+  LaunchPlan* plans[] = {&p_tiles,     &p_quiet,     &p_stream[0], &p_stream[1], &p_stream[2], &p_prep[0],
+                         &p_prep[1],   &p_prep[2],   &p_faces[0],  &p_faces[1],  &p_faces[2],  &p_update[0],
+                         &p_update[1], &p_update[2], &p_sh[0],     &p_sh[1],     &p_sh[2],     &p_sh[3],
+                         &p_sh[4],     &p_red1};
   const size_t nb = (size_t)nbox;
   size_t t = tables;
   const size_t o_tiles = t;  t += align256(nb * sizeof(TileArgs));
@@ -316,10 +303,6 @@ static vof_status group_plan(const vof_box* boxes, int nbox, double* sums, int w
   for (int a = 0; a < 3; ++a) { o_sweep[a] = t; t += align256(nb * sizeof(SweepArgs)); }
   const size_t o_shift = t;  t += align256(nb * sizeof(ShiftArgs));
   const size_t o_red = t;    t += align256(nb * sizeof(ReduceBox));
-  const size_t o_zstate = t; t += align256(nb * sizeof(ZeroRange));
-  size_t o_zcnt[3];
-  for (int a = 0; a < 3; ++a) { o_zcnt[a] = t; t += align256(nb * sizeof(ZeroRange)); }
-  const size_t o_zshift = t; t += align256(3 * nb * sizeof(ZeroRange));
   const size_t o_maps = t;
   for (LaunchPlan* lp : plans) t += lp->bytes();
   if (need) *need = t;
@@ -334,28 +317,22 @@ static vof_status group_plan(const vof_box* boxes, int nbox, double* sums, int w
     std::vector<SweepArgs> sa(nb);
     std::vector<ShiftArgs> sh(nb);
     std::vector<ReduceBox> rb(nb);
-    std::vector<ZeroRange> zr(nb);
     for (size_t b = 0; b < nb; ++b) ta[b] = sb[b].tiles;
     put(o_tiles, ta.data(), nb * sizeof(TileArgs));
     for (int a = 0; a < 3; ++a) {
       for (size_t b = 0; b < nb; ++b) sa[b] = sb[b].sweep[a];
       put(o_sweep[a], sa.data(), nb * sizeof(SweepArgs));
-      for (size_t b = 0; b < nb; ++b) zr[b] = sb[b].zero_counters[a];
-      put(o_zcnt[a], zr.data(), nb * sizeof(ZeroRange));
     }
     for (size_t b = 0; b < nb; ++b) sh[b] = sb[b].shift;
     put(o_shift, sh.data(), nb * sizeof(ShiftArgs));
     for (size_t b = 0; b < nb; ++b) rb[b] = sb[b].red;
     put(o_red, rb.data(), nb * sizeof(ReduceBox));
-    for (size_t b = 0; b < nb; ++b) zr[b] = sb[b].zero_state;
-    put(o_zstate, zr.data(), nb * sizeof(ZeroRange));
-    put(o_zshift, zshift.data(), zshift.size() * sizeof(ZeroRange));
   }
-  Launch* launches[] = {&out->l_zstate, &out->l_tiles, &out->l_quiet, &out->l_zcnt[0], &out->l_zcnt[1],
-                        &out->l_zcnt[2], &out->l_stream[0], &out->l_stream[1], &out->l_stream[2], &out->l_prep[0],
-                        &out->l_prep[1], &out->l_prep[2], &out->l_faces[0], &out->l_faces[1], &out->l_faces[2],
-                        &out->l_update[0], &out->l_update[1], &out->l_update[2], &out->l_zshift, &out->l_sh[0],
-                        &out->l_sh[1], &out->l_sh[2], &out->l_sh[3], &out->l_sh[4], &out->l_red1};
+  Launch* launches[] = {&out->l_tiles,     &out->l_quiet,     &out->l_stream[0], &out->l_stream[1],
+                        &out->l_stream[2], &out->l_prep[0],   &out->l_prep[1],   &out->l_prep[2],
+                        &out->l_faces[0],  &out->l_faces[1],  &out->l_faces[2],  &out->l_update[0],
+                        &out->l_update[1], &out->l_update[2], &out->l_sh[0],     &out->l_sh[1],
+                        &out->l_sh[2],     &out->l_sh[3],     &out->l_sh[4],     &out->l_red1};
   size_t o = o_maps;
   for (size_t i = 0; i < sizeof(plans) / sizeof(plans[0]); ++i) {
     const LaunchPlan& lp = *plans[i];
@@ -386,14 +363,9 @@ static vof_status group_plan(const vof_box* boxes, int nbox, double* sums, int w
   out->f32 = prec == VOF_F32_FLUX ? 1 : 0;
   out->youngs = nrm == VOF_NORMAL_YOUNGS ? 1 : 0;
   out->tiles = reinterpret_cast<const TileArgs*>(dev + o_tiles);
-  for (int a = 0; a < 3; ++a) {
-    out->sweep[a] = reinterpret_cast<const SweepArgs*>(dev + o_sweep[a]);
-    out->zcnt[a] = reinterpret_cast<const ZeroRange*>(dev + o_zcnt[a]);
-  }
+  for (int a = 0; a < 3; ++a) out->sweep[a] = reinterpret_cast<const SweepArgs*>(dev + o_sweep[a]);
   out->shift = reinterpret_cast<const ShiftArgs*>(dev + o_shift);
   out->red = reinterpret_cast<const ReduceBox*>(dev + o_red);
-  out->zstate = reinterpret_cast<const ZeroRange*>(dev + o_zstate);
-  out->zshift = reinterpret_cast<const ZeroRange*>(dev + o_zshift);
   out->sums = sums != nullptr;
   return VOF_OK;
 }
@@ -438,19 +410,16 @@ vof_status vof_group_create(const vof_box* boxes, int nbox, double* sums, int wo
 vof_status vof_group_step(vof_group* grp, long step_index, void* stream) {
   if (!grp || grp->nbox < 1 || step_index < 0) return VOF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t err = launch_zero_grp(grp->l_zstate.m, grp->zstate, grp->l_zstate.ctas, st);
-  if (err == cudaSuccess)
-    err = launch_tiles_grp(grp->l_tiles.m, grp->l_quiet.m, grp->tiles, grp->l_tiles.ctas, grp->l_quiet.ctas, st);
+  // the tile pass also clears every box's frozen-state flags and counters
+  cudaError_t err =
+      launch_tiles_grp(grp->l_tiles.m, grp->l_quiet.m, grp->tiles, grp->l_tiles.ctas, grp->l_quiet.ctas, st);
   for (int s = 0; s < 3 && err == cudaSuccess; ++s) {
     const int ax = (step_index % 2 == 0) ? s : 2 - s;
-    err = launch_zero_grp(grp->l_zcnt[ax].m, grp->zcnt[ax], grp->l_zcnt[ax].ctas, st);
-    if (err != cudaSuccess) break;
     const GroupMap maps[4] = {grp->l_stream[ax].m, grp->l_prep[ax].m, grp->l_faces[ax].m, grp->l_update[ax].m};
     const unsigned ctas[4] = {grp->l_stream[ax].ctas, grp->l_prep[ax].ctas, grp->l_faces[ax].ctas,
                               grp->l_update[ax].ctas};
     err = launch_sweep_grp(ax, grp->f32, grp->youngs, maps, grp->sweep[ax], ctas, st);
   }
-  if (err == cudaSuccess) err = launch_zero_grp(grp->l_zshift.m, grp->zshift, grp->l_zshift.ctas, st);
   if (err == cudaSuccess) {
     GroupMap maps[5];
     unsigned ctas[5];

@@ -295,24 +295,16 @@ __device__ __forceinline__ float alpha_guess_f(float m1, float m2, float m3, flo
   for (int it = 0; it < 22; ++it) {
     const float u = 0.5f * (lo + hi);
     const float a = 0.5f * u * u * u;
-    float v;
-    if (a < m1) {
-      v = a * a * a * r6;
-    } else {
-      const float v2 = a * (a - m1) * r2 + v2c;
-      if (a < m2) {
-        v = v2;
-      } else {
-        const float t2 = a - m2;
-        const float v3 = v2 - t2 * t2 * t2 * r6;
-        if (a < top) v = v3;
-        else if (lin) v = (2.0f * a - m12) * 0.5f * r3;
-        else {
-          const float t3 = a - m3;
-          v = v3 - t3 * t3 * t3 * r6;
-        }
-      }
-    }
+    // every branch's value, then the branch's (no divergent paths; the
+    // same operations, so the same floats, as taking the branch)
+    const float v1 = a * a * a * r6;
+    const float v2 = a * (a - m1) * r2 + v2c;
+    const float t2 = a - m2;
+    const float v3 = v2 - t2 * t2 * t2 * r6;
+    const float v4 = (2.0f * a - m12) * 0.5f * r3;
+    const float t3 = a - m3;
+    const float v5 = v3 - t3 * t3 * t3 * r6;
+    const float v = a < m1 ? v1 : (a < m2 ? v2 : (a < top ? v3 : (lin ? v4 : v5)));
     if (v < c) lo = u; else hi = u;
   }
   const float u = 0.5f * (lo + hi);
@@ -366,6 +358,39 @@ __device__ __forceinline__ double alpha_low(double m1, double m2, double m3, dou
   return best;
 }
 
+// An estimate of the same plane constant (float guess, two Newton steps on
+// the same branch form; no check of the result), for callers that verify it.
+__device__ __forceinline__ double alpha_low_est(double m1, double m2, double m3, double c) {
+  const double m12 = m1 + m2;
+  const double top = nn_lt(m12, m3) ? m12 : m3;
+  const bool lin = !nn_lt(m3, m12);
+  const double r6 = 1.0 / (6.0 * m1 * m2 * m3);
+  const double r2 = 1.0 / (2.0 * m2 * m3);
+  const double r3 = 1.0 / m3;
+  const double v2c = m1 * m1 * r2 * (1.0 / 3.0);
+  double a = (double)alpha_guess_f((float)m1, (float)m2, (float)m3, (float)c);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double t1 = a - m1, t2 = a - m2, t3 = a - m3;
+    const double v1 = a * a * a * r6, d1 = 3.0 * a * a * r6;
+    const double v2 = a * t1 * r2 + v2c, d2 = (a + t1) * r2;
+    const double v3 = v2 - t2 * t2 * t2 * r6, d3 = d2 - 3.0 * t2 * t2 * r6;
+    const double v4 = (a + (a - m12)) * 0.5 * r3, d4 = r3;
+    const double v5 = v3 - t3 * t3 * t3 * r6, d5 = d3 - 3.0 * t3 * t3 * r6;
+    double v, d;
+    if (nn_lt(a, m1)) { v = v1; d = d1; }
+    else if (nn_lt(a, m2)) { v = v2; d = d2; }
+    else if (nn_lt(a, top)) { v = v3; d = d3; }
+    else if (lin) { v = v4; d = d4; }
+    else { v = v5; d = d5; }
+    double an = a - (v - c) / d;
+    if (!(dbits(an) > 0)) an = 0.5 * a;
+    if (nn_lt(0.5, an)) an = 0.5;
+    a = an;
+  }
+  return a;
+}
+
 // alpha with volume(m, alpha) = c for any m (mirror, normalise, invert,
 // undo): the same outer steps as the volume function.
 __device__ __forceinline__ double plane_alpha(double m0, double m1, double m2, double c) {
@@ -375,9 +400,12 @@ __device__ __forceinline__ double plane_alpha(double m0, double m1, double m2, d
   if (c >= 1.0) return r.l1 - r.sh;
   double s0 = r.mp[0], s1 = r.mp[1], s2 = r.mp[2];
   sort3(s0, s1, s2);
-  double am;
-  if (c <= 0.5) am = alpha_low(s0, s1, s2, c);
-  else am = 1.0 - alpha_low(s0, s1, s2, 1.0 - c);
+  // one call for both halves (c or 1 - c picked per lane): an FP64
+  // instruction costs its full issue time whatever the active lanes, so a
+  // warp that took both branches would pay for the inversion twice
+  const bool up = !(c <= 0.5);
+  const double al = alpha_low(s0, s1, s2, up ? 1.0 - c : c);
+  const double am = up ? 1.0 - al : al;
   return am * r.l1 - r.sh;
 }
 
@@ -387,6 +415,18 @@ __device__ __forceinline__ double plane_alpha(double m0, double m1, double m2, d
 // volume is closer to c).  Used where alpha(c) is ill-conditioned (c within
 // 1e-3 of 0 or 1) and the plane is extrapolated into neighbouring cells,
 // which would amplify the last-bit differences of any other inversion.
+//
+// Two bounds on the FP64 volume (these operations, no contraction) make it
+// cheaper without changing a midpoint or a decision: (1) it is within 256
+// ulps of the exact volume V (relative below the cube's middle, relative to
+// 1 - V above it, plus an ulp); a rounding analysis of the branch forms
+// gives ~54 ulps, 4.4 were seen over 3.2e5 normals and constants spanning
+// every branch, the branch boundaries and degenerate normals against exact
+// rational arithmetic; (2) its form with rounded reciprocals is within 256
+// ulps of it (5 seen); with the branch forms' cancellation bounds (v2 <=
+// 1.5 v3, (a - m2)^3 / d6 <= v3 / 2, and in the last branch v3 <= 1.04 v5,
+// (a - m3)^3 / d6 <= 0.04 v5) the rounding analysis gives ~14 ulps, so a
+// 64-ulp margin decides.
 static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, double m2, double c) {
   Mirror r = mirror_normalise(m0, m1, m2);
   if (r.l1 == 0.0) return 0.0;
@@ -413,9 +453,10 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
     const double t3 = a - s2;
     return v3 - t3 * t3 * t3 / d6;
   };
-  auto vpos = [&](double a) -> double {  // a in (0, 1) here
-    if (!nn_lt(0.5, a)) return vlow(a);
-    return 1.0 - vlow(1.0 - a);
+  auto vpos = [&](double a) -> double {  // a in (0, 1) here; one vlow for both halves
+    const bool up = nn_lt(0.5, a);
+    const double w = vlow(up ? 1.0 - a : a);
+    return up ? 1.0 - w : w;
   };
   // The same volume with the divisions replaced by products with the
   // rounded reciprocals: within a few ulps of it (relative below the middle
@@ -436,16 +477,82 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
     const double t3 = a - s2;
     return v3 - t3 * t3 * t3 * r6;
   };
-  const double margin_low = 1e-12 * c;
-  const double margin_high = nn_lt(1e-14, 1e-12 * (1.0 - c)) ? 1e-12 * (1.0 - c) : 1e-14;
+  // Above the cube's middle the decision vpos(mid) < c, vpos = RN(1 - w)
+  // with w the volume at 1 - mid, is w > t exactly, t = (1 - c) + 2^-54 (c
+  // in [1/2, 1): 1 - c exact, RN(1 - w) < c iff 1 - w lies below the
+  // midpoint between c and its predecessor; w = t is a tie and goes to the
+  // exact evaluation), a comparison with relative bounds only.
+  const double t = (1.0 - c) + 0x1p-54;
+  // bound (2): a fast volume farther from its threshold than this is on the
+  // exact volume's side of it
+  const double margin_low = 0x1p-47 * c, margin_high = 0x1p-47 * t;
   double lo = 0.0, hi = 1.0;
-  for (int it = 0; it < 200; ++it) {
+  int it = 0;
+  // Levels whose midpoint lies clear of the root are decided without a
+  // volume: with the Newton root ae, bound (1) and the monotone exact volume
+  // show that every a < aL is below and every a > aR is not (else nothing
+  // is skipped).  Until a midpoint falls in [aL, aR] the bisection's
+  // decisions are then known; its midpoints are computed as it computes
+  // them, and the loop below resumes at that midpoint.  (For c <= 1/4 every
+  // a > 1/2 has a volume >= 1/2 - 2^-45 > c; for c >= 3/4 every a <= 1/2 one
+  // <= 1/2 + 2^-45 < c.)
+  if (nn_lt(c, 0.25) || nn_lt(0.75, c)) {
+    // (every step below is taken by every lane, the halves picked per
+    // lane, so a warp evaluates each volume once)
+    const bool low_c = nn_lt(c, 0.25);
+    const double al = alpha_low_est(s0, s1, s2, low_c ? c : 1.0 - c);
+    const double ae = low_c ? al : 1.0 - al;
+    double dz = (low_c ? ae : 1.0 - ae) * 0x1p-36;
+    if (!low_c && nn_lt(dz, 0x1p-50)) dz = 0x1p-50;  // a few ulps of 1 at least
+    const double aL = ae - dz, aR = ae + dz;
+    // below the middle: vlow(aL) < c <= vlow(aR); above it, with w(a) =
+    // vlow(1 - a) falling in a (1 - aL and 1 - aR exact): w(aL) > t > w(aR)
+    const double wL = vlow(low_c ? aL : 1.0 - aL), wR = vlow(low_c ? aR : 1.0 - aR);
+    bool ok;
+    if (low_c) {
+      ok = dgt0(aL) && nn_lt(aL, aR) && !nn_lt(0.5, aR) && nn_lt(wL * (1.0 + 0x1p-43), c) &&
+           !nn_lt(wR * (1.0 - 0x1p-43), c);
+    } else {
+      ok = !nn_lt(aL, 0.5) && nn_lt(aL, aR) && nn_lt(aR, 1.0) && nn_lt(t, wL * (1.0 - 0x1p-43)) &&
+           nn_lt(wR * (1.0 + 0x1p-43), t);
+    }
+    if (ok && !(low_c && nn_lt(aR, 0x1p-900))) {  // (the units stay normal doubles)
+      // The skipped levels on integers.  Below the middle the bisection
+      // first halves [0, 1] to [0, 2^(e+1)] (e: aR's exponent; the midpoints
+      // 2^-1 .. 2^(e+1) all exceed aR); then, as above the middle from [0, 1],
+      // the bracket is [L, L + H] in units 2^(e+1-62) (2^-62): midpoints
+      // L + H/2 exact, compared with ceil(aL / unit) and floor(aR / unit).
+      // While H >= 2^10 every midpoint has at most 53 significant bits, so
+      // the doubles the bisection would compute are these integers times
+      // the unit.
+      const int e = (int)((dbits(aR) >> 52) & 0x7FF) - 1023;
+      const int k0 = low_c ? -e - 1 : 0;       // halvings of hi from 1
+      const int sc = low_c ? 61 - e : 62;      // 1 / unit = 2^sc
+      const double up = __longlong_as_double((long long)(sc + 1023) << 52);
+      const double dn = __longlong_as_double((long long)(1023 - sc) << 52);
+      const unsigned long long ZL = __double2ull_ru(aL * up), ZR = __double2ull_rd(aR * up);
+      unsigned long long L = 0ull, H = 1ull << 62;
+      it = k0;
+      for (; it < 200 && H >= (1ull << 10); ++it) {
+        const unsigned long long M = L + (H >> 1);
+        if (M < ZL) L = M;
+        else if (M > ZR) {}
+        else break;
+        H >>= 1;
+      }
+      lo = (double)L * dn;
+      hi = (double)(L + H) * dn;
+    }
+  }
+  for (; it < 200; ++it) {
     double mid = lo + 0.5 * (hi - lo);
     if (!(nn_lt(lo, mid) && nn_lt(mid, hi))) break;
-    const bool low = !nn_lt(0.5, mid);
-    const double d = (low ? vlow_fast(mid) : 1.0 - vlow_fast(1.0 - mid)) - c;
+    // below the middle: below iff the volume at mid is < c; above it iff
+    // the volume at 1 - mid is > t (one fast volume per lane either way)
+    const bool up = nn_lt(0.5, mid);
+    const double d = vlow_fast(up ? 1.0 - mid : mid) - (up ? t : c);
     bool below;
-    if (nn_lt(low ? margin_low : margin_high, fabs(d))) below = dlt0(d);
+    if (nn_lt(up ? margin_high : margin_low, fabs(d))) below = up ? dgt0(d) : dlt0(d);
     else below = nn_lt(vpos(mid), c);
     if (below) lo = mid;
     else hi = mid;
@@ -477,25 +584,46 @@ __device__ __forceinline__ double vol_low_nn(double m1, double m2, double m3, do
   return v3 - t3 * t3 * t3 / (6.0 * m1 * m2 * m3);
 }
 
-__device__ __forceinline__ double volume_nn(double m0, double m1, double m2, double alpha) {
-  double sh = 0.0;
-  if (dlt0(m0)) sh -= m0;
-  if (dlt0(m1)) sh -= m1;
-  if (dlt0(m2)) sh -= m2;
+// The volume function split in two: the normal's mirror, normalisation and
+// sort (once per normal), then the volume at a plane constant.  volume_nn is
+// the two in a row, so several volumes of one normal are bit for bit the
+// single calls'.
+struct VolNormal {
+  double sh, l1, a0, a1, a2;
+};
+__device__ __forceinline__ VolNormal volume_normal_nn(double m0, double m1, double m2) {
+  VolNormal p;
+  p.sh = 0.0;
+  if (dlt0(m0)) p.sh -= m0;
+  if (dlt0(m1)) p.sh -= m1;
+  if (dlt0(m2)) p.sh -= m2;
   double a0 = fabs(m0), a1 = fabs(m1), a2 = fabs(m2);
-  const double l1 = a0 + a1 + a2;
-  if (!dnz(l1)) return dlt0(alpha) ? 0.0 : 1.0;
-  a0 /= l1; a1 /= l1; a2 /= l1;
-  const double a = (alpha + sh) / l1;
+  p.l1 = a0 + a1 + a2;
+  if (dnz(p.l1)) {
+    a0 /= p.l1; a1 /= p.l1; a2 /= p.l1;
+    // sort the three non-negative components
+    double t;
+    if (nn_lt(a1, a0)) { t = a0; a0 = a1; a1 = t; }
+    if (nn_lt(a2, a1)) { t = a1; a1 = a2; a2 = t; }
+    if (nn_lt(a1, a0)) { t = a0; a0 = a1; a1 = t; }
+  }
+  p.a0 = a0; p.a1 = a1; p.a2 = a2;
+  return p;
+}
+
+__device__ __forceinline__ double volume_at_nn(const VolNormal& p, double alpha) {
+  if (!dnz(p.l1)) return dlt0(alpha) ? 0.0 : 1.0;
+  const double a = (alpha + p.sh) / p.l1;
   if (!dgt0(a)) return 0.0;
   if (!nn_lt(a, 1.0)) return 1.0;
-  // sort the three non-negative components
-  double t;
-  if (nn_lt(a1, a0)) { t = a0; a0 = a1; a1 = t; }
-  if (nn_lt(a2, a1)) { t = a1; a1 = a2; a2 = t; }
-  if (nn_lt(a1, a0)) { t = a0; a0 = a1; a1 = t; }
-  if (!nn_lt(0.5, a)) return vol_low_nn(a0, a1, a2, a);
-  return 1.0 - vol_low_nn(a0, a1, a2, 1.0 - a);
+  // one call for both halves (the argument picked per lane, as above)
+  const bool up = nn_lt(0.5, a);
+  const double v = vol_low_nn(p.a0, p.a1, p.a2, up ? 1.0 - a : a);
+  return up ? 1.0 - v : v;
+}
+
+__device__ __forceinline__ double volume_nn(double m0, double m1, double m2, double alpha) {
+  return volume_at_nn(volume_normal_nn(m0, m1, m2), alpha);
 }
 
 // liquid volume (cell units) in the slab x_axis in [x0, x0+delta], any m,
@@ -660,18 +788,24 @@ __device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
   } else {
     ymax = 1.0;  // degenerate Youngs normal (1, 0, 0)
   }
-  if (!nn_lt(ymax, dom[bd])) {  // cmax <= ymax: the centred-columns candidate
-    const int t1 = bd == 0 ? 1 : 0, t2 = bd == 2 ? 1 : 2;
-    m[t1] = c[bd].a1 / c[bd].l1;
-    m[t2] = c[bd].a2 / c[bd].l1;
-    m[bd] = dbits(c[bd].sg) < 0 ? -dom[bd] : dom[bd];
-  } else if (dnz(l1y)) {
-    m[0] = y[0] / l1y;
-    m[1] = y[1] / l1y;
-    m[2] = y[2] / l1y;
-  } else {
-    m[0] = 1.0; m[1] = 0.0; m[2] = 0.0;
-  }
+  // cmax <= ymax: the centred-columns candidate (a1, a2 on the transverse
+  // axes, +-1 on its own, over l1; (+-1) / l1 is +-dom exactly), else
+  // Youngs' (y / l1y; (1, 0, 0) when y = 0).  Numerators and denominator
+  // are picked first, so both cases share three divisions (a warp whose
+  // lanes took both branches would pay for five).
+  const bool use_cc = !nn_lt(ymax, dom[bd]);
+  const CCParts cb = bd == 0 ? c[0] : (bd == 1 ? c[1] : c[2]);
+  const double own = dbits(cb.sg) < 0 ? -1.0 : 1.0;
+  // transverse axes of bd: t1 = bd == 0 ? 1 : 0, t2 = bd == 2 ? 1 : 2
+  const double n0 = bd == 0 ? own : cb.a1;
+  const double n1 = bd == 1 ? own : (bd == 0 ? cb.a1 : cb.a2);
+  const double n2 = bd == 2 ? own : cb.a2;
+  const double den = use_cc ? cb.l1 : l1y;
+  const double q0 = (use_cc ? n0 : y[0]) / den, q1 = (use_cc ? n1 : y[1]) / den, q2 = (use_cc ? n2 : y[2]) / den;
+  const bool deg = !use_cc && !dnz(l1y);
+  m[0] = deg ? 1.0 : q0;
+  m[1] = deg ? 0.0 : q1;
+  m[2] = deg ? 0.0 : q2;
 }
 
 // ---------------------------------------------------------------------------

@@ -137,6 +137,8 @@ struct ShiftScratch {
   double* sweep;  // [N]
   double* cnew;   // [N] shifted volume of a moving mixed cell
   uint32_t* own;  // [N]
+  // reach and claim are written (and cleared) by the stream kernel for
+  // every cell it visits; the cells of quiet tiles it skips are never read
   uint8_t* reach; // [N] 1: moving mixed cell with shift < 0, 2: > 0, else 0
   uint32_t* claim;  // [N] receivers: bit 31 - b set by the reaching neighbour at offset index b
   TileMap tiles;  // quiet tiles (in-place steps only)
@@ -164,12 +166,16 @@ bool tiles_usable(const GridDev& g);
 int tile_blocks(const GridDev& g);
 size_t tile_scratch_bytes(const GridDev& g);
 TileScratch carve_tile_scratch(const GridDev& g, void* ws);
+// The tile pass of a time step also clears the step's frozen-state flags
+// (state[N], nullable) and its list counters (counters[kStepCounters],
+// nullable), so that the step needs no memset.
+constexpr int kStepCounters = 16;  // 4 per sweep axis, then the shift's 3
 cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, TileScratch ts, SumOut sums,
-                         cudaStream_t st);
+                         uint8_t* state, int* counters, cudaStream_t st);
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
-                         SweepScratch sc, cudaStream_t st);
+                         SweepScratch sc, bool zero_counters, cudaStream_t st);
 
 cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, const double* c_after,
                           const double* e_in, double* e_out, const double* F, const double* uf, uint8_t* state,
@@ -177,7 +183,7 @@ cudaError_t launch_energy(int axis, const GridDev& g, const double* c_before, co
 
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
                          const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut stream_sums,
-                         SumOut sums, cudaStream_t st);
+                         SumOut sums, bool zero_counters, cudaStream_t st);
 
 cudaError_t launch_reconstruct(const GridDev& g, const double* c, double* m, double* alpha, uint8_t* mixed,
                                cudaStream_t st);
@@ -220,6 +226,8 @@ struct TileArgs {
   TileScratch ts;
   int nt[3];
   SumOut sums;
+  uint8_t* state;  // cleared by the tile pass
+  int* counters;   // kStepCounters, cleared by the tile pass
 };
 struct ShiftArgs {
   GridDev g;
@@ -231,18 +239,12 @@ struct ShiftArgs {
   SumOut sums;
   long long nw;
 };
-struct ZeroRange {  // bytes to clear (one CTA per 64 KiB chunk)
-  unsigned char* p;
-  unsigned long long bytes;
-};
 struct ReduceBox {  // one box's sum rows and its output
   const double* rows;
   int nblocks;
   double* out;
   double* scratch;  // kReduceCTAs x kMaxReduceK partials
 };
-constexpr unsigned kZeroChunk = 65536;
-cudaError_t launch_zero_grp(const GroupMap& m, const ZeroRange* r, unsigned ctas, cudaStream_t st);
 cudaError_t launch_tiles_grp(const GroupMap& mt, const GroupMap& mq, const TileArgs* a, unsigned ct, unsigned cq,
                              cudaStream_t st);
 // maps / ctas: [0] kernel A, [1] prep, [2] faces, [3] update
@@ -261,9 +263,6 @@ struct StepBox {
   SweepArgs sweep[3];
   ShiftArgs shift;
   ReduceBox red;
-  ZeroRange zero_state;         // the frozen-state flags, at the step start
-  ZeroRange zero_counters[3];   // a sweep's list counters, before its kernel A
-  ZeroRange zero_shift[3];      // the shift's counters, reach bytes and claims
   dim3 grid_tiles, grid_stream[3], grid_shift_stream;
   unsigned grid_quiet, grid_update[3], grid_shift_sums;
 };

@@ -69,31 +69,6 @@ __device__ __forceinline__ bool neighbour(const GridDev& g, int x, int y, int z,
   return true;
 }
 
-// Bit b (offset index, scan order) set when the neighbour at that offset
-// is a moving mixed cell whose shift reaches pure cells of the kind `want`
-// (1: full cells, shift < 0; 2: empty cells, shift > 0), from the per-cell
-// reach bytes the stream kernel wrote.  The 26 byte loads are independent.
-__device__ __forceinline__ unsigned reach_mask(const GridDev& g, const uint8_t* __restrict__ reach, int x, int y,
-                                               int z, unsigned want) {
-  unsigned mask = 0u;
-#pragma unroll
-  for (int b = 0; b < 27; ++b) {
-    if (b == 13) continue;
-    const int ox = b % 3 - 1, oy = (b / 3) % 3 - 1, oz = b / 9 - 1;
-    int px = x + ox, py = y + oy, pz = z + oz;
-    bool ok = true;
-    if (g.bc[0] != 0 && (px < 0 || px >= g.n[0])) ok = false;
-    if (g.bc[1] != 0 && (py < 0 || py >= g.n[1])) ok = false;
-    if (g.bc[2] != 0 && (pz < 0 || pz >= g.n[2])) ok = false;
-    px = map_idx(px, g.n[0], g.bc[0]);
-    py = map_idx(py, g.n[1], g.bc[1]);
-    pz = map_idx(pz, g.n[2], g.bc[2]);
-    const unsigned r = __ldg(reach + ((size_t)pz * g.n[1] + py) * g.n[0] + px);
-    if (ok && (r & want)) mask |= 1u << b;
-  }
-  return mask;
-}
-
 // offsets as bit indices: ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1), 0..26
 __device__ __forceinline__ int offset_bit(int ox, int oy, int oz) { return ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1); }
 
@@ -147,7 +122,13 @@ __device__ __forceinline__ void k_shift_stream_body(const GridDev& g, const doub
         if (dd) ddv = __ldg(dd + id);
         moving = dd ? dnz(ddv) : uni_moving;
       }
-      if (moving) sc.reach[id] = dlt0(ddv) ? 1 : 2;  // the other cells stay 0
+      // every visited cell's reach byte and claim word are written here, so
+      // the later kernels (which read them only next to moving cells, never
+      // in a skipped quiet tile) need no cleared arrays
+      if (ok) {
+        sc.reach[id] = moving ? (dlt0(ddv) ? 1 : 2) : 0;
+        sc.claim[id] = 0u;
+      }
       const unsigned m = __ballot_sync(kFullMask, moving);
       if (moving) list[n + __popc(m & lt)] = (uint32_t)id;
       n += __popc(m);
@@ -323,41 +304,75 @@ k_shift_own(GridDev g, const double* __restrict__ c_in, const double* __restrict
   k_shift_own_body(g, c_in, dd, dd_uniform, sc, vb_self());
 }
 
+// Per receiver (a pure cell some moving neighbour settles): the largest
+// change |V(alpha* + s) - V(alpha + s)| among the planes of its reaching
+// neighbours, extended into it (s: the plane's offset seen from the
+// receiver), the first such maximum in the scan order of the offsets.  Four
+// lanes share a receiver, lane j taking the offsets b = j mod 4; the lanes'
+// results are combined by the same rule (larger change, then smaller b), so
+// the result is the one-lane scan's.
+constexpr int kRecvLanes = 4;
 __device__ __forceinline__ void k_shift_receivers_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform, const ShiftScratch& sc, const VB vb) {
   const int nr = sc.counters[2];
-  for (int i = vb.bx * blockDim.x + threadIdx.x; i < nr; i += vb.gx * blockDim.x) {
-    const size_t pid = sc.recv[i];
-    const double cp = __ldg(c_in + pid);
-    const bool full = is_full_b(cp, g);
-    int px, py, pz;
-    decode(g, pid, px, py, pz);
+  const int lane = threadIdx.x & 31, sub = lane & (kRecvLanes - 1);
+  constexpr int kPerWarp = 32 / kRecvLanes;
+  const int gw = (int)((vb.bx * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((vb.gx * blockDim.x) >> 5);
+  // whole warps iterate together (the combination below is a shuffle)
+  for (int r0 = gw * kPerWarp; r0 < nr; r0 += nwarps * kPerWarp) {
+    const int i = r0 + lane / kRecvLanes;
+    const bool valid = i < nr;
     double best = 0.0;
-    unsigned rm = reach_mask(g, sc.reach, px, py, pz, full ? 1u : 2u);
-    while (rm) {  // reaching neighbours in scan order
-      const int b = __ffs(rm) - 1;
-      rm &= rm - 1u;
-      const int rx = b % 3 - 1, ry = (b / 3) % 3 - 1, rz = b / 9 - 1;
-      size_t sid;
-      neighbour(g, px, py, pz, rx, ry, rz, sid);
-      const double sft = sc.shift[sid];
-      if (!dnz(sft)) continue;  // a zero normal does not move
-      const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
-      const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
-      // the receiver sits at offset -(rx, ry, rz) from the source
-      const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
-      const double a_old = al + shiftv;
-      const double a_new = (al + sft) + shiftv;
-      double lo = 0.0, hi = 0.0;
-      if (dlt0(m0)) lo += m0; else hi += m0;
-      if (dlt0(m1)) lo += m1; else hi += m1;
-      if (dlt0(m2)) lo += m2; else hi += m2;
-      // the extended plane stays outside the receiver: both volumes are
-      // exactly 1 (or 0); the margin clears the rounding of that test
-      if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
-      const double sw = volume_nn(m0, m1, m2, a_new) - volume_nn(m0, m1, m2, a_old);
-      if (nn_lt(fabs(best), fabs(sw))) best = sw;
+    int bestb = 27;
+    size_t pid = 0;
+    if (valid) {
+      pid = sc.recv[i];
+      const double cp = __ldg(c_in + pid);
+      const unsigned want = is_full_b(cp, g) ? 1u : 2u;
+      const bool full = want == 1u;
+      int px, py, pz;
+      decode(g, pid, px, py, pz);
+      for (int b = sub; b < 27; b += kRecvLanes) {  // this lane's offsets in scan order
+        if (b == 13) continue;
+        const int rx = b % 3 - 1, ry = (b / 3) % 3 - 1, rz = b / 9 - 1;
+        size_t sid;
+        if (!neighbour(g, px, py, pz, rx, ry, rz, sid)) continue;
+        if (!(__ldg(sc.reach + sid) & want)) continue;  // not a reaching neighbour
+        const double sft = sc.shift[sid];
+        if (!dnz(sft)) continue;  // a zero normal does not move
+        const double4 pl = reinterpret_cast<const double4*>(sc.plane)[sid];
+        const double m0 = pl.x, m1 = pl.y, m2 = pl.z, al = pl.w;
+        // the receiver sits at offset -(rx, ry, rz) from the source
+        const double shiftv = -((m0 * (double)(-rx) + m1 * (double)(-ry)) + m2 * (double)(-rz));
+        const double a_old = al + shiftv;
+        const double a_new = (al + sft) + shiftv;
+        double lo = 0.0, hi = 0.0;
+        if (dlt0(m0)) lo += m0; else hi += m0;
+        if (dlt0(m1)) lo += m1; else hi += m1;
+        if (dlt0(m2)) lo += m2; else hi += m2;
+        // the extended plane stays outside the receiver: both volumes are
+        // exactly 1 (or 0); the margin clears the rounding of that test
+        if (full ? (a_new >= hi + 1e-9) : (a_new <= lo - 1e-9)) continue;
+        const VolNormal vn = volume_normal_nn(m0, m1, m2);
+        const double sw = volume_at_nn(vn, a_new) - volume_at_nn(vn, a_old);
+        if (nn_lt(fabs(best), fabs(sw))) {
+          best = sw;
+          bestb = b;
+        }
+      }
     }
-    sc.sweep[pid] = best;  // applied by the sums kernel
+    // combine the receiver's lanes: larger |change|, then the earlier offset
+#pragma unroll
+    for (int o = 1; o < kRecvLanes; o <<= 1) {
+      const double ob = __shfl_xor_sync(kFullMask, best, o);
+      const int obb = __shfl_xor_sync(kFullMask, bestb, o);
+      const long long mine = dbits(fabs(best)), other = dbits(fabs(ob));
+      if (other > mine || (other == mine && obb < bestb)) {
+        best = ob;
+        bestb = obb;
+      }
+    }
+    if (valid && sub == 0) sc.sweep[pid] = best;  // applied by the sums kernel
   }
 }
 
@@ -596,13 +611,14 @@ dim3 shift_stream_grid_of(const GridDev& g) { return shift_stream_grid(g); }
 
 cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out,
                          const double* dd, double dd_uniform, uint8_t* state, ShiftScratch sc, SumOut stream_sums,
-                         SumOut sums, cudaStream_t st) {
+                         SumOut sums, bool zero_counters, cudaStream_t st) {
   const long long nw = shift_warps(g);
-  cudaError_t err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
-  if (err == cudaSuccess) err = cudaMemsetAsync(sc.reach, 0, (size_t)g.n[0] * g.n[1] * g.n[2], st);
-  if (err == cudaSuccess) err = cudaMemsetAsync(sc.claim, 0, (size_t)g.n[0] * g.n[1] * g.n[2] * 4, st);
-  if (err != cudaSuccess) return err;
-  prof_mark("shift.memset", st);
+  cudaError_t err = cudaSuccess;
+  if (zero_counters) {  // else the caller's tile pass cleared them
+    err = cudaMemsetAsync(sc.counters, 0, 3 * sizeof(int), st);
+    if (err != cudaSuccess) return err;
+    prof_mark("shift.memset", st);
+  }
   k_shift_stream<<<shift_stream_grid(g), dim3(32, 8), 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc,
                                                                stream_sums, c_out != c_in);
   prof_mark("shift.stream", st);

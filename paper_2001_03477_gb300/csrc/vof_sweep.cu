@@ -959,12 +959,14 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
 
 cudaError_t launch_sweep(int axis, const GridDev& g, const double* c_in, const double* e_in, double* c_out,
                          double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
-                         SweepScratch sc, cudaStream_t st) {
+                         SweepScratch sc, bool zero_counters, cudaStream_t st) {
   int* status = device_status_ptr();
   const SweepPlan p = sweep_plan(axis, g);
-  const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(int), st);
-  if (err != cudaSuccess) return err;
-  prof_mark("sweep.memset", st);
+  if (zero_counters) {  // else the caller's tile pass cleared them
+    const cudaError_t err = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(int), st);
+    if (err != cudaSuccess) return err;
+    prof_mark("sweep.memset", st);
+  }
   if (e_in) {
     if (axis == 0) launch_ab<0, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);
     else if (axis == 1) launch_ab<1, true>(p, g, c_in, e_in, c_out, e_out, uf, state, theta, flux_out, sc, status, st);

@@ -36,7 +36,7 @@ __device__ __noinline__ void add_tile_cells(const double (&cv)[kTile], const dou
 
 // CTA: 32 x 8 threads covering four tiles along x (32 cells), one along y
 // and one along z (the threads walk its 8 planes).
-__device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, const SumOut& sums, const VB vb) {
+__device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, const SumOut& sums, uint8_t* __restrict__ state, int* __restrict__ counters, const VB vb) {
   __shared__ unsigned uni_w[8];
   __shared__ double ref[4][2];
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -54,7 +54,9 @@ __device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __r
     const size_t id = ((size_t)z * ny + y) * nx + x;
     cv[zi] = ok ? __ldg(c + id) : 0.0;
     ev[zi] = ok ? __ldg(e + id) : 0.0;
+    if (ok && state) state[id] = 0;  // the step's frozen-state flags start clear
   }
+  if (counters && (vb.bx | vb.by | vb.bz) == 0 && ty == 0 && tx < kStepCounters) counters[tx] = 0;
   // reference of each tile: its first cell, which this CTA's thread
   // (8 j, 0) holds as its first value
   if (ty == 0 && (tx & 7) == 0 && tile_ok) {
@@ -105,8 +107,9 @@ __device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __r
 
 __global__ void __launch_bounds__(256)
 k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e,
-                                               TileScratch ts, int ntx, int nty, SumOut sums) {
-  k_tiles_body(g, c, e, ts, ntx, nty, sums, vb_self());
+                                               TileScratch ts, int ntx, int nty, SumOut sums, uint8_t* state,
+                                               int* counters) {
+  k_tiles_body(g, c, e, ts, ntx, nty, sums, state, counters, vb_self());
 }
 
 __device__ __forceinline__ void k_quiet_body(const GridDev& g, const TileScratch& ts, int ntx, int nty, int ntz, const VB vb) {
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(256) k_tiles_grp(GroupMap m, const TileArgs* _
   unsigned b;
   const VB vb = vb_group(m, b);
   const TileArgs A = args[b];
-  k_tiles_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.sums, vb);
+  k_tiles_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.sums, A.state, A.counters, vb);
 }
 __global__ void __launch_bounds__(256) k_quiet_grp(GroupMap m, const TileArgs* __restrict__ args) {
   unsigned b;
@@ -218,29 +221,12 @@ unsigned quiet_blocks(const GridDev& g) {
   return (unsigned)((T + 255) / 256 < 152 * 8 ? (T + 255) / 256 : 152 * 8);
 }
 
-// clears every range of a batch: one CTA per 64 KiB chunk of a range
-__global__ void __launch_bounds__(256) k_zero_grp(GroupMap m, const ZeroRange* __restrict__ r) {
-  unsigned b;
-  const VB vb = vb_group(m, b);
-  const ZeroRange R = r[b];
-  const unsigned long long lo = (unsigned long long)vb.bx * kZeroChunk;
-  unsigned long long hi = lo + kZeroChunk;
-  if (hi > R.bytes) hi = R.bytes;
-  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) R.p[i] = 0;
-}
-
-cudaError_t launch_zero_grp(const GroupMap& m, const ZeroRange* r, unsigned ctas, cudaStream_t st) {
-  if (ctas) k_zero_grp<<<ctas, 256, 0, st>>>(m, r);
-  prof_mark("group.zero", st);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, TileScratch ts, SumOut sums,
-                         cudaStream_t st) {
+                         uint8_t* state, int* counters, cudaStream_t st) {
   int nt[3];
   tile_counts(g, nt);
   k_tiles<<<dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]), dim3(32, 8), 0, st>>>(
-      g, c, e, ts, nt[0], nt[1], sums);
+      g, c, e, ts, nt[0], nt[1], sums, state, counters);
   prof_mark("tiles", st);
   k_quiet<<<quiet_blocks(g), 256, 0, st>>>(g, ts, nt[0], nt[1], nt[2]);
   prof_mark("tiles.quiet", st);

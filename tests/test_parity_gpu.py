@@ -238,6 +238,48 @@ def test_shift(P, name):
         assert abs(d[4] - math.fsum(eo.ravel())) <= 1e-12 * max(1.0, abs(math.fsum(eo.ravel())))
 
 
+def edge_case():
+    """A 48^3 sphere whose mixed cells are pushed within 1e-3 of 0 or 1 at
+    random (log-uniform distance 1e-11 .. 6e-4): the shift's cells whose
+    plane constant is ill-conditioned, among ordinary mixed cells."""
+    import paper_2001_03477_gb300 as P
+    n = 48
+    h = 1.0 / n
+    c = W.sphere_fractions((n, n, n), h, (0.5, 0.47, 0.52), 0.3, nsub=12)
+    g = P.Grid(n, n, n, (0, 1, 0), h, 1000.0, 1.0, 1.0)
+    rng = np.random.default_rng(91)
+    mixed = (c > 1e-12) & (c < 1 - 1e-12)
+    r = rng.random(c.shape)
+    d = 10.0 ** rng.uniform(-11.0, -3.2, c.shape)
+    lo, hi = mixed & (r < 0.3), mixed & (r > 0.7)
+    c = c.copy()
+    c[lo] = d[lo]
+    c[hi] = 1.0 - d[hi]
+    e = (g.Cp_l * c + g.Cp_g * (1 - c)) * (1.0 + 0.1 * rng.random(c.shape))
+    return g, c, e
+
+
+@pytest.mark.parametrize("ddv", [-0.01, 0.013, None])
+def test_shift_edge_cells_bit_exact(P, ddv):
+    """Cells within 1e-3 of 0 or 1 take the plane constant of the plain
+    bisection, step for step: their new fractions V(m, alpha + |m| dd)
+    equal the oracle's bit for bit."""
+    import torch
+    g, c, e = edge_case()
+    og = ogrid(g)
+    ddarr = None if ddv is not None else np.random.default_rng(3).uniform(-0.05, 0.05, g.shape)
+    co, eo, _ = O.phase_shift(og, c, e, dd=ddarr, dd_uniform=ddv or 0.0)
+    cd, ed = dev(c), dev(e)
+    c2 = torch.empty_like(cd); e2 = torch.empty_like(ed)
+    P.vof_phase_change_shift(g, cd, ed, c2, e2, dev(ddarr) if ddarr is not None else None, ddv or 0.0)
+    cg = host(c2)
+    mixed = (c > g.eps_mixed) & (c < 1 - g.eps_mixed)
+    edge = mixed & ((c < 1e-3) | (c > 0.999))
+    assert np.count_nonzero(edge) > 500 and np.count_nonzero(mixed & ~edge) > 500
+    assert np.array_equal(cg[edge], co[edge])
+    assert np.abs(cg - co).max() <= C_TOL
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_in_place_equals_out_of_place(P, name):
     """Sweeps and the shift called in place (c_out == c_in, e_out == e_in)
