@@ -17,11 +17,15 @@
 //
 // Kernels: k_ext_init / k_ext_dilate (layer codes, full grid, 1 B per
 // cell), k_ext_list (compact the unknowns), k_ext_assemble (the six
-// couplings and the source of each unknown, CG start), per CG iteration
-// k_ext_spmv, k_ext_update, k_ext_dir over the unknowns, and k_ext_faces
-// (the face correction, full face grid per axis).  Inner products are per-CTA
-// partial sums that every CTA of the next kernel adds up in the same fixed
-// order, so all CTAs use the same scalars.
+// couplings and the source of each unknown, CG start), the CG iterations,
+// and k_ext_faces (the face correction, full face grid per axis).  The CG
+// iterations run in one cooperative launch, k_ext_cg: its CTAs pass three
+// grid barriers per iteration (after the matrix product, the update and the
+// new direction) and test the residual every iteration on the device; where
+// a cooperative launch of that size is refused, the same three phases run as
+// the kernels k_ext_spmv, k_ext_update, k_ext_dir with a host test every 8
+// iterations.  Inner products are per-CTA partial sums that every CTA adds
+// up in the same fixed order, so all CTAs use the same scalars.
 #include <algorithm>
 #include <vector>
 
@@ -34,8 +38,9 @@ namespace {
 
 constexpr uint8_t kOut = 255;  // pure liquid
 constexpr uint8_t kGas = 254;  // pure gas beyond the layers reached so far
-constexpr int kExtThreads = 256;
-constexpr int kExtCTAs = 152 * 4;
+constexpr int kExtThreads = 256;    // grid-wide cell and face kernels
+constexpr int kSolveThreads = 1024;  // the unknowns' kernels (assembly, CG): one CTA per SM
+constexpr int kExtCTAs = 152;
 constexpr int kNoNb = -1;       // no-slip face (liquid cell or wall)
 constexpr int kFreeNb = -2;     // free-flow face (p~ = 0 beyond)
 
@@ -168,7 +173,7 @@ __device__ double cut_area(const double m[3], double alpha) {
 
 // fixed-order sum of the per-CTA partials (the same value in every CTA)
 __device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n) {
-  __shared__ double red[kExtThreads];
+  __shared__ double red[kSolveThreads];
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
   red[threadIdx.x] = v;
@@ -184,7 +189,7 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
 
 // a CTA's partial sum of v in a fixed order (thread sums, then a tree)
 __device__ __forceinline__ void block_partial(double v, double* __restrict__ out) {
-  __shared__ double red[kExtThreads];
+  __shared__ double red[kSolveThreads];
   red[threadIdx.x] = v;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -207,11 +212,12 @@ struct ExtVec {
   int* counters;  // [0] unknowns, [1] free-flow faces
 };
 
-__global__ void __launch_bounds__(kExtThreads)
+__global__ void __launch_bounds__(kExtThreads)  // (heavy per unknown: no register cap)
 k_ext_assemble(GridDev g, double h, double dt, double rho_l, double rho_g, const double* __restrict__ c,
                const double* __restrict__ mdot, const uint8_t* __restrict__ code, const int* __restrict__ map,
-               const uint32_t* __restrict__ list, ExtVec v) {
+               const uint32_t* __restrict__ list, ExtVec v, unsigned char* __restrict__ cg_state) {
   const int n = v.counters[0];
+  if (blockIdx.x == 0 && threadIdx.x < 32) reinterpret_cast<unsigned long long*>(cg_state)[threadIdx.x] = 0ull;
   double bb = 0.0, rz = 0.0;
   int free_faces = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -270,7 +276,7 @@ k_ext_assemble(GridDev g, double h, double dt, double rho_l, double rho_g, const
 }
 
 // q = M d, partial d . q
-__global__ void __launch_bounds__(kExtThreads) k_ext_spmv(ExtVec v) {
+__global__ void __launch_bounds__(kSolveThreads) k_ext_spmv(ExtVec v) {
   const int n = v.counters[0];
   double dq = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(kExtThreads) k_ext_spmv(ExtVec v) {
 }
 
 // alpha = r.z / d.q; x += alpha d; r -= alpha q; partial r.z (new) and r.r
-__global__ void __launch_bounds__(kExtThreads) k_ext_update(ExtVec v, int cur) {
+__global__ void __launch_bounds__(kSolveThreads) k_ext_update(ExtVec v, int cur) {
   const double rz = sum_partials(v.part + (1 + cur) * kExtCTAs, kExtCTAs);
   const double dq = sum_partials(v.part + 3 * kExtCTAs, kExtCTAs);
   const double alpha = dq > 0.0 ? rz / dq : 0.0;
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(kExtThreads) k_ext_update(ExtVec v, int cur) {
 }
 
 // d = z + (r.z new / r.z old) d
-__global__ void __launch_bounds__(kExtThreads) k_ext_dir(ExtVec v, int cur) {
+__global__ void __launch_bounds__(kSolveThreads) k_ext_dir(ExtVec v, int cur) {
   const double rz = sum_partials(v.part + (1 + cur) * kExtCTAs, kExtCTAs);
   const double rzn = sum_partials(v.part + (2 - cur) * kExtCTAs, kExtCTAs);
   const double beta = rz > 0.0 ? rzn / rz : 0.0;
@@ -313,6 +319,154 @@ __global__ void __launch_bounds__(kExtThreads) k_ext_dir(ExtVec v, int cur) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double zi = v.diag[i] > 0.0 ? v.r[i] / v.diag[i] : 0.0;
     v.d[i] = zi + beta * v.d[i];
+  }
+}
+
+// sum_partials for values other CTAs of the same launch wrote: the loads
+// skip L1 (not coherent across SMs), reading L2
+__device__ __forceinline__ double sum_partials_l2(const double* part, int n) {
+  __shared__ double red[kSolveThreads];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Device state of the persistent solver (in the workspace; the assemble
+// kernel clears it).
+constexpr int kBarGroup = 32;  // CTAs per first-level arrival counter
+struct ExtCG {
+  unsigned arrive;  // grid barrier: groups arrived at the current barrier
+  unsigned gen;     // grid barrier: barriers completed
+  int iters;        // iterations done
+  int flag;         // 1 converged, 2 iteration limit, 3 a barrier wait gave up
+  double res;       // |r| at the end
+  unsigned sub[(kExtCTAs + kBarGroup - 1) / kBarGroup];  // CTAs arrived, per group
+};
+static_assert(sizeof(ExtCG) <= 256, "the solver state lives in 256 bytes of the workspace");
+
+__device__ __forceinline__ unsigned long long ext_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier of a cooperative launch (all CTAs resident): each CTA
+// arrives on its group's counter, the last of a group on the top counter,
+// and the last group starts the next generation (two short chains of
+// atomics instead of one of all CTAs).  The wait is bounded (1 s): on
+// expiry the CTA records DEV_WAIT and returns false, and the solver stops.
+__device__ __forceinline__ bool ext_grid_barrier(ExtCG* cg, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &cg->gen;
+    const unsigned g0 = *vgen;
+    __threadfence();  // this CTA's writes, and g0, before its arrival
+    const unsigned grp = blockIdx.x / kBarGroup, ngrp = (gridDim.x + kBarGroup - 1) / kBarGroup;
+    const unsigned gsize = min((unsigned)kBarGroup, gridDim.x - grp * kBarGroup);
+    bool last = false;
+    if (atomicAdd(&cg->sub[grp], 1u) == gsize - 1) {
+      atomicExch(&cg->sub[grp], 0u);
+      __threadfence();
+      last = atomicAdd(&cg->arrive, 1u) == ngrp - 1;
+    }
+    if (last) {
+      atomicExch(&cg->arrive, 0u);
+      __threadfence();
+      atomicAdd(&cg->gen, 1u);
+    } else {
+      const unsigned long long t0 = ext_now_ns();
+      while (*vgen == g0) {
+        if (ext_now_ns() - t0 > 1000000000ull) {
+          ok = 0;
+          if (status) atomicOr(status, DEV_WAIT);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();  // the other CTAs' writes before this CTA reads them
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The CG iterations in one launch: the phases of k_ext_spmv, k_ext_update
+// and k_ext_dir (the same element arithmetic, partial slots and grid), each
+// followed by a grid barrier; r.z carried from one phase to the next (the
+// values the kernels re-sum), the residual from the update's r.r partials.
+// A thread's own elements are read and written by it alone (the same
+// grid-stride mapping in every phase); the partials and the neighbours'
+// directions, written by other CTAs, are read from L2.
+__global__ void __launch_bounds__(kSolveThreads)
+k_ext_cg(ExtVec v, ExtCG* cg, double tol, int max_iter, int* status) {
+  const int n = v.counters[0];
+  const double bb = sum_partials_l2(v.part, kExtCTAs);
+  const double target = tol * sqrt(bb);
+  double res = sqrt(bb);
+  double rz = sum_partials_l2(v.part + kExtCTAs, kExtCTAs);  // r.z, carried between phases
+  int cur = 0, it = 0;
+  bool ok = true;
+  while (res > target && it < max_iter) {  // the same values in every CTA
+    // q = M d, partial d . q
+    double dq = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      double q = v.diag[i] * v.d[i];
+      for (int f = 0; f < 6; ++f) {
+        const int nb = v.nb[6 * (size_t)i + f];
+        if (nb >= 0) q -= v.beta[6 * (size_t)i + f] * __ldcg(v.d + nb);  // another CTA's
+      }
+      v.q[i] = q;
+      dq += v.d[i] * q;
+    }
+    block_partial(dq, v.part + 3 * kExtCTAs);
+    if (!(ok = ext_grid_barrier(cg, status))) break;
+    // alpha = r.z / d.q; x += alpha d; r -= alpha q; partial r.z and r.r
+    {
+      const double dqs = sum_partials_l2(v.part + 3 * kExtCTAs, kExtCTAs);
+      const double alpha = dqs > 0.0 ? rz / dqs : 0.0;
+      double rzn = 0.0, rr = 0.0;
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        v.x[i] += alpha * v.d[i];
+        const double r = v.r[i] - alpha * v.q[i];
+        v.r[i] = r;
+        const double zi = v.diag[i] > 0.0 ? r / v.diag[i] : 0.0;
+        rzn += r * zi;
+        rr += r * r;
+      }
+      block_partial(rzn, v.part + (2 - cur) * kExtCTAs);
+      block_partial(rr, v.part + 4 * kExtCTAs);
+    }
+    if (!(ok = ext_grid_barrier(cg, status))) break;
+    // d = z + (r.z new / r.z old) d
+    {
+      const double rzn = sum_partials_l2(v.part + (2 - cur) * kExtCTAs, kExtCTAs);
+      const double beta = rz > 0.0 ? rzn / rz : 0.0;
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double zi = v.diag[i] > 0.0 ? v.r[i] / v.diag[i] : 0.0;
+        v.d[i] = zi + beta * v.d[i];
+      }
+      rz = rzn;
+    }
+    res = sqrt(sum_partials_l2(v.part + 4 * kExtCTAs, kExtCTAs));
+    cur ^= 1;
+    ++it;
+    if (!(ok = ext_grid_barrier(cg, status))) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cg->iters = it;
+    cg->res = res;
+    cg->flag = !ok ? 3 : (res > target ? 2 : 1);
   }
 }
 
@@ -362,7 +516,7 @@ k_ext_faces(GridDev g, double h, double dt, double rho_l, double rho_g, const do
 }
 
 struct ExtLayout {
-  size_t code, map, list, nb, beta, diag, x, r, d, q, part, counters, total;
+  size_t code, map, list, nb, beta, diag, x, r, d, q, part, counters, cg, total;
 };
 
 ExtLayout ext_layout(size_t N) {
@@ -381,6 +535,7 @@ ExtLayout ext_layout(size_t N) {
   L.q = o; o += a(N * 8);
   L.part = o; o += a(5 * kExtCTAs * 8);
   L.counters = o; o += a(4 * 4);
+  L.cg = o; o += 256;
   L.total = o;
   return L;
 }
@@ -417,7 +572,8 @@ cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* 
   for (int layer = 1; layer <= 2; ++layer) k_ext_dilate<<<grid_cells, kExtThreads, 0, st>>>(g, code, layer, N);
   k_ext_list<<<grid_cells, kExtThreads, 0, st>>>(code, list, map, vec.counters, N);
   prof_mark("ext.layers", st);
-  k_ext_assemble<<<kExtCTAs, kExtThreads, 0, st>>>(g, h, dt, rho_l, rho_g, c, mdot, code, map, list, vec);
+  unsigned char* cg_state = reinterpret_cast<unsigned char*>(ws + L.cg);
+  k_ext_assemble<<<kExtCTAs, kExtThreads, 0, st>>>(g, h, dt, rho_l, rho_g, c, mdot, code, map, list, vec, cg_state);
   prof_mark("ext.assemble", st);
   int host_counts[2] = {0, 0};
   err = cudaMemcpyAsync(host_counts, vec.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -436,11 +592,37 @@ cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* 
   };
   int it = 0;
   double res = 0.0;
+  bool n_done = false;  // solved by the cooperative launch
   if (n > 0) {
     if (host_counts[1] == 0) {
       *status = 1;  // nothing fixes p~
       return cudaSuccess;
     }
+    // one cooperative launch when all kExtCTAs CTAs fit at once (the grid
+    // barriers need them resident); else the three kernels per iteration
+    int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ext_cg, kSolveThreads, 0) == cudaSuccess && coop &&
+        (long long)per_sm * nsm >= kExtCTAs) {
+      ExtCG* cg = reinterpret_cast<ExtCG*>(cg_state);
+      int* dstat = device_status_ptr();
+      void* args[] = {&vec, &cg, &tol, &max_iter, &dstat};
+      err = cudaLaunchCooperativeKernel((const void*)k_ext_cg, dim3(kExtCTAs), dim3(kSolveThreads), args, 0, st);
+      if (err != cudaSuccess) return err;
+      prof_mark("ext.cg", st);
+      ExtCG hcg{};
+      err = cudaMemcpyAsync(&hcg, cg, sizeof(ExtCG), cudaMemcpyDeviceToHost, st);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+      if (err != cudaSuccess) return err;
+      it = hcg.iters;
+      res = hcg.res;
+      if (hcg.flag != 1) *status = 2;  // not converged (or a barrier wait gave up: DEV_WAIT is set)
+      n_done = true;
+    }
+  }
+  if (n > 0 && !n_done) {
     double bb = 0.0;
     err = host_sum(0, &bb);
     if (err != cudaSuccess) return err;
@@ -448,9 +630,9 @@ cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* 
     res = sqrt(bb);
     int cur = 0;
     while (res > target && it < max_iter) {
-      k_ext_spmv<<<kExtCTAs, kExtThreads, 0, st>>>(vec);
-      k_ext_update<<<kExtCTAs, kExtThreads, 0, st>>>(vec, cur);
-      k_ext_dir<<<kExtCTAs, kExtThreads, 0, st>>>(vec, cur);
+      k_ext_spmv<<<kExtCTAs, kSolveThreads, 0, st>>>(vec);
+      k_ext_update<<<kExtCTAs, kSolveThreads, 0, st>>>(vec, cur);
+      k_ext_dir<<<kExtCTAs, kSolveThreads, 0, st>>>(vec, cur);
       cur ^= 1;
       ++it;
       if (it % 8 == 0 || it == max_iter) {

@@ -24,21 +24,52 @@ constexpr unsigned kFullT = 0xffffffffu;
 
 __device__ __forceinline__ bool same_bits_t(double a, double b) { return dbits(a) == dbits(b); }
 
-__device__ __noinline__ void add_tile_cells(const double (&cv)[kTile], const double (&ev)[kTile], bool on,
-                                           double (&v)[kNSums]) {
-  if (!on) return;
+// Sums of the tiles that are not uniform.  These helpers are not inlined
+// and are called under warp-uniform branches, so that the compiler cannot
+// turn a branch into predicated FP64 adds that every warp would issue (an
+// FP64 instruction costs its full issue time whatever its active lanes; a
+// by-value form was measured to lose the branch).
+//
+// this thread's 8 cells, then over the 8 lanes of its tile's x-row (lane 8j
+// of the warp ends with the row's sums); every lane of the warp calls it
+__device__ __noinline__ void tile_row_sums(const double (&cv)[kTile], const double (&ev)[kTile], bool on,
+                                           double (&s)[2]) {
+  double sc = 0.0, se = 0.0;
+  if (on) {
 #pragma unroll
-  for (int zi = 0; zi < kTile; ++zi) {
-    v[kSumC] += cv[zi];
-    v[kSumE] += ev[zi];
+    for (int zi = 0; zi < kTile; ++zi) {
+      sc += cv[zi];
+      se += ev[zi];
+    }
   }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    sc += __shfl_down_sync(kFullT, sc, o, 8);
+    se += __shfl_down_sync(kFullT, se, o, 8);
+  }
+  s[0] = sc;
+  s[1] = se;
+}
+// the 8 rows of a tile (its y extent), from shared memory, in order
+__device__ __noinline__ void tile_sum_rows(const double (*rows)[2], double (&s)[2]) {
+  double sc = 0.0, se = 0.0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    sc += rows[r][0];
+    se += rows[r][1];
+  }
+  s[0] = sc;
+  s[1] = se;
 }
 
 // CTA: 32 x 8 threads covering four tiles along x (32 cells), one along y
-// and one along z (the threads walk its 8 planes).
+// and one along z (the threads walk its 8 planes).  Each tile writes one
+// sum row (4 rows per CTA): a uniform tile (cells) x value, another its
+// cells' sum (threads over z, lanes over x, warps over y).
 __device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, const SumOut& sums, uint8_t* __restrict__ state, int* __restrict__ counters, const VB vb) {
   __shared__ unsigned uni_w[8];
   __shared__ double ref[4][2];
+  __shared__ double rows[4][8][2];  // non-uniform tiles: [tile][y row][c, e]
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int j = tx >> 3;  // tile of this thread within the CTA
@@ -76,33 +107,48 @@ __device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __r
 #pragma unroll
   for (int w = 0; w < 8; ++w) all &= uni_w[w];
   const bool tile_uni = ((all >> (8 * j)) & 0xFFu) == 0xFFu;
-  double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (tile_ok) {
-    if (tile_uni) {
-      // one thread per tile: (cells of the tile) x value
-      if (ty == 0 && (tx & 7) == 0) {
-        const int cx = min(kTile, nx - xt * kTile), cy = min(kTile, ny - (int)vb.by * kTile),
-                  cz = min(kTile, nz - z0);
-        const double n = (double)(cx * cy * cz);
-        v[kSumC] = n * cr;
-        v[kSumE] = n * er;
-        const size_t t = ((size_t)vb.bz * nty + vb.by) * ntx + xt;
-        ts.uni[t] = 1;
-        ts.vc[t] = cr;
-        ts.ve[t] = er;
-      }
-    } else if (ty == 0 && (tx & 7) == 0) {
-      ts.uni[((size_t)vb.bz * nty + vb.by) * ntx + xt] = 0;
+  // non-uniform tiles: each warp's x-row sums into shared memory
+  const bool add_cells = tile_ok && !tile_uni && xy_ok;
+  const bool warp_adds = __any_sync(kFullT, tile_ok && !tile_uni);
+  if (warp_adds) {
+    double rs[2];
+    tile_row_sums(cv, ev, add_cells, rs);
+    if ((tx & 7) == 0) {
+      rows[j][ty][0] = rs[0];
+      rows[j][ty][1] = rs[1];
     }
   }
-  // cell by cell only in the tiles that are not uniform; the branch is
-  // taken per warp so that the adds are not executed (predicated) for the
-  // uniform majority -- an FP64 add costs ~80 cycles of the SM partition's
-  // FP64 unit per warp on this part
-  const bool add_cells = tile_ok && !tile_uni && xy_ok;
-  if (__any_sync(kFullT, add_cells)) add_tile_cells(cv, ev, add_cells, v);
-
-  block_sums(v, sums, vb.bx + vb.gx * (vb.by + vb.gy * vb.bz));
+  __syncthreads();
+  if (ty == 0 && (tx & 7) == 0) {
+    const size_t t = ((size_t)vb.bz * nty + vb.by) * ntx + xt;
+    double sc = 0.0, se = 0.0;  // a slot beyond the grid: a zero row
+    if (!tile_ok) {
+    } else if (tile_uni) {
+      const int cx = min(kTile, nx - xt * kTile), cy = min(kTile, ny - (int)vb.by * kTile),
+                cz = min(kTile, nz - z0);
+      const double n = (double)(cx * cy * cz);
+      sc = n * cr;
+      se = n * er;
+      ts.uni[t] = 1;
+      ts.vc[t] = cr;
+      ts.ve[t] = er;
+    } else {
+      ts.uni[t] = 0;
+      double s2[2];
+      tile_sum_rows(rows[j], s2);  // rows beyond ny hold 0
+      sc = s2[0];
+      se = s2[1];
+    }
+    if (sums.partials) {
+      double* row = sums.partials + ((size_t)(vb.bx + vb.gx * (vb.by + vb.gy * vb.bz)) * 4 + j) * sums.stride;
+      row[kSumC] = sc;
+      row[kSumE] = se;
+      row[kSumClip] = 0.0;
+      row[kSumShDc] = 0.0;
+      row[kSumUnpl] = 0.0;
+      row[kSumShDe] = 0.0;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256)
@@ -110,6 +156,15 @@ k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e,
                                                TileScratch ts, int ntx, int nty, SumOut sums, uint8_t* state,
                                                int* counters) {
   k_tiles_body(g, c, e, ts, ntx, nty, sums, state, counters, vb_self());
+}
+
+// neighbour tile index along one axis: -1 when it lies beyond a
+// zero-gradient boundary (the halo repeats the boundary: counts as equal),
+// wrapped on a periodic axis
+__device__ __forceinline__ int tile_nb(int p, int n, int bc) {
+  if (p < 0) return bc ? -1 : p + n;
+  if (p >= n) return bc ? -1 : p - n;
+  return p;
 }
 
 __device__ __forceinline__ void k_quiet_body(const GridDev& g, const TileScratch& ts, int ntx, int nty, int ntz, const VB vb) {
@@ -124,23 +179,21 @@ __device__ __forceinline__ void k_quiet_body(const GridDev& g, const TileScratch
       const long long cb = dbits(cr);
       q = cb == 0 || cb == 0x3FF0000000000000LL;
     }
-    const int ntv[3] = {ntx, nty, ntz};
-    for (int oz = -1; oz <= 1 && q; ++oz)
-      for (int oy = -1; oy <= 1 && q; ++oy)
-        for (int ox = -1; ox <= 1 && q; ++ox) {
-          if (!ox && !oy && !oz) continue;
-          int p[3] = {tx + ox, ty + oy, tz + oz};
-          bool skip = false;
-          for (int a = 0; a < 3; ++a) {
-            if (p[a] < 0 || p[a] >= ntv[a]) {
-              if (g.bc[a] != 0) skip = true;  // zero-gradient: the halo repeats the boundary
-              else p[a] = (p[a] + ntv[a]) % ntv[a];
-            }
-          }
-          if (skip) continue;
-          const size_t u = ((size_t)p[2] * nty + p[1]) * ntx + p[0];
-          q = ts.uni[u] != 0 && same_bits_t(ts.vc[u], cr) && same_bits_t(ts.ve[u], er);
-        }
+    if (q) {
+      // the 26 neighbours' flags and values, loaded independently (no
+      // early exit: one round trip instead of a chain of 26)
+      bool all = true;
+#pragma unroll
+      for (int o = 0; o < 27; ++o) {
+        if (o == 13) continue;
+        const int px = tile_nb(tx + o % 3 - 1, ntx, g.bc[0]), py = tile_nb(ty + (o / 3) % 3 - 1, nty, g.bc[1]),
+                  pz = tile_nb(tz + o / 9 - 1, ntz, g.bc[2]);
+        if ((px | py | pz) < 0) continue;
+        const size_t u = ((size_t)pz * nty + py) * ntx + px;
+        all = all & (ts.uni[u] != 0) & same_bits_t(ts.vc[u], cr) & same_bits_t(ts.ve[u], er);
+      }
+      q = all;
+    }
     ts.quiet[t] = q ? 1 : 0;
   }
 }
@@ -166,10 +219,11 @@ bool tiles_usable(const GridDev& g) {
   return true;
 }
 
+// sum rows of the tile pass: 4 per CTA (one per tile slot along x)
 int tile_blocks(const GridDev& g) {
   int nt[3];
   tile_counts(g, nt);
-  return ((nt[0] + 3) / 4) * nt[1] * nt[2];
+  return ((nt[0] + 3) / 4) * nt[1] * nt[2] * 4;
 }
 
 size_t tile_scratch_bytes(const GridDev& g) {
