@@ -380,6 +380,8 @@ def run_gpu(args):
 # conductivities of water and steam at 1 atm (W/m/K) and the latent heat of
 # the bubble workload: the scale of mdot only
 K_L_WATER, K_G_STEAM = 0.68, 0.025
+# droplet boxes of the grouped step that --kernels-once runs (a few GB)
+KERNELS_ONCE_BOXES = 64
 
 
 def mass_transfer_measure(P, g, wl, c, e, stream, barrier, reps=20):
@@ -1045,8 +1047,31 @@ def kernels_once():
     m = torch.empty((131072, 3), dtype=torch.float64, device=dev)
     P.vof_mlp_normals(mlp.packed, X, m)
     mlp.train_step(X, N, 16384, 1e-3, seed=1)
+    # the two solvers of the state reached: the velocity extension driven by
+    # that mdot and the implicit interface-Dirichlet heat diffusion
+    nz, ny, nx = c.shape
+    ut = torch.empty((nz, ny, nx + 1), dtype=torch.float64, device=dev)
+    vt = torch.empty((nz, ny + 1, nx), dtype=torch.float64, device=dev)
+    wt = torch.empty((nz + 1, ny, nx), dtype=torch.float64, device=dev)
+    ext_it, _ = P.vof_velocity_extension(g, c, mdot, W.RHO_L, W.RHO_G, wl.dt, ut=ut, vt=vt, wt=wt)
+    dif_it, _ = P.vof_heat_diffusion(g, c, e.clone(), K_L_WATER, K_G_STEAM, wl.dt, tol=1e-9, max_iter=1000)
+    del ut, vt, wt
+    # one grouped step of a small droplet batch (the batched form's kernels)
+    boxes = []
+    for cb, h, dt, dd, vel in _droplet_part(range(KERNELS_ONCE_BOXES), 4):
+        n = cb.shape[0]
+        cd = torch.from_numpy(cb).to(dev)
+        gb = P.Grid(n, n, n, (0, 0, 0), h, 1000.0, 1.0, 1.0)
+        boxes.append(P.Box(gb, cd, 1000.0 * cd, torch.full((n, n, n + 1), vel[0], dtype=torch.float64, device=dev),
+                           torch.full((n, n + 1, n), vel[1], dtype=torch.float64, device=dev),
+                           torch.full((n + 1, n, n), vel[2], dtype=torch.float64, device=dev), dt, None, dd))
+    grp = P.Group(boxes, 1024, dev)
+    grp.step(0)
     torch.cuda.synchronize()
-    print("kernels-once ok", [float(x) for x in st.sums.cpu()], float(mdot.sum()), float(y.abs().sum()))
+    gs = grp.sums.cpu().numpy()
+    grp.close()
+    print("kernels-once ok", [float(x) for x in st.sums.cpu()], float(mdot.sum()), float(y.abs().sum()),
+          "extension", ext_it, "diffusion", dif_it, "group", len(boxes), bool(np.isfinite(gs).all()))
 
 
 def main():

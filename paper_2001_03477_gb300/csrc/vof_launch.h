@@ -35,6 +35,21 @@ __device__ __forceinline__ VB vb_group(const GroupMap& m, unsigned& b) {
   return VB{l % d.x, (l / d.x) % d.y, l / (d.x * d.y), d.x, d.y, d.z};
 }
 
+// A grouped launch's per-box arguments, copied once per CTA into shared
+// memory (the struct's words spread over the threads) instead of loaded
+// whole by every thread.
+template <class T>
+__device__ __forceinline__ const T& cta_args(const T* __restrict__ args, unsigned b, T& smem) {
+  static_assert(sizeof(T) % 8 == 0 && alignof(T) >= 8, "argument structs are whole 8-byte words");
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(args + b);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&smem);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  for (int i = tid; i < (int)(sizeof(T) / 8); i += nthr) dst[i] = __ldg(src + i);
+  __syncthreads();
+  return smem;
+}
+
 // Sums.  Every kernel that sums produces one row of kNSums values per CTA,
 // in one layout:
 //   [kSumC] sum of c contributions   [kSumE] sum of e contributions

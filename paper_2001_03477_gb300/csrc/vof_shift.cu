@@ -562,32 +562,37 @@ ShiftScratch carve_shift_scratch(const GridDev& g, void* ws) {
 __global__ void __launch_bounds__(256) k_shift_stream_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const ShiftArgs A = args[b];
+  __shared__ ShiftArgs sA;
+  const ShiftArgs& A = cta_args(args, b, sA);
   const SumOut none = sums_to_partials(nullptr, kNSums);
   k_shift_stream_body(A.g, A.c, A.e, A.c, A.e, A.dd, A.dd_uniform, A.sc, none, 0, vb);
 }
 __global__ void __launch_bounds__(kListThreads) k_shift_planes_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const ShiftArgs A = args[b];
+  __shared__ ShiftArgs sA;
+  const ShiftArgs& A = cta_args(args, b, sA);
   k_shift_planes_body(A.g, A.c, A.dd, A.dd_uniform, A.sc, vb);
 }
 __global__ void __launch_bounds__(kListThreads) k_shift_own_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const ShiftArgs A = args[b];
+  __shared__ ShiftArgs sA;
+  const ShiftArgs& A = cta_args(args, b, sA);
   k_shift_own_body(A.g, A.c, A.dd, A.dd_uniform, A.sc, vb);
 }
 __global__ void __launch_bounds__(kListThreads) k_shift_receivers_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const ShiftArgs A = args[b];
+  __shared__ ShiftArgs sA;
+  const ShiftArgs& A = cta_args(args, b, sA);
   k_shift_receivers_body(A.g, A.c, A.dd, A.dd_uniform, A.sc, vb);
 }
 __global__ void __launch_bounds__(256) k_shift_sums_grp(GroupMap m, const ShiftArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const ShiftArgs A = args[b];
+  __shared__ ShiftArgs sA;
+  const ShiftArgs& A = cta_args(args, b, sA);
   k_shift_sums_body(A.g, A.c, A.e, A.c, A.e, A.sc, A.nw, A.sums, vb);
 }
 

@@ -81,7 +81,9 @@ __device__ __forceinline__ double face_energy_flux(double Cp_l, double Cp_g, dou
 }
 
 // WY update of one cell from its two faces; returns the clipped volume
-template <bool ENERGY>
+// LAG: the Lagrangian-explicit form (a compile-time choice, so that the
+// Weymouth-Yue kernel carries none of its FP64 arithmetic)
+template <bool ENERGY, bool LAG>
 __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, double c, double e, double T, uint8_t stv,
                                               double Fl, double Gl, double al, double Fr, double Gr, double ar,
                                               double* __restrict__ c_out, double* __restrict__ e_out,
@@ -89,7 +91,7 @@ __device__ __forceinline__ double update_cell(const GridDev& g, size_t id, doubl
                                               double& de) {
   // Lagrangian-explicit sweeps: the dilatation terms use the cell's own
   // c and Theta; no frozen state
-  const bool lag = g.le != 0;
+  constexpr bool lag = LAG;
   const bool dirty = !lag && (stv & 1);
   const bool ccb = dirty ? ((stv >> 1) & 1) != 0 : dgthalf(c);
   // Weymouth-Yue: cc is 0 or 1, so cc a is a or 0 exactly (no multiply);
@@ -246,6 +248,12 @@ __device__ __forceinline__ void k_stream_col_body(const GridDev& g, const double
     qc[i] = __ldg(c_in + id);
     qe[i] = ENERGY ? __ldg(e_in + id) : 0.0;
   }
+  // frozen-state flags of cells k .. k+3, loaded ahead like c and e (a
+  // flag read in the iteration that needs it would put one memory round
+  // trip into every step of the walk)
+  uint8_t sq[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) sq[i] = (act && state && s0 + i < s1) ? state[cbase + stride * (s0 + i)] : (uint8_t)0;
   for (int k = s0; k < s1; ++k) {
     // cell k + 4 from the queue; cell k + 8 joins it
     const double cn = qc[0], en = qe[0];
@@ -257,7 +265,10 @@ __device__ __forceinline__ void k_stream_col_body(const GridDev& g, const double
       qe[3] = ENERGY ? __ldg(e_in + idq) : 0.0;
     }
     const size_t id = cbase + stride * k;
-    const uint8_t stv = (act && state) ? state[id] : (uint8_t)0;
+    const uint8_t stv = sq[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sq[i] = sq[i + 1];
+    sq[3] = (act && state && k + 4 < s1) ? state[id + stride * 4] : (uint8_t)0;
     // cells k-3..k+3 equal <=> run (ending at k+3) >= 7
     const bool noop = act && !force_all && run >= 7 && is01(wc[0]) && !(stv & 1);
     if (act && noop && copy) {  // out of place: no-op cells are copied
@@ -370,11 +381,17 @@ __device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double
   unsigned eqC = eqmask(__shfl_sync(kFull, cP, 31), __shfl_sync(kFull, eP, 31), cC, eC);
   unsigned eqN = eqmask(__shfl_sync(kFull, cC, 31), __shfl_sync(kFull, eC, 31), cN, eN);
   bool mixed_carry = is_mixed_b(__shfl_sync(kFull, cP, 31), g);  // cell base - 1 mixed
+  // frozen-state flags of the current chunk and of the next, loaded one
+  // chunk ahead with c and e (cell X + 1 past the row end wraps on a
+  // periodic axis; past a zero-gradient end its flag is not used)
+  auto lds_ = [&](int X) { return state ? state[rbase + map_idx(X, nx, bcx)] : (uint8_t)0; };
+  uint8_t stC = lds_(base + lane);
   for (; base < x1; base += 32) {
     const double cNN = ldc(base + 64 + lane), eNN = lde(base + 64 + lane);
+    const uint8_t stN = lds_(base + 32 + lane);
     const int X = base + lane;
     const bool cell_ok = X < x1;
-    const uint8_t stv = (cell_ok && state) ? state[rbase + X] : (uint8_t)0;
+    const uint8_t stv = cell_ok ? stC : (uint8_t)0;
     const unsigned long long M1 = ((unsigned long long)eqC << 32) | eqP;
     const unsigned long long M2 = ((unsigned long long)eqN << 32) | eqC;
     // cells X-3..X+3 equal <=> eq bits of X-2..X+3
@@ -409,7 +426,9 @@ __device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double
     const double c_next = lane == 31 ? c_n0 : c_dn;
     const int Xn = X + 1;
     const bool in_line = Xn < nx || bcx == 0;
-    const uint8_t stn = (listed && in_line && state) ? state[rbase + map_idx(Xn, nx, bcx)] : (uint8_t)0;
+    const uint8_t st_dn = (uint8_t)__shfl_down_sync(kFull, (unsigned)stC, 1);
+    const uint8_t st_n0 = (uint8_t)__shfl_sync(kFull, (unsigned)stN, 0);
+    const uint8_t stn = (listed && in_line) ? (lane == 31 ? st_n0 : st_dn) : (uint8_t)0;
     const bool next_listed = in_line && !(!force_all && uni_n && is01(c_next) && !(stn & 1));
     const bool rend = listed && !next_listed;
     const uint32_t madj_r = (mx_raw || is_mixed_b(c_next, g)) ? kMixedAdj : 0u;  // face X + 1
@@ -423,6 +442,7 @@ __device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double
     cC = cN; eC = eN;
     cN = cNN; eN = eNN;
     eqP = eqC; eqC = eqN; eqN = eqNN;
+    stC = stN;
   }
   if (lane == 0) sc.count[sub] = nlist;
   append_lists(sc, list, nlist, nlist_m, mlist, nmixed, rlist, nrun, nrun_m, lane);
@@ -661,23 +681,30 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 }
 
 // ---------------------------------------------------------------------------
-// Kernel U: one CTA per `ngrp` groups of 8 consecutive kernel-A lists
-// (fixed order, so the sums are reproducible), one listed cell per thread:
+// Kernel U: each CTA takes `ngrp` groups of 8 consecutive kernel-A lists,
+// dealt in turn (a fixed assignment and order, so the sums are
+// reproducible), one listed cell per thread:
 // the WY update from the two face fluxes.  It reads no cell but its own, so
 // it may update in place (c_out == c_in, e_out == e_in); kernel A then
 // copies nothing.
 // ---------------------------------------------------------------------------
-template <int AX, bool ENERGY>
-__device__ __forceinline__ void k_update_body(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out, const double* __restrict__ uf, uint8_t* __restrict__ state, double* __restrict__ theta, const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb) {
-  const int nx = g.n[0], ny = g.n[1];
+// The groups of lists this CTA takes, cell by cell; v accumulates the
+// CTA's contributions to the sums in a fixed order.
+template <int AX, bool ENERGY, bool LAG>
+__device__ __forceinline__ void update_groups(const GridDev& g, const double* c_in, const double* e_in, double* c_out,
+                                              double* e_out, const double* __restrict__ uf,
+                                              uint8_t* __restrict__ state, double* __restrict__ theta,
+                                              const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb,
+                                              int (&pre)[9], double (&v)[kNSums]) {
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  __shared__ int pre[9];
-  double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int grp = 0; grp < ngrp; ++grp) {
     // the group's 8 lists sub0 .. sub0+7 as one sequence (fixed order):
-    // short lists then still fill whole warps
-    const int sub0 = (vb.bx * ngrp + grp) * 8;
+    // short lists then still fill whole warps.  Groups are dealt to the
+    // CTAs in turn (CTA b takes groups b, b + gx, ...): the lists of one
+    // region of the grid spread over all CTAs, whatever the interface's
+    // position
+    const int sub0 = (grp * (int)vb.gx + (int)vb.bx) * 8;
     if (sub0 >= nsub) break;  // uniform over the CTA
     if (threadIdx.x == 0) {
       int t = 0;
@@ -708,13 +735,23 @@ __device__ __forceinline__ void k_update_body(const GridDev& g, const double* c_
       const double T = ENERGY ? sc.T[id] : 0.0;
       const uint8_t stv = state ? state[id] : (uint8_t)0;
       double dc, de;
-      v[kSumClip] += update_cell<ENERGY>(g, id, c, e, T, stv, Fl, Gl, al, Fr, Gr, ar, c_out, e_out, state, theta,
-                                         dc, de);
+      v[kSumClip] += update_cell<ENERGY, LAG>(g, id, c, e, T, stv, Fl, Gl, al, Fr, Gr, ar, c_out, e_out, state,
+                                              theta, dc, de);
       v[kSumC] += dc;
       v[kSumE] += de;
     }
     __syncthreads();  // pre[] is rewritten by the next group
   }
+}
+
+template <int AX, bool ENERGY>
+__device__ __forceinline__ void k_update_body(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out, const double* __restrict__ uf, uint8_t* __restrict__ state, double* __restrict__ theta, const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb) {
+  __shared__ int pre[9];
+  double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (g.le)  // uniform: one loop or the other, never both forms' arithmetic
+    update_groups<AX, ENERGY, true>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre, v);
+  else
+    update_groups<AX, ENERGY, false>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre, v);
   // work counts of this sweep (kernel A's counters are final by now)
   if (sc.stats && vb.bx == 0 && threadIdx.x == 0) {
     sc.stats[0] = sc.counters[0];
@@ -854,13 +891,17 @@ SweepPlan sweep_plan(int axis, const GridDev& g) {
     p.cap = (g.n[0] < 32 ? g.n[0] : 32) * (g.n[axis] < kSegA ? g.n[axis] : kSegA);
     p.nsub = (long long)p.gridA.x * p.gridA.y * p.gridA.z * kWarpsA;
   }
-  // kernel U: groups of 8 consecutive lists per CTA, enough groups that the
-  // CTAs (and their FP64 sum trees) number at most ~16 per SM whatever the
-  // list count
-  int ngrp = 1;
-  while (ngrp < 64 && p.nsub / (8 * ngrp) > 152 * 16) ngrp *= 2;
-  p.lpc = 8 * ngrp;
-  p.gridB = (unsigned)((p.nsub + p.lpc - 1) / p.lpc);
+  // kernel U: groups of 8 consecutive lists, dealt to the CTAs in turn;
+  // about one CTA per 4096 cells, at most one wave (4 per SM): each CTA's
+  // FP64 sum tree then serves many listed cells
+  const long long cells = (long long)g.n[0] * g.n[1] * g.n[2];
+  const long long groups = (p.nsub + 7) / 8;
+  long long target = (cells + 4095) / 4096;
+  if (target > 152 * 4) target = 152 * 4;
+  if (target < 1) target = 1;
+  const long long ngrp = (groups + target - 1) / target;
+  p.lpc = (int)(8 * ngrp);
+  p.gridB = (unsigned)((groups + ngrp - 1) / ngrp);
   return p;
 }
 
@@ -988,7 +1029,8 @@ template <int AX>
 __global__ void __launch_bounds__(256) k_stream_grp(GroupMap m, const SweepArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
+  __shared__ SweepArgs sA;
+  const SweepArgs& A = cta_args(args, b, sA);
   if (AX == 0)
     k_stream_row_body<true>(A.g, A.c, A.e, A.c, A.e, A.state, A.sc, 0, A.cap, 0, vb);
   else
@@ -998,21 +1040,24 @@ template <bool F32, int NRM>
 __global__ void __launch_bounds__(kPlaneThreads) k_prep_grp(GroupMap m, const SweepArgs* __restrict__ args, int ax) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
+  __shared__ SweepArgs sA;
+  const SweepArgs& A = cta_args(args, b, sA);
   k_prep_body<F32, NRM>(A.g, A.c, A.e, A.sc, ax, vb);
 }
 template <int AX>
 __global__ void __launch_bounds__(kFaceThreads) k_faces_grp(GroupMap m, const SweepArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
+  __shared__ SweepArgs sA;
+  const SweepArgs& A = cta_args(args, b, sA);
   k_faces_body<AX, true>(A.g, A.c, A.e, A.uf, nullptr, A.sc, A.status, vb);
 }
 template <int AX>
 __global__ void __launch_bounds__(256) k_update_grp(GroupMap m, const SweepArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const SweepArgs A = args[b];  // a local copy: no reloads after the body's stores
+  __shared__ SweepArgs sA;
+  const SweepArgs& A = cta_args(args, b, sA);
   k_update_body<AX, true>(A.g, A.c, A.e, A.c, A.e, A.uf, A.state, A.theta, A.sc, A.nsub, A.cap, A.ngrp, vb);
 }
 

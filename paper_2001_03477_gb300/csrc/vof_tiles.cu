@@ -22,140 +22,63 @@ namespace {
 
 constexpr unsigned kFullT = 0xffffffffu;
 
-__device__ __forceinline__ bool same_bits_t(double a, double b) { return dbits(a) == dbits(b); }
-
-// Sums of the tiles that are not uniform.  These helpers are not inlined
-// and are called under warp-uniform branches, so that the compiler cannot
-// turn a branch into predicated FP64 adds that every warp would issue (an
-// FP64 instruction costs its full issue time whatever its active lanes; a
-// by-value form was measured to lose the branch).
-//
-// this thread's 8 cells, then over the 8 lanes of its tile's x-row (lane 8j
-// of the warp ends with the row's sums); every lane of the warp calls it
-__device__ __noinline__ void tile_row_sums(const double (&cv)[kTile], const double (&ev)[kTile], bool on,
-                                           double (&s)[2]) {
-  double sc = 0.0, se = 0.0;
-  if (on) {
-#pragma unroll
-    for (int zi = 0; zi < kTile; ++zi) {
-      sc += cv[zi];
-      se += ev[zi];
-    }
-  }
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1) {
-    sc += __shfl_down_sync(kFullT, sc, o, 8);
-    se += __shfl_down_sync(kFullT, se, o, 8);
-  }
-  s[0] = sc;
-  s[1] = se;
-}
-// the 8 rows of a tile (its y extent), from shared memory, in order
-__device__ __noinline__ void tile_sum_rows(const double (*rows)[2], double (&s)[2]) {
-  double sc = 0.0, se = 0.0;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    sc += rows[r][0];
-    se += rows[r][1];
-  }
-  s[0] = sc;
-  s[1] = se;
-}
 
 // CTA: 32 x 8 threads covering four tiles along x (32 cells), one along y
-// and one along z (the threads walk its 8 planes).  Each tile writes one
-// sum row (4 rows per CTA): a uniform tile (cells) x value, another its
-// cells' sum (threads over z, lanes over x, warps over y).
-__device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, const SumOut& sums, uint8_t* __restrict__ state, int* __restrict__ counters, const VB vb) {
+// and one along z (the threads walk its 8 planes).  Each tile's flag and
+// reference values; integer compares only (no FP64 work and nothing kept
+// beyond registers), so the pass streams c and e at the memory's rate.
+__device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, uint8_t* __restrict__ state, int* __restrict__ counters, const VB vb) {
   __shared__ unsigned uni_w[8];
   __shared__ double ref[4][2];
-  __shared__ double rows[4][8][2];  // non-uniform tiles: [tile][y row][c, e]
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int j = tx >> 3;  // tile of this thread within the CTA
   const int x = vb.bx * 32 + tx, y = vb.by * kTile + ty, z0 = vb.bz * kTile;
   const int xt = vb.bx * 4 + j;
   const bool tile_ok = xt * kTile < nx;
-  double cv[kTile], ev[kTile];
+  long long cb[kTile], eb[kTile];
   const bool xy_ok = x < nx && y < ny;
 #pragma unroll
   for (int zi = 0; zi < kTile; ++zi) {
     const int z = z0 + zi;
     const bool ok = xy_ok && z < nz;
     const size_t id = ((size_t)z * ny + y) * nx + x;
-    cv[zi] = ok ? __ldg(c + id) : 0.0;
-    ev[zi] = ok ? __ldg(e + id) : 0.0;
+    cb[zi] = ok ? dbits(__ldg(c + id)) : 0;
+    eb[zi] = ok ? dbits(__ldg(e + id)) : 0;
     if (ok && state) state[id] = 0;  // the step's frozen-state flags start clear
   }
   if (counters && (vb.bx | vb.by | vb.bz) == 0 && ty == 0 && tx < kStepCounters) counters[tx] = 0;
   // reference of each tile: its first cell, which this CTA's thread
   // (8 j, 0) holds as its first value
   if (ty == 0 && (tx & 7) == 0 && tile_ok) {
-    ref[j][0] = cv[0];
-    ref[j][1] = ev[0];
+    ref[j][0] = __longlong_as_double(cb[0]);
+    ref[j][1] = __longlong_as_double(eb[0]);
   }
   __syncthreads();
-  const double cr = tile_ok ? ref[j][0] : 0.0, er = tile_ok ? ref[j][1] : 0.0;
+  const long long cr = tile_ok ? dbits(ref[j][0]) : 0, er = tile_ok ? dbits(ref[j][1]) : 0;
   bool uniform = true;
 #pragma unroll
   for (int zi = 0; zi < kTile; ++zi)
-    if (xy_ok && z0 + zi < nz) uniform = uniform && same_bits_t(cv[zi], cr) && same_bits_t(ev[zi], er);
-  const unsigned b = __ballot_sync(kFullT, uniform);
-  if (tx == 0) uni_w[ty] = b;
+    if (xy_ok && z0 + zi < nz) uniform = uniform && cb[zi] == cr && eb[zi] == er;
+  const unsigned bal = __ballot_sync(kFullT, uniform);
+  if (tx == 0) uni_w[ty] = bal;
   __syncthreads();
-  unsigned all = 0xffffffffu;
+  if (ty == 0 && (tx & 7) == 0 && tile_ok) {
+    unsigned all = 0xffffffffu;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) all &= uni_w[w];
-  const bool tile_uni = ((all >> (8 * j)) & 0xFFu) == 0xFFu;
-  // non-uniform tiles: each warp's x-row sums into shared memory
-  const bool add_cells = tile_ok && !tile_uni && xy_ok;
-  const bool warp_adds = __any_sync(kFullT, tile_ok && !tile_uni);
-  if (warp_adds) {
-    double rs[2];
-    tile_row_sums(cv, ev, add_cells, rs);
-    if ((tx & 7) == 0) {
-      rows[j][ty][0] = rs[0];
-      rows[j][ty][1] = rs[1];
-    }
-  }
-  __syncthreads();
-  if (ty == 0 && (tx & 7) == 0) {
+    for (int w = 0; w < 8; ++w) all &= uni_w[w];
+    const bool tile_uni = ((all >> (8 * j)) & 0xFFu) == 0xFFu;
     const size_t t = ((size_t)vb.bz * nty + vb.by) * ntx + xt;
-    double sc = 0.0, se = 0.0;  // a slot beyond the grid: a zero row
-    if (!tile_ok) {
-    } else if (tile_uni) {
-      const int cx = min(kTile, nx - xt * kTile), cy = min(kTile, ny - (int)vb.by * kTile),
-                cz = min(kTile, nz - z0);
-      const double n = (double)(cx * cy * cz);
-      sc = n * cr;
-      se = n * er;
-      ts.uni[t] = 1;
-      ts.vc[t] = cr;
-      ts.ve[t] = er;
-    } else {
-      ts.uni[t] = 0;
-      double s2[2];
-      tile_sum_rows(rows[j], s2);  // rows beyond ny hold 0
-      sc = s2[0];
-      se = s2[1];
-    }
-    if (sums.partials) {
-      double* row = sums.partials + ((size_t)(vb.bx + vb.gx * (vb.by + vb.gy * vb.bz)) * 4 + j) * sums.stride;
-      row[kSumC] = sc;
-      row[kSumE] = se;
-      row[kSumClip] = 0.0;
-      row[kSumShDc] = 0.0;
-      row[kSumUnpl] = 0.0;
-      row[kSumShDe] = 0.0;
-    }
+    ts.uni[t] = tile_uni ? 1 : 0;
+    ts.vc[t] = __longlong_as_double(cr);
+    ts.ve[t] = __longlong_as_double(er);
   }
 }
 
 __global__ void __launch_bounds__(256)
-k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e,
-                                               TileScratch ts, int ntx, int nty, SumOut sums, uint8_t* state,
-                                               int* counters) {
-  k_tiles_body(g, c, e, ts, ntx, nty, sums, state, counters, vb_self());
+k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e, TileScratch ts, int ntx, int nty,
+        uint8_t* state, int* counters) {
+  k_tiles_body(g, c, e, ts, ntx, nty, state, counters, vb_self());
 }
 
 // neighbour tile index along one axis: -1 when it lies beyond a
@@ -167,40 +90,101 @@ __device__ __forceinline__ int tile_nb(int p, int n, int bc) {
   return p;
 }
 
-__device__ __forceinline__ void k_quiet_body(const GridDev& g, const TileScratch& ts, int ntx, int nty, int ntz, const VB vb) {
-  const long long nt = (long long)ntx * nty * ntz;
-  for (long long t = vb.bx * (long long)blockDim.x + threadIdx.x; t < nt; t += (long long)vb.gx * blockDim.x) {
-    const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
-    bool q = ts.uni[t] != 0;
-    double cr = 0.0, er = 0.0;
-    if (q) {
-      cr = ts.vc[t];
-      er = ts.ve[t];
-      const long long cb = dbits(cr);
-      q = cb == 0 || cb == 0x3FF0000000000000LL;
+// Sums of c and e over a tile whose cells differ: each lane its cells
+// q = lane + 32 r (x fastest within the tile) in order, then the lanes in a
+// fixed tree; lane 0 holds the result.  Not inlined and called under a
+// warp-uniform branch, so that uniform tiles issue none of its FP64 adds
+// (an FP64 instruction costs its full issue time whatever its active lanes).
+__device__ __noinline__ double2 tile_cell_sums(int nx, int ny, int nz, const double* __restrict__ c,
+                                               const double* __restrict__ e, int x0, int y0, int z0) {
+  const int lane = threadIdx.x & 31;
+  double sc = 0.0, se = 0.0;
+#pragma unroll 4
+  for (int r = 0; r < kTile * kTile * kTile / 32; ++r) {
+    const int q = lane + 32 * r;
+    const int x = x0 + (q & 7), y = y0 + ((q >> 3) & 7), z = z0 + (q >> 6);
+    if (x < nx && y < ny && z < nz) {
+      const size_t id = ((size_t)z * ny + y) * nx + x;
+      sc += __ldg(c + id);
+      se += __ldg(e + id);
     }
-    if (q) {
-      // the 26 neighbours' flags and values, loaded independently (no
-      // early exit: one round trip instead of a chain of 26)
-      bool all = true;
+  }
 #pragma unroll
-      for (int o = 0; o < 27; ++o) {
-        if (o == 13) continue;
-        const int px = tile_nb(tx + o % 3 - 1, ntx, g.bc[0]), py = tile_nb(ty + (o / 3) % 3 - 1, nty, g.bc[1]),
-                  pz = tile_nb(tz + o / 9 - 1, ntz, g.bc[2]);
-        if ((px | py | pz) < 0) continue;
+  for (int o = 16; o > 0; o >>= 1) {
+    sc += __shfl_down_sync(kFullT, sc, o);
+    se += __shfl_down_sync(kFullT, se, o);
+  }
+  return make_double2(sc, se);
+}
+
+// One warp per tile: quiet flag (lanes 0..26 check the tile and its 26
+// neighbours at once) and the tile's sum row -- a uniform tile's is
+// (cells) x value, another's the sum of its cells.  Rows are placed at
+// (tz nty + ty) 4 ceil(ntx / 4) + tx; the slots past the last tile of an
+// x-row of tiles hold zero rows.
+__device__ __forceinline__ void k_quiet_body(const GridDev& g, const double* __restrict__ c, const double* __restrict__ e, const TileScratch& ts, int ntx, int nty, int ntz, const SumOut& sums, const VB vb) {
+  const long long nt = (long long)ntx * nty * ntz;
+  const int lane = threadIdx.x & 31;
+  const long long wpb = blockDim.x >> 5;
+  const int rstride = 4 * ((ntx + 3) / 4);
+  for (long long t = vb.bx * wpb + (threadIdx.x >> 5); t < nt; t += (long long)vb.gx * wpb) {
+    const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
+    // lane o < 27: the tile at offset (o % 3 - 1, o / 3 % 3 - 1, o / 9 - 1);
+    // one beyond a zero-gradient boundary counts as equal
+    bool nb_ok = true, nb_uni = true;
+    long long nb_c = 0, nb_e = 0;
+    if (lane < 27) {
+      const int px = tile_nb(tx + lane % 3 - 1, ntx, g.bc[0]), py = tile_nb(ty + (lane / 3) % 3 - 1, nty, g.bc[1]),
+                pz = tile_nb(tz + lane / 9 - 1, ntz, g.bc[2]);
+      nb_ok = (px | py | pz) >= 0;
+      if (nb_ok) {
         const size_t u = ((size_t)pz * nty + py) * ntx + px;
-        all = all & (ts.uni[u] != 0) & same_bits_t(ts.vc[u], cr) & same_bits_t(ts.ve[u], er);
+        nb_uni = ts.uni[u] != 0;
+        nb_c = dbits(ts.vc[u]);
+        nb_e = dbits(ts.ve[u]);
       }
-      q = all;
     }
-    ts.quiet[t] = q ? 1 : 0;
+    const bool uni = __shfl_sync(kFullT, nb_uni ? 1 : 0, 13) != 0;  // lane 13: the tile itself
+    const long long cr = __shfl_sync(kFullT, nb_c, 13), er = __shfl_sync(kFullT, nb_e, 13);
+    const bool same = !nb_ok || (nb_uni && nb_c == cr && nb_e == er);
+    const bool all = __all_sync(kFullT, lane >= 27 || same);
+    const bool q = uni && (cr == 0 || cr == 0x3FF0000000000000LL) && all;
+    if (lane == 0) ts.quiet[t] = q ? 1 : 0;
+    if (!sums.partials) continue;
+    double sc, se;
+    if (uni) {
+      const int cx = min(kTile, g.n[0] - tx * kTile), cy = min(kTile, g.n[1] - ty * kTile),
+                cz = min(kTile, g.n[2] - tz * kTile);
+      const double n = (double)(cx * cy * cz);
+      sc = n * __longlong_as_double(cr);
+      se = n * __longlong_as_double(er);
+    } else {
+      const double2 s2 = tile_cell_sums(g.n[0], g.n[1], g.n[2], c, e, tx * kTile, ty * kTile, tz * kTile);
+      sc = s2.x;
+      se = s2.y;
+    }
+    const size_t slot = ((size_t)tz * nty + ty) * rstride + tx;
+    if (lane == 0) {
+      double* row = sums.partials + slot * sums.stride;
+      row[kSumC] = sc;
+      row[kSumE] = se;
+      row[kSumClip] = 0.0;
+      row[kSumShDc] = 0.0;
+      row[kSumUnpl] = 0.0;
+      row[kSumShDe] = 0.0;
+    }
+    if (tx == ntx - 1 && lane >= 1 && lane < rstride - ntx + 1) {
+      // zero rows of the slots past the row's last tile
+      double* row = sums.partials + (slot + lane) * sums.stride;
+      for (int k = 0; k < kNSums; ++k) row[k] = 0.0;
+    }
   }
 }
 
 __global__ void __launch_bounds__(256)
-k_quiet(GridDev g, TileScratch ts, int ntx, int nty, int ntz) {
-  k_quiet_body(g, ts, ntx, nty, ntz, vb_self());
+k_quiet(GridDev g, const double* __restrict__ c, const double* __restrict__ e, TileScratch ts, int ntx, int nty,
+        int ntz, SumOut sums) {
+  k_quiet_body(g, c, e, ts, ntx, nty, ntz, sums, vb_self());
 }
 
 size_t al256t(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -249,14 +233,16 @@ TileScratch carve_tile_scratch(const GridDev& g, void* ws) {
 __global__ void __launch_bounds__(256) k_tiles_grp(GroupMap m, const TileArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const TileArgs A = args[b];
-  k_tiles_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.sums, A.state, A.counters, vb);
+  __shared__ TileArgs sA;
+  const TileArgs& A = cta_args(args, b, sA);
+  k_tiles_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.state, A.counters, vb);
 }
 __global__ void __launch_bounds__(256) k_quiet_grp(GroupMap m, const TileArgs* __restrict__ args) {
   unsigned b;
   const VB vb = vb_group(m, b);
-  const TileArgs A = args[b];
-  k_quiet_body(A.g, A.ts, A.nt[0], A.nt[1], A.nt[2], vb);
+  __shared__ TileArgs sA;
+  const TileArgs& A = cta_args(args, b, sA);
+  k_quiet_body(A.g, A.c, A.e, A.ts, A.nt[0], A.nt[1], A.nt[2], A.sums, vb);
 }
 
 cudaError_t launch_tiles_grp(const GroupMap& mt, const GroupMap& mq, const TileArgs* a, unsigned ct, unsigned cq,
@@ -272,7 +258,8 @@ unsigned quiet_blocks(const GridDev& g) {
   int nt[3];
   tile_counts(g, nt);
   const long long T = (long long)nt[0] * nt[1] * nt[2];
-  return (unsigned)((T + 255) / 256 < 152 * 8 ? (T + 255) / 256 : 152 * 8);
+  // one warp per tile, 8 per CTA
+  return (unsigned)((T + 7) / 8 < 152 * 8 ? (T + 7) / 8 : 152 * 8);
 }
 
 cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, TileScratch ts, SumOut sums,
@@ -280,9 +267,9 @@ cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, Til
   int nt[3];
   tile_counts(g, nt);
   k_tiles<<<dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]), dim3(32, 8), 0, st>>>(
-      g, c, e, ts, nt[0], nt[1], sums, state, counters);
+      g, c, e, ts, nt[0], nt[1], state, counters);
   prof_mark("tiles", st);
-  k_quiet<<<quiet_blocks(g), 256, 0, st>>>(g, ts, nt[0], nt[1], nt[2]);
+  k_quiet<<<quiet_blocks(g), 256, 0, st>>>(g, c, e, ts, nt[0], nt[1], nt[2], sums);
   prof_mark("tiles.quiet", st);
   return cudaGetLastError();
 }
