@@ -319,7 +319,7 @@ bool step_box(const vof_grid* g, double* c, double* e, const double* u, const do
     A.sc = sc;
     A.cap = p.cap;
     A.nsub = (int)p.nsub;
-    A.ngrp = p.lpc / 8;
+    A.ngrp = p.lpc / kUpdLists;
     A.status = device_status_ptr();
     B.grid_stream[a] = p.gridA;
     B.grid_update[a] = p.gridB;

@@ -64,6 +64,26 @@ __device__ __forceinline__ bool dgt1(double a) { return dbits(a) > 0x3FF00000000
 // a > 0.5
 __device__ __forceinline__ bool dgthalf(double a) { return dbits(a) > 0x3FE0000000000000LL; }
 
+// Exact scalings on the integer pipe, the same bits as the FP64 products
+// (|x| < 2^1022).  2 x: a normal x by its exponent field, zero and subnormal
+// x by a shift of the magnitude bits, which carries into the exponent field
+// exactly as the product does.
+__device__ __forceinline__ double dtwice(double x) {
+  const unsigned long long b = (unsigned long long)dbits(x);
+  const unsigned long long sg = b & 0x8000000000000000ull, mg = b & 0x7FFFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)((mg >> 52) ? b + (1ull << 52) : (sg | (mg << 1))));
+}
+// -x (the sign bit flipped)
+__device__ __forceinline__ double dneg(double x) { return __longlong_as_double(dbits(x) ^ (long long)0x8000000000000000ull); }
+// x / 2 where that is exact without rounding: x = 0, or the half a normal
+// number (exponent field >= 2); ok = false otherwise (the caller multiplies)
+__device__ __forceinline__ double dhalf_exact(double x, bool& ok) {
+  const unsigned long long b = (unsigned long long)dbits(x);
+  const unsigned e = (unsigned)((b >> 52) & 0x7FF);
+  ok = e >= 2 || (b << 1) == 0ull;
+  return __longlong_as_double((long long)(e >= 2 ? b - (1ull << 52) : b));
+}
+
 __device__ __forceinline__ int map_idx(int i, int n, int bc) {
   if (bc == 0) {
     int r = i % n;
@@ -427,7 +447,15 @@ __device__ __forceinline__ double plane_alpha(double m0, double m1, double m2, d
 // 1.5 v3, (a - m2)^3 / d6 <= v3 / 2, and in the last branch v3 <= 1.04 v5,
 // (a - m3)^3 / d6 <= 0.04 v5) the rounding analysis gives ~14 ulps, so a
 // 64-ulp margin decides.
-static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, double m2, double c) {
+//
+// LANES = 3: three lanes of a warp (lanes leader .. leader + 2, mask gmask,
+// sub = lane - leader) share one cell and take two levels per round -- the
+// midpoint and both midpoints of the level after it, each lane deciding
+// one, so a round costs one volume per lane -- with the same midpoints and
+// decisions as the one-lane loop.
+template <int LANES>
+static __device__ __noinline__ double plane_alpha_bisect_t(double m0, double m1, double m2, double c, unsigned gmask,
+                                                           int leader, int sub) {
   Mirror r = mirror_normalise(m0, m1, m2);
   if (r.l1 == 0.0) return 0.0;
   if (c <= 0.0) return 0.0 - r.sh;
@@ -544,18 +572,40 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
       hi = (double)(L + H) * dn;
     }
   }
-  for (; it < 200; ++it) {
-    double mid = lo + 0.5 * (hi - lo);
-    if (!(nn_lt(lo, mid) && nn_lt(mid, hi))) break;
-    // below the middle: below iff the volume at mid is < c; above it iff
-    // the volume at 1 - mid is > t (one fast volume per lane either way)
+  // below the middle: mid is below iff the volume at mid is < c; above it
+  // iff the volume at 1 - mid is > t (one fast volume per lane either way)
+  auto below_at = [&](double mid) -> bool {
     const bool up = nn_lt(0.5, mid);
     const double d = vlow_fast(up ? 1.0 - mid : mid) - (up ? t : c);
-    bool below;
-    if (nn_lt(up ? margin_high : margin_low, fabs(d))) below = up ? dgt0(d) : dlt0(d);
-    else below = nn_lt(vpos(mid), c);
-    if (below) lo = mid;
-    else hi = mid;
+    if (nn_lt(up ? margin_high : margin_low, fabs(d))) return up ? dgt0(d) : dlt0(d);
+    return nn_lt(vpos(mid), c);
+  };
+  if (LANES == 1) {
+    for (; it < 200; ++it) {
+      double mid = lo + 0.5 * (hi - lo);
+      if (!(nn_lt(lo, mid) && nn_lt(mid, hi))) break;
+      if (below_at(mid)) lo = mid;
+      else hi = mid;
+    }
+  } else {
+    while (it < 200) {
+      const double mid = lo + 0.5 * (hi - lo);
+      if (!(nn_lt(lo, mid) && nn_lt(mid, hi))) break;
+      // the next level's midpoint after either decision, as the loop above
+      // would compute it from its new bracket
+      const double midL = lo + 0.5 * (mid - lo), midR = mid + 0.5 * (hi - mid);
+      const bool b = below_at(sub == 0 ? mid : (sub == 1 ? midL : midR));
+      const bool bA = __shfl_sync(gmask, b, leader), bL = __shfl_sync(gmask, b, leader + 1),
+                 bR = __shfl_sync(gmask, b, leader + 2);
+      if (bA) lo = mid;
+      else hi = mid;
+      if (++it >= 200) break;
+      const double m2n = bA ? midR : midL;
+      if (!(nn_lt(lo, m2n) && nn_lt(m2n, hi))) break;
+      if (bA ? bR : bL) lo = m2n;
+      else hi = m2n;
+      ++it;
+    }
   }
   // lo and hi are 0 or 1 only at a bracket end never left (vpos's end cases)
   const double vlo = dbits(lo) == 0 ? 0.0 : vpos(lo);
@@ -563,6 +613,9 @@ static __device__ __noinline__ double plane_alpha_bisect(double m0, double m1, d
   const long long el = dbits(vlo - c) & 0x7FFFFFFFFFFFFFFFLL, eh = dbits(vhi - c) & 0x7FFFFFFFFFFFFFFFLL;
   double am = (eh < el) ? hi : lo;
   return am * r.l1 - r.sh;
+}
+static __device__ __forceinline__ double plane_alpha_bisect(double m0, double m1, double m2, double c) {
+  return plane_alpha_bisect_t<1>(m0, m1, m2, c, 0u, 0, 0);
 }
 
 // The volume function with every compare on the integer pipe: the normal is
@@ -738,10 +791,37 @@ __device__ __forceinline__ CCParts cc_parts(const double* s, int d) {
     }
   CCParts r;
   r.sg = !nn_lt(lower, upper) ? 1.0 : -1.0;  // lower >= upper (both >= 0)
-  r.a1 = -(h[2][1] - h[0][1]) * 0.5;
-  r.a2 = -(h[1][2] - h[1][0]) * 0.5;
+  // the central differences' halves on the integer pipe; a difference
+  // whose half would be subnormal (never met in practice) takes the product
+  // (a1 = -(h21 - h01) / 2, a2 = -(h12 - h10) / 2, the sign flipped on the
+  // bit pattern)
+  const double d1 = h[2][1] - h[0][1], d2 = h[1][2] - h[1][0];
+  bool ok1, ok2;
+  double e1 = dhalf_exact(d1, ok1), e2 = dhalf_exact(d2, ok2);
+  if (__any_sync(__activemask(), !(ok1 && ok2))) {
+    e1 = ok1 ? e1 : d1 * 0.5;
+    e2 = ok2 ? e2 : d2 * 0.5;
+  }
+  r.a1 = dneg(e1);
+  r.a2 = dneg(e2);
   r.l1 = fabs(r.a1) + fabs(r.a2) + 1.0;
   return r;
+}
+
+// The choices of the MYC rule from the candidates' L1 norms l1_d (own-axis
+// components 1 / l1_d) and Youngs' largest |g| over its L1 norm, with the
+// divisions the plain rule takes: the best candidate bd (largest own-axis
+// component, lowest axis on ties) and whether it is kept (its component not
+// below Youngs' largest).
+static __device__ __noinline__ void myc_choice_exact(double l10, double l11, double l12, double amax, double l1y, int& bd,
+                                              bool& use_cc) {
+  const double d0 = 1.0 / l10, d1 = 1.0 / l11, d2 = 1.0 / l12;
+  bd = 0;
+  double dm = d0;
+  if (nn_lt(dm, d1)) { bd = 1; dm = d1; }
+  if (nn_lt(dm, d2)) { bd = 2; dm = d2; }
+  const double ymax = dnz(l1y) ? amax / l1y : 1.0;
+  use_cc = !nn_lt(ymax, dm);
 }
 
 // Best centred-columns candidate (largest own-axis component, lowest axis on
@@ -753,17 +833,9 @@ __device__ __forceinline__ CCParts cc_parts(const double* s, int d) {
 // values are compared as integers.
 __device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
   CCParts c[3];
-  double dom[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    c[d] = cc_parts(s, d);
-    dom[d] = 1.0 / c[d].l1;
-  }
-  int bd = 0;
-  if (nn_lt(dom[0], dom[1])) bd = 1;
-  if (nn_lt(dom[bd], dom[2])) bd = 2;
-  // Youngs gradient
-  const double w[3] = {1.0, 2.0, 1.0};
+  for (int d = 0; d < 3; ++d) c[d] = cc_parts(s, d);
+  // Youngs gradient; the weights 2 and 4 applied on the integer pipe
   double y[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -772,28 +844,53 @@ __device__ __forceinline__ void myc_normal(const double* s, double m[3]) {
     for (int q = -1; q <= 1; ++q)
 #pragma unroll
       for (int p = -1; p <= 1; ++p) {
-        double diff = sax(s, d, 1, p, q) - sax(s, d, -1, p, q);
-        g = g + (w[p + 1] * w[q + 1]) * diff;
+        const double diff = sax(s, d, 1, p, q) - sax(s, d, -1, p, q);
+        const int k = (p == 0) + (q == 0);  // weight 2^k
+        const double wd = k == 0 ? diff : (k == 1 ? dtwice(diff) : dtwice(dtwice(diff)));
+        g = g + wd;
       }
     y[d] = -g;
   }
   const double ay0 = fabs(y[0]), ay1 = fabs(y[1]), ay2 = fabs(y[2]);
   const double l1y = ay0 + ay1 + ay2;
-  double ymax;
+  double amax = ay0;
+  if (nn_lt(amax, ay1)) amax = ay1;
+  if (nn_lt(amax, ay2)) amax = ay2;
+  // The rule's choices compare rounded quotients (1 / l1_d, amax / l1y);
+  // they are taken here from the operands wherever those are far enough
+  // apart that the quotients' rounding cannot tie or reorder them (L1 norms
+  // >= 1 and non-negative values compare as integers; 8 units in the last
+  // place is a relative gap > 2^-50, 4 roundings' worth), else with the
+  // divisions themselves.
+  const long long b0 = dbits(c[0].l1), b1 = dbits(c[1].l1), b2 = dbits(c[2].l1);
+  bool amb = false;
+  // 1/l1_a < 1/l1_b  <=>  l1_a > l1_b, unless they are within 8 ulps
+  auto dom_lt = [&](long long la, long long lb) {
+    if (la - lb > 0 && la - lb < 8) amb = true;
+    return la - lb >= 8;
+  };
+  int bd = dom_lt(b0, b1) ? 1 : 0;
+  const long long bb = bd ? b1 : b0;
+  if (dom_lt(bb, b2)) bd = 2;
+  const double lbd = bd == 0 ? c[0].l1 : (bd == 1 ? c[1].l1 : c[2].l1);
+  // amax / l1y < 1 / l1_bd  <=>  amax l1_bd < l1y (the product within an
+  // ulp; 16 ulps apart decides)
+  bool use_cc = true;  // l1y = 0: Youngs' largest component is 1, not below
   if (dnz(l1y)) {
-    double amax = ay0;
-    if (nn_lt(amax, ay1)) amax = ay1;
-    if (nn_lt(amax, ay2)) amax = ay2;
-    ymax = amax / l1y;
-  } else {
-    ymax = 1.0;  // degenerate Youngs normal (1, 0, 0)
+    const long long pb = dbits(amax * lbd), yb = dbits(l1y);
+    if (pb + 16 <= yb) use_cc = false;
+    else if (!(pb >= yb + 16)) amb = true;
   }
-  // cmax <= ymax: the centred-columns candidate (a1, a2 on the transverse
-  // axes, +-1 on its own, over l1; (+-1) / l1 is +-dom exactly), else
-  // Youngs' (y / l1y; (1, 0, 0) when y = 0).  Numerators and denominator
-  // are picked first, so both cases share three divisions (a warp whose
-  // lanes took both branches would pay for five).
-  const bool use_cc = !nn_lt(ymax, dom[bd]);
+  if (__any_sync(__activemask(), amb)) {
+    int bx;
+    bool ux;
+    myc_choice_exact(c[0].l1, c[1].l1, c[2].l1, amax, l1y, bx, ux);
+    if (amb) { bd = bx; use_cc = ux; }
+  }
+  // the centred-columns candidate (a1, a2 on the transverse axes, +-1 on
+  // its own, over l1) or Youngs' (y / l1y; (1, 0, 0) when y = 0).
+  // Numerators and denominator are picked first, so both cases share three
+  // divisions (a warp whose lanes took both branches would pay for five).
   const CCParts cb = bd == 0 ? c[0] : (bd == 1 ? c[1] : c[2]);
   const double own = dbits(cb.sg) < 0 ? -1.0 : 1.0;
   // transverse axes of bd: t1 = bd == 0 ? 1 : 0, t2 = bd == 2 ? 1 : 2

@@ -39,7 +39,7 @@ namespace {
 constexpr uint8_t kOut = 255;  // pure liquid
 constexpr uint8_t kGas = 254;  // pure gas beyond the layers reached so far
 constexpr int kExtThreads = 256;    // grid-wide cell and face kernels
-constexpr int kSolveThreads = 1024;  // the unknowns' kernels (assembly, CG): one CTA per SM
+constexpr int kSolveThreads = 256;   // the CG kernels: one CTA per SM (few warps per FP64 sum tree)
 constexpr int kExtCTAs = 152;
 constexpr int kNoNb = -1;       // no-slip face (liquid cell or wall)
 constexpr int kFreeNb = -2;     // free-flow face (p~ = 0 beyond)
@@ -171,42 +171,91 @@ __device__ double cut_area(const double m[3], double alpha) {
   return 0.5 * fabs(s) / nd;
 }
 
-// fixed-order sum of the per-CTA partials (the same value in every CTA)
-__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n) {
-  __shared__ double red[kSolveThreads];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+// Fixed-order sums of the per-CTA partials (the same values in every CTA):
+// warp 0 alone, each lane its partials lane, lane + 32, ... in order, then a
+// shuffle tree; K sums at once (one barrier).  L2: the partials were written
+// by other CTAs of the same launch, so the loads skip L1 (not coherent
+// across SMs).
+template <int K, bool L2>
+__device__ __forceinline__ void sum_partials_k(const double* const (&part)[K], int n, double (&out)[K]) {
+  __shared__ double res[K];
+  __syncthreads();  // res may still be read from the previous call
+  if (threadIdx.x < 32) {
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32)
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += L2 ? __ldcg(part[k] + i) : part[k][i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < K; ++k) res[k] = v[k];
   }
-  const double r = red[0];
   __syncthreads();
-  return r;
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = res[k];
+}
+// The same sums in warp 0 alone (valid in its lane 0), for a scalar step
+// that lane 0 takes before sharing the result.
+template <int K, bool L2>
+__device__ __forceinline__ void warp0_sums(const double* const (&part)[K], int n, double (&out)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32)
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] += L2 ? __ldcg(part[k] + i) : part[k][i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] += __shfl_down_sync(0xffffffffu, out[k], o);
 }
 
-// a CTA's partial sum of v in a fixed order (thread sums, then a tree)
-__device__ __forceinline__ void block_partial(double v, double* __restrict__ out) {
-  __shared__ double red[kSolveThreads];
-  red[threadIdx.x] = v;
+// A CTA's partial sums of K values in a fixed order (the threads' values
+// staged in shared memory; warp 0 sums them, each lane its entries lane,
+// lane + 32, ... in order, then a shuffle tree: few FP64 instructions per
+// value), written to out[k][blockIdx.x].
+template <int K>
+__device__ __forceinline__ void block_partial_k(const double (&v)[K], double* const (&out)[K]) {
+  __shared__ double red[K][kSolveThreads];
+  __syncthreads();  // red may still be read from the previous call
+#pragma unroll
+  for (int k = 0; k < K; ++k) red[k][threadIdx.x] = v[k];
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    double x[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      x[k] = 0.0;
+      for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) x[k] += red[k][i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k) x[k] += __shfl_down_sync(0xffffffffu, x[k], o);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < K; ++k) out[k][blockIdx.x] = x[k];
   }
-  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
-  __syncthreads();
+}
+__device__ __forceinline__ void block_partial(double v, double* __restrict__ out) {
+  const double vv[1] = {v};
+  double* const o[1] = {out};
+  block_partial_k<1>(vv, o);
 }
 
 struct ExtVec {
   int* nb;        // [6 n]: neighbour unknown, kNoNb, or kFreeNb
   double* beta;   // [6 n]
   double* diag;   // [n]
+  double* rdiag;  // [n]: 1 / diag (0 where diag is 0), the Jacobi preconditioner
   double* x;      // p~
   double* r;
   double* d;
+  double* d2;     // the cooperative solver's second direction buffer (the two take turns)
   double* q;
   double* part;   // [5][kExtCTAs]: b.b, r.z (two, alternating), d.q, r.r
   int* counters;  // [0] unknowns, [1] free-flow faces
@@ -262,81 +311,80 @@ k_ext_assemble(GridDev g, double h, double dt, double rho_l, double rho_g, const
     }
     // M = -A: diagonal sum beta, off-diagonal -beta; b = -rhs
     const double b = -rhs;
+    const double rd = dsum > 0.0 ? 1.0 / dsum : 0.0;
     v.diag[i] = dsum;
+    v.rdiag[i] = rd;
     v.x[i] = 0.0;
     v.r[i] = b;
-    const double zi = dsum > 0.0 ? b / dsum : 0.0;
+    const double zi = b * rd;
     v.d[i] = zi;
-    bb += b * b;
-    rz += b * zi;
+    bb = fma(b, b, bb);
+    rz = fma(b, zi, rz);
   }
   if (free_faces) atomicAdd(v.counters + 1, free_faces);
-  block_partial(bb, v.part);
-  block_partial(rz, v.part + kExtCTAs);
+  const double pv[2] = {bb, rz};
+  double* const po[2] = {v.part, v.part + kExtCTAs};
+  block_partial_k<2>(pv, po);
+}
+
+// The element arithmetic of one CG iteration (both forms of the solver use
+// it): q = M d with its partial d . q; x += alpha d, r -= alpha q, z = r /
+// diag with the partials r . z and r . r; d = z + beta d.
+__device__ __forceinline__ double ext_spmv_elem(const ExtVec& v, int i, bool l2) {
+  double q = v.diag[i] * v.d[i];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int nb = v.nb[6 * (size_t)i + f];
+    if (nb >= 0) q = fma(-v.beta[6 * (size_t)i + f], l2 ? __ldcg(v.d + nb) : v.d[nb], q);  // another CTA's
+  }
+  v.q[i] = q;
+  return q;
 }
 
 // q = M d, partial d . q
 __global__ void __launch_bounds__(kSolveThreads) k_ext_spmv(ExtVec v) {
   const int n = v.counters[0];
   double dq = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double q = v.diag[i] * v.d[i];
-    for (int f = 0; f < 6; ++f) {
-      const int nb = v.nb[6 * (size_t)i + f];
-      if (nb >= 0) q -= v.beta[6 * (size_t)i + f] * v.d[nb];
-    }
-    v.q[i] = q;
-    dq += v.d[i] * q;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dq = fma(v.d[i], ext_spmv_elem(v, i, false), dq);
   block_partial(dq, v.part + 3 * kExtCTAs);
 }
 
 // alpha = r.z / d.q; x += alpha d; r -= alpha q; partial r.z (new) and r.r
-__global__ void __launch_bounds__(kSolveThreads) k_ext_update(ExtVec v, int cur) {
-  const double rz = sum_partials(v.part + (1 + cur) * kExtCTAs, kExtCTAs);
-  const double dq = sum_partials(v.part + 3 * kExtCTAs, kExtCTAs);
-  const double alpha = dq > 0.0 ? rz / dq : 0.0;
-  const int n = v.counters[0];
-  double rzn = 0.0, rr = 0.0;
+__device__ __forceinline__ void ext_update_elems(const ExtVec& v, int n, double alpha, double& rzn, double& rr) {
+  rzn = 0.0;
+  rr = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    v.x[i] += alpha * v.d[i];
-    const double r = v.r[i] - alpha * v.q[i];
+    v.x[i] = fma(alpha, v.d[i], v.x[i]);
+    const double r = fma(-alpha, v.q[i], v.r[i]);
     v.r[i] = r;
-    const double zi = v.diag[i] > 0.0 ? r / v.diag[i] : 0.0;
-    rzn += r * zi;
-    rr += r * r;
+    rzn = fma(r, r * v.rdiag[i], rzn);
+    rr = fma(r, r, rr);
   }
-  block_partial(rzn, v.part + (2 - cur) * kExtCTAs);
-  block_partial(rr, v.part + 4 * kExtCTAs);
+}
+__global__ void __launch_bounds__(kSolveThreads) k_ext_update(ExtVec v, int cur) {
+  const double* pp[2] = {v.part + (1 + cur) * kExtCTAs, v.part + 3 * kExtCTAs};
+  double s2[2];
+  sum_partials_k<2, false>(pp, kExtCTAs, s2);
+  const double alpha = s2[1] > 0.0 ? s2[0] / s2[1] : 0.0;
+  double rzn, rr;
+  ext_update_elems(v, v.counters[0], alpha, rzn, rr);
+  const double pv[2] = {rzn, rr};
+  double* const po[2] = {v.part + (2 - cur) * kExtCTAs, v.part + 4 * kExtCTAs};
+  block_partial_k<2>(pv, po);
 }
 
 // d = z + (r.z new / r.z old) d
-__global__ void __launch_bounds__(kSolveThreads) k_ext_dir(ExtVec v, int cur) {
-  const double rz = sum_partials(v.part + (1 + cur) * kExtCTAs, kExtCTAs);
-  const double rzn = sum_partials(v.part + (2 - cur) * kExtCTAs, kExtCTAs);
-  const double beta = rz > 0.0 ? rzn / rz : 0.0;
-  const int n = v.counters[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double zi = v.diag[i] > 0.0 ? v.r[i] / v.diag[i] : 0.0;
-    v.d[i] = zi + beta * v.d[i];
-  }
+__device__ __forceinline__ void ext_dir_elems(const ExtVec& v, int n, double beta) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v.d[i] = fma(beta, v.d[i], v.r[i] * v.rdiag[i]);
 }
-
-// sum_partials for values other CTAs of the same launch wrote: the loads
-// skip L1 (not coherent across SMs), reading L2
-__device__ __forceinline__ double sum_partials_l2(const double* part, int n) {
-  __shared__ double red[kSolveThreads];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
+__global__ void __launch_bounds__(kSolveThreads) k_ext_dir(ExtVec v, int cur) {
+  const double* pp[2] = {v.part + (1 + cur) * kExtCTAs, v.part + (2 - cur) * kExtCTAs};
+  double s2[2];
+  sum_partials_k<2, false>(pp, kExtCTAs, s2);
+  const double beta = s2[0] > 0.0 ? s2[1] / s2[0] : 0.0;
+  ext_dir_elems(v, v.counters[0], beta);
 }
 
 // Device state of the persistent solver (in the workspace; the assemble
@@ -401,67 +449,107 @@ __device__ __forceinline__ bool ext_grid_barrier(ExtCG* cg, int* status) {
   return ok_s != 0;
 }
 
-// The CG iterations in one launch: the phases of k_ext_spmv, k_ext_update
-// and k_ext_dir (the same element arithmetic, partial slots and grid), each
-// followed by a grid barrier; r.z carried from one phase to the next (the
-// values the kernels re-sum), the residual from the update's r.r partials.
-// A thread's own elements are read and written by it alone (the same
-// grid-stride mapping in every phase); the partials and the neighbours'
-// directions, written by other CTAs, are read from L2.
+// The CG iterations in one launch, two grid barriers per iteration: the
+// direction d_k = z_k + beta_k d_(k-1) (d_0 = z_0) is formed where the
+// matrix product needs it -- each thread its own elements, written to the
+// other of two buffers, and the neighbours' again from their r and previous
+// d, the same arithmetic, so the values are the owners' -- and the product,
+// its partial d . q, then (after a barrier) alpha, x += alpha d, r -=
+// alpha q and the partials r . z, r . r (then a barrier) follow; beta and
+// |r| are formed from those partials at the top of the next iteration.  The
+// same element arithmetic, partial slots and grid as k_ext_spmv,
+// k_ext_update and k_ext_dir, so both forms of the solver give the same
+// iterates.  The iteration's scalars are formed once per CTA by thread 0
+// and shared; partials written by other CTAs are read from L2.
 __global__ void __launch_bounds__(kSolveThreads)
 k_ext_cg(ExtVec v, ExtCG* cg, double tol, int max_iter, int* status) {
+  // [0] alpha, [1] beta, [2] r.z, [3] |r|, [4] target
+  __shared__ double scal[5];
   const int n = v.counters[0];
-  const double bb = sum_partials_l2(v.part, kExtCTAs);
-  const double target = tol * sqrt(bb);
-  double res = sqrt(bb);
-  double rz = sum_partials_l2(v.part + kExtCTAs, kExtCTAs);  // r.z, carried between phases
+  if (threadIdx.x < 32) {
+    const double* pp[2] = {v.part, v.part + kExtCTAs};
+    double s2[2];
+    warp0_sums<2, true>(pp, kExtCTAs, s2);
+    if (threadIdx.x == 0) {
+      scal[2] = s2[1];
+      scal[3] = sqrt(s2[0]);
+      scal[4] = tol * scal[3];
+    }
+  }
+  __syncthreads();
+  double rz = scal[2];  // r.z, carried between phases
+  double res = scal[3];
+  const double target = scal[4];
+  double* dcur = v.d;   // d_(k-1); d_0 itself in the first iteration
+  double* dnew = v.d2;  // d_k
   int cur = 0, it = 0;
   bool ok = true;
+  double beta = 0.0;
   while (res > target && it < max_iter) {  // the same values in every CTA
-    // q = M d, partial d . q
+    const bool first = it == 0;
+    // d_k and q = M d_k, partial d_k . q
     double dq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      double q = v.diag[i] * v.d[i];
+      const double di = first ? dcur[i] : fma(beta, dcur[i], v.r[i] * v.rdiag[i]);
+      dnew[i] = di;
+      double q = v.diag[i] * di;
+#pragma unroll
       for (int f = 0; f < 6; ++f) {
         const int nb = v.nb[6 * (size_t)i + f];
-        if (nb >= 0) q -= v.beta[6 * (size_t)i + f] * __ldcg(v.d + nb);  // another CTA's
+        if (nb >= 0) {
+          const double dn = first ? __ldcg(dcur + nb)
+                                  : fma(beta, __ldcg(dcur + nb), __ldcg(v.r + nb) * __ldcg(v.rdiag + nb));
+          q = fma(-v.beta[6 * (size_t)i + f], dn, q);
+        }
       }
       v.q[i] = q;
-      dq += v.d[i] * q;
+      dq = fma(di, q, dq);
     }
     block_partial(dq, v.part + 3 * kExtCTAs);
     if (!(ok = ext_grid_barrier(cg, status))) break;
     // alpha = r.z / d.q; x += alpha d; r -= alpha q; partial r.z and r.r
+    if (threadIdx.x < 32) {
+      const double* pp[1] = {v.part + 3 * kExtCTAs};
+      double dqs[1];
+      warp0_sums<1, true>(pp, kExtCTAs, dqs);
+      if (threadIdx.x == 0) scal[0] = dqs[0] > 0.0 ? rz / dqs[0] : 0.0;
+    }
+    __syncthreads();
     {
-      const double dqs = sum_partials_l2(v.part + 3 * kExtCTAs, kExtCTAs);
-      const double alpha = dqs > 0.0 ? rz / dqs : 0.0;
+      const double alpha = scal[0];
       double rzn = 0.0, rr = 0.0;
       for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        v.x[i] += alpha * v.d[i];
-        const double r = v.r[i] - alpha * v.q[i];
+        v.x[i] = fma(alpha, dnew[i], v.x[i]);
+        const double r = fma(-alpha, v.q[i], v.r[i]);
         v.r[i] = r;
-        const double zi = v.diag[i] > 0.0 ? r / v.diag[i] : 0.0;
-        rzn += r * zi;
-        rr += r * r;
+        rzn = fma(r, r * v.rdiag[i], rzn);
+        rr = fma(r, r, rr);
       }
-      block_partial(rzn, v.part + (2 - cur) * kExtCTAs);
-      block_partial(rr, v.part + 4 * kExtCTAs);
+      const double pv[2] = {rzn, rr};
+      double* const po[2] = {v.part + (2 - cur) * kExtCTAs, v.part + 4 * kExtCTAs};
+      block_partial_k<2>(pv, po);
     }
     if (!(ok = ext_grid_barrier(cg, status))) break;
-    // d = z + (r.z new / r.z old) d
-    {
-      const double rzn = sum_partials_l2(v.part + (2 - cur) * kExtCTAs, kExtCTAs);
-      const double beta = rz > 0.0 ? rzn / rz : 0.0;
-      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double zi = v.diag[i] > 0.0 ? v.r[i] / v.diag[i] : 0.0;
-        v.d[i] = zi + beta * v.d[i];
+    // beta = r.z new / r.z old, |r|
+    if (threadIdx.x < 32) {
+      const double* pp[2] = {v.part + (2 - cur) * kExtCTAs, v.part + 4 * kExtCTAs};
+      double s2[2];
+      warp0_sums<2, true>(pp, kExtCTAs, s2);
+      if (threadIdx.x == 0) {
+        scal[1] = rz > 0.0 ? s2[0] / rz : 0.0;
+        scal[2] = s2[0];
+        scal[3] = sqrt(s2[1]);
       }
-      rz = rzn;
     }
-    res = sqrt(sum_partials_l2(v.part + 4 * kExtCTAs, kExtCTAs));
+    __syncthreads();
+    beta = scal[1];
+    rz = scal[2];
+    res = scal[3];
+    double* t = dcur;  // the buffers take turns
+    dcur = dnew;
+    dnew = t;
     cur ^= 1;
     ++it;
-    if (!(ok = ext_grid_barrier(cg, status))) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     cg->iters = it;
@@ -516,7 +604,7 @@ k_ext_faces(GridDev g, double h, double dt, double rho_l, double rho_g, const do
 }
 
 struct ExtLayout {
-  size_t code, map, list, nb, beta, diag, x, r, d, q, part, counters, cg, total;
+  size_t code, map, list, nb, beta, diag, rdiag, x, r, d, d2, q, part, counters, cg, total;
 };
 
 ExtLayout ext_layout(size_t N) {
@@ -529,9 +617,11 @@ ExtLayout ext_layout(size_t N) {
   L.nb = o; o += a(N * 6 * 4);
   L.beta = o; o += a(N * 6 * 8);
   L.diag = o; o += a(N * 8);
+  L.rdiag = o; o += a(N * 8);
   L.x = o; o += a(N * 8);
   L.r = o; o += a(N * 8);
   L.d = o; o += a(N * 8);
+  L.d2 = o; o += a(N * 8);
   L.q = o; o += a(N * 8);
   L.part = o; o += a(5 * kExtCTAs * 8);
   L.counters = o; o += a(4 * 4);
@@ -558,9 +648,11 @@ cudaError_t launch_velocity_extension(const GridDev& g, double h, const double* 
   vec.nb = reinterpret_cast<int*>(ws + L.nb);
   vec.beta = reinterpret_cast<double*>(ws + L.beta);
   vec.diag = reinterpret_cast<double*>(ws + L.diag);
+  vec.rdiag = reinterpret_cast<double*>(ws + L.rdiag);
   vec.x = reinterpret_cast<double*>(ws + L.x);
   vec.r = reinterpret_cast<double*>(ws + L.r);
   vec.d = reinterpret_cast<double*>(ws + L.d);
+  vec.d2 = reinterpret_cast<double*>(ws + L.d2);
   vec.q = reinterpret_cast<double*>(ws + L.q);
   vec.part = reinterpret_cast<double*>(ws + L.part);
   vec.counters = reinterpret_cast<int*>(ws + L.counters);

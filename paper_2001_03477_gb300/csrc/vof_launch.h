@@ -121,12 +121,16 @@ struct SweepScratch {
   double* G;
 };
 
+// kernel U walks the kernel-A lists in groups of this many consecutive
+// lists, each group as one sequence of cells
+constexpr int kUpdLists = 8;
+
 struct SweepPlan {
   dim3 gridA, blockA;
   int cap;          // list capacity per warp of kernel A
   long long nsub;   // number of lists (warps of kernel A)
   unsigned gridB;   // CTAs of kernel U (lpc lists each)
-  int lpc;          // kernel-A lists per CTA of kernel U (groups of 8)
+  int lpc;          // kernel-A lists per CTA of kernel U (groups of kUpdLists)
 };
 
 SweepPlan sweep_plan(int axis, const GridDev& g);

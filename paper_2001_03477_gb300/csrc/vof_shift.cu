@@ -167,70 +167,92 @@ k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restr
   k_shift_stream_body(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, sums, copy, vb_self());
 }
 
+// One moving mixed cell: plane (MYC normal + plane constant), shift
+// |m|_2 dd, its own shifted volume, and the claims on the receivers it
+// reaches.  LANES = 3: the three lanes leader .. leader + 2 (mask gmask) of
+// one cell share its bisection (edge cells); every lane computes the same
+// values, and the stores and the claims' atomic ORs repeat them harmlessly.
+template <int LANES>
+__device__ __forceinline__ void shift_plane_cell(const GridDev& g, const double* __restrict__ c_in,
+                                                 const double* __restrict__ dd, double dd_uniform,
+                                                 const ShiftScratch& sc, size_t id, unsigned gmask, int leader,
+                                                 int sub) {
+  int x, y, z;
+  decode(g, id, x, y, z);
+  double st[27];
+#pragma unroll
+  for (int oz = 0; oz < 3; ++oz) {
+    const int zz = map_idx(z + oz - 1, g.n[2], g.bc[2]);
+#pragma unroll
+    for (int oy = 0; oy < 3; ++oy) {
+      const int yy = map_idx(y + oy - 1, g.n[1], g.bc[1]);
+#pragma unroll
+      for (int ox = 0; ox < 3; ++ox) {
+        const int xx = map_idx(x + ox - 1, g.n[0], g.bc[0]);
+        st[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_id(g, xx, yy, zz));
+      }
+    }
+  }
+  const double ct = st[13];
+  double m[3];
+  myc_normal(st, m);
+  double al;
+  if (LANES == 3) al = plane_alpha_bisect_t<3>(m[0], m[1], m[2], ct, gmask, leader, sub);
+  else al = edge_cell(ct) ? plane_alpha_bisect(m[0], m[1], m[2], ct) : plane_alpha(m[0], m[1], m[2], ct);
+  const double ddv = dd ? __ldg(dd + id) : dd_uniform;
+  const double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  const double sft = mn2 * ddv;
+  double4 pl;
+  pl.x = m[0]; pl.y = m[1]; pl.z = m[2]; pl.w = al;
+  reinterpret_cast<double4*>(sc.plane)[id] = pl;
+  sc.shift[id] = sft;
+  // own shift, capped to the cell
+  double lo = 0.0, hi = 0.0;
+  if (m[0] < 0.0) lo += m[0]; else hi += m[0];
+  if (m[1] < 0.0) lo += m[1]; else hi += m[1];
+  if (m[2] < 0.0) lo += m[2]; else hi += m[2];
+  double ast = al + sft;
+  if (ast < lo) ast = lo;
+  if (ast > hi) ast = hi;
+  sc.cnew[id] = volume_nn(m[0], m[1], m[2], ast);  // applied by the sums kernel
+  // claim the receivers this shift reaches: bit 31 - b of a pure
+  // neighbour's claim word, b = this cell's offset index seen from it
+  // (scan order); the first reaching neighbour in the scan order -- the
+  // one that settles the receiver -- holds the highest set bit whatever
+  // the order of the atomics
+  const bool full = dlt0(ddv);  // the kind of pure cell this shift reaches
+  for (int oz = -1; oz <= 1; ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int ox = -1; ox <= 1; ++ox) {
+        if (!ox && !oy && !oz) continue;
+        size_t pid;
+        if (!neighbour(g, x, y, z, ox, oy, oz, pid)) continue;
+        const double cp = __ldg(c_in + pid);
+        if (is_mixed_b(cp, g) || is_full_b(cp, g) != full) continue;
+        atomicOr(sc.claim + pid, 0x80000000u >> offset_bit(-ox, -oy, -oz));
+      }
+}
+
+// The list's front (cells whose plane constant is inverted directly): one
+// per thread.  Its back (edge cells, whose constant takes the bisection): ten
+// per warp, three lanes each, the warps' chunks taken from the grid's last
+// warp down -- warps the front leaves idle, on SMs of their own -- so the
+// bisections' long FP64 chains run side by side.
 __device__ __forceinline__ void k_shift_planes_body(const GridDev& g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform, const ShiftScratch& sc, const VB vb) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int nn = sc.counters[0], ne = sc.counters[1];
   const int lane = threadIdx.x & 31;
-  const int total = nn + ne;
   const int stride = vb.gx * blockDim.x;
-  for (int i0 = vb.bx * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
-    const int i = i0 + lane;
-    const bool v = i < total;
-    int x = 0, y = 0, z = 0;
-    if (v) {
-      const size_t id = i < nn ? sc.gmix[i] : sc.gmix[N - 1 - (size_t)(i - nn)];
-      decode(g, id, x, y, z);
-      double st[27];
-#pragma unroll
-      for (int oz = 0; oz < 3; ++oz) {
-        const int zz = map_idx(z + oz - 1, g.n[2], g.bc[2]);
-#pragma unroll
-        for (int oy = 0; oy < 3; ++oy) {
-          const int yy = map_idx(y + oy - 1, g.n[1], g.bc[1]);
-#pragma unroll
-          for (int ox = 0; ox < 3; ++ox) {
-            const int xx = map_idx(x + ox - 1, g.n[0], g.bc[0]);
-            st[(oz * 3 + oy) * 3 + ox] = __ldg(c_in + cell_id(g, xx, yy, zz));
-          }
-        }
-      }
-      const double ct = st[13];
-      double m[3];
-      myc_normal(st, m);
-      const double al = edge_cell(ct) ? plane_alpha_bisect(m[0], m[1], m[2], ct) : plane_alpha(m[0], m[1], m[2], ct);
-      const double ddv = dd ? __ldg(dd + id) : dd_uniform;
-      const double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-      const double sft = mn2 * ddv;
-      double4 pl;
-      pl.x = m[0]; pl.y = m[1]; pl.z = m[2]; pl.w = al;
-      reinterpret_cast<double4*>(sc.plane)[id] = pl;
-      sc.shift[id] = sft;
-      // own shift, capped to the cell
-      double lo = 0.0, hi = 0.0;
-      if (m[0] < 0.0) lo += m[0]; else hi += m[0];
-      if (m[1] < 0.0) lo += m[1]; else hi += m[1];
-      if (m[2] < 0.0) lo += m[2]; else hi += m[2];
-      double ast = al + sft;
-      if (ast < lo) ast = lo;
-      if (ast > hi) ast = hi;
-      sc.cnew[id] = volume_nn(m[0], m[1], m[2], ast);  // applied by the sums kernel
-      // claim the receivers this shift reaches: bit 31 - b of a pure
-      // neighbour's claim word, b = this cell's offset index seen from it
-      // (scan order); the first reaching neighbour in the scan order -- the
-      // one that settles the receiver -- holds the highest set bit whatever
-      // the order of the atomics
-      const bool full = dlt0(ddv);  // the kind of pure cell this shift reaches
-      for (int oz = -1; oz <= 1; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-          for (int ox = -1; ox <= 1; ++ox) {
-            if (!ox && !oy && !oz) continue;
-            size_t pid;
-            if (!neighbour(g, x, y, z, ox, oy, oz, pid)) continue;
-            const double cp = __ldg(c_in + pid);
-            if (is_mixed_b(cp, g) || is_full_b(cp, g) != full) continue;
-            atomicOr(sc.claim + pid, 0x80000000u >> offset_bit(-ox, -oy, -oz));
-          }
-    }
+  for (int i = vb.bx * blockDim.x + threadIdx.x; i < nn; i += stride)
+    shift_plane_cell<1>(g, c_in, dd, dd_uniform, sc, sc.gmix[i], 0u, 0, 0);
+  const int nw = (int)(vb.gx * (blockDim.x >> 5)), gw = (int)((vb.bx * blockDim.x + threadIdx.x) >> 5);
+  const int nchunk = (ne + 9) / 10;
+  for (int wc = nw - 1 - gw; wc < nchunk; wc += nw) {
+    const int j = wc * 10 + lane / 3;
+    if (lane >= 30 || j >= ne) continue;
+    const int leader = (lane / 3) * 3;
+    shift_plane_cell<3>(g, c_in, dd, dd_uniform, sc, sc.gmix[N - 1 - (size_t)j], 7u << leader, leader,
+                        lane - leader);
   }
 }
 

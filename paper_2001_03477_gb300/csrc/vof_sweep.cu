@@ -681,7 +681,7 @@ k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e
 }
 
 // ---------------------------------------------------------------------------
-// Kernel U: each CTA takes `ngrp` groups of 8 consecutive kernel-A lists,
+// Kernel U: each CTA takes `ngrp` groups of kUpdLists consecutive kernel-A lists,
 // dealt in turn (a fixed assignment and order, so the sums are
 // reproducible), one listed cell per thread:
 // the WY update from the two face fluxes.  It reads no cell but its own, so
@@ -695,31 +695,38 @@ __device__ __forceinline__ void update_groups(const GridDev& g, const double* c_
                                               double* e_out, const double* __restrict__ uf,
                                               uint8_t* __restrict__ state, double* __restrict__ theta,
                                               const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb,
-                                              int (&pre)[9], double (&v)[kNSums]) {
+                                              int (&pre)[kUpdLists + 1], double (&v)[kNSums]) {
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
   for (int grp = 0; grp < ngrp; ++grp) {
-    // the group's 8 lists sub0 .. sub0+7 as one sequence (fixed order):
-    // short lists then still fill whole warps.  Groups are dealt to the
-    // CTAs in turn (CTA b takes groups b, b + gx, ...): the lists of one
-    // region of the grid spread over all CTAs, whatever the interface's
-    // position
-    const int sub0 = (grp * (int)vb.gx + (int)vb.bx) * 8;
+    // the group's lists sub0 .. sub0 + kUpdLists - 1 as one sequence
+    // (fixed order): short lists then still fill whole warps.  Groups are
+    // dealt to the CTAs in turn (CTA b takes groups b, b + gx, ...): the
+    // lists of one region of the grid spread over all CTAs, whatever the
+    // interface's position
+    const int sub0 = (grp * (int)vb.gx + (int)vb.bx) * kUpdLists;
     if (sub0 >= nsub) break;  // uniform over the CTA
-    if (threadIdx.x == 0) {
-      int t = 0;
-      for (int w = 0; w < 8; ++w) {
-        pre[w] = t;
-        t += (sub0 + w < nsub) ? sc.count[sub0 + w] : 0;
+    if (threadIdx.x < 32) {
+      // the lists' starts: an inclusive scan of their counts over warp 0
+      static_assert(kUpdLists <= 32 && (kUpdLists & (kUpdLists - 1)) == 0, "one count per lane of warp 0");
+      const int l = threadIdx.x;
+      int incl = (l < kUpdLists && sub0 + l < nsub) ? sc.count[sub0 + l] : 0;
+#pragma unroll
+      for (int o = 1; o < kUpdLists; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += t;
       }
-      pre[8] = t;
+      if (l < kUpdLists) pre[l + 1] = incl;
+      if (l == 0) pre[0] = 0;
     }
     __syncthreads();
-    const int total = pre[8];
+    const int total = pre[kUpdLists];
     for (int j = threadIdx.x; j < total; j += blockDim.x) {
+      // the list of entry j: the last w with pre[w] <= j (pre[0] = 0)
       int w = 0;
 #pragma unroll
-      for (int q = 1; q < 8; ++q) w += (j >= pre[q]) ? 1 : 0;
+      for (int step = kUpdLists / 2; step > 0; step >>= 1)
+        if (pre[w + step] <= j) w += step;
       const size_t id = sc.list[(size_t)(sub0 + w) * cap + (j - pre[w])] & ~kMixedAdj;
       int x, y, z;
       cell_xyz(g, id, x, y, z);
@@ -746,7 +753,7 @@ __device__ __forceinline__ void update_groups(const GridDev& g, const double* c_
 
 template <int AX, bool ENERGY>
 __device__ __forceinline__ void k_update_body(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out, const double* __restrict__ uf, uint8_t* __restrict__ state, double* __restrict__ theta, const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb) {
-  __shared__ int pre[9];
+  __shared__ int pre[kUpdLists + 1];
   double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (g.le)  // uniform: one loop or the other, never both forms' arithmetic
     update_groups<AX, ENERGY, true>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre, v);
@@ -891,16 +898,16 @@ SweepPlan sweep_plan(int axis, const GridDev& g) {
     p.cap = (g.n[0] < 32 ? g.n[0] : 32) * (g.n[axis] < kSegA ? g.n[axis] : kSegA);
     p.nsub = (long long)p.gridA.x * p.gridA.y * p.gridA.z * kWarpsA;
   }
-  // kernel U: groups of 8 consecutive lists, dealt to the CTAs in turn;
-  // about one CTA per 4096 cells, at most one wave (4 per SM): each CTA's
-  // FP64 sum tree then serves many listed cells
+  // kernel U: groups of kUpdLists consecutive lists, dealt to the CTAs in
+  // turn; about one CTA per 4096 cells, at most one wave (4 per SM): each
+  // CTA's FP64 sum tree then serves many listed cells
   const long long cells = (long long)g.n[0] * g.n[1] * g.n[2];
-  const long long groups = (p.nsub + 7) / 8;
+  const long long groups = (p.nsub + kUpdLists - 1) / kUpdLists;
   long long target = (cells + 4095) / 4096;
   if (target > 152 * 4) target = 152 * 4;
   if (target < 1) target = 1;
   const long long ngrp = (groups + target - 1) / target;
-  p.lpc = (int)(8 * ngrp);
+  p.lpc = (int)(kUpdLists * ngrp);
   p.gridB = (unsigned)((groups + ngrp - 1) / ngrp);
   return p;
 }
@@ -994,7 +1001,7 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
   k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
   k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,
-                                                 p.cap, p.lpc / 8);
+                                                 p.cap, p.lpc / kUpdLists);
   prof_mark(AX == 0 ? "sweep_x.update" : (AX == 1 ? "sweep_y.update" : "sweep_z.update"), st);
 }
 

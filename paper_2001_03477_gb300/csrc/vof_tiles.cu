@@ -117,6 +117,21 @@ __device__ __noinline__ double2 tile_cell_sums(int nx, int ny, int nz, const dou
   return make_double2(sc, se);
 }
 
+// n x v for the bit pattern v (the same for every lane of the warp): a
+// whole tile (n = 512 = 2^9) by adding 9 to the exponent when the product is
+// a normal number, and +-0 as itself -- both exact, as the FP64 product is,
+// and without an FP64 instruction; otherwise the FP64 product, in a call
+// under a warp vote so that the common case issues no predicated multiply
+__device__ __noinline__ double times_cells_mul(int n, long long v) { return (double)n * __longlong_as_double(v); }
+__device__ __forceinline__ double times_cells(int n, long long v) {
+  const int ex = (int)((v >> 52) & 0x7FF);
+  const bool shift = n == kTile * kTile * kTile && ex >= 1 && ex <= 0x7FE - 9;
+  const bool zero = ((unsigned long long)v << 1) == 0ull;
+  double r = __longlong_as_double(shift ? v + (9LL << 52) : v);
+  if (__any_sync(kFullT, !shift && !zero)) r = times_cells_mul(n, v);
+  return r;
+}
+
 // One warp per tile: quiet flag (lanes 0..26 check the tile and its 26
 // neighbours at once) and the tile's sum row -- a uniform tile's is
 // (cells) x value, another's the sum of its cells.  Rows are placed at
@@ -127,7 +142,9 @@ __device__ __forceinline__ void k_quiet_body(const GridDev& g, const double* __r
   const int lane = threadIdx.x & 31;
   const long long wpb = blockDim.x >> 5;
   const int rstride = 4 * ((ntx + 3) / 4);
-  for (long long t = vb.bx * wpb + (threadIdx.x >> 5); t < nt; t += (long long)vb.gx * wpb) {
+  // tile t goes to CTA t mod gx: neighbouring tiles (the interface's, whose
+  // sums take FP64 adds) spread over the SMs
+  for (long long t = vb.bx + (long long)vb.gx * (threadIdx.x >> 5); t < nt; t += (long long)vb.gx * wpb) {
     const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
     // lane o < 27: the tile at offset (o % 3 - 1, o / 3 % 3 - 1, o / 9 - 1);
     // one beyond a zero-gradient boundary counts as equal
@@ -155,9 +172,9 @@ __device__ __forceinline__ void k_quiet_body(const GridDev& g, const double* __r
     if (uni) {
       const int cx = min(kTile, g.n[0] - tx * kTile), cy = min(kTile, g.n[1] - ty * kTile),
                 cz = min(kTile, g.n[2] - tz * kTile);
-      const double n = (double)(cx * cy * cz);
-      sc = n * __longlong_as_double(cr);
-      se = n * __longlong_as_double(er);
+      const int n = cx * cy * cz;
+      sc = times_cells(n, cr);
+      se = times_cells(n, er);
     } else {
       const double2 s2 = tile_cell_sums(g.n[0], g.n[1], g.n[2], c, e, tx * kTile, ty * kTile, tz * kTile);
       sc = s2.x;
