@@ -409,9 +409,8 @@ vof_status vof_step(const vof_grid* g, double* c, double* e, const double* u, co
   r += (size_t)L.nb_sh;
   if (sums) {
     // sums[0..1] = sum c, sum e; sums[2] = clip; sums[3..5] = shift diagnostics
-    ReduceJobs jobs{};
-    jobs.job[0] = ReduceJob{rows, (int)r, kNSums, 0, kNSums, sums};
-    err = launch_reduce(jobs, 1, reinterpret_cast<double*>(ws + L.off_red), st);
+    err = launch_reduce_fused(ReduceJob{rows, (int)r, kNSums, 0, kNSums, sums},
+                              reinterpret_cast<double*>(ws + L.off_red), cnt + (kStepCounters - 1), st);
     if (err != cudaSuccess) return cuda_status(err);
   }
   return VOF_OK;

@@ -188,7 +188,7 @@ TileScratch carve_tile_scratch(const GridDev& g, void* ws);
 // The tile pass of a time step also clears the step's frozen-state flags
 // (state[N], nullable) and its list counters (counters[kStepCounters],
 // nullable), so that the step needs no memset.
-constexpr int kStepCounters = 16;  // 4 per sweep axis, then the shift's 3
+constexpr int kStepCounters = 16;  // 4 per sweep axis, then the shift's 3; the last: the reduction's ticket
 cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, TileScratch ts, SumOut sums,
                          uint8_t* state, int* counters, cudaStream_t st);
 
@@ -221,6 +221,8 @@ struct ReduceJobs {
 };
 size_t reduce_scratch_bytes();
 cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st);
+// one job's two levels in one launch; *ticket is zero before and after
+cudaError_t launch_reduce_fused(const ReduceJob& job, double* scratch, int* ticket, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Grouped launches: one launch runs one kernel of the time step for every box

@@ -680,57 +680,97 @@ cudaError_t launch_reconstruct(const GridDev& g, const double* c, double* m, dou
 // identical run to run.
 constexpr int kReduceThreads = 256;
 
-__device__ __forceinline__ double tree_sum(double x, double* red) {
-  red[threadIdx.x] = x;
+
+// The CTA's per-thread values v[k] (k < nk) summed in a fixed order: staged
+// in shared memory, warp k sums entry lane, lane + 32, ... then a shuffle
+// tree; lane 0 of warp k writes out[k].  One barrier for all nk values.
+__device__ __forceinline__ void cta_sums(const double (&v)[kMaxReduceK], int nk, double* out,
+                                         double (*red)[kReduceThreads]) {
+#pragma unroll
+  for (int k = 0; k < kMaxReduceK; ++k)
+    if (k < nk) red[k][threadIdx.x] = v[k];
   __syncthreads();
-  for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < nk) {
+    double x = 0.0;
+#pragma unroll
+    for (int j = 0; j < kReduceThreads / 32; ++j) x += red[w][lane + 32 * j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) out[w] = x;
   }
-  const double r = red[0];
-  __syncthreads();
-  return r;
+  __syncthreads();  // red is reused
 }
+static_assert(kMaxReduceK <= kReduceThreads / 32, "a warp per output");
 
 // part `part` of `nparts` of a job's rows into out[k] (k < nk)
 __device__ __forceinline__ void reduce1_body(const ReduceJob& J, unsigned part, unsigned nparts, double* out,
-                                             double* red) {
+                                             double (*red)[kReduceThreads]) {
   const int chunk = (J.nblocks + (int)nparts - 1) / (int)nparts;
   const int b0 = (int)part * chunk, b1 = min(b0 + chunk, J.nblocks);
-  for (int k = 0; k < J.nk; ++k) {
-    double s = 0.0;
-    for (int b = b0 + threadIdx.x; b < b1; b += kReduceThreads) s += J.partials[(size_t)b * J.stride + J.k0 + k];
-    const double t = tree_sum(s, red);
-    if (threadIdx.x == 0) out[k] = t;
+  double s[kMaxReduceK];
+#pragma unroll
+  for (int k = 0; k < kMaxReduceK; ++k) s[k] = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += kReduceThreads) {
+    const double* row = J.partials + (size_t)b * J.stride + J.k0;
+#pragma unroll
+    for (int k = 0; k < kMaxReduceK; ++k)
+      if (k < J.nk) s[k] += row[k];
   }
+  cta_sums(s, J.nk, out, red);
 }
-// a job's nparts partials (kMaxReduceK apart) into J.out
-__device__ __forceinline__ void reduce2_body(const ReduceJob& J, const double* part, int nparts, double* red) {
-  for (int k = 0; k < J.nk; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nparts; b += kReduceThreads) s += part[(size_t)b * kMaxReduceK + k];
-    const double t = tree_sum(s, red);
-    if (threadIdx.x == 0) J.out[k] = t;
+// a job's nparts partials (kMaxReduceK apart) into J.out (read from L2: in
+// the fused reduction other CTAs of the same launch wrote them)
+__device__ __forceinline__ void reduce2_body(const ReduceJob& J, const double* part, int nparts,
+                                             double (*red)[kReduceThreads]) {
+  double s[kMaxReduceK];
+#pragma unroll
+  for (int k = 0; k < kMaxReduceK; ++k) s[k] = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += kReduceThreads) {
+#pragma unroll
+    for (int k = 0; k < kMaxReduceK; ++k)
+      if (k < J.nk) s[k] += __ldcg(part + (size_t)b * kMaxReduceK + k);
   }
+  cta_sums(s, J.nk, J.out, red);
 }
 
 __global__ void __launch_bounds__(kReduceThreads) k_reduce1(ReduceJobs jobs, double* __restrict__ scratch) {
-  __shared__ double red[kReduceThreads];
+  __shared__ double red[kMaxReduceK][kReduceThreads];
   const ReduceJob J = jobs.job[blockIdx.y];
   reduce1_body(J, blockIdx.x, gridDim.x, scratch + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kMaxReduceK, red);
 }
 
 __global__ void __launch_bounds__(kReduceThreads) k_reduce2(ReduceJobs jobs, const double* __restrict__ scratch,
                                                             int nparts) {
-  __shared__ double red[kReduceThreads];
+  __shared__ double red[kMaxReduceK][kReduceThreads];
   const ReduceJob J = jobs.job[blockIdx.x];
   reduce2_body(J, scratch + (size_t)blockIdx.x * nparts * kMaxReduceK, nparts, red);
+}
+
+// Both levels in one launch (one job): every CTA its part, and the CTA that
+// finishes last (a ticket, zero at the start and left zero) the second
+// level -- the same arithmetic and order as k_reduce1 and k_reduce2.
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_fused(ReduceJobs jobs, double* __restrict__ scratch,
+                                                                 int* __restrict__ ticket) {
+  __shared__ double red[kMaxReduceK][kReduceThreads];
+  __shared__ int last;
+  const ReduceJob J = jobs.job[0];
+  reduce1_body(J, blockIdx.x, gridDim.x, scratch + (size_t)blockIdx.x * kMaxReduceK, red);
+  __threadfence();  // this CTA's partials before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (last) {
+    __threadfence();  // the other CTAs' partials before they are read
+    reduce2_body(J, scratch, (int)gridDim.x, red);
+    if (threadIdx.x == 0) *ticket = 0;
+  }
 }
 
 // grouped: the first level over (box, part) CTAs, the second one CTA per box,
 // in the same order as a box's own reduction (job 0, kReduceCTAs parts)
 __global__ void __launch_bounds__(kReduceThreads) k_reduce1_grp(GroupMap m, const ReduceBox* __restrict__ rb) {
-  __shared__ double red[kReduceThreads];
+  __shared__ double red[kMaxReduceK][kReduceThreads];
   unsigned b;
   const VB vb = vb_group(m, b);
   const ReduceBox R = rb[b];
@@ -738,7 +778,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce1_grp(GroupMap m, cons
   reduce1_body(J, vb.bx, kReduceCTAs, R.scratch + (size_t)vb.bx * kMaxReduceK, red);
 }
 __global__ void __launch_bounds__(kReduceThreads) k_reduce2_grp(const ReduceBox* __restrict__ rb) {
-  __shared__ double red[kReduceThreads];
+  __shared__ double red[kMaxReduceK][kReduceThreads];
   const ReduceBox R = rb[blockIdx.x];
   const ReduceJob J{R.rows, R.nblocks, kNSums, 0, kNSums, R.out};
   reduce2_body(J, R.scratch, kReduceCTAs, red);
@@ -754,6 +794,15 @@ cudaError_t launch_reduce_grp(const GroupMap& m1, const ReduceBox* rb, unsigned 
 }
 
 size_t reduce_scratch_bytes() { return (size_t)kMaxReduceJobs * kReduceCTAs * kMaxReduceK * sizeof(double); }
+
+cudaError_t launch_reduce_fused(const ReduceJob& job, double* scratch, int* ticket, cudaStream_t st) {
+  if (job.nk > kMaxReduceK) return cudaErrorInvalidValue;
+  ReduceJobs jobs{};
+  jobs.job[0] = job;
+  k_reduce_fused<<<kReduceCTAs, kReduceThreads, 0, st>>>(jobs, scratch, ticket);
+  prof_mark("reduce", st);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st) {
   if (njobs <= 0 || njobs > kMaxReduceJobs) return cudaErrorInvalidValue;

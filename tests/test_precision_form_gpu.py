@@ -116,14 +116,16 @@ def test_step_close_to_fp64(P, name, shift):
         nflip = np.count_nonzero(flipped)
         if not shift:
             # only ties of the MYC candidates (TIES) send a decision the
-            # other way; with a shift, every cell that the sweeps leave
-            # within FP32 round-off of 0 or 1 is classified by round-off
-            # (module docstring), a number that depends on the workload
-            # (measured 3-9 % of the interface cells), so only the size of
-            # each difference and the invariants are held there
+            # other way
             assert nflip <= 2 + 0.05 * interface
             if name not in TIES:
                 assert nflip == 0
+        else:
+            # with a shift, every cell that the sweeps leave within FP32
+            # round-off of 0 or 1 is classified by round-off (module
+            # docstring), a number that depends on the workload (measured
+            # 3-9 % of the interface cells)
+            assert nflip <= 2 + 0.12 * interface
         assert err.max() <= 2 * amax + 2 * abs(dd) + C_TOL_STEP
         assert np.abs(eg - eo)[~flipped].max() <= C_TOL_STEP * energy_scale(g, ci, ei)
         # the step's sums are the sums of its result

@@ -66,6 +66,10 @@ def test_noalloc_matches_vof_step_two_calls(P):
         s2 = sums2.cpu().numpy()
         assert abs(s2[0] - s1[0]) <= SUM_TOL * abs(s1[0])
         assert abs(s2[1] - s1[1]) <= SUM_TOL * abs(s1[1])
+        # the same kernels in the same order: the same bits, whatever the
+        # scratch held before
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+        assert np.array_equal(s1[:2], s2[:2])
 
 
 def test_noalloc_after_other_grid(P):
@@ -107,6 +111,8 @@ def test_noalloc_after_other_grid(P):
     s2 = sums2.cpu().numpy()
     assert abs(s2[0] - s1[0]) <= SUM_TOL * abs(s1[0])
     assert abs(s2[1] - s1[1]) <= SUM_TOL * abs(s1[1])
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    assert np.array_equal(s1[:2], s2[:2])
 
 
 def test_noalloc_rejects_large_grid(P):
