@@ -349,6 +349,8 @@ __device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double
   uint32_t* mlist = sc.mlist + sub * (size_t)cap;
   uint32_t* rlist = sc.rlist + sub * (size_t)cap;
   const unsigned lt = (1u << lane) - 1u;
+  // quiet tiles of the segment (bit l: its l-th tile)
+  unsigned qmask = 0u;
   if (sc.tiles.quiet && !force_all) {
     // in place: a warp whose row segment lies in quiet tiles has no work
     // (lane l checks the l-th tile of the segment)
@@ -362,6 +364,7 @@ __device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double
       if (lane == 0) sc.count[sub] = 0;
       return;
     }
+    qmask = __ballot_sync(kFull, q);
   }
   int nlist = 0, nmixed = 0, nrun = 0, nlist_m = 0, nrun_m = 0;
   auto ldc = [&](int X) { return __ldg(c_in + rbase + map_idx(X, nx, bcx)); };
@@ -389,6 +392,20 @@ __device__ __forceinline__ void k_stream_row_body(const GridDev& g, const double
   for (; base < x1; base += 32) {
     const double cNN = ldc(base + 64 + lane), eNN = lde(base + 64 + lane);
     const uint8_t stN = lds_(base + 32 + lane);
+    if (((qmask >> ((base - x0) >> 3)) & 0xFu) == 0xFu) {
+      // a chunk of quiet tiles: no-op cells only, none listed or mixed (the
+      // previous chunk's run ends were found looking into this one); the
+      // pipeline moves on
+      const double c31 = __shfl_sync(kFull, cN, 31), e31 = __shfl_sync(kFull, eN, 31);
+      const unsigned eqNN = eqmask(c31, e31, cNN, eNN);
+      mixed_carry = false;
+      cP = cC; eP = eC;
+      cC = cN; eC = eN;
+      cN = cNN; eN = eNN;
+      eqP = eqC; eqC = eqN; eqN = eqNN;
+      stC = stN;
+      continue;
+    }
     const int X = base + lane;
     const bool cell_ok = X < x1;
     const uint8_t stv = cell_ok ? stC : (uint8_t)0;
