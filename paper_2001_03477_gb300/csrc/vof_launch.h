@@ -124,6 +124,7 @@ struct SweepScratch {
 // kernel U walks the kernel-A lists in groups of this many consecutive
 // lists, each group as one sequence of cells
 constexpr int kUpdLists = 8;
+constexpr int kUpdBatch = 4;  // groups a CTA of kernel U walks per scan
 
 struct SweepPlan {
   dim3 gridA, blockA;

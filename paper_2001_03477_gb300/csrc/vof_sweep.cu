@@ -712,39 +712,42 @@ __device__ __forceinline__ void update_groups(const GridDev& g, const double* c_
                                               double* e_out, const double* __restrict__ uf,
                                               uint8_t* __restrict__ state, double* __restrict__ theta,
                                               const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb,
-                                              int (&pre)[kUpdLists + 1], double (&v)[kNSums]) {
+                                              int (&pre)[33], int (&lst)[32], double (&v)[kNSums]) {
   const int n_ax = g.n[AX];
   const int bca = g.bc[AX];
-  for (int grp = 0; grp < ngrp; ++grp) {
-    // the group's lists sub0 .. sub0 + kUpdLists - 1 as one sequence
-    // (fixed order): short lists then still fill whole warps.  Groups are
-    // dealt to the CTAs in turn (CTA b takes groups b, b + gx, ...): the
-    // lists of one region of the grid spread over all CTAs, whatever the
-    // interface's position
-    const int sub0 = (grp * (int)vb.gx + (int)vb.bx) * kUpdLists;
-    if (sub0 >= nsub) break;  // uniform over the CTA
+  static_assert(kUpdLists * kUpdBatch == 32, "one list per lane of warp 0");
+  for (int grp = 0; grp < ngrp; grp += kUpdBatch) {
+    // Groups of kUpdLists consecutive lists are dealt to the CTAs in turn
+    // (CTA b takes groups b, b + gx, ...), so the lists of one region of the
+    // grid spread over all CTAs whatever the interface's position; the CTA
+    // walks kUpdBatch of its groups at a time, their lists in order as one
+    // sequence of cells (fixed order): short lists still fill whole warps,
+    // and one scan and one barrier serve the batch.
+    if ((grp * (int)vb.gx + (int)vb.bx) * kUpdLists >= nsub) break;  // uniform over the CTA
     if (threadIdx.x < 32) {
       // the lists' starts: an inclusive scan of their counts over warp 0
-      static_assert(kUpdLists <= 32 && (kUpdLists & (kUpdLists - 1)) == 0, "one count per lane of warp 0");
       const int l = threadIdx.x;
-      int incl = (l < kUpdLists && sub0 + l < nsub) ? sc.count[sub0 + l] : 0;
+      const int gi = grp + l / kUpdLists;
+      const int sub = (gi * (int)vb.gx + (int)vb.bx) * kUpdLists + (l % kUpdLists);
+      int incl = (gi < ngrp && sub < nsub) ? sc.count[sub] : 0;
 #pragma unroll
-      for (int o = 1; o < kUpdLists; o <<= 1) {
+      for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, o);
         if (l >= o) incl += t;
       }
-      if (l < kUpdLists) pre[l + 1] = incl;
+      pre[l + 1] = incl;
+      lst[l] = sub;
       if (l == 0) pre[0] = 0;
     }
     __syncthreads();
-    const int total = pre[kUpdLists];
+    const int total = pre[32];
     for (int j = threadIdx.x; j < total; j += blockDim.x) {
       // the list of entry j: the last w with pre[w] <= j (pre[0] = 0)
       int w = 0;
 #pragma unroll
-      for (int step = kUpdLists / 2; step > 0; step >>= 1)
+      for (int step = 16; step > 0; step >>= 1)
         if (pre[w + step] <= j) w += step;
-      const size_t id = sc.list[(size_t)(sub0 + w) * cap + (j - pre[w])] & ~kMixedAdj;
+      const size_t id = sc.list[(size_t)lst[w] * cap + (j - pre[w])] & ~kMixedAdj;
       int x, y, z;
       cell_xyz(g, id, x, y, z);
       const int k = AX == 0 ? x : (AX == 1 ? y : z);
@@ -764,18 +767,21 @@ __device__ __forceinline__ void update_groups(const GridDev& g, const double* c_
       v[kSumC] += dc;
       v[kSumE] += de;
     }
-    __syncthreads();  // pre[] is rewritten by the next group
+    __syncthreads();  // pre[] and lst[] are rewritten by the next batch
   }
 }
 
 template <int AX, bool ENERGY>
 __device__ __forceinline__ void k_update_body(const GridDev& g, const double* c_in, const double* e_in, double* c_out, double* e_out, const double* __restrict__ uf, uint8_t* __restrict__ state, double* __restrict__ theta, const SweepScratch& sc, int nsub, int cap, int ngrp, const VB vb) {
-  __shared__ int pre[kUpdLists + 1];
+  __shared__ int pre[33];
+  __shared__ int lst[32];
   double v[kNSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (g.le)  // uniform: one loop or the other, never both forms' arithmetic
-    update_groups<AX, ENERGY, true>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre, v);
+    update_groups<AX, ENERGY, true>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre, lst,
+                                    v);
   else
-    update_groups<AX, ENERGY, false>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre, v);
+    update_groups<AX, ENERGY, false>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb, pre,
+                                     lst, v);
   // work counts of this sweep (kernel A's counters are final by now)
   if (sc.stats && vb.bx == 0 && threadIdx.x == 0) {
     sc.stats[0] = sc.counters[0];
