@@ -11,6 +11,35 @@
 
 namespace vofgb {
 
+// Programmatic dependent launch between the kernels of one time step.  A
+// kernel launched by launch_pdl may be scheduled before the kernel ahead of it
+// on the stream has completed: once every CTA of that kernel has exited, its
+// launch and CTA placement overlap the previous grid's completion and memory
+// flush.  The wrapper of every such kernel calls pdl_wait() as its first
+// statement: griddepcontrol.wait blocks until the previous grid has completed
+// and its writes are visible, the same ordering as a plain launch, so nothing
+// is read early.  It returns at once when the kernel was launched without the
+// attribute.  No kernel signals its dependents before it exits
+// (griddepcontrol.launch_dependents): on the 256^3 step that placed the next
+// kernel's waiting CTAs on the SMs that happened to be free, unevenly, and the
+// step took 1.05 ms instead of 0.83 ms (0.88 ms with plain launches).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);  // errors: cudaGetLastError()
+}
+
 // Virtual block index of a kernel body: the hardware's for a launch over one
 // grid; in a grouped launch over many boxes (vof_batched_step without lanes)
 // the CTA's box and its block within the box's own launch shape, from the

@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(256)
 k_shift_stream(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
                double* __restrict__ e_out, const double* __restrict__ dd, double dd_uniform, ShiftScratch sc,
                SumOut sums, int copy) {
+  pdl_wait();
   k_shift_stream_body(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc, sums, copy, vb_self());
 }
 
@@ -259,6 +260,7 @@ __device__ __forceinline__ void k_shift_planes_body(const GridDev& g, const doub
 __global__ void __launch_bounds__(kListThreads)
 k_shift_planes(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
                ShiftScratch sc) {
+  pdl_wait();
   k_shift_planes_body(g, c_in, dd, dd_uniform, sc, vb_self());
 }
 
@@ -323,6 +325,7 @@ __device__ __forceinline__ void k_shift_own_body(const GridDev& g, const double*
 __global__ void __launch_bounds__(kListThreads)
 k_shift_own(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
             ShiftScratch sc) {
+  pdl_wait();
   k_shift_own_body(g, c_in, dd, dd_uniform, sc, vb_self());
 }
 
@@ -401,6 +404,7 @@ __device__ __forceinline__ void k_shift_receivers_body(const GridDev& g, const d
 __global__ void __launch_bounds__(kListThreads)
 k_shift_receivers(GridDev g, const double* __restrict__ c_in, const double* __restrict__ dd, double dd_uniform,
                   ShiftScratch sc) {
+  pdl_wait();
   k_shift_receivers_body(g, c_in, dd, dd_uniform, sc, vb_self());
 }
 
@@ -472,6 +476,7 @@ __device__ __forceinline__ void k_shift_sums_body(const GridDev& g, const double
 __global__ void __launch_bounds__(256)
 k_shift_sums(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out, ShiftScratch sc,
              long long nwarps, SumOut sums) {
+  pdl_wait();
   k_shift_sums_body(g, c_in, e_in, c_out, e_out, sc, nwarps, sums, vb_self());
 }
 
@@ -646,16 +651,16 @@ cudaError_t launch_shift(const GridDev& g, const double* c_in, const double* e_i
     if (err != cudaSuccess) return err;
     prof_mark("shift.memset", st);
   }
-  k_shift_stream<<<shift_stream_grid(g), dim3(32, 8), 0, st>>>(g, c_in, e_in, c_out, e_out, dd, dd_uniform, sc,
-                                                               stream_sums, c_out != c_in);
+  launch_pdl(k_shift_stream, shift_stream_grid(g), dim3(32, 8), st, g, c_in, e_in, c_out, e_out, dd, dd_uniform,
+             sc, stream_sums, c_out != c_in);
   prof_mark("shift.stream", st);
-  k_shift_planes<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
+  launch_pdl(k_shift_planes, kListCTAs, kListThreads, st, g, c_in, dd, dd_uniform, sc);
   prof_mark("shift.planes", st);
-  k_shift_own<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
+  launch_pdl(k_shift_own, kListCTAs, kListThreads, st, g, c_in, dd, dd_uniform, sc);
   prof_mark("shift.own", st);
-  k_shift_receivers<<<kListCTAs, kListThreads, 0, st>>>(g, c_in, dd, dd_uniform, sc);
+  launch_pdl(k_shift_receivers, kListCTAs, kListThreads, st, g, c_in, dd, dd_uniform, sc);
   prof_mark("shift.receivers", st);
-  k_shift_sums<<<shift_sum_blocks(g), 256, 0, st>>>(g, c_in, e_in, c_out, e_out, sc, nw, sums);
+  launch_pdl(k_shift_sums, shift_sum_blocks(g), 256, st, g, c_in, e_in, c_out, e_out, sc, nw, sums);
   prof_mark("shift.sums", st);
   err = cudaGetLastError();
   if (err == cudaSuccess && state) {
@@ -754,6 +759,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_fused(ReduceJobs jobs
                                                                  int* __restrict__ ticket) {
   __shared__ double red[kMaxReduceK][kReduceThreads];
   __shared__ int last;
+  pdl_wait();
   const ReduceJob J = jobs.job[0];
   reduce1_body(J, blockIdx.x, gridDim.x, scratch + (size_t)blockIdx.x * kMaxReduceK, red);
   __threadfence();  // this CTA's partials before its ticket
@@ -799,7 +805,7 @@ cudaError_t launch_reduce_fused(const ReduceJob& job, double* scratch, int* tick
   if (job.nk > kMaxReduceK) return cudaErrorInvalidValue;
   ReduceJobs jobs{};
   jobs.job[0] = job;
-  k_reduce_fused<<<kReduceCTAs, kReduceThreads, 0, st>>>(jobs, scratch, ticket);
+  launch_pdl(k_reduce_fused, kReduceCTAs, kReduceThreads, st, jobs, scratch, ticket);
   prof_mark("reduce", st);
   return cudaGetLastError();
 }

@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(32 * kWarpsA)
 k_stream_col(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
              double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
              int cap, int copy) {
+  pdl_wait();
   k_stream_col_body<AX, ENERGY>(g, c_in, e_in, c_out, e_out, state, sc, force_all, cap, copy, vb_self());
 }
 
@@ -470,6 +471,7 @@ __global__ void __launch_bounds__(256)
 k_stream_row(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, double* __restrict__ c_out,
              double* __restrict__ e_out, const uint8_t* __restrict__ state, SweepScratch sc, int force_all,
              int cap, int copy) {
+  pdl_wait();
   k_stream_row_body<ENERGY>(g, c_in, e_in, c_out, e_out, state, sc, force_all, cap, copy, vb_self());
 }
 
@@ -573,6 +575,7 @@ __device__ __forceinline__ void k_prep_body(const GridDev& g, const double* __re
 template <bool F32, int NRM>
 __global__ void __launch_bounds__(kPlaneThreads)
 k_prep(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, SweepScratch sc, int ax) {
+  pdl_wait();
   k_prep_body<F32, NRM>(g, c_in, e_in, sc, ax, vb_self());
 }
 
@@ -694,6 +697,7 @@ template <int AX, bool ENERGY>
 __global__ void __launch_bounds__(kFaceThreads)
 k_faces(GridDev g, const double* __restrict__ c_in, const double* __restrict__ e_in, const double* __restrict__ uf,
         double* __restrict__ flux_out, SweepScratch sc, int* __restrict__ status) {
+  pdl_wait();
   k_faces_body<AX, ENERGY>(g, c_in, e_in, uf, flux_out, sc, status, vb_self());
 }
 
@@ -798,6 +802,7 @@ __global__ void __launch_bounds__(256)
 k_update(GridDev g, const double* c_in, const double* e_in, double* c_out, double* e_out,
          const double* __restrict__ uf, uint8_t* __restrict__ state,
          double* __restrict__ theta, SweepScratch sc, int nsub, int cap, int ngrp) {
+  pdl_wait();
   k_update_body<AX, ENERGY>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, nsub, cap, ngrp, vb_self());
 }
 
@@ -1002,29 +1007,29 @@ static void launch_ab(const SweepPlan& p, const GridDev& g, const double* c_in, 
                       double* e_out, const double* uf, uint8_t* state, double* theta, double* flux_out,
                       SweepScratch sc, int* status, cudaStream_t st) {
   if (AX == 0)
-    k_stream_row<ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc, flux_out != nullptr,
-                                                        p.cap, c_out != c_in);
+    launch_pdl(k_stream_row<ENERGY>, p.gridA, p.blockA, st, g, c_in, e_in, c_out, e_out, state, sc,
+               flux_out != nullptr, p.cap, c_out != c_in);
   else
-    k_stream_col<AX == 0 ? 1 : AX, ENERGY><<<p.gridA, p.blockA, 0, st>>>(g, c_in, e_in, c_out, e_out, state, sc,
-                                                                          flux_out != nullptr, p.cap, c_out != c_in);
+    launch_pdl(k_stream_col<AX == 0 ? 1 : AX, ENERGY>, p.gridA, p.blockA, st, g, c_in, e_in, c_out, e_out,
+               state, sc, flux_out != nullptr, p.cap, c_out != c_in);
   prof_mark(AX == 0 ? "sweep_x.stream" : (AX == 1 ? "sweep_y.stream" : "sweep_z.stream"), st);
   if (g.mlp == 1) {
     // learned normals of the mixed cells (tensor cores), then their planes
     launch_mlp_sweep_normals(g, c_in, sc, st);
-    if (g.f32) k_prep<true, 1><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
-    else k_prep<false, 1><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+    if (g.f32) launch_pdl(k_prep<true, 1>, kPlaneCTAs, kPlaneThreads, st, g, c_in, e_in, sc, AX);
+    else launch_pdl(k_prep<false, 1>, kPlaneCTAs, kPlaneThreads, st, g, c_in, e_in, sc, AX);
   } else if (g.mlp == 2) {
-    k_prep<false, 2><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+    launch_pdl(k_prep<false, 2>, kPlaneCTAs, kPlaneThreads, st, g, c_in, e_in, sc, AX);
   } else if (g.f32) {
-    k_prep<true, 0><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+    launch_pdl(k_prep<true, 0>, kPlaneCTAs, kPlaneThreads, st, g, c_in, e_in, sc, AX);
   } else {
-    k_prep<false, 0><<<kPlaneCTAs, kPlaneThreads, 0, st>>>(g, c_in, e_in, sc, AX);
+    launch_pdl(k_prep<false, 0>, kPlaneCTAs, kPlaneThreads, st, g, c_in, e_in, sc, AX);
   }
   prof_mark(AX == 0 ? "sweep_x.prep" : (AX == 1 ? "sweep_y.prep" : "sweep_z.prep"), st);
-  k_faces<AX, ENERGY><<<kFaceCTAs, kFaceThreads, 0, st>>>(g, c_in, e_in, uf, flux_out, sc, status);
+  launch_pdl(k_faces<AX, ENERGY>, kFaceCTAs, kFaceThreads, st, g, c_in, e_in, uf, flux_out, sc, status);
   prof_mark(AX == 0 ? "sweep_x.faces" : (AX == 1 ? "sweep_y.faces" : "sweep_z.faces"), st);
-  k_update<AX, ENERGY><<<p.gridB, 256, 0, st>>>(g, c_in, e_in, c_out, e_out, uf, state, theta, sc, (int)p.nsub,
-                                                 p.cap, p.lpc / kUpdLists);
+  launch_pdl(k_update<AX, ENERGY>, p.gridB, 256, st, g, c_in, e_in, c_out, e_out, uf, state, theta, sc,
+             (int)p.nsub, p.cap, p.lpc / kUpdLists);
   prof_mark(AX == 0 ? "sweep_x.update" : (AX == 1 ? "sweep_y.update" : "sweep_z.update"), st);
 }
 

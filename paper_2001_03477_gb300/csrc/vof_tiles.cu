@@ -78,6 +78,7 @@ __device__ __forceinline__ void k_tiles_body(const GridDev& g, const double* __r
 __global__ void __launch_bounds__(256)
 k_tiles(GridDev g, const double* __restrict__ c, const double* __restrict__ e, TileScratch ts, int ntx, int nty,
         uint8_t* state, int* counters) {
+  pdl_wait();
   k_tiles_body(g, c, e, ts, ntx, nty, state, counters, vb_self());
 }
 
@@ -201,6 +202,7 @@ __device__ __forceinline__ void k_quiet_body(const GridDev& g, const double* __r
 __global__ void __launch_bounds__(256)
 k_quiet(GridDev g, const double* __restrict__ c, const double* __restrict__ e, TileScratch ts, int ntx, int nty,
         int ntz, SumOut sums) {
+  pdl_wait();
   k_quiet_body(g, c, e, ts, ntx, nty, ntz, sums, vb_self());
 }
 
@@ -283,10 +285,10 @@ cudaError_t launch_tiles(const GridDev& g, const double* c, const double* e, Til
                          uint8_t* state, int* counters, cudaStream_t st) {
   int nt[3];
   tile_counts(g, nt);
-  k_tiles<<<dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]), dim3(32, 8), 0, st>>>(
-      g, c, e, ts, nt[0], nt[1], state, counters);
+  launch_pdl(k_tiles, dim3((unsigned)((nt[0] + 3) / 4), (unsigned)nt[1], (unsigned)nt[2]), dim3(32, 8), st,
+             g, c, e, ts, nt[0], nt[1], state, counters);
   prof_mark("tiles", st);
-  k_quiet<<<quiet_blocks(g), 256, 0, st>>>(g, c, e, ts, nt[0], nt[1], nt[2], sums);
+  launch_pdl(k_quiet, quiet_blocks(g), 256, st, g, c, e, ts, nt[0], nt[1], nt[2], sums);
   prof_mark("tiles.quiet", st);
   return cudaGetLastError();
 }
