@@ -121,6 +121,24 @@ class TestInverse:
                 a = O.alpha(np.array(m, float), c)
                 assert abs(O.volume(m, a) - c) < 1e-15
 
+    def test_alpha_is_the_nearest_double(self):
+        # The plane constant is the double whose volume is nearest to c: no
+        # neighbouring double gives a volume closer to c.  The normals are
+        # non-negative dyadic rationals summing to exactly 1, so the oracle's
+        # mirroring and L1 scaling are exact and alpha is returned unscaled.
+        for it in range(400):
+            k = rng.integers(1, 2 ** 20, size=3).astype(float)
+            if it % 4 == 0:
+                k[rng.integers(0, 3)] = 0.0  # 2D normals too
+            k[2] = 2.0 ** 21 - k[0] - k[1]
+            m = k / 2.0 ** 21
+            assert m.sum() == 1.0
+            c = float(rng.choice([rng.uniform(1e-9, 1e-3), rng.uniform(0.0, 1.0), 1.0 - rng.uniform(1e-9, 1e-3)]))
+            a = O.alpha(m, c)
+            err = abs(O.volume(m, a) - c)
+            for nb in (np.nextafter(a, -np.inf), np.nextafter(a, np.inf)):
+                assert err <= abs(O.volume(m, nb) - c), (m, c, a, nb)
+
     def test_roundtrip_alpha_v_alpha(self):
         worst = 0.0
         for _ in range(300):
@@ -238,6 +256,22 @@ class TestNormals:
                 theory = (off - m @ dx) / np.linalg.norm(m)
                 assert abs(dG - theory) < 1e-13
 
+    def test_youngs_is_the_mean_of_the_corner_gradients(self):
+        # Youngs' normal is minus the mean of the gradients at the cell's
+        # eight vertices, each vertex gradient the mean of the differences
+        # across the 2 x 2 x 2 block of cells around that vertex; then
+        # L1-normalised.  Built here from that construction for random
+        # stencils (s[z, y, x], offsets -1..1).
+        for _ in range(200):
+            st = rng.random((3, 3, 3))
+            g = np.zeros(3)
+            for cz, cy, cx in itertools.product((0, 1), repeat=3):
+                blk = st[cz:cz + 2, cy:cy + 2, cx:cx + 2]  # the cells around vertex (cx, cy, cz)
+                g += [(blk[:, :, 1] - blk[:, :, 0]).mean(), (blk[:, 1, :] - blk[:, 0, :]).mean(),
+                      (blk[1, :, :] - blk[0, :, :]).mean()]
+            m = -g / np.abs(g).sum()
+            assert np.abs(O.youngs(st) - m).max() < 1e-14
+
     def test_youngs_axis_aligned(self):
         for d in range(3):
             for sgn in (1, -1):
@@ -291,6 +325,57 @@ class TestWeno:
             v = [float(cell_avg_poly(coefs, j)) for j in (-2, -1, 0, 1, 2)]
             ex = float(poly_at(coefs, Fr(1, 2)))
             assert abs(O.weno5(v, 1e30) - ex) < 1e-11 * (1 + abs(ex))
+
+    def test_matches_its_construction(self):
+        # WENO5 built from its definition (Jiang & Shu; Shu 2009, cited in
+        # Sec. 3.4.1): p_k is the quadratic with the cell averages of stencil
+        # k (cells -2..0, -1..1, 0..2 around the donor 0), q_k = p_k(1/2);
+        # the linear weights d_k are the ones that make sum d_k q_k the
+        # quartic's face value for every quartic; the smoothness indicator is
+        # beta_k = sum over l = 1, 2 of the integral over the donor cell of
+        # (d^l p_k / dx^l)^2; alpha_k = d_k / (eps + beta_k)^2.  Every piece
+        # is computed generically (linear solves, polynomial derivatives and
+        # integrals), none from the scheme's printed coefficients.
+        P = np.polynomial.Polynomial
+
+        def cell_avg_matrix(cells, deg):
+            return np.array([[((j + 0.5) ** (p + 1) - (j - 0.5) ** (p + 1)) / (p + 1) for p in range(deg + 1)]
+                             for j in cells])
+
+        stencils = [(-2, -1, 0), (-1, 0, 1), (0, 1, 2)]
+        # linear weights from the monomials x^0 .. x^4
+        A5 = cell_avg_matrix((-2, -1, 0, 1, 2), 4)
+        rows, rhs = [], []
+        for p in range(5):
+            vals = A5[:, p]  # cell averages of x^p
+            rows.append([P(np.linalg.solve(cell_avg_matrix(st, 2), vals[[j + 2 for j in st]]))(0.5)
+                         for st in stencils])
+            rhs.append(0.5 ** p)
+        d = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]
+        assert np.allclose(d, [0.1, 0.6, 0.3], atol=1e-14)
+
+        def expected(v, eps=1e-6):
+            q, beta = [], []
+            for st in stencils:
+                p = P(np.linalg.solve(cell_avg_matrix(st, 2), np.array([v[j + 2] for j in st])))
+                q.append(p(0.5))
+                b = 0.0
+                for l in (1, 2):
+                    sq = (p.deriv(l) ** 2).integ()
+                    b += sq(0.5) - sq(-0.5)
+                beta.append(b)
+            a = d / (eps + np.array(beta)) ** 2
+            return float((a * np.array(q)).sum() / a.sum())
+
+        gen = np.random.default_rng(11)
+        cases = [gen.random(5) for _ in range(200)]
+        cases += [373.15 + 0.01 * gen.standard_normal(5) for _ in range(100)]
+        cases += [np.sin(0.7 * np.arange(5) + gen.random() * 6) * gen.random() for _ in range(100)]
+        cases += [np.where(np.arange(5) < gen.integers(1, 5), 1.0, 0.0) + 1e-3 * gen.random(5) for _ in range(50)]
+        for v in cases:
+            ex = expected(v)
+            scale = np.abs(v).max()
+            assert abs(O.weno5(list(v)) - ex) <= 1e-12 * scale, (v, O.weno5(list(v)), ex)
 
     def test_eno_at_step(self):
         # discontinuity downwind of the donor: the face value stays on the

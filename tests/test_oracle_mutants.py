@@ -1,0 +1,207 @@
+"""The oracle's pins reject plausible slips in the oracle itself.
+
+Every parity claim of the CUDA path rests on the oracle, and the oracle is
+trusted because its pins (tests/test_oracle_geometry.py, _invariants.py,
+_boundary.py, _le.py, _mass_transfer.py) tie it to what the paper and the
+mathematics fix: exact volumes, exact plane motion, conservation, uniform
+temperature preserved, closed-form mass-transfer rates, and so on.  This file
+checks that those pins have teeth.  Each mutant below is one plausible
+mistake planted in a copy of oracle/vof_oracle.c (a wrong constant, a dropped
+term, a flipped sign, a transposed index or operand).  The copy is compiled
+on the CPU with the oracle's own compiler flags into a temporary directory,
+the pins run against it in a child process, and at least one pin must fail.
+The unchanged source, compiled the same way, must pass the same pins, so a
+broken harness cannot pass for a caught mutant.  Nothing here touches the
+committed oracle or its library.
+
+The pin set leaves out the 32^3 sphere return of one period (a minute of
+CPU time; every mutant below is caught without it).  Two kinds of change are
+deliberately not mutants: the Strang order (x, y, z on even steps; reading
+of the configuration, not of a physical law that a pin could fix) and the
+tie rules of the readings (c_c at exactly 1/2, the MYC tie), which only
+parity with a second implementation can pin.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "vof_oracle.c")
+
+PINS = [
+    "tests/test_oracle_geometry.py",
+    "tests/test_oracle_invariants.py",
+    "tests/test_oracle_boundary.py",
+    "tests/test_oracle_le.py",
+    "tests/test_oracle_mass_transfer.py",
+]
+SKIP = ["tests/test_oracle_invariants.py::TestTranslation::test_sphere_translation_returns"]
+
+# (name, text in vof_oracle.c, replacement).  Each text occurs exactly once.
+MUTANTS = [
+    # volume V(m, alpha), Sec. 3.2 (Scardovelli-Zaleski inclusion-exclusion)
+    ("volume: first branch constant 6 -> 2",
+     "return a * a * a / (6.0 * m1 * m2 * m3);", "return a * a * a / (2.0 * m1 * m2 * m3);"),
+    ("volume: second branch drops its m1^2 term",
+     "double v2 = a * (a - m1) / (2.0 * m2 * m3) + m1 * m1 / (6.0 * m2 * m3);",
+     "double v2 = a * (a - m1) / (2.0 * m2 * m3);"),
+    ("volume: symmetry V(alpha) = 1 - V(1 - alpha) taken at alpha",
+     "return 1.0 - vol_sorted_low(s[0], s[1], s[2], 1.0 - alpha);",
+     "return 1.0 - vol_sorted_low(s[0], s[1], s[2], alpha);"),
+    ("volume: mirror shift with the wrong sign",
+     "if (m[d] < 0.0) { mpos[d] = -m[d]; sh -= m[d]; }", "if (m[d] < 0.0) { mpos[d] = -m[d]; sh += m[d]; }"),
+    ("slab volume: offset of the slab with the wrong sign",
+     "double a2 = alpha - m[axis] * x0;", "double a2 = alpha + m[axis] * x0;"),
+    ("plane area: polygon area without the factor 1/2",
+     "area += 0.5 * (cx * n[0] + cy * n[1] + cz * n[2]);", "area += (cx * n[0] + cy * n[1] + cz * n[2]);"),
+    ("plane constant: bisection returns the worse end of its bracket",
+     "double am = (vh < vl) ? hi : lo;", "double am = (vh < vl) ? lo : hi;"),
+    # MYC normal, Sec. 3.2 [Aulisa07]
+    ("Youngs: m = +grad c",
+     "        m[d] = -g;\n", "        m[d] = g;\n"),
+    ("centred columns: transverse slope from the other axis' column pair",
+     "double a1 = -(h[2][1] - h[0][1]) * 0.5;", "double a1 = -(h[1][2] - h[1][0]) * 0.5;"),
+    ("centred columns: orientation reversed",
+     "double sg = (lower >= upper) ? 1.0 : -1.0;", "double sg = (lower >= upper) ? -1.0 : 1.0;"),
+    ("MYC: the candidate test reversed",
+     "int use_cc = (rule == 0) ? (cmax <= ymax) : (cmax >= ymax);",
+     "int use_cc = (rule == 0) ? (cmax >= ymax) : (cmax <= ymax);"),
+    ("Youngs: unweighted transverse sums",
+     "static const double w[3] = {1.0, 2.0, 1.0};", "static const double w[3] = {1.0, 1.0, 1.0};"),
+    # WENO5 face temperature, Sec. 3.4.1 [Shu09]
+    ("WENO5: candidate q0 coefficient -7 -> -6",
+     "double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;", "double q0 = (2.0 * vm2 - 6.0 * vm1 + 11.0 * v0) / 6.0;"),
+    ("WENO5: linear weight 0.6 -> 0.5",
+     "double a1 = 0.6 / ((epsw + b1) * (epsw + b1));", "double a1 = 0.5 / ((epsw + b1) * (epsw + b1));"),
+    ("WENO5: smoothness indicator of stencil 1 takes stencil 0's slope",
+     "double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;", "double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e0 * e0;"),
+    # Weymouth-Yue sweep with tandem energy, Sec. 3.3.1, Eq. disc_et_adv
+    ("sweep: donor slab on the wrong side of the donor",
+     "double x0 = a > 0.0 ? 1.0 - da : 0.0;\n        double vol = orc_slab_volume(m, al, axis, x0, da);",
+     "double x0 = a > 0.0 ? 0.0 : 1.0 - da;\n        double vol = orc_slab_volume(m, al, axis, x0, da);"),
+    ("sweep: pure donor fluxes c of the downwind cell",
+     "    } else {\n        Fv = cd * a;\n    }\n    /* WENO5 stencil centred on the donor",
+     "    } else {\n        Fv = c[cell_id(dims, bc, pos[0], pos[1], pos[2])] * a;\n    }\n"
+     "    /* WENO5 stencil centred on the donor"),
+    ("sweep: dilatation term c_c (a_r - a_l) dropped",
+     "double lf = Fl - ccv * al, rf = Fr - ccv * ar;", "double lf = Fl, rf = Fr;"),
+    ("sweep: phase heat capacities swapped in the energy flux G",
+     "    *G = (Tf * par[1]) * Fv + (Tf * par[2]) * (a - Fv);\n}\n\n/* Sweep along",
+     "    *G = (Tf * par[2]) * Fv + (Tf * par[1]) * (a - Fv);\n}\n\n/* Sweep along"),
+    ("frozen state: Theta from C_p(c) instead of C_p(c_c)",
+     "theta[id] = heat_cap(par, (double)b) * Tn;", "theta[id] = heat_cap(par, c[id]) * Tn;"),
+    ("sweep: clipped volume with the wrong sign",
+     "double enew = (e[id] + le) - re;\n                double cc2 = cnew;\n                if (cc2 < 0.0) cc2 = 0.0;\n"
+     "                if (cc2 > 1.0) cc2 = 1.0;\n                clipv[id] = cnew - cc2;",
+     "double enew = (e[id] + le) - re;\n                double cc2 = cnew;\n                if (cc2 < 0.0) cc2 = 0.0;\n"
+     "                if (cc2 > 1.0) cc2 = 1.0;\n                clipv[id] = cc2 - cnew;"),
+    # phase-change shift, Sec. 3.3.2 and the energy jump of Sec. 3.4.1
+    ("shift: |m|_1 instead of |m|_2 in alpha + |m| dd",
+     "double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);\n                double sft = mn2 * ddv;",
+     "double mn2 = fabs(m[0]) + fabs(m[1]) + fabs(m[2]);\n                double sft = mn2 * ddv;"),
+    ("shift: energy jump with the wrong sign",
+     "double de = dc * dCp * par[3];", "double de = -dc * dCp * par[3];"),
+    ("shift: receivers of the advancing phase instead of the receding one",
+     "if ((sft < 0.0) != full) continue;", "if ((sft < 0.0) == full) continue;"),
+    ("shift: neighbour's plane extended with the offset's sign flipped",
+     "double shiftv = -(mq[0] * (-ox) + mq[1] * (-oy) + mq[2] * (-oz));",
+     "double shiftv = (mq[0] * (-ox) + mq[1] * (-oy) + mq[2] * (-oz));"),
+    ("unfused energy update: phase heat capacities swapped in G",
+     "Gs[side] = (Tf * par[1]) * F + (Tf * par[2]) * (a - F);", "Gs[side] = (Tf * par[2]) * F + (Tf * par[1]) * (a - F);"),
+    ("frozen state: c_c = 1 below one half",
+     "unsigned char b = c[id] > 0.5 ? 1 : 0;", "unsigned char b = c[id] > 0.5 ? 0 : 1;"),
+    ("zero-gradient boundary: the ghost copies the far end of the line",
+     "    if (i < 0) return 0;\n    if (i >= n) return n - 1;", "    if (i < 0) return n - 1;\n    if (i >= n) return 0;"),
+    # mass transfer rate from PLIC distances, Sec. 3.2
+    ("mass transfer: normal gradient with the wrong sign",
+     "double g = c[id] > 0.5 ? (Tg - T) / dist : (T - Tg) / dist;",
+     "double g = c[id] > 0.5 ? (T - Tg) / dist : (Tg - T) / dist;"),
+    ("mass transfer: Delta x from the node to the mixed cell",
+     "double X[3] = {0.5 - dx, 0.5 - dy, 0.5 - dz};", "double X[3] = {0.5 + dx, 0.5 + dy, 0.5 + dz};"),
+    ("mass transfer: conductivities of the two phases transposed",
+     "mdot[id] = (k_g * gg - k_l * gl) / h_fg;", "mdot[id] = (k_l * gg - k_g * gl) / h_fg;"),
+    ("mass transfer: weights gamma without the 1 / |Delta x|^2",
+     "double gam = xi / (double)(dx * dx + dy * dy + dz * dz);", "double gam = xi;"),
+    # Li's Lagrangian-explicit sweep (Sec. 3.3.1, reading A19)
+    ("Lagrangian explicit: stretch 1 + (a_l - a_r)",
+     "return 1.0 + (ar - al);  /* exactly 1 where the velocity is uniform */",
+     "return 1.0 + (al - ar);  /* exactly 1 where the velocity is uniform */"),
+    ("Lagrangian explicit: preimage width |a| J instead of |a| / J",
+     "double w = (J > da) ? da / J : 1.0;", "double w = (J > da) ? da * J : 1.0;"),
+]
+
+# the oracle's own compile line (oracle/__init__.py, build())
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp", "-std=c99"]
+
+CHILD = r"""
+import os, sys
+root, lib = sys.argv[1], sys.argv[2]
+sys.path.insert(0, root)
+os.chdir(root)
+import oracle
+oracle._LIB_PATH = lib
+oracle.build = lambda force=False: lib
+import pytest
+args = sys.argv[3:]
+sys.exit(pytest.main(args))
+"""
+
+
+def _compile(src_text: str, work: str, tag: str) -> str:
+    src = os.path.join(work, f"{tag}.c")
+    lib = os.path.join(work, f"lib{tag}.so")
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", *CFLAGS, "-o", lib, src, "-lm"], check=True, capture_output=True)
+    return lib
+
+
+def _run_pins(lib: str) -> tuple[int, str]:
+    args = [*PINS, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+    for s in SKIP:
+        args += ["--deselect", s]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, lib, *args], capture_output=True, text=True,
+                       env=env, timeout=600)
+    tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-3:])
+    return r.returncode, tail
+
+
+def _source() -> str:
+    with open(SRC) as f:
+        return f.read()
+
+
+def test_mutant_texts_occur_once():
+    src = _source()
+    names = [m[0] for m in MUTANTS]
+    assert len(set(names)) == len(names)
+    for name, old, new in MUTANTS:
+        assert src.count(old) == 1, name
+        assert old != new, name
+
+
+def test_pins_reject_every_mutant():
+    src = _source()
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with tempfile.TemporaryDirectory() as work:
+        jobs = [("unchanged", src)] + [(name, src.replace(old, new)) for name, old, new in MUTANTS]
+        libs = {}
+        for i, (name, text) in enumerate(jobs):
+            libs[name] = _compile(text, work, f"m{i}")
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            res = dict(zip(libs, ex.map(_run_pins, libs.values())))
+    rc, tail = res.pop("unchanged")
+    assert rc == 0, f"the unchanged oracle fails its own pins under this harness:\n{tail}"
+    # pytest exit code 1: tests ran and at least one failed; anything else
+    # (an import error, a crash) is a harness failure, not a caught mutant
+    survivors = [n for n, (rc, _) in res.items() if rc == 0]
+    broken = {n: t for n, (rc, t) in res.items() if rc not in (0, 1)}
+    assert not broken, f"harness failures: {broken}"
+    assert not survivors, f"mutants no pin rejects: {survivors}"
