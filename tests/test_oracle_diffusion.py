@@ -66,6 +66,36 @@ def test_linear_profile_is_steady(seed):
     assert np.abs(L[inner]).max() <= 1e-9 * 3.0 / h
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_quadratic_profile_second_difference_exact(axis):
+    # Each phase holds its own quadratic in the coordinate across a plane
+    # interface normal to `axis`, both equal to T_Gamma on the plane.  The
+    # three-point second difference over unequal distances (h to a node of
+    # the same phase, theta to the interface) is exact for quadratics, so
+    # k_p sum L(T) is k_p T'' at every node whose stencil stays off the
+    # walls: the regular nodes and the two next to the interface alike.
+    n_ax = 14
+    shape = [6, 6, 6]
+    shape[2 - axis] = n_ax
+    shape = tuple(shape)
+    D = 6.37  # the plane x_axis = D (cell units): liquid below it
+    xs = [np.newaxis] * 3
+    xs[2 - axis] = slice(None)
+    line = lambda v: np.broadcast_to(v[tuple(xs)], shape)
+    c = line(np.clip(D - np.arange(n_ax), 0.0, 1.0)).copy()  # exact fractions of the cut
+    h, Tg, k_l, k_g = 0.1, 2.0, 0.7, 0.03
+    A_l, B_l, A_g, B_g = 3.0, 5.0, -1.5, -2.0
+    x = line((np.arange(n_ax) + 0.5 - D) * h)
+    T = np.where(c >= 0.5, Tg + A_l * x + B_l * x * x, Tg + A_g * x + B_g * x * x)
+    g = O.Grid(shape[2], shape[1], shape[0], (1, 1, 1), h, 4.0, 1.0, Tg)
+    L = diffusion_operator(g, c, T, k_l, k_g).reshape(shape)
+    want = np.where(c >= 0.5, 2.0 * B_l * k_l, 2.0 * B_g * k_g)
+    inner = [slice(None)] * 3
+    inner[2 - axis] = slice(1, n_ax - 1)  # off the two walls across the plane
+    inner = tuple(inner)
+    assert np.abs(L[inner] - want[inner]).max() <= 1e-8 * np.abs(want).max()
+
+
 def test_saturation_temperature_is_a_fixed_point():
     shape = (10, 10, 10)
     n, D = tilted(1)

@@ -59,6 +59,12 @@ def test_bf16_matches_library_rounding():
     x = np.concatenate([rng.normal(size=2000) * 10.0 ** rng.integers(-30, 30, 2000),
                         1.0 + np.arange(1, 512) * 2.0 ** -16,       # ties and near ties
                         -(1.0 + np.arange(1, 512) * 2.0 ** -16), [0.0, -0.0, 1e-40]])
+    # exact ties (the dropped 16 bits are 0x8000) above both even and odd
+    # upper halves, so that round-to-even is told apart from any fixed rule
+    upper = rng.integers(0x0080, 0x7F00, size=1000).astype(np.uint32)
+    ties = ((upper << 16) | 0x8000).view(np.float32).astype(np.float64)
+    assert (upper & 1).any() and not (upper & 1).all()
+    x = np.concatenate([x, ties, -ties])
     want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
     assert np.array_equal(M.bf16(x), want)
 
@@ -168,3 +174,21 @@ def test_fallback_keeps_myc_where_it_is_exact():
         m, fell = M.learned_normal(q, s, weights=lambda w: w)
         assert fell and np.array_equal(m, m_myc)
     assert checked >= 15
+
+
+def test_adam_first_step_closed_form():
+    # Adam (Kingma & Ba) with bias-corrected moments: after one step the
+    # corrected first moment is g and the second g^2, so every parameter
+    # moves by -lr g / (|g| + eps).  All rows of the batch are one stencil,
+    # so the sampled mini-batch's gradient is the full gradient.
+    rng = np.random.default_rng(7)
+    X1, N1 = M.dataset(1, rng)
+    X, N = np.repeat(X1, 32, axis=0), np.repeat(N1, 32, axis=0)
+    p0 = M.init_params(np.random.default_rng(8))
+    _, g = M.loss_and_grad(p0, X, N)
+    p = {k: v.copy() for k, v in p0.items()}
+    lr, eps = 1e-3, 1e-8
+    M.adam(p, X, N, 1, lr=lr, batch=16, rng=np.random.default_rng(9), eps=eps)
+    for k in p:
+        want = p0[k] - lr * g[k] / (np.abs(g[k]) + eps)
+        assert np.allclose(p[k], want, rtol=1e-12, atol=1e-15), k

@@ -14,6 +14,11 @@ The unchanged source, compiled the same way, must pass the same pins, so a
 broken harness cannot pass for a caught mutant.  Nothing here touches the
 committed oracle or its library.
 
+The numpy oracles of the learned normal (oracle/mlp.py), the interface-
+Dirichlet diffusion (oracle/diffusion.py) and the velocity extension
+(oracle/extension.py) get the same treatment: the mutated module is loaded
+under its own name in the child before its pins run.
+
 The pin set leaves out the 32^3 sphere return of one period (a minute of
 CPU time; every mutant below is caught without it).  Two kinds of change are
 deliberately not mutants: the Strang order (x, y, z on even steps; reading
@@ -203,5 +208,121 @@ def test_pins_reject_every_mutant():
     # (an import error, a crash) is a harness failure, not a caught mutant
     survivors = [n for n, (rc, _) in res.items() if rc == 0]
     broken = {n: t for n, (rc, t) in res.items() if rc not in (0, 1)}
+    assert not broken, f"harness failures: {broken}"
+    assert not survivors, f"mutants no pin rejects: {survivors}"
+
+
+# (module, name, text in oracle/<module>.py, replacement)
+PY_PINS = {
+    "mlp": ["tests/test_oracle_mlp.py"],
+    "diffusion": ["tests/test_oracle_diffusion.py"],
+    "extension": ["tests/test_oracle_extension.py"],
+}
+PY_MUTANTS = [
+    # learned normal (the network, its gradient, Adam, BF16, the fallback)
+    ("mlp", "GELU with erf(x / 2)",
+     "return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))", "return 0.5 * x * (1.0 + erf(x / 2.0))"),
+    ("mlp", "GELU derivative: density term without its 1/sqrt(2)",
+     "x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)", "x * np.exp(-0.5 * x * x) / math.sqrt(math.pi)"),
+    ("mlp", "gradient of W3 from the first hidden layer",
+     'g["W3"] = g_y.T @ a2', 'g["W3"] = g_y.T @ a1'),
+    ("mlp", "gradient through the unit normalisation without its projection",
+     "g_y = (g_yh - yh * np.sum(g_yh * yh, axis=1, keepdims=True)) / ny", "g_y = g_yh / ny"),
+    ("mlp", "Adam without the first moment's bias correction",
+     "mh = mom[k] / (1 - beta1 ** t)", "mh = mom[k]"),
+    ("mlp", "BF16 ties rounded down instead of to even",
+     "lsb = (bits >> 16) & 1", "lsb = 0 * bits"),
+    ("mlp", "plane residual: neighbour offsets with the wrong sign",
+     "r.append(volume(mm, al - mm @ o) - s[k])", "r.append(volume(mm, al + mm @ o) - s[k])"),
+    ("mlp", "ellipsoid nearest point with a2 - t",
+     "    return a2 * y / (a2 + t)", "    return a2 * y / (a2 - t)"),
+    ("mlp", "plane stencil: cell corner at o + 1/2",
+     "a = (d - n @ (o - 0.5)) / l1", "a = (d - n @ (o + 0.5)) / l1"),
+    # interface-Dirichlet diffusion (Sec. 3.4.2)
+    ("diffusion", "height function: interface at H - 3",
+     "theta = (H - 3.5) if liquid_p else (3.5 - H)", "theta = (H - 3.0) if liquid_p else (3.0 - H)"),
+    ("diffusion", "plane distance with the node's offset added",
+     "t = (al[M] - mm @ x0) / ma", "t = (al[M] + mm @ x0) / ma"),
+    ("diffusion", "second difference over one side's distance",
+     "denom = 0.5 * (dists[-1] + dists[1])", "denom = dists[1]"),
+    ("diffusion", "heated wall a whole cell away",
+     "terms[s] = (2.0 / h, None, 0.0, Tw * 2.0 / h)", "terms[s] = (1.0 / h, None, 0.0, Tw * 1.0 / h)"),
+    ("diffusion", "phase-wise energy replaced by the mixture's",
+     "        return e + Cd * (T1 - T0)", "        return Cd * T1"),
+    ("diffusion", "conductivities of the phases swapped",
+     "kp = k_l if liquid_p else k_g", "kp = k_g if liquid_p else k_l"),
+    # velocity extension (Sec. 3.3.1)
+    ("extension", "face density from one cell only",
+     "cf = 0.5 * (c[P] + c[Q])", "cf = c[P]"),
+    ("extension", "source with the density jump reversed",
+     "(1.0 / rho_g - 1.0 / rho_l)", "(1.0 / rho_l - 1.0 / rho_g)"),
+    ("extension", "face correction along +grad p",
+     "val = -(dt / rho_f(L, R)) * (p[R] - p[L]) / h", "val = -(dt / rho_f(L, R)) * (p[L] - p[R]) / h"),
+    ("extension", "one gas layer instead of two",
+     "    for L in (1, 2):\n        new = []", "    for L in (1,):\n        new = []"),
+    ("extension", "couplings over h instead of h^2",
+     "beta = dt / rho_f(P, Q) / (h * h)", "beta = dt / rho_f(P, Q) / h"),
+]
+
+PY_CHILD = r"""
+import importlib.util, os, sys
+root, name, path = sys.argv[1], sys.argv[2], sys.argv[3]
+sys.path.insert(0, root)
+os.chdir(root)
+import oracle
+spec = importlib.util.spec_from_file_location("oracle." + name, path)
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle." + name] = mod
+spec.loader.exec_module(mod)
+setattr(oracle, name, mod)
+import pytest
+sys.exit(pytest.main(sys.argv[4:]))
+"""
+
+
+def _py_source(name: str) -> str:
+    with open(os.path.join(ROOT, "oracle", name + ".py")) as f:
+        return f.read()
+
+
+def _run_py_pins(job) -> tuple[int, str]:
+    name, path = job
+    args = [*PY_PINS[name], "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-c", PY_CHILD, ROOT, name, path, *args], capture_output=True, text=True,
+                       env=env, timeout=600)
+    tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-3:])
+    return r.returncode, tail
+
+
+def test_py_mutant_texts_occur_once():
+    names = [(m[0], m[1]) for m in PY_MUTANTS]
+    assert len(set(names)) == len(names)
+    for name, label, old, new in PY_MUTANTS:
+        assert _py_source(name).count(old) == 1, label
+        assert old != new, label
+
+
+def test_pins_reject_every_numpy_oracle_mutant():
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with tempfile.TemporaryDirectory() as work:
+        jobs = {}
+        for name in PY_PINS:  # the unchanged modules, loaded the same way
+            path = os.path.join(work, f"unchanged_{name}.py")
+            with open(path, "w") as f:
+                f.write(_py_source(name))
+            jobs[("unchanged", name)] = (name, path)
+        for i, (name, label, old, new) in enumerate(PY_MUTANTS):
+            path = os.path.join(work, f"m{i}_{name}.py")
+            with open(path, "w") as f:
+                f.write(_py_source(name).replace(old, new))
+            jobs[(label, name)] = (name, path)
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            res = dict(zip(jobs, ex.map(_run_py_pins, jobs.values())))
+    for name in PY_PINS:
+        rc, tail = res.pop(("unchanged", name))
+        assert rc == 0, f"the unchanged oracle/{name}.py fails its own pins under this harness:\n{tail}"
+    survivors = [k for k, (rc, _) in res.items() if rc == 0]
+    broken = {k: t for k, (rc, t) in res.items() if rc not in (0, 1)}
     assert not broken, f"harness failures: {broken}"
     assert not survivors, f"mutants no pin rejects: {survivors}"
