@@ -250,7 +250,6 @@ struct ReduceJobs {
   ReduceJob job[kMaxReduceJobs];
 };
 size_t reduce_scratch_bytes();
-cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st);
 // one job's two levels in one launch; *ticket is zero before and after
 cudaError_t launch_reduce_fused(const ReduceJob& job, double* scratch, int* ticket, cudaStream_t st);
 

@@ -739,22 +739,10 @@ __device__ __forceinline__ void reduce2_body(const ReduceJob& J, const double* p
   cta_sums(s, J.nk, J.out, red);
 }
 
-__global__ void __launch_bounds__(kReduceThreads) k_reduce1(ReduceJobs jobs, double* __restrict__ scratch) {
-  __shared__ double red[kMaxReduceK][kReduceThreads];
-  const ReduceJob J = jobs.job[blockIdx.y];
-  reduce1_body(J, blockIdx.x, gridDim.x, scratch + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kMaxReduceK, red);
-}
-
-__global__ void __launch_bounds__(kReduceThreads) k_reduce2(ReduceJobs jobs, const double* __restrict__ scratch,
-                                                            int nparts) {
-  __shared__ double red[kMaxReduceK][kReduceThreads];
-  const ReduceJob J = jobs.job[blockIdx.x];
-  reduce2_body(J, scratch + (size_t)blockIdx.x * nparts * kMaxReduceK, nparts, red);
-}
-
 // Both levels in one launch (one job): every CTA its part, and the CTA that
 // finishes last (a ticket, zero at the start and left zero) the second
-// level -- the same arithmetic and order as k_reduce1 and k_reduce2.
+// level -- the same arithmetic and order as the grouped pair k_reduce1_grp
+// and k_reduce2_grp below, so a box sums to the same bits either way.
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_fused(ReduceJobs jobs, double* __restrict__ scratch,
                                                                  int* __restrict__ ticket) {
   __shared__ double red[kMaxReduceK][kReduceThreads];
@@ -807,17 +795,6 @@ cudaError_t launch_reduce_fused(const ReduceJob& job, double* scratch, int* tick
   jobs.job[0] = job;
   launch_pdl(k_reduce_fused, kReduceCTAs, kReduceThreads, st, jobs, scratch, ticket);
   prof_mark("reduce", st);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(const ReduceJobs& jobs, int njobs, double* scratch, cudaStream_t st) {
-  if (njobs <= 0 || njobs > kMaxReduceJobs) return cudaErrorInvalidValue;
-  for (int j = 0; j < njobs; ++j)
-    if (jobs.job[j].nk > kMaxReduceK) return cudaErrorInvalidValue;
-  k_reduce1<<<dim3(kReduceCTAs, njobs), kReduceThreads, 0, st>>>(jobs, scratch);
-  prof_mark("reduce.1", st);
-  k_reduce2<<<njobs, kReduceThreads, 0, st>>>(jobs, scratch, kReduceCTAs);
-  prof_mark("reduce.2", st);
   return cudaGetLastError();
 }
 
