@@ -94,6 +94,32 @@ MUTANTS = [
      "    } else {\n        Fv = cd * a;\n    }\n    /* WENO5 stencil centred on the donor",
      "    } else {\n        Fv = c[cell_id(dims, bc, pos[0], pos[1], pos[2])] * a;\n    }\n"
      "    /* WENO5 stencil centred on the donor"),
+    ("sweep: WENO5 stencil ordered downwind to upwind",
+     "    /* WENO5 stencil centred on the donor, ordered upwind to downwind */\n    double v[5];\n"
+     "    for (int r = -2; r <= 2; ++r) {\n        int q[3] = {don[0], don[1], don[2]};\n"
+     "        q[axis] += (a > 0.0) ? r : -r;",
+     "    /* WENO5 stencil centred on the donor, ordered upwind to downwind */\n    double v[5];\n"
+     "    for (int r = -2; r <= 2; ++r) {\n        int q[3] = {don[0], don[1], don[2]};\n"
+     "        q[axis] += (a > 0.0) ? -r : r;"),
+    ("sweep: T of the cells as e without the heat capacity",
+     "const double *theta, double *Fout,\n                       double *Gout, double *diag) {\n"
+     "    long N = (long)dims[0] * dims[1] * dims[2];\n    double lam = dt / par[0];\n"
+     "    double *T = (double *)malloc(sizeof(double) * N);\n    double *cn = (double *)malloc(sizeof(double) * N);\n"
+     "    double *en = (double *)malloc(sizeof(double) * N);\n    double *clipv = (double *)malloc(sizeof(double) * N);\n"
+     "#pragma omp parallel for schedule(static)\n"
+     "    for (long id = 0; id < N; ++id) T[id] = e[id] / heat_cap(par, c[id]);",
+     "const double *theta, double *Fout,\n                       double *Gout, double *diag) {\n"
+     "    long N = (long)dims[0] * dims[1] * dims[2];\n    double lam = dt / par[0];\n"
+     "    double *T = (double *)malloc(sizeof(double) * N);\n    double *cn = (double *)malloc(sizeof(double) * N);\n"
+     "    double *en = (double *)malloc(sizeof(double) * N);\n    double *clipv = (double *)malloc(sizeof(double) * N);\n"
+     "#pragma omp parallel for schedule(static)\n"
+     "    for (long id = 0; id < N; ++id) T[id] = e[id];"),
+    ("heat capacity: the gas term weighted by c",
+     "return par[1] * c + par[2] * (1.0 - c); }", "return par[1] * c + par[2] * c; }"),
+    ("frozen state: T^n from the liquid heat capacity",
+     "double Tn = e[id] / heat_cap(par, c[id]);", "double Tn = e[id] / par[1];"),
+    ("periodic axis: the last face read from its own slot, not from face 0",
+     "    if (bc[axis] == 0 && p[axis] == dims[axis]) p[axis] = 0;\n", ""),
     ("sweep: dilatation term c_c (a_r - a_l) dropped",
      "double lf = Fl - ccv * al, rf = Fr - ccv * ar;", "double lf = Fl, rf = Fr;"),
     ("sweep: phase heat capacities swapped in the energy flux G",
@@ -110,6 +136,8 @@ MUTANTS = [
     ("shift: |m|_1 instead of |m|_2 in alpha + |m| dd",
      "double mn2 = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);\n                double sft = mn2 * ddv;",
      "double mn2 = fabs(m[0]) + fabs(m[1]) + fabs(m[2]);\n                double sft = mn2 * ddv;"),
+    ("shift: the plane moved against the sign of dd",
+     "double sft = mn2 * ddv;", "double sft = -mn2 * ddv;"),
     ("shift: energy jump with the wrong sign",
      "double de = dc * dCp * par[3];", "double de = -dc * dCp * par[3];"),
     ("shift: receivers of the advancing phase instead of the receding one",
@@ -129,6 +157,10 @@ MUTANTS = [
      "double g = c[id] > 0.5 ? (T - Tg) / dist : (Tg - T) / dist;"),
     ("mass transfer: Delta x from the node to the mixed cell",
      "double X[3] = {0.5 - dx, 0.5 - dy, 0.5 - dz};", "double X[3] = {0.5 + dx, 0.5 + dy, 0.5 + dz};"),
+    ("mass transfer: node distance with the plane's offset added",
+     "bs = dpl[q] - ndx;", "bs = dpl[q] + ndx;"),
+    ("mass transfer: neighbours' phases swapped in the averages",
+     "int ph = c[q] > 0.5 ? 1 : 0;", "int ph = c[q] > 0.5 ? 0 : 1;"),
     ("mass transfer: conductivities of the two phases transposed",
      "mdot[id] = (k_g * gg - k_l * gl) / h_fg;", "mdot[id] = (k_l * gg - k_g * gl) / h_fg;"),
     ("mass transfer: weights gamma without the 1 / |Delta x|^2",
@@ -137,6 +169,10 @@ MUTANTS = [
     ("Lagrangian explicit: stretch 1 + (a_l - a_r)",
      "return 1.0 + (ar - al);  /* exactly 1 where the velocity is uniform */",
      "return 1.0 + (al - ar);  /* exactly 1 where the velocity is uniform */"),
+    ("Lagrangian explicit: dilatation term of the cell's own c dropped",
+     "double cnew = (cv + (Fl - cv * al)) - (Fr - cv * ar);", "double cnew = (cv + Fl) - Fr;"),
+    ("Lagrangian explicit: Theta from the liquid heat capacity only",
+     "double th = (T[id] * par[1]) * cv + (T[id] * par[2]) * (1.0 - cv);", "double th = T[id] * par[1];"),
     ("Lagrangian explicit: preimage width |a| J instead of |a| / J",
      "double w = (J > da) ? da / J : 1.0;", "double w = (J > da) ? da * J : 1.0;"),
 ]
@@ -232,6 +268,8 @@ PY_MUTANTS = [
      "mh = mom[k] / (1 - beta1 ** t)", "mh = mom[k]"),
     ("mlp", "BF16 ties rounded down instead of to even",
      "lsb = (bits >> 16) & 1", "lsb = 0 * bits"),
+    ("mlp", "second layer takes the first layer's bias",
+     'z2 = a1 @ weights(p["W2"]).T + p["b2"]', 'z2 = a1 @ weights(p["W2"]).T + p["b1"]'),
     ("mlp", "plane residual: neighbour offsets with the wrong sign",
      "r.append(volume(mm, al - mm @ o) - s[k])", "r.append(volume(mm, al + mm @ o) - s[k])"),
     ("mlp", "ellipsoid nearest point with a2 - t",
@@ -260,6 +298,8 @@ PY_MUTANTS = [
      "val = -(dt / rho_f(L, R)) * (p[R] - p[L]) / h", "val = -(dt / rho_f(L, R)) * (p[L] - p[R]) / h"),
     ("extension", "one gas layer instead of two",
      "    for L in (1, 2):\n        new = []", "    for L in (1,):\n        new = []"),
+    ("extension", "liquid neighbours coupled instead of no-slip",
+     "if Q is None or liquid[Q]:", "if Q is None:"),
     ("extension", "couplings over h instead of h^2",
      "beta = dt / rho_f(P, Q) / (h * h)", "beta = dt / rho_f(P, Q) / h"),
 ]
