@@ -207,7 +207,7 @@ def _run_pins(lib: str) -> tuple[int, str]:
     args = [*PINS, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
     for s in SKIP:
         args += ["--deselect", s]
-    env = dict(os.environ, OMP_NUM_THREADS="2")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT, lib, *args], capture_output=True, text=True,
                        env=env, timeout=600)
     tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-3:])
@@ -230,14 +230,15 @@ def test_mutant_texts_occur_once():
 
 def test_pins_reject_every_mutant():
     src = _source()
-    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    workers = max(1, min(8, os.cpu_count() or 1))
     with tempfile.TemporaryDirectory() as work:
         jobs = [("unchanged", src)] + [(name, src.replace(old, new)) for name, old, new in MUTANTS]
-        libs = {}
-        for i, (name, text) in enumerate(jobs):
-            libs[name] = _compile(text, work, f"m{i}")
+
+        def compile_and_run(i):
+            return _run_pins(_compile(jobs[i][1], work, f"m{i}"))
+
         with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-            res = dict(zip(libs, ex.map(_run_pins, libs.values())))
+            res = dict(zip([name for name, _ in jobs], ex.map(compile_and_run, range(len(jobs)))))
     rc, tail = res.pop("unchanged")
     assert rc == 0, f"the unchanged oracle fails its own pins under this harness:\n{tail}"
     # pytest exit code 1: tests ran and at least one failed; anything else
@@ -328,7 +329,7 @@ def _py_source(name: str) -> str:
 def _run_py_pins(job) -> tuple[int, str]:
     name, path = job
     args = [*PY_PINS[name], "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
-    env = dict(os.environ, OMP_NUM_THREADS="2")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", PY_CHILD, ROOT, name, path, *args], capture_output=True, text=True,
                        env=env, timeout=600)
     tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-3:])
@@ -344,7 +345,7 @@ def test_py_mutant_texts_occur_once():
 
 
 def test_pins_reject_every_numpy_oracle_mutant():
-    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    workers = max(1, min(8, os.cpu_count() or 1))
     with tempfile.TemporaryDirectory() as work:
         jobs = {}
         for name in PY_PINS:  # the unchanged modules, loaded the same way
