@@ -217,7 +217,10 @@ VOF_API vof_status vof_phase_change_shift(const vof_grid* g, const double* c_in,
                                   void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * One full time step on the caller's stream: zero the frozen state, three
+ * One full time step of the method (Sec. 3.1 steps 1-2: Step 1 the split
+ * VOF sweeps of Sec. 3.3.1 with the thermal energy fluxed in tandem, Sec.
+ * 3.4.1, Eq. disc_et_adv; Step 2 the interface shift of Sec. 3.3.2) on the
+ * caller's stream: zero the frozen state, three
  * (g->scheme: Weymouth-Yue or Lagrangian-explicit)
  * sweeps in Strang-alternated order (x,y,z on even step_index, z,y,x on odd),
  * then the shift; c and e are updated in place (every sweep and the shift
@@ -240,8 +243,8 @@ VOF_API vof_status vof_step(const vof_grid* g, double* c, double* e, const doubl
                     void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Many independent subdomains ("boxes") stepped together (the paper steps one
- * domain; this serves workloads of thousands of small, uneven domains such as
+ * Many independent subdomains ("boxes") stepped together (the paper has no
+ * counterpart: it steps one domain; this serves workloads of thousands of small, uneven domains such as
  * separate droplets).  Each box is one vof_step() on its own grid, arrays and
  * time step; the boxes are spread over `lanes` streams that run concurrently
  * and share nothing but the read-only inputs.
@@ -298,7 +301,7 @@ VOF_API vof_status vof_batched_step(const vof_box* boxes, int nbox, long step_in
 
 /*
  * The same batch as ONE launch per kernel of the time step (the grouped
- * form): vof_group_create() carves every box's own step workspace out of
+ * form; the paper has no counterpart: it steps one domain per MPI rank): vof_group_create() carves every box's own step workspace out of
  * the caller's buffer and writes, once, every kernel's per-box arguments
  * and the CTA -> box maps of the grouped launches into the same buffer
  * (synchronising `stream`); vof_group_step() then runs a time step of every
@@ -374,8 +377,9 @@ VOF_API vof_status vof_mass_transfer(const vof_grid* g, const double* c, const d
                                      double h_fg, double* mdot, double* d_gamma, double* grad_n, double dd_per_mdot,
                                      double* dd, void* workspace, size_t workspace_bytes, void* stream);
 /* {mixed cells, pure cells with a mixed neighbour} of the last
- * vof_mass_transfer() run with this workspace (instrumentation), copied to
- * host memory after the work queued on `stream` completes. */
+ * vof_mass_transfer() run with this workspace (instrumentation; the paper
+ * has no counterpart), copied to host memory after the work queued on
+ * `stream` completes. */
 VOF_API vof_status vof_mass_transfer_work_counts(const vof_grid* g, const void* workspace, int* counts,
                                                  void* stream);
 
@@ -579,9 +583,11 @@ VOF_API vof_status vof_mlp_normals(const void* packed, const double* X, long n, 
                                    void* stream);
 
 /*
- * One training step of the learned normal on the GPU (forward, backward and
- * Adam in the library's kernels; the loss is the batch mean of the squared
- * distance between y / |y|_2 and the label).  The batch holds `batch`
+ * One training step of the learned normal on the GPU (the paper has no
+ * counterpart: the network stands in for the MYC normal of Sec. 3.2,
+ * Eq. plane_m).  Forward, backward and Adam run in the library's kernels.
+ * The loss is the batch mean of the squared distance between y / |y|_2 and
+ * the label.  The batch holds `batch`
  * samples (a multiple of 128, 128 ... 65536) of the training set X[ntrain][27]
  * (FP64 fractions), N[ntrain][3] (FP64 unit normals): with idx == NULL
  * drawn with replacement, sample s of step `step` being
@@ -605,12 +611,15 @@ VOF_API vof_status vof_mlp_train_step(const double* X, const double* N, long ntr
                                       float* adam_v, void* packed, float* grad, float* loss, const int64_t* idx,
                                       void* workspace, size_t workspace_bytes, void* stream);
 
-/* Sticky device status (synchronises the device): VOF_OK, VOF_ECFL or
- * VOF_EWAIT; reading clears it. */
+/* Error reporting (the paper has no counterpart).
+ *   vof_get_device_status()  the sticky device status (synchronises the
+ *                            device): VOF_OK, VOF_ECFL or VOF_EWAIT;
+ *                            reading clears it
+ *   vof_status_string()      message for a status code (static string)
+ *   vof_last_cuda_error()    the cudaError_t of the last call that returned
+ *                            VOF_ECUDA */
 VOF_API vof_status vof_get_device_status(void);
-/* Message for a status code (static string). */
 VOF_API const char* vof_status_string(int status);
-/* The cudaError_t of the last call that returned VOF_ECUDA. */
 VOF_API int vof_last_cuda_error(void);
 
 #ifdef __cplusplus

@@ -226,3 +226,20 @@ def test_header_compiles_alone(tmp_path, lang, std):
     r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_every_declaration_cites_its_passage():
+    # Each entry point of the C header sits under a comment that cites the
+    # paper's passage defining the operation (a section, equation or table)
+    # or says that the paper has no counterpart.
+    with open(os.path.join(ROOT, "include", "vofgb.h")) as f:
+        h = f.read()
+    names = []
+    for m in re.finditer(r"VOF_API [^;]*?\b(vof_\w+|energy_\w+)\(", h):
+        # the nearest comment that starts a line (not a struct field's)
+        start = h.rfind("\n/*", 0, m.start())
+        comment = h[start:h.index("*/", start)]
+        text = " ".join(comment.replace("*", " ").split())
+        if not any(t in text for t in ("Sec.", "Eq.", "Table", "no counterpart")):
+            names.append(m.group(1))
+    assert not names, f"declarations without a citation: {names}"
