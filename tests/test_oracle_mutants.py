@@ -32,7 +32,6 @@ import concurrent.futures as cf
 import os
 import subprocess
 import sys
-import tempfile
 
 import pytest
 
@@ -228,17 +227,17 @@ def test_mutant_texts_occur_once():
         assert old != new, name
 
 
-def test_pins_reject_every_mutant():
+def test_pins_reject_every_mutant(tmp_path):
     src = _source()
     workers = max(1, min(8, os.cpu_count() or 1))
-    with tempfile.TemporaryDirectory() as work:
-        jobs = [("unchanged", src)] + [(name, src.replace(old, new)) for name, old, new in MUTANTS]
+    work = str(tmp_path)
+    jobs = [("unchanged", src)] + [(name, src.replace(old, new)) for name, old, new in MUTANTS]
 
-        def compile_and_run(i):
-            return _run_pins(_compile(jobs[i][1], work, f"m{i}"))
+    def compile_and_run(i):
+        return _run_pins(_compile(jobs[i][1], work, f"m{i}"))
 
-        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-            res = dict(zip([name for name, _ in jobs], ex.map(compile_and_run, range(len(jobs)))))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        res = dict(zip([name for name, _ in jobs], ex.map(compile_and_run, range(len(jobs)))))
     rc, tail = res.pop("unchanged")
     assert rc == 0, f"the unchanged oracle fails its own pins under this harness:\n{tail}"
     # pytest exit code 1: tests ran and at least one failed; anything else
@@ -344,22 +343,22 @@ def test_py_mutant_texts_occur_once():
         assert old != new, label
 
 
-def test_pins_reject_every_numpy_oracle_mutant():
+def test_pins_reject_every_numpy_oracle_mutant(tmp_path):
     workers = max(1, min(8, os.cpu_count() or 1))
-    with tempfile.TemporaryDirectory() as work:
-        jobs = {}
-        for name in PY_PINS:  # the unchanged modules, loaded the same way
-            path = os.path.join(work, f"unchanged_{name}.py")
-            with open(path, "w") as f:
-                f.write(_py_source(name))
-            jobs[("unchanged", name)] = (name, path)
-        for i, (name, label, old, new) in enumerate(PY_MUTANTS):
-            path = os.path.join(work, f"m{i}_{name}.py")
-            with open(path, "w") as f:
-                f.write(_py_source(name).replace(old, new))
-            jobs[(label, name)] = (name, path)
-        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-            res = dict(zip(jobs, ex.map(_run_py_pins, jobs.values())))
+    work = str(tmp_path)
+    jobs = {}
+    for name in PY_PINS:  # the unchanged modules, loaded the same way
+        path = os.path.join(work, f"unchanged_{name}.py")
+        with open(path, "w") as f:
+            f.write(_py_source(name))
+        jobs[("unchanged", name)] = (name, path)
+    for i, (name, label, old, new) in enumerate(PY_MUTANTS):
+        path = os.path.join(work, f"m{i}_{name}.py")
+        with open(path, "w") as f:
+            f.write(_py_source(name).replace(old, new))
+        jobs[(label, name)] = (name, path)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        res = dict(zip(jobs, ex.map(_run_py_pins, jobs.values())))
     for name in PY_PINS:
         rc, tail = res.pop(("unchanged", name))
         assert rc == 0, f"the unchanged oracle/{name}.py fails its own pins under this harness:\n{tail}"
