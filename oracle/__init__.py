@@ -31,6 +31,8 @@ Parity status per function (pins live in tests/test_oracle_*.py):
       invariants (conservation, uniform-T preservation, translation return,
       plane translation, exact motion of a shifted plane, kinematic Stefan
       front, evaporating-droplet volume)
+The pins themselves are checked by tests/test_oracle_mutants.py: a plausible
+slip planted in a copy of any of these sources must fail at least one pin.
 """
 from __future__ import annotations
 
