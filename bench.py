@@ -43,6 +43,8 @@ N_CELLS = 256
 # written only for cells that change, and quiet tiles are skipped.)
 SWEEP_BYTES_PER_CELL = 8 + 8 + 8 + 8 + 1 + 8 + 8
 STEP_BYTES_PER_CELL = 3 * SWEEP_BYTES_PER_CELL + 9 + 40
+# nominal HBM3e bandwidth of one GB300 (the roofline itself uses the measured copy rate)
+HBM_NOMINAL_GBS = 7900.0
 
 
 def max_over_ranks(x, world, device):
@@ -357,7 +359,9 @@ def run_gpu(args):
                          "flop_per_face": FACE_FLOP, "faces_per_launch": round(faces_per_step / 3),
                          "ms_per_launch": round(faces_ms / 3, 5),
                          "share_of_step": round(faces_ms / step_ms_prof, 4) if step_ms_prof > 0 else None,
-                         "hbm_frac_step": round(value / world * STEP_BYTES_PER_CELL / peak, 4), "hbm_peak_gbs": peak},
+                         "hbm_frac_step": round(value / world * STEP_BYTES_PER_CELL / peak, 4), "hbm_peak_gbs": peak,
+                         "hbm_frac_step_nominal": round(value / world * STEP_BYTES_PER_CELL / HBM_NOMINAL_GBS, 4),
+                         "hbm_nominal_gbs": HBM_NOMINAL_GBS},
             "work_counts": counts,
             "kernel_ms": {k: round(v_, 5) for k, v_ in sorted(kern_ms.items(), key=lambda kv: -kv[1])},
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
